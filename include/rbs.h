@@ -1,0 +1,168 @@
+/*
+ * rbs.h -- C ABI of the GB300 rigid-body Stokes mobility library.
+ *
+ * The library solves the mobility problem of Corona, Greengard, Rachh and Veerapaneni, "An
+ * integral equation formulation for rigid bodies in Stokes flow in three dimensions"
+ * (arXiv:1606.07428): given the force F_i and torque T_i on every rigid particle, find its
+ * translational velocity v_i and rotational velocity omega_i (Section 2, Eqs. 1-5), by the
+ * second-kind single-layer formulation (Section 2.3, Eq. 25)
+ *
+ *     (1/2 I + K + L) mu = -(1/2 I + K) rho,     u = S[rho + mu],
+ *
+ * with rho the incident density of Eq. 19, K the traction operator (Eqs. 13, 22-23), S the
+ * single-layer operator (Eqs. 10-11) and L the rigid force/torque projection (Eq. 26); v_i and
+ * omega_i follow from u by Eqs. 41-42.  Particles are ellipsoids discretised on the spherical
+ * grid of Eq. 33 with the quadrature of Eq. 35.
+ *
+ * Conventions for every call:
+ *  - Return value: RBS_OK (0) or a negative status below; rbs_last_error() then holds a message.
+ *  - Pointers named *_dev are CUDA device pointers on the context's device; all other array
+ *    pointers are host pointers.  Arrays are row-major float64 unless stated otherwise.
+ *  - Inputs are copied in; the caller keeps ownership of every buffer it passes.  Outputs are
+ *    written into caller-allocated buffers of the stated size.
+ *  - Surface fields (densities, velocities on the surface) are (total_nodes, 3) arrays; nodes are
+ *    ordered particle-major, then by the polar index j (Gauss-Legendre nodes t_j ascending, i.e.
+ *    theta descending), then by the azimuthal index k, node = j * n_phi + k.
+ *  - A context is not thread-safe; use one context per host thread.  All device work of a context
+ *    runs on the stream given at creation (or the legacy default stream when it is NULL).
+ */
+#ifndef RBS_H
+#define RBS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RBS_OK 0
+#define RBS_EINVAL -1    /* invalid argument (null pointer, bad size, non-finite input, p out of range) */
+#define RBS_EOVERLAP -2  /* particles closer than the gap the quadrature is built for */
+#define RBS_ENOTCONV -3  /* GMRES hit max_iters; outputs are still written, iterations reported */
+#define RBS_ECUDA -4     /* a CUDA runtime error; the message names the call */
+#define RBS_ENOMEM -5    /* device allocation failed */
+#define RBS_ETIMEOUT -6  /* a bounded device wait expired */
+#define RBS_ESTATE -7    /* call out of order (e.g. a solve before rbs_set_geometry) */
+
+/* Arithmetic of a solve. */
+#define RBS_PREC_FP64 0  /* every step in float64 */
+#define RBS_PREC_MIXED 1 /* float32 inner GMRES, float64 right-hand side, residuals, refinement
+                            updates, projection and velocity extraction */
+
+/* Operators for rbs_apply_operator (each acts on a surface field, Section 2). */
+#define RBS_OP_A 0        /* (1/2 I + K + L), the system operator of Eq. 25 */
+#define RBS_OP_HALF_K 1   /* (1/2 I + K), the right-hand-side operator of Eq. 25 */
+#define RBS_OP_S 2        /* S, Eq. 11, as used for u = S[rho + mu] */
+#define RBS_OP_K_OFF 3    /* K restricted to pairs of distinct particles (smooth and upsampled rules) */
+#define RBS_OP_K_SELF 4   /* K restricted to each particle's own surface (singular rule) */
+#define RBS_OP_S_OFF 5
+#define RBS_OP_S_SELF 6
+#define RBS_OP_L 7        /* L of Eq. 26 */
+
+typedef struct rbs_ctx rbs_ctx;
+
+typedef struct {
+  int precision;       /* RBS_PREC_FP64 (default) or RBS_PREC_MIXED */
+  int restart;         /* GMRES restart length (default 50) */
+  int max_iters;       /* cap on GMRES iterations per solve (default 500) */
+  int preconditioner;  /* 1 (default): right block-diagonal preconditioner, the inverse of each
+                          particle's own 1/2 I + K_ii + L_i (Section 3.2); 0: none */
+  double near_delta;   /* particles i, j are near when |c_i - c_j| < R_i + R_j + near_delta, R the
+                          largest semi-axis (default 1.0); near sources use an upsampled grid */
+  int p_up_factor;     /* near sources are upsampled to order p_up_factor * p (default 2) */
+  int p_self_factor;   /* singular self rule of order p_self_factor * p (default 2) */
+  double viscosity;    /* fluid viscosity (default 1.0) */
+  double inner_tol;    /* RBS_PREC_MIXED: relative tolerance of each float32 inner solve (default 1e-5) */
+  int max_refinements; /* RBS_PREC_MIXED: cap on float64 refinement steps (default 20) */
+  int device;          /* CUDA device ordinal (default 0) */
+  void* stream;        /* cudaStream_t for all device work, NULL = legacy default stream */
+} rbs_options;
+
+typedef struct {
+  int iterations;        /* total GMRES iterations of the last solve (inner iterations for mixed) */
+  int refinements;       /* outer float64 refinement steps of the last solve (0 for FP64) */
+  double residual;       /* final relative residual ||b - A mu|| / ||b|| in float64 */
+  double setup_ms;       /* wall time of the last rbs_set_geometry */
+  double solve_ms;       /* wall time of the last rbs_mobility_solve */
+  long long total_nodes;
+  int n_particles;
+  int n_shapes;          /* distinct (semi-axes, p, n_phi) body shapes */
+  long long near_pairs;  /* ordered (target, source) particle pairs treated as near */
+  long long far_pairs;   /* (target node, source node) pairs of the smooth pair sum per apply */
+} rbs_stats;
+
+/* Fill *opt with the defaults listed above. */
+void rbs_default_options(rbs_options* opt);
+
+/* Create a context on opt->device (opt may be NULL for the defaults).  *out receives the handle. */
+int rbs_create(const rbs_options* opt, rbs_ctx** out);
+
+/* Release every device and host resource of the context.  NULL is ignored. */
+void rbs_destroy(rbs_ctx* ctx);
+
+/*
+ * Define the suspension (Section 3: surfaces and grids; Section 3.1: self blocks computed once per
+ * body shape and rotated, Eq. 38; Section 3.2: block-diagonal preconditioner).
+ *  n            number of particles, n >= 1
+ *  semi_axes    n x 3, ellipsoid semi-axes (a, b, c) along the body x, y, z axes, all > 0
+ *  p            n, spherical-harmonic order per particle, 2 <= p <= 32
+ *  nphi         n, azimuthal points per particle (even, >= 2p; NULL means 2p for every particle)
+ *  centres      n x 3
+ *  quats        n x 4, orientations as quaternions (w, x, y, z); normalised here
+ *  suspension_id  n (NULL: all particles in one suspension); particles with different ids do not
+ *               interact.  Particles of one suspension must be contiguous.
+ * Returns RBS_EOVERLAP when two interacting particles' bounding spheres intersect.
+ */
+int rbs_set_geometry(rbs_ctx* ctx, int n, const double* semi_axes, const int* p, const int* nphi,
+                     const double* centres, const double* quats, const int* suspension_id);
+
+/* Number of surface nodes of the current geometry (3 * that many unknowns). */
+long long rbs_total_nodes(const rbs_ctx* ctx);
+
+/* Copy the lab-frame nodes, unit normals and quadrature weights (Eqs. 33-36) of the current
+ * geometry: x and normal are total_nodes x 3, weight is total_nodes (any may be NULL). */
+int rbs_get_surface(rbs_ctx* ctx, double* x, double* normal, double* weight);
+
+/*
+ * The mobility solve (the three steps at the start of Section 3; Algorithm 1 lines 3-5 without
+ * contact).
+ *  F, T        n x 3 forces and torques
+ *  tol         relative residual ||b - A mu||_2 / ||b||_2 at which GMRES stops (b the right-hand side
+ *              of Eq. 25); for RBS_PREC_MIXED the float64 refinement stops at this tolerance
+ *  v, omega    n x 3 outputs
+ *  density     NULL, or total_nodes x 3 output receiving mu (lab frame)
+ *  iterations  NULL, or one int receiving the GMRES iteration count
+ * Returns RBS_ENOTCONV (outputs written) when max_iters is reached first.
+ */
+int rbs_mobility_solve(rbs_ctx* ctx, const double* F, const double* T, double tol, double* v,
+                       double* omega, double* density, int* iterations);
+
+/* The same solve on device buffers (F_dev, T_dev, v_dev, omega_dev: n x 3; density_dev: NULL or
+ * total_nodes x 3).  Work is ordered on the context's stream; the call returns after it completes. */
+int rbs_mobility_solve_device(rbs_ctx* ctx, const double* F_dev, const double* T_dev, double tol,
+                              double* v_dev, double* omega_dev, double* density_dev, int* iterations);
+
+/* Incident density rho of Eq. 19 for forces F and torques T (n x 3 each); rho is total_nodes x 3. */
+int rbs_incident_density(rbs_ctx* ctx, const double* F, const double* T, double* rho);
+
+/* Rigid velocities of Eqs. 41-42 from a surface velocity u (total_nodes x 3): v, omega n x 3. */
+int rbs_rigid_velocities(rbs_ctx* ctx, const double* u, double* v, double* omega);
+
+/*
+ * Apply one discrete operator (RBS_OP_*) to a surface field: y = op(x), x and y total_nodes x 3 host
+ * arrays.  precision RBS_PREC_FP64 applies it in float64; RBS_PREC_MIXED in the float32 arithmetic of
+ * the inner solve (pair sums with compensated accumulation, float32 self blocks).
+ */
+int rbs_apply_operator(rbs_ctx* ctx, int op, int precision, const double* x, double* y);
+
+/* The same with device buffers (x_dev, y_dev: total_nodes x 3 float64). */
+int rbs_apply_operator_device(rbs_ctx* ctx, int op, int precision, const double* x_dev, double* y_dev);
+
+/* Statistics of the last rbs_set_geometry / rbs_mobility_solve. */
+int rbs_get_stats(const rbs_ctx* ctx, rbs_stats* out);
+
+/* Message describing the last error of the context (empty when none); valid until the next call. */
+const char* rbs_last_error(const rbs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBS_H */

@@ -1,0 +1,280 @@
+// The C ABI of include/rbs.h: argument checks, host <-> device copies and dispatch.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+using rbs::Context;
+using rbs::Status;
+
+namespace {
+
+int finish(Context& c, const Status& s) {
+  c.err = s.ok() ? std::string() : s.msg;
+  return s.code;
+}
+
+Status enter(Context& c) {
+  RBS_CUDA_TRY(cudaSetDevice(c.device));
+  return Status::Ok();
+}
+
+bool finite_all(const double* a, long long n) {
+  for (long long i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+namespace rbs {
+Context::~Context() {
+  for (Grid* g : grids) delete g;
+  grids.clear();
+  if (h_pinned) cudaFreeHost(h_pinned);
+  h_pinned = nullptr;
+}
+}  // namespace rbs
+
+extern "C" {
+
+void rbs_default_options(rbs_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = RBS_PREC_FP64;
+  o->restart = 50;
+  o->max_iters = 500;
+  o->preconditioner = 1;
+  o->near_delta = 1.0;
+  o->p_up_factor = 2;
+  o->p_self_factor = 2;
+  o->viscosity = 1.0;
+  o->inner_tol = 1e-5;
+  o->max_refinements = 20;
+  o->device = 0;
+  o->stream = nullptr;
+}
+
+int rbs_create(const rbs_options* opt, rbs_ctx** out) {
+  if (!out) return RBS_EINVAL;
+  *out = nullptr;
+  rbs_options o;
+  if (opt)
+    o = *opt;
+  else
+    rbs_default_options(&o);
+  if (o.restart < 1 || o.restart > 500 || o.max_iters < 1 || o.p_up_factor < 1 || o.p_up_factor > 4 ||
+      o.p_self_factor < 1 || o.p_self_factor > 4 || !(o.viscosity > 0) || !(o.near_delta >= 0) ||
+      !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_refinements < 1 ||
+      (o.precision != RBS_PREC_FP64 && o.precision != RBS_PREC_MIXED))
+    return RBS_EINVAL;
+  rbs_ctx* h = new rbs_ctx();
+  Context& c = h->c;
+  c.opt = o;
+  c.device = o.device;
+  c.stream = (cudaStream_t)o.stream;
+  Status s = enter(c);
+  if (s.ok()) {
+    cudaError_t e = cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, c.device);
+    if (e == cudaSuccess) e = cudaMallocHost(&c.h_pinned, 64 * sizeof(double));
+    if (e != cudaSuccess) s = Status::Err(RBS_ECUDA, std::string("device set-up: ") + cudaGetErrorString(e));
+  }
+  if (!s.ok()) {
+    delete h;
+    return s.code;
+  }
+  *out = h;
+  return RBS_OK;
+}
+
+void rbs_destroy(rbs_ctx* h) {
+  if (!h) return;
+  cudaSetDevice(h->c.device);
+  cudaStreamSynchronize(h->c.stream);
+  delete h;
+}
+
+int rbs_set_geometry(rbs_ctx* h, int n, const double* semi_axes, const int* p, const int* nphi, const double* centres,
+                     const double* quats, const int* suspension_id) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (n < 1 || !semi_axes || !p || !centres || !quats)
+    return finish(c, Status::Err(RBS_EINVAL, "set_geometry: null array or n < 1"));
+  if (!finite_all(semi_axes, 3LL * n) || !finite_all(centres, 3LL * n) || !finite_all(quats, 4LL * n))
+    return finish(c, Status::Err(RBS_EINVAL, "set_geometry: non-finite input"));
+  for (int i = 0; i < n; ++i) {
+    if (!(semi_axes[3 * i] > 0 && semi_axes[3 * i + 1] > 0 && semi_axes[3 * i + 2] > 0))
+      return finish(c, Status::Err(RBS_EINVAL, "set_geometry: semi-axes must be positive"));
+    if (p[i] < 2 || p[i] > 32) return finish(c, Status::Err(RBS_EINVAL, "set_geometry: p must be in [2, 32]"));
+    int nf = nphi ? nphi[i] : 2 * p[i];
+    if (nf < 2 * p[i] || nf % 2 != 0 || nf > 4 * p[i] + 4)
+      return finish(c, Status::Err(RBS_EINVAL, "set_geometry: nphi must be even and in [2p, 4p + 4]"));
+    const double* q = quats + 4 * i;
+    double qn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    if (!(qn > 1e-12)) return finish(c, Status::Err(RBS_EINVAL, "set_geometry: zero quaternion"));
+    if (suspension_id && i > 0 && suspension_id[i] != suspension_id[i - 1]) {
+      for (int k = 0; k < i - 1; ++k)
+        if (suspension_id[k] == suspension_id[i])
+          return finish(c, Status::Err(RBS_EINVAL, "set_geometry: particles of one suspension must be contiguous"));
+    }
+  }
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  c.have_geometry = false;
+  c.n = n;
+  c.axes.assign(semi_axes, semi_axes + 3LL * n);
+  c.centres.assign(centres, centres + 3LL * n);
+  c.quats.assign(quats, quats + 4LL * n);
+  c.p.assign(p, p + n);
+  c.nphi.resize(n);
+  for (int i = 0; i < n; ++i) c.nphi[i] = nphi ? nphi[i] : 2 * p[i];
+  c.sid.assign(n, 0);
+  if (suspension_id) c.sid.assign(suspension_id, suspension_id + n);
+  return finish(c, rbs::build_geometry(c));
+}
+
+long long rbs_total_nodes(const rbs_ctx* h) { return (h && h->c.have_geometry) ? h->c.N : 0; }
+
+int rbs_get_surface(rbs_ctx* h, double* x, double* normal, double* weight) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  std::vector<double4> hx(c.N), hn(c.N);
+  cudaError_t e = cudaMemcpyAsync(hx.data(), c.d_x.ptr, sizeof(double4) * c.N, cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hn.data(), c.d_nrm.ptr, sizeof(double4) * c.N, cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return finish(c, Status::Err(RBS_ECUDA, std::string("get_surface: ") + cudaGetErrorString(e)));
+  for (long long t = 0; t < c.N; ++t) {
+    if (x) {
+      x[3 * t] = hx[t].x;
+      x[3 * t + 1] = hx[t].y;
+      x[3 * t + 2] = hx[t].z;
+    }
+    if (normal) {
+      normal[3 * t] = hn[t].x;
+      normal[3 * t + 1] = hn[t].y;
+      normal[3 * t + 2] = hn[t].z;
+    }
+    if (weight) weight[t] = hx[t].w;
+  }
+  return finish(c, Status::Ok());
+}
+
+static int solve_common(rbs_ctx* h, const double* F, const double* T, double tol, double* v, double* omega,
+                        double* density, int* iterations, bool device_io) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "mobility_solve before set_geometry"));
+  if (!F || !T || !v || !omega) return finish(c, Status::Err(RBS_EINVAL, "mobility_solve: null array"));
+  if (!(tol > 0 && tol < 1)) return finish(c, Status::Err(RBS_EINVAL, "mobility_solve: tol must be in (0, 1)"));
+  if (!device_io && (!finite_all(F, 3LL * c.n) || !finite_all(T, 3LL * c.n)))
+    return finish(c, Status::Err(RBS_EINVAL, "mobility_solve: non-finite force or torque"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  return finish(c, rbs::mobility_solve(c, F, T, tol, v, omega, density, iterations, device_io));
+}
+
+int rbs_mobility_solve(rbs_ctx* h, const double* F, const double* T, double tol, double* v, double* omega,
+                       double* density, int* iterations) {
+  return solve_common(h, F, T, tol, v, omega, density, iterations, false);
+}
+
+int rbs_mobility_solve_device(rbs_ctx* h, const double* F_dev, const double* T_dev, double tol, double* v_dev,
+                              double* omega_dev, double* density_dev, int* iterations) {
+  return solve_common(h, F_dev, T_dev, tol, v_dev, omega_dev, density_dev, iterations, true);
+}
+
+int rbs_incident_density(rbs_ctx* h, const double* F, const double* T, double* rho) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  if (!F || !T || !rho) return finish(c, Status::Err(RBS_EINVAL, "incident_density: null array"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  std::vector<double> ft(6 * (size_t)c.n);
+  for (int i = 0; i < c.n; ++i)
+    for (int q = 0; q < 3; ++q) {
+      ft[6 * i + q] = F[3 * i + q];
+      ft[6 * i + 3 + q] = T[3 * i + q];
+    }
+  cudaError_t e = cudaMemcpyAsync(c.d_FT.ptr, ft.data(), sizeof(double) * ft.size(), cudaMemcpyHostToDevice, c.stream);
+  if (e != cudaSuccess) return finish(c, Status::Err(RBS_ECUDA, cudaGetErrorString(e)));
+  s = rbs::incident_density(c, c.d_FT.ptr, c.d_vec[0].ptr);
+  if (!s.ok()) return finish(c, s);
+  e = cudaMemcpyAsync(rho, c.d_vec[0].ptr, sizeof(double) * 3 * c.N, cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return finish(c, Status::Err(RBS_ECUDA, cudaGetErrorString(e)));
+  return finish(c, Status::Ok());
+}
+
+int rbs_rigid_velocities(rbs_ctx* h, const double* u, double* v, double* omega) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  if (!u || !v || !omega) return finish(c, Status::Err(RBS_EINVAL, "rigid_velocities: null array"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  cudaError_t e = cudaMemcpyAsync(c.d_vec[0].ptr, u, sizeof(double) * 3 * c.N, cudaMemcpyHostToDevice, c.stream);
+  if (e != cudaSuccess) return finish(c, Status::Err(RBS_ECUDA, cudaGetErrorString(e)));
+  s = rbs::rigid_velocities(c, c.d_vec[0].ptr, c.d_vo.ptr);
+  if (!s.ok()) return finish(c, s);
+  std::vector<double> vo(6 * (size_t)c.n);
+  e = cudaMemcpyAsync(vo.data(), c.d_vo.ptr, sizeof(double) * vo.size(), cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return finish(c, Status::Err(RBS_ECUDA, cudaGetErrorString(e)));
+  for (int i = 0; i < c.n; ++i)
+    for (int q = 0; q < 3; ++q) {
+      v[3 * i + q] = vo[6 * i + q];
+      omega[3 * i + q] = vo[6 * i + 3 + q];
+    }
+  return finish(c, Status::Ok());
+}
+
+int rbs_apply_operator_device(rbs_ctx* h, int op, int precision, const double* x_dev, double* y_dev) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  if (!x_dev || !y_dev || x_dev == y_dev) return finish(c, Status::Err(RBS_EINVAL, "apply_operator: bad buffers"));
+  if (precision != RBS_PREC_FP64 && precision != RBS_PREC_MIXED)
+    return finish(c, Status::Err(RBS_EINVAL, "apply_operator: bad precision"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  s = rbs::apply_operator(c, op, precision, x_dev, y_dev);
+  if (s.ok()) {
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) s = Status::Err(RBS_ECUDA, cudaGetErrorString(e));
+  }
+  return finish(c, s);
+}
+
+int rbs_apply_operator(rbs_ctx* h, int op, int precision, const double* x, double* y) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  if (!x || !y) return finish(c, Status::Err(RBS_EINVAL, "apply_operator: null array"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  cudaError_t e = cudaMemcpyAsync(c.d_vec[0].ptr, x, sizeof(double) * 3 * c.N, cudaMemcpyHostToDevice, c.stream);
+  if (e != cudaSuccess) return finish(c, Status::Err(RBS_ECUDA, cudaGetErrorString(e)));
+  int rc = rbs_apply_operator_device(h, op, precision, c.d_vec[0].ptr, c.d_vec[1].ptr);
+  if (rc != RBS_OK) return rc;
+  e = cudaMemcpyAsync(y, c.d_vec[1].ptr, sizeof(double) * 3 * c.N, cudaMemcpyDeviceToHost, c.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return finish(c, Status::Err(RBS_ECUDA, cudaGetErrorString(e)));
+  return finish(c, Status::Ok());
+}
+
+int rbs_get_stats(const rbs_ctx* h, rbs_stats* out) {
+  if (!h || !out) return RBS_EINVAL;
+  *out = h->c.stats;
+  return RBS_OK;
+}
+
+const char* rbs_last_error(const rbs_ctx* h) {
+  if (!h) return "null context";
+  return h->c.err.c_str();
+}
+
+}  // extern "C"

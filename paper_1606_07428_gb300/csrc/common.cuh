@@ -1,0 +1,201 @@
+// Internal declarations shared by the translation units of the rbs library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/rbs.h"
+
+namespace rbs {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Status carried through the host code: RBS_OK or a negative code plus a message.
+struct Status {
+  int code = RBS_OK;
+  std::string msg;
+  bool ok() const { return code == RBS_OK; }
+  static Status Ok() { return Status(); }
+  static Status Err(int c, const std::string& m) {
+    Status s;
+    s.code = c;
+    s.msg = m;
+    return s;
+  }
+};
+
+#define RBS_CUDA_TRY(call)                                                                   \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      return ::rbs::Status::Err(e_ == cudaErrorMemoryAllocation ? RBS_ENOMEM : RBS_ECUDA,    \
+                                std::string(#call) + ": " + cudaGetErrorString(e_));         \
+    }                                                                                        \
+  } while (0)
+
+#define RBS_TRY(expr)              \
+  do {                             \
+    ::rbs::Status s_ = (expr);     \
+    if (!s_.ok()) return s_;       \
+  } while (0)
+
+// A device allocation owned by the context.
+template <typename T>
+struct DevBuf {
+  T* ptr = nullptr;
+  size_t n = 0;
+  Status alloc(size_t count) {
+    release();
+    if (count == 0) return Status::Ok();
+    RBS_CUDA_TRY(cudaMalloc(&ptr, count * sizeof(T)));
+    n = count;
+    return Status::Ok();
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    n = 0;
+  }
+  ~DevBuf() { release(); }
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+};
+
+// One parametric grid (p, n_phi) and everything derived from it alone (Section 3, Eq. 33).
+struct Grid {
+  int p = 0, nphi = 0, np = 0;  // np = (p + 1) * nphi nodes
+  int mmax = 0, nbasis = 0;     // retained real harmonics: n <= p, |m| <= min(n, mmax)
+  int ps = 0, nrot = 0;         // singular rule order and its point count (ps + 1) * (2 ps + 2)
+  int pup = 0, nphi_up = 0, nup = 0;  // upsampled grid for near sources
+  std::vector<double> t, lam;         // Gauss-Legendre nodes (ascending) and weights, p + 1
+  std::vector<double> t_up, lam_up;   // the same for the upsampled grid
+  DevBuf<double> d_t, d_lam, d_t_up, d_lam_up;
+  DevBuf<double> d_interp;  // (p + 1) x nrot x np: singular-rule interpolation, target (j, 0)
+  DevBuf<double> d_rotpts;  // (p + 1) x nrot x 4: rotated-rule points (x, y, z, weight)
+  DevBuf<double> d_up;      // nup x np: interpolation to the upsampled grid
+  DevBuf<float> d_up32;
+};
+
+// One distinct body shape (semi-axes, p, n_phi).
+struct Shape {
+  double a = 0, b = 0, c = 0;
+  int grid = 0;
+  int np = 0;
+  size_t block_off = 0;  // offset (in elements) of its 3np x 3np blocks in the block arrays
+};
+
+struct Context {
+  rbs_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int device = 0;
+  int sm_count = 0;
+
+  // geometry (host)
+  int n = 0;
+  long long N = 0;  // total nodes
+  std::vector<double> axes, centres, quats, rot;  // rot: n x 9 row-major R
+  std::vector<int> p, nphi, sid, shape_of;
+  std::vector<long long> offset;  // n + 1
+  std::vector<Grid*> grids;
+  std::vector<Shape> shapes;
+  size_t block_elems = 0;  // sum over shapes of (3 np)^2
+  bool have_geometry = false;
+
+  // per-particle device data
+  DevBuf<double> d_centre, d_rot, d_area, d_tauinv;  // n x 3, n x 9, n, n x 9
+  DevBuf<int> d_shape, d_nodes;                      // n: shape id, node count
+  DevBuf<long long> d_offset;                        // n + 1
+  // per-node device data
+  DevBuf<double4> d_x;  // lab position, w = quadrature weight
+  DevBuf<double4> d_nrm;  // lab normal, w = unused
+  DevBuf<int> d_pid;
+  // shape-level device data
+  DevBuf<double> d_shape_axes;  // nshape x 3
+  DevBuf<int> d_shape_grid_np;  // nshape x 2 (np, grid index)
+  DevBuf<double> d_blockK, d_blockS, d_precond;  // body-frame 3np x 3np per shape, float64
+  DevBuf<float> d_blockK32, d_precond32;
+  DevBuf<long long> d_block_off;  // nshape
+
+  // near-field data
+  std::vector<int2> near_pairs;   // (target particle, source particle)
+  DevBuf<int2> d_near;
+  std::vector<int> up_index;      // per particle: index into upsampled-source list or -1
+  std::vector<long long> up_offset;  // per upsampled source particle: first upsampled node
+  std::vector<int> up_particle;
+  long long n_up_nodes = 0;
+  DevBuf<double4> d_up_x;          // upsampled lab nodes (x, y, z, weight)
+  DevBuf<long long> d_up_off;      // per upsampled source particle
+  DevBuf<int> d_up_particle, d_up_index;
+  DevBuf<double> d_up_mu;          // upsampled densities, n_up_nodes x 3
+
+  // particle-block work list: (particle, first node, end node, 0), 24 nodes per block
+  std::vector<int4> bwork;
+  DevBuf<int4> d_bwork;
+  int max_np = 0;
+  // per upsampled-source particle: interpolation matrix of its grid (float64 and float32)
+  DevBuf<const double*> d_upU;
+  DevBuf<const float*> d_upU32;
+
+  // smooth pair-sum work list: (target begin, target end, source begin, source end)
+  std::vector<longlong4> work;
+  DevBuf<longlong4> d_work;
+
+  // scratch vectors (3N doubles each) and GMRES workspace
+  DevBuf<double> d_vec[8];
+  DevBuf<double> d_V, d_H, d_givens, d_partials;
+  DevBuf<double> d_FT;  // forces and torques, n x 6
+  DevBuf<double> d_vo;  // velocities, n x 6
+  double* h_pinned = nullptr;
+
+  rbs_stats stats{};
+
+  Context() = default;
+  ~Context();
+  Context(const Context&) = delete;
+  Context& operator=(const Context&) = delete;
+};
+
+// ---- setup (setup.cu)
+Status build_geometry(Context& c);
+void gauss_legendre_newton(int n, std::vector<double>& t, std::vector<double>& w);
+
+// ---- dense kernels (linalg.cu)
+Status dgemm_batched(cudaStream_t s, int M, int N, int K, const double* A, long long lda, long long strideA,
+                     const double* B, long long ldb, long long strideB, double* C, long long ldc, long long strideC,
+                     int batch);
+Status invert_batched(Context& c, double* mats, int n, int count);
+
+// ---- operator pieces (operators.cu)
+// Particle-block kernel modes.
+enum BlockMode {
+  kModeSelfK = 0,      // y = 1/2 x + R K0 R^T x + L x      (system operator, self part)
+  kModeSelfKNoL = 1,   // y = 1/2 x + R K0 R^T x            (right-hand-side operator, self part)
+  kModeSelfS = 2,      // y = R S0 R^T x
+  kModeKOnlySelf = 3,  // y = R K0 R^T x
+  kModeL = 4,          // y = L x
+  kModePrecond = 5,    // y = R P0 R^T x, and copy x to aux
+  kModeZero = 6,       // y = 0
+};
+Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, double* aux, double scale);
+Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y);  // y += off-diagonal kind (0 K, 1 S)
+Status apply_operator(Context& c, int op, int prec, const double* x, double* y);
+
+// ---- solver (solver.cu)
+Status mobility_solve(Context& c, const double* F, const double* T, double tol, double* v, double* om,
+                      double* density, int* iters, bool device_io);
+Status incident_density(Context& c, const double* FT_dev, double* rho);
+Status rigid_velocities(Context& c, const double* u, double* vo_dev);
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace rbs
+
+struct rbs_ctx {
+  rbs::Context c;
+};

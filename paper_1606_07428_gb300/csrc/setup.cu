@@ -1,0 +1,810 @@
+// Geometry set-up: grids (Section 3, Eq. 33), surface nodes, normals and weights (Eqs. 35-36),
+// moments (Eq. 18), the singular-rule and upsampling interpolation operators, the body-frame self
+// blocks of each distinct shape (Section 3.1, Eq. 38), the block-diagonal preconditioner
+// (Section 3.2), the near-pair list and the smooth pair-sum work list.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <tuple>
+#include <unordered_map>
+
+#include "common.cuh"
+
+namespace rbs {
+
+// ------------------------------------------------------------------------------------------
+// Host constants: Gauss-Legendre rules by Newton's method on the Legendre three-term recurrence
+// (initial guesses cos(pi (i + 3/4) / (n + 1/2))); weights 2 / ((1 - t^2) P_n'(t)^2).
+
+void gauss_legendre_newton(int n, std::vector<double>& t, std::vector<double>& w) {
+  t.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double x = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      double pn = (n == 1) ? x : p1, pn1 = (n == 1) ? 1.0 : p0;
+      dp = n * (x * pn - pn1) / (x * x - 1.0);
+      double dx = pn / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) {
+        // one more evaluation of the derivative at the converged node
+        p0 = 1.0;
+        p1 = x;
+        for (int k = 2; k <= n; ++k) {
+          double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = pk;
+        }
+        pn = (n == 1) ? x : p1;
+        pn1 = (n == 1) ? 1.0 : p0;
+        dp = n * (x * pn - pn1) / (x * x - 1.0);
+        break;
+      }
+    }
+    t[n - 1 - i] = x;  // ascending
+    w[n - 1 - i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Device helpers
+
+// Real orthonormal spherical harmonics (Eq. 32 with cos / sin in place of e^{i m phi}) of degree
+// <= p and order <= mmax at (cos_t, sin_t, phi), written to out[b * stride] in the library's own
+// basis order: m = 0..mmax, n = m..p, cos variant then (m > 0) sin variant.
+__device__ void real_sh_eval(int p, int mmax, double ct, double st, double phi, double* out, long long stride) {
+  double pmm = 0.28209479177387814;  // 1 / sqrt(4 pi)
+  int b = 0;
+  const double sq2 = 1.4142135623730951;
+  for (int m = 0; m <= mmax; ++m) {
+    if (m > 0) pmm *= sqrt((2.0 * m + 1.0) / (2.0 * m)) * st;
+    double cm = 1.0, sm = 0.0;
+    if (m > 0) {
+      sincos(m * phi, &sm, &cm);
+      cm *= sq2;
+      sm *= sq2;
+    }
+    double pnm2 = 0.0, pnm1 = pmm;
+    for (int n = m; n <= p; ++n) {
+      double pn;
+      if (n == m) {
+        pn = pmm;
+      } else if (n == m + 1) {
+        pn = sqrt(2.0 * m + 3.0) * ct * pmm;
+      } else {
+        double a = sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+        double bb = sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
+        pn = a * (ct * pnm1 - bb * pnm2);
+      }
+      if (n > m) {
+        pnm2 = pnm1;
+        pnm1 = pn;
+      }
+      if (m == 0) {
+        out[(long long)(b++) * stride] = pn;
+      } else {
+        out[(long long)(b++) * stride] = pn * cm;
+        out[(long long)(b++) * stride] = pn * sm;
+      }
+    }
+  }
+}
+
+// Y at a set of points given as unit vectors (x, y, z, *): Y[pt * nbasis + b].
+__global__ void k_sh_at_points(int p, int mmax, int nbasis, const double4* pts, int npts, double* Y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npts) return;
+  double4 s = pts[i];
+  double ct = s.z, st = sqrt(fmax(0.0, s.x * s.x + s.y * s.y));
+  double phi = atan2(s.y, s.x);
+  real_sh_eval(p, mmax, ct, st, phi, Y + (long long)i * nbasis, 1);
+}
+
+// Grid points of a (p, nphi) grid as unit vectors, w = unit-sphere weight (2 pi / nphi) lambda_j.
+__global__ void k_grid_points(int p, int nphi, const double* t, const double* lam, double4* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int np = (p + 1) * nphi;
+  if (i >= np) return;
+  int j = i / nphi, k = i % nphi;
+  double ct = t[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+  double sp, cp;
+  sincospi(2.0 * k / nphi, &sp, &cp);
+  out[i] = make_double4(st * cp, st * sp, ct, 2.0 * kPi / nphi * lam[j]);
+}
+
+// Analysis matrix An[b * np + node] = Y_b(node) * weight(node), from Yg[node * nbasis + b].
+__global__ void k_analysis(int np, int nbasis, const double* Yg, const double4* gp, double* An) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)np * nbasis) return;
+  int b = (int)(i / np), node = (int)(i % np);
+  An[i] = Yg[(long long)node * nbasis + b] * gp[node].w;
+}
+
+// Surface nodes of all particles (lab frame): x = c + R D s, n = R normalise(D^{-1} s),
+// weight = (2 pi / nphi) lambda_j |cof(D) s| (Eq. 35 with W / sin(theta) = |cof(D) s|).
+__global__ void k_nodes(int n, const long long* offset, const int* pvec, const int* nphivec, const double* axes,
+                        const double* centre, const double* rot, const long long* gtab_off, const double* gtab,
+                        double4* x, double4* nrm, int* pid) {
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+  long long o = offset[i];
+  int nphi = nphivec[i], p = pvec[i];
+  int np = (p + 1) * nphi;
+  const double* t = gtab + gtab_off[i];
+  const double* lam = t + (p + 1);
+  double a = axes[3 * i], b = axes[3 * i + 1], cc = axes[3 * i + 2];
+  const double* R = rot + 9 * i;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < np; l += gridDim.x * blockDim.x) {
+    int j = l / nphi, k = l % nphi;
+    double ct = t[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double sp, cp;
+    sincospi(2.0 * k / nphi, &sp, &cp);
+    double sx = st * cp, sy = st * sp, sz = ct;
+    double bx = a * sx, by = b * sy, bz = cc * sz;
+    double gx = sx / a, gy = sy / b, gz = sz / cc;
+    double gn = rsqrt(gx * gx + gy * gy + gz * gz);
+    gx *= gn;
+    gy *= gn;
+    gz *= gn;
+    double J = sqrt((b * cc * sx) * (b * cc * sx) + (a * cc * sy) * (a * cc * sy) + (a * b * sz) * (a * b * sz));
+    double w = 2.0 * kPi / nphi * lam[j] * J;
+    double lx = R[0] * bx + R[1] * by + R[2] * bz + centre[3 * i];
+    double ly = R[3] * bx + R[4] * by + R[5] * bz + centre[3 * i + 1];
+    double lz = R[6] * bx + R[7] * by + R[8] * bz + centre[3 * i + 2];
+    x[o + l] = make_double4(lx, ly, lz, w);
+    nrm[o + l] = make_double4(R[0] * gx + R[1] * gy + R[2] * gz, R[3] * gx + R[4] * gy + R[5] * gz,
+                              R[6] * gx + R[7] * gy + R[8] * gz, 0.0);
+    pid[o + l] = i;
+  }
+  }
+}
+
+// Per-particle area |Gamma_i| = sum w and inverse moment tensor (Eq. 18), one block per particle.
+__global__ void k_moments(int n, const long long* offset, const double4* x, const double* centre, double* area,
+                          double* tauinv) {
+  int i = blockIdx.x;
+  if (i >= n) return;
+  __shared__ double red[7][256];
+  // sums of w, w rx^2, w ry^2, w rz^2, w rx ry, w rx rz, w ry rz
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  double accyz = 0.0;
+  double cx = centre[3 * i], cy = centre[3 * i + 1], cz = centre[3 * i + 2];
+  for (long long s = offset[i] + threadIdx.x; s < offset[i + 1]; s += blockDim.x) {
+    double4 p = x[s];
+    double rx = p.x - cx, ry = p.y - cy, rz = p.z - cz, w = p.w;
+    acc[0] += w;
+    acc[1] += w * rx * rx;
+    acc[2] += w * ry * ry;
+    acc[3] += w * rz * rz;
+    acc[4] += w * rx * ry;
+    acc[5] += w * rx * rz;
+    accyz += w * ry * rz;
+  }
+  acc[6] = accyz;
+  for (int q = 0; q < 7; ++q) red[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int q = 0; q < 7; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double W = red[0][0], xx = red[1][0], yy = red[2][0], zz = red[3][0], xy = red[4][0], xz = red[5][0],
+           yz = red[6][0];
+    double t[9] = {yy + zz, -xy, -xz, -xy, xx + zz, -yz, -xz, -yz, xx + yy};
+    double c00 = t[4] * t[8] - t[5] * t[7], c01 = t[5] * t[6] - t[3] * t[8], c02 = t[3] * t[7] - t[4] * t[6];
+    double det = t[0] * c00 + t[1] * c01 + t[2] * c02;
+    double inv[9] = {c00, t[2] * t[7] - t[1] * t[8], t[1] * t[5] - t[2] * t[4],
+                     c01, t[0] * t[8] - t[2] * t[6], t[2] * t[3] - t[0] * t[5],
+                     c02, t[1] * t[6] - t[0] * t[7], t[0] * t[4] - t[1] * t[3]};
+    area[i] = W;
+    for (int q = 0; q < 9; ++q) tauinv[9 * i + q] = inv[q] / det;
+  }
+}
+
+// Kernel-value matrix of the singular rule for one shape and polar index j, all azimuthal k:
+// C[((kind * nphi + k) * 9 + 3 al + be) * nrot + a] = omega_a J(s_a) kernel_{al be}(x_t - x(s_a)),
+// target t = (j, k), rotated point s_a = R_z(phi_k) rotpts[j][a]; kind 0 = traction (Eqs. 13, 22),
+// kind 1 = Stokeslet (Eq. 10).
+__global__ void k_self_kernel_values(int nphi, int nrot, double tj, const double* axes, const double4* rotpts_j,
+                                     double* Cbase, size_t perC) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = blockIdx.y;
+  if (a >= nrot) return;
+  double ax = axes[3 * blockIdx.z], bx = axes[3 * blockIdx.z + 1], cx = axes[3 * blockIdx.z + 2];
+  double* C = Cbase + perC * blockIdx.z;
+  double sp, cp;
+  sincospi(2.0 * k / nphi, &sp, &cp);
+  double4 q = rotpts_j[a];
+  double sx = cp * q.x - sp * q.y, sy = sp * q.x + cp * q.y, sz = q.z;
+  double st = sqrt(fmax(0.0, 1.0 - tj * tj));
+  double tx = st * cp, ty = st * sp, tz = tj;
+  double xt0 = ax * tx, xt1 = bx * ty, xt2 = cx * tz;
+  double g0 = tx / ax, g1 = ty / bx, g2 = tz / cx;
+  double gn = rsqrt(g0 * g0 + g1 * g1 + g2 * g2);
+  g0 *= gn;
+  g1 *= gn;
+  g2 *= gn;
+  double r0 = xt0 - ax * sx, r1 = xt1 - bx * sy, r2 = xt2 - cx * sz;
+  double J = sqrt((bx * cx * sx) * (bx * cx * sx) + (ax * cx * sy) * (ax * cx * sy) + (ax * bx * sz) * (ax * bx * sz));
+  double wJ = q.w * J;
+  double d2 = r0 * r0 + r1 * r1 + r2 * r2;
+  double inv = rsqrt(d2);
+  double inv2 = inv * inv;
+  double rr[3] = {r0, r1, r2};
+  double rn = r0 * g0 + r1 * g1 + r2 * g2;
+  double ck = -3.0 / (4.0 * kPi) * rn * inv2 * inv2 * inv * wJ;
+  double cs = wJ / (8.0 * kPi);
+  for (int al = 0; al < 3; ++al)
+    for (int be = 0; be < 3; ++be) {
+      double rab = rr[al] * rr[be];
+      C[((long long)(0 * nphi + k) * 9 + 3 * al + be) * nrot + a] = ck * rab;
+      C[((long long)(1 * nphi + k) * 9 + 3 * al + be) * nrot + a] =
+          cs * ((al == be ? inv : 0.0) + rab * inv2 * inv);
+    }
+}
+
+// Scatter G[((kind * nphi + k) * 9 + 3 al + be) * np + (j' nphi + k')] into the body blocks:
+// row 3 t + al, t = j nphi + k; column 3 s + be, s = j' nphi + (k' + k) mod nphi.
+__global__ void k_self_scatter(int nphi, int np, int j, const double* Gbase, size_t perG, const long long* block_off,
+                               double* BKbase, double* BSbase) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const double* G = Gbase + perG * blockIdx.y;
+  double* BK = BKbase + block_off[blockIdx.y];
+  double* BS = BSbase + block_off[blockIdx.y];
+  long long total = 2LL * nphi * 9 * np;
+  if (i >= total) return;
+  int col = (int)(i % np);
+  long long row = i / np;
+  int ab = (int)(row % 9);
+  long long kk = row / 9;
+  int k = (int)(kk % nphi), kind = (int)(kk / nphi);
+  int al = ab / 3, be = ab % 3;
+  int jp = col / nphi, kp = col % nphi;
+  int t = j * nphi + k, s = jp * nphi + (kp + k) % nphi;
+  double* B = kind == 0 ? BK : BS;
+  B[(long long)(3 * t + al) * (3 * np) + 3 * s + be] = G[i];
+}
+
+// Preconditioner matrix before inversion: M = 1/2 I + K0 + L0 in the body frame, with
+// L0_ts = w_s (I - [r_t]x [r_s]x) (Eq. 26 written as a block; r the body-frame node).
+__global__ void k_precond_matrix(int np, int nphi, const double* t, const double* lam, double ax, double bx,
+                                 double cx, const double* BK, double* M) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long dim = 3LL * np;
+  if (i >= dim * dim) return;
+  int row = (int)(i / dim), col = (int)(i % dim);
+  int tn = row / 3, al = row % 3, sn = col / 3, be = col % 3;
+  auto node = [&](int l, double* r, double* w) {
+    int j = l / nphi, k = l % nphi;
+    double ct = t[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double sp, cp;
+    sincospi(2.0 * k / nphi, &sp, &cp);
+    double sx = st * cp, sy = st * sp, sz = ct;
+    r[0] = ax * sx;
+    r[1] = bx * sy;
+    r[2] = cx * sz;
+    *w = 2.0 * kPi / nphi * lam[j] *
+         sqrt((bx * cx * sx) * (bx * cx * sx) + (ax * cx * sy) * (ax * cx * sy) + (ax * bx * sz) * (ax * bx * sz));
+  };
+  double rt[3], rs[3], wt, ws;
+  node(tn, rt, &wt);
+  node(sn, rs, &ws);
+  // ([a]x [b]x)_{al be} = a_be b_al - (a . b) delta_{al be}
+  double dot = rt[0] * rs[0] + rt[1] * rs[1] + rt[2] * rs[2];
+  double cc = rt[be] * rs[al] - (al == be ? dot : 0.0);
+  double Lv = ws * ((al == be ? 1.0 : 0.0) - cc);
+  M[i] = BK[i] + Lv + (row == col ? 0.5 : 0.0);
+}
+
+__global__ void k_to_float(const double* in, float* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// Upsampled source nodes of every near-source particle: lab positions and weights on its
+// (pup + 1) x nphi_up grid.
+__global__ void k_up_nodes(int nu, const int* up_particle, const long long* up_off, const int* pvec, const int* nphivec,
+                           const int* pupvec, const double* axes, const double* centre, const double* rot,
+                           const long long* gtab_up_off, const double* gtab, double4* out) {
+  for (int u = blockIdx.y; u < nu; u += gridDim.y) {
+  int i = up_particle[u];
+  int pup = pupvec[i];
+  int nphi_up = nphivec[i] + 2 * (pup - pvec[i]);
+  int nup = (pup + 1) * nphi_up;
+  const double* t = gtab + gtab_up_off[i];
+  const double* lam = t + (pup + 1);
+  double a = axes[3 * i], b = axes[3 * i + 1], cc = axes[3 * i + 2];
+  const double* R = rot + 9 * i;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nup; l += gridDim.x * blockDim.x) {
+    int j = l / nphi_up, k = l % nphi_up;
+    double ct = t[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double sp, cp;
+    sincospi(2.0 * k / nphi_up, &sp, &cp);
+    double sx = st * cp, sy = st * sp, sz = ct;
+    double bx = a * sx, by = b * sy, bz = cc * sz;
+    double J = sqrt((b * cc * sx) * (b * cc * sx) + (a * cc * sy) * (a * cc * sy) + (a * b * sz) * (a * b * sz));
+    out[up_off[u] + l] = make_double4(R[0] * bx + R[1] * by + R[2] * bz + centre[3 * i],
+                                      R[3] * bx + R[4] * by + R[5] * bz + centre[3 * i + 1],
+                                      R[6] * bx + R[7] * by + R[8] * bz + centre[3 * i + 2],
+                                      2.0 * kPi / nphi_up * lam[j] * J);
+  }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Host orchestration
+
+static void quat_to_rot_host(const double* q, double* R) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  double nrm = std::sqrt(w * w + x * x + y * y + z * z);
+  w /= nrm;
+  x /= nrm;
+  y /= nrm;
+  z /= nrm;
+  R[0] = 1 - 2 * (y * y + z * z);
+  R[1] = 2 * (x * y - w * z);
+  R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);
+  R[4] = 1 - 2 * (x * x + z * z);
+  R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);
+  R[7] = 2 * (y * z + w * x);
+  R[8] = 1 - 2 * (x * x + y * y);
+}
+
+template <typename T>
+static Status upload(DevBuf<T>& buf, const std::vector<T>& host, cudaStream_t s) {
+  RBS_TRY(buf.alloc(host.size()));
+  if (!host.empty()) RBS_CUDA_TRY(cudaMemcpyAsync(buf.ptr, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return Status::Ok();
+}
+
+static int count_basis(int p, int mmax) {
+  int nb = p + 1;
+  for (int m = 1; m <= mmax; ++m) nb += 2 * (p - m + 1);
+  return nb;
+}
+
+// Build one grid's tables.
+static Status build_grid(Context& c, Grid& g) {
+  cudaStream_t s = c.stream;
+  g.np = (g.p + 1) * g.nphi;
+  g.mmax = (g.nphi - 1) / 2;
+  if (g.mmax > g.p) g.mmax = g.p;
+  g.nbasis = count_basis(g.p, g.mmax);
+  g.ps = c.opt.p_self_factor * g.p;
+  g.nrot = (g.ps + 1) * (2 * g.ps + 2);
+  g.pup = c.opt.p_up_factor * g.p;
+  g.nphi_up = g.nphi + 2 * (g.pup - g.p);
+  g.nup = (g.pup + 1) * g.nphi_up;
+  gauss_legendre_newton(g.p + 1, g.t, g.lam);
+  gauss_legendre_newton(g.pup + 1, g.t_up, g.lam_up);
+  RBS_TRY(upload(g.d_t, g.t, s));
+  RBS_TRY(upload(g.d_lam, g.lam, s));
+  RBS_TRY(upload(g.d_t_up, g.t_up, s));
+  RBS_TRY(upload(g.d_lam_up, g.lam_up, s));
+
+  // rotated singular-rule points for targets (theta_j, phi = 0): R_y(theta_j) applied to the rule
+  // around the pole; theta' by Gauss-Legendre on [0, pi], phi' uniform (2 ps + 2 points).
+  std::vector<double> u, lu;
+  gauss_legendre_newton(g.ps + 1, u, lu);
+  int nb = 2 * g.ps + 2;
+  std::vector<double> rot((size_t)(g.p + 1) * g.nrot * 4);
+  for (int j = 0; j <= g.p; ++j) {
+    double ct = g.t[j], st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+    for (int a = 0; a <= g.ps; ++a) {
+      double th = 0.5 * kPi * (u[a] + 1.0);
+      double wth = 0.5 * kPi * lu[a];
+      for (int bb = 0; bb < nb; ++bb) {
+        double ph = 2.0 * kPi * bb / nb;
+        double px = std::sin(th) * std::cos(ph), py = std::sin(th) * std::sin(ph), pz = std::cos(th);
+        // R_y(theta) = [[ct, 0, st], [0, 1, 0], [-st, 0, ct]]
+        size_t idx = ((size_t)j * g.nrot + (size_t)a * nb + bb) * 4;
+        rot[idx + 0] = ct * px + st * pz;
+        rot[idx + 1] = py;
+        rot[idx + 2] = -st * px + ct * pz;
+        rot[idx + 3] = wth * std::sin(th) * (2.0 * kPi / nb);
+      }
+    }
+  }
+  RBS_TRY(upload(g.d_rotpts, rot, s));
+
+  // analysis matrix on the grid
+  DevBuf<double4> gp;
+  RBS_TRY(gp.alloc(g.np));
+  k_grid_points<<<cdiv(g.np, 128), 128, 0, s>>>(g.p, g.nphi, g.d_t.ptr, g.d_lam.ptr, gp.ptr);
+  DevBuf<double> Yg, An;
+  RBS_TRY(Yg.alloc((size_t)g.np * g.nbasis));
+  RBS_TRY(An.alloc((size_t)g.np * g.nbasis));
+  k_sh_at_points<<<cdiv(g.np, 128), 128, 0, s>>>(g.p, g.mmax, g.nbasis, gp.ptr, g.np, Yg.ptr);
+  k_analysis<<<cdiv((long long)g.np * g.nbasis, 256), 256, 0, s>>>(g.np, g.nbasis, Yg.ptr, gp.ptr, An.ptr);
+  RBS_CUDA_TRY(cudaGetLastError());
+
+  // singular-rule interpolation: Interp_j = Y(rotated points of j) x An
+  DevBuf<double> Yr;
+  long long nrp = (long long)(g.p + 1) * g.nrot;
+  RBS_TRY(Yr.alloc((size_t)nrp * g.nbasis));
+  k_sh_at_points<<<cdiv(nrp, 128), 128, 0, s>>>(g.p, g.mmax, g.nbasis, (const double4*)g.d_rotpts.ptr, (int)nrp,
+                                                Yr.ptr);
+  RBS_TRY(g.d_interp.alloc((size_t)nrp * g.np));
+  RBS_TRY(dgemm_batched(s, (int)nrp, g.np, g.nbasis, Yr.ptr, g.nbasis, 0, An.ptr, g.np, 0, g.d_interp.ptr, g.np, 0, 1));
+
+  // upsampling interpolation U = Y(upsampled grid) x An
+  DevBuf<double4> gup;
+  RBS_TRY(gup.alloc(g.nup));
+  k_grid_points<<<cdiv(g.nup, 128), 128, 0, s>>>(g.pup, g.nphi_up, g.d_t_up.ptr, g.d_lam_up.ptr, gup.ptr);
+  DevBuf<double> Yu;
+  RBS_TRY(Yu.alloc((size_t)g.nup * g.nbasis));
+  k_sh_at_points<<<cdiv(g.nup, 128), 128, 0, s>>>(g.p, g.mmax, g.nbasis, gup.ptr, g.nup, Yu.ptr);
+  RBS_TRY(g.d_up.alloc((size_t)g.nup * g.np));
+  RBS_TRY(dgemm_batched(s, g.nup, g.np, g.nbasis, Yu.ptr, g.nbasis, 0, An.ptr, g.np, 0, g.d_up.ptr, g.np, 0, 1));
+  RBS_TRY(g.d_up32.alloc((size_t)g.nup * g.np));
+  k_to_float<<<256, 256, 0, s>>>(g.d_up.ptr, g.d_up32.ptr, (long long)g.nup * g.np);
+  RBS_CUDA_TRY(cudaGetLastError());
+  RBS_CUDA_TRY(cudaStreamSynchronize(s));  // temporaries are released on return
+  return Status::Ok();
+}
+
+// Self blocks of every shape of one grid, in chunks of shapes.  For each chunk and polar index j:
+// kernel values C (18 nphi x nrot per shape), one batched GEMM G = C x Interp_j, and the scatter
+// into the body-frame blocks with the azimuthal shift.
+static Status build_self_blocks(Context& c, int gi, const std::vector<int>& shape_ids) {
+  cudaStream_t s = c.stream;
+  Grid& g = *c.grids[gi];
+  long long rowsC = 18LL * g.nphi;
+  size_t perC = (size_t)rowsC * g.nrot, perG = (size_t)rowsC * g.np;
+  size_t budget = (size_t)1 << 27;  // doubles, 1 GB
+  int per_chunk = (int)std::max<size_t>(1, budget / (perC + perG));
+  int nsh = (int)shape_ids.size();
+  int chunk = std::min(std::min(per_chunk, nsh), 65535);
+  DevBuf<double> C, G;
+  RBS_TRY(C.alloc(perC * chunk));
+  RBS_TRY(G.alloc(perG * chunk));
+  std::vector<double> ax(3 * (size_t)nsh);
+  std::vector<long long> off(nsh);
+  for (int k = 0; k < nsh; ++k) {
+    const Shape& sh = c.shapes[shape_ids[k]];
+    ax[3 * k] = sh.a;
+    ax[3 * k + 1] = sh.b;
+    ax[3 * k + 2] = sh.c;
+    off[k] = (long long)sh.block_off;
+  }
+  DevBuf<double> d_ax;
+  DevBuf<long long> d_off;
+  RBS_TRY(upload(d_ax, ax, s));
+  RBS_TRY(upload(d_off, off, s));
+  for (int start = 0; start < nsh; start += chunk) {
+    int cnt = std::min(chunk, nsh - start);
+    for (int j = 0; j <= g.p; ++j) {
+      dim3 grd(cdiv(g.nrot, 128), g.nphi, cnt);
+      k_self_kernel_values<<<grd, 128, 0, s>>>(g.nphi, g.nrot, g.t[j], d_ax.ptr + 3 * (size_t)start,
+                                               (const double4*)g.d_rotpts.ptr + (size_t)j * g.nrot, C.ptr, perC);
+      RBS_CUDA_TRY(cudaGetLastError());
+      RBS_TRY(dgemm_batched(s, (int)rowsC, g.np, g.nrot, C.ptr, g.nrot, (long long)perC,
+                            g.d_interp.ptr + (size_t)j * g.nrot * g.np, g.np, 0, G.ptr, g.np, (long long)perG, cnt));
+      long long tot = 2LL * g.nphi * 9 * g.np;
+      dim3 grs(cdiv(tot, 256), cnt);
+      k_self_scatter<<<grs, 256, 0, s>>>(g.nphi, g.np, j, G.ptr, perG, d_off.ptr + start, c.d_blockK.ptr,
+                                         c.d_blockS.ptr);
+      RBS_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  RBS_CUDA_TRY(cudaStreamSynchronize(s));
+  return Status::Ok();
+}
+
+Status build_geometry(Context& c) {
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = c.stream;
+  const int n = c.n;
+  // rotations
+  c.rot.assign((size_t)9 * n, 0.0);
+  for (int i = 0; i < n; ++i) quat_to_rot_host(&c.quats[4 * i], &c.rot[9 * i]);
+  // node offsets
+  c.offset.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) c.offset[i + 1] = c.offset[i] + (long long)(c.p[i] + 1) * c.nphi[i];
+  c.N = c.offset[n];
+
+  // grids
+  for (Grid* g : c.grids) delete g;
+  c.grids.clear();
+  std::map<std::pair<int, int>, int> grid_id;
+  std::vector<int> grid_of(n);
+  for (int i = 0; i < n; ++i) {
+    auto key = std::make_pair(c.p[i], c.nphi[i]);
+    auto it = grid_id.find(key);
+    if (it == grid_id.end()) {
+      Grid* g = new Grid();
+      g->p = c.p[i];
+      g->nphi = c.nphi[i];
+      it = grid_id.emplace(key, (int)c.grids.size()).first;
+      c.grids.push_back(g);
+    }
+    grid_of[i] = it->second;
+  }
+  for (Grid* g : c.grids) RBS_TRY(build_grid(c, *g));
+
+  // shapes
+  c.shapes.clear();
+  c.shape_of.assign(n, 0);
+  std::map<std::tuple<double, double, double, int, int>, int> shape_id;
+  c.block_elems = 0;
+  for (int i = 0; i < n; ++i) {
+    auto key = std::make_tuple(c.axes[3 * i], c.axes[3 * i + 1], c.axes[3 * i + 2], c.p[i], c.nphi[i]);
+    auto it = shape_id.find(key);
+    if (it == shape_id.end()) {
+      Shape sh;
+      sh.a = c.axes[3 * i];
+      sh.b = c.axes[3 * i + 1];
+      sh.c = c.axes[3 * i + 2];
+      sh.grid = grid_of[i];
+      sh.np = c.grids[sh.grid]->np;
+      sh.block_off = c.block_elems;
+      c.block_elems += (size_t)9 * sh.np * sh.np;
+      it = shape_id.emplace(key, (int)c.shapes.size()).first;
+      c.shapes.push_back(sh);
+    }
+    c.shape_of[i] = it->second;
+  }
+
+  // per-particle device arrays
+  std::vector<long long> gtab_off(n), gtab_up_off(n);
+  std::vector<double> gtab;
+  std::vector<long long> grid_tab_off(c.grids.size()), grid_tab_up_off(c.grids.size());
+  for (size_t gi = 0; gi < c.grids.size(); ++gi) {
+    Grid& g = *c.grids[gi];
+    grid_tab_off[gi] = (long long)gtab.size();
+    gtab.insert(gtab.end(), g.t.begin(), g.t.end());
+    gtab.insert(gtab.end(), g.lam.begin(), g.lam.end());
+    grid_tab_up_off[gi] = (long long)gtab.size();
+    gtab.insert(gtab.end(), g.t_up.begin(), g.t_up.end());
+    gtab.insert(gtab.end(), g.lam_up.begin(), g.lam_up.end());
+  }
+  std::vector<int> pup(n);
+  for (int i = 0; i < n; ++i) {
+    gtab_off[i] = grid_tab_off[grid_of[i]];
+    gtab_up_off[i] = grid_tab_up_off[grid_of[i]];
+    pup[i] = c.grids[grid_of[i]]->pup;
+  }
+  DevBuf<long long> d_gtab_off, d_gtab_up_off;
+  DevBuf<double> d_gtab, d_axes;
+  DevBuf<int> d_p, d_nphi, d_pup;
+  RBS_TRY(upload(d_gtab_off, gtab_off, s));
+  RBS_TRY(upload(d_gtab_up_off, gtab_up_off, s));
+  RBS_TRY(upload(d_gtab, gtab, s));
+  RBS_TRY(upload(d_axes, c.axes, s));
+  RBS_TRY(upload(d_p, c.p, s));
+  RBS_TRY(upload(d_nphi, c.nphi, s));
+  RBS_TRY(upload(d_pup, pup, s));
+  RBS_TRY(upload(c.d_centre, c.centres, s));
+  RBS_TRY(upload(c.d_rot, c.rot, s));
+  RBS_TRY(upload(c.d_offset, c.offset, s));
+  RBS_TRY(upload(c.d_shape, c.shape_of, s));
+  std::vector<int> nodes(n);
+  for (int i = 0; i < n; ++i) nodes[i] = (int)(c.offset[i + 1] - c.offset[i]);
+  RBS_TRY(upload(c.d_nodes, nodes, s));
+  RBS_TRY(c.d_x.alloc(c.N));
+  RBS_TRY(c.d_nrm.alloc(c.N));
+  RBS_TRY(c.d_pid.alloc(c.N));
+  RBS_TRY(c.d_area.alloc(n));
+  RBS_TRY(c.d_tauinv.alloc((size_t)9 * n));
+  {
+    int maxnp = 0;
+    for (int i = 0; i < n; ++i) maxnp = std::max(maxnp, nodes[i]);
+    dim3 grd(cdiv(maxnp, 128), std::min(n, 65535));
+    k_nodes<<<grd, 128, 0, s>>>(n, c.d_offset.ptr, d_p.ptr, d_nphi.ptr, d_axes.ptr, c.d_centre.ptr, c.d_rot.ptr,
+                                d_gtab_off.ptr, d_gtab.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr);
+    k_moments<<<n, 256, 0, s>>>(n, c.d_offset.ptr, c.d_x.ptr, c.d_centre.ptr, c.d_area.ptr, c.d_tauinv.ptr);
+    RBS_CUDA_TRY(cudaGetLastError());
+  }
+
+  // self blocks (body frame) of every shape
+  RBS_TRY(c.d_blockK.alloc(c.block_elems));
+  RBS_TRY(c.d_blockS.alloc(c.block_elems));
+  {
+    std::vector<std::vector<int>> by_grid(c.grids.size());
+    for (size_t k = 0; k < c.shapes.size(); ++k) by_grid[c.shapes[k].grid].push_back((int)k);
+    for (size_t gi = 0; gi < c.grids.size(); ++gi)
+      if (!by_grid[gi].empty()) RBS_TRY(build_self_blocks(c, (int)gi, by_grid[gi]));
+  }
+  std::vector<long long> boff(c.shapes.size());
+  for (size_t k = 0; k < c.shapes.size(); ++k) boff[k] = (long long)c.shapes[k].block_off;
+  RBS_TRY(upload(c.d_block_off, boff, s));
+
+  // block-diagonal preconditioner P0 = (1/2 I + K0 + L0)^{-1} per shape (Section 3.2)
+  if (c.opt.preconditioner) {
+    RBS_TRY(c.d_precond.alloc(c.block_elems));
+    std::map<int, std::vector<int>> by_np;
+    for (size_t k = 0; k < c.shapes.size(); ++k) {
+      const Shape& sh = c.shapes[k];
+      Grid& g = *c.grids[sh.grid];
+      long long dim2 = 9LL * sh.np * sh.np;
+      k_precond_matrix<<<cdiv(dim2, 256), 256, 0, s>>>(sh.np, g.nphi, g.d_t.ptr, g.d_lam.ptr, sh.a, sh.b, sh.c,
+                                                       c.d_blockK.ptr + sh.block_off, c.d_precond.ptr + sh.block_off);
+      by_np[sh.np].push_back((int)k);
+    }
+    RBS_CUDA_TRY(cudaGetLastError());
+    // shapes of equal size are contiguous in the block arrays only if allocated in order; invert
+    // runs of contiguous equal-size shapes together.
+    size_t k = 0;
+    while (k < c.shapes.size()) {
+      size_t e = k + 1;
+      while (e < c.shapes.size() && c.shapes[e].np == c.shapes[k].np) ++e;
+      RBS_TRY(invert_batched(c, c.d_precond.ptr + c.shapes[k].block_off, 3 * c.shapes[k].np, (int)(e - k)));
+      k = e;
+    }
+    RBS_TRY(c.d_precond32.alloc(c.block_elems));
+    k_to_float<<<1024, 256, 0, s>>>(c.d_precond.ptr, c.d_precond32.ptr, (long long)c.block_elems);
+  }
+  RBS_TRY(c.d_blockK32.alloc(c.block_elems));
+  k_to_float<<<1024, 256, 0, s>>>(c.d_blockK.ptr, c.d_blockK32.ptr, (long long)c.block_elems);
+  RBS_CUDA_TRY(cudaGetLastError());
+
+  // near pairs: |c_i - c_j| < R_i + R_j + delta within one suspension, by a cell list
+  c.near_pairs.clear();
+  {
+    std::vector<double> R(n);
+    double rmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      R[i] = std::max(c.axes[3 * i], std::max(c.axes[3 * i + 1], c.axes[3 * i + 2]));
+      rmax = std::max(rmax, R[i]);
+    }
+    double cell = 2.0 * rmax + c.opt.near_delta;
+    std::unordered_map<long long, std::vector<int>> cells;
+    auto key = [&](long long a, long long b, long long d) { return (a * 73856093LL) ^ (b * 19349663LL) ^ (d * 83492791LL); };
+    std::vector<long long> ci(3 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+      for (int d = 0; d < 3; ++d) ci[3 * i + d] = (long long)std::floor(c.centres[3 * i + d] / cell);
+      cells[key(ci[3 * i], ci[3 * i + 1], ci[3 * i + 2])].push_back(i);
+    }
+    for (int i = 0; i < n; ++i) {
+      std::vector<int> cand;
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            auto it = cells.find(key(ci[3 * i] + dx, ci[3 * i + 1] + dy, ci[3 * i + 2] + dz));
+            if (it == cells.end()) continue;
+            for (int j : it->second) cand.push_back(j);
+          }
+      std::sort(cand.begin(), cand.end());
+      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+      for (int j : cand) {
+        if (j == i || c.sid[j] != c.sid[i]) continue;
+        double dx = c.centres[3 * i] - c.centres[3 * j], dy = c.centres[3 * i + 1] - c.centres[3 * j + 1],
+               dz = c.centres[3 * i + 2] - c.centres[3 * j + 2];
+        double d = std::sqrt(dx * dx + dy * dy + dz * dz);
+        double rmin_i = std::min(c.axes[3 * i], std::min(c.axes[3 * i + 1], c.axes[3 * i + 2]));
+        double rmin_j = std::min(c.axes[3 * j], std::min(c.axes[3 * j + 1], c.axes[3 * j + 2]));
+        if (d < rmin_i + rmin_j)
+          return Status::Err(RBS_EOVERLAP, "particles " + std::to_string(i) + " and " + std::to_string(j) +
+                                               " overlap (inscribed spheres intersect)");
+        if (d < R[i] + R[j] + c.opt.near_delta) c.near_pairs.push_back(make_int2(i, j));
+      }
+    }
+  }
+  RBS_TRY(upload(c.d_near, c.near_pairs, s));
+  // upsampled sources
+  c.up_index.assign(n, -1);
+  c.up_particle.clear();
+  c.up_offset.clear();
+  c.n_up_nodes = 0;
+  for (const int2& pr : c.near_pairs) {
+    int j = pr.y;
+    if (c.up_index[j] < 0) {
+      c.up_index[j] = (int)c.up_particle.size();
+      c.up_particle.push_back(j);
+      c.up_offset.push_back(c.n_up_nodes);
+      c.n_up_nodes += c.grids[grid_of[j]]->nup;
+    }
+  }
+  c.up_offset.push_back(c.n_up_nodes);
+  {
+    std::vector<const double*> U;
+    std::vector<const float*> U32;
+    for (int j : c.up_particle) {
+      U.push_back(c.grids[grid_of[j]]->d_up.ptr);
+      U32.push_back(c.grids[grid_of[j]]->d_up32.ptr);
+    }
+    RBS_TRY(upload(c.d_upU, U, s));
+    RBS_TRY(upload(c.d_upU32, U32, s));
+  }
+  RBS_TRY(upload(c.d_up_particle, c.up_particle, s));
+  RBS_TRY(upload(c.d_up_off, c.up_offset, s));
+  RBS_TRY(upload(c.d_up_index, c.up_index, s));
+  RBS_TRY(c.d_up_x.alloc(c.n_up_nodes));
+  RBS_TRY(c.d_up_mu.alloc(3 * c.n_up_nodes));
+  if (!c.up_particle.empty()) {
+    int maxnup = 0;
+    for (Grid* g : c.grids) maxnup = std::max(maxnup, g->nup);
+    dim3 grd(cdiv(maxnup, 128), (unsigned)std::min<size_t>(c.up_particle.size(), 65535));
+    k_up_nodes<<<grd, 128, 0, s>>>((int)c.up_particle.size(), c.d_up_particle.ptr, c.d_up_off.ptr, d_p.ptr, d_nphi.ptr,
+                                   d_pup.ptr, d_axes.ptr, c.d_centre.ptr, c.d_rot.ptr, d_gtab_up_off.ptr, d_gtab.ptr,
+                                   c.d_up_x.ptr);
+    RBS_CUDA_TRY(cudaGetLastError());
+  }
+
+  // smooth pair-sum work list: target tiles of 128 nodes, never straddling a suspension, each
+  // paired with source chunks of that suspension; chunks split so the grid covers the GPU.
+  c.work.clear();
+  {
+    std::vector<std::pair<long long, long long>> susp;
+    int i = 0;
+    while (i < n) {
+      int e = i + 1;
+      while (e < n && c.sid[e] == c.sid[i]) ++e;
+      susp.emplace_back(c.offset[i], c.offset[e]);
+      i = e;
+    }
+    const long long TT = 128;
+    long long tiles = 0;
+    for (auto& sp : susp) tiles += (sp.second - sp.first + TT - 1) / TT;
+    long long want = 4LL * std::max(1, c.sm_count);
+    int splits = (int)std::max(1LL, (want + tiles - 1) / std::max(1LL, tiles));
+    for (auto& sp : susp) {
+      long long ns = sp.second - sp.first;
+      int sc = (int)std::min<long long>(splits, std::max(1LL, ns / 256));
+      long long chunk = (ns + sc - 1) / sc;
+      for (long long tb = sp.first; tb < sp.second; tb += TT)
+        for (long long sb = sp.first; sb < sp.second; sb += chunk) {
+          longlong4 w;
+          w.x = tb;
+          w.y = std::min(tb + TT, sp.second);
+          w.z = sb;
+          w.w = std::min(sb + chunk, sp.second);
+          c.work.push_back(w);
+        }
+    }
+  }
+  RBS_TRY(upload(c.d_work, c.work, s));
+
+  // particle-block work list
+  c.bwork.clear();
+  c.max_np = 0;
+  for (int i = 0; i < n; ++i) {
+    c.max_np = std::max(c.max_np, nodes[i]);
+    for (int b = 0; b < nodes[i]; b += 24) c.bwork.push_back(make_int4(i, b, std::min(b + 24, nodes[i]), 0));
+  }
+  RBS_TRY(upload(c.d_bwork, c.bwork, s));
+
+  // workspace
+  for (auto& v : c.d_vec) RBS_TRY(v.alloc(3 * c.N));
+  int m = c.opt.restart;
+  RBS_TRY(c.d_V.alloc((size_t)(m + 1) * 3 * c.N));
+  RBS_TRY(c.d_H.alloc((size_t)(m + 1) * (m + 1) + 4 * (size_t)(m + 2)));
+  RBS_TRY(c.d_partials.alloc((size_t)(m + 2) * 1024));
+  RBS_TRY(c.d_FT.alloc((size_t)6 * n));
+  RBS_TRY(c.d_vo.alloc((size_t)6 * n));
+  RBS_CUDA_TRY(cudaStreamSynchronize(s));
+
+  // stats
+  c.stats.total_nodes = c.N;
+  c.stats.n_particles = n;
+  c.stats.n_shapes = (int)c.shapes.size();
+  c.stats.near_pairs = (long long)c.near_pairs.size();
+  long long fp = 0;
+  {
+    int i = 0;
+    while (i < n) {
+      int e = i + 1;
+      while (e < n && c.sid[e] == c.sid[i]) ++e;
+      long long ns = c.offset[e] - c.offset[i];
+      fp += ns * ns;
+      for (int k = i; k < e; ++k) fp -= (long long)nodes[k] * nodes[k];
+      i = e;
+    }
+  }
+  c.stats.far_pairs = fp;
+  c.stats.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  c.have_geometry = true;
+  return Status::Ok();
+}
+
+}  // namespace rbs

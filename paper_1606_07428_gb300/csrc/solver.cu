@@ -1,0 +1,454 @@
+// The mobility solve (Section 3's three steps; Algorithm 1 lines 3-5 without contact):
+//   1. incident density rho (Eq. 19);
+//   2. (1/2 I + K + L) mu = -(1/2 I + K) rho (Eq. 25) by GMRES (Section 3.2) with the right
+//      block-diagonal preconditioner; in the mixed mode the operator of the inner GMRES is applied in
+//      float32 and float64 iterative refinement recovers the float64 solution;
+//   3. u = S[rho + mu] and the rigid velocities v (Eq. 41), omega (Eq. 42).
+// Arnoldi (two-pass classical Gram-Schmidt), Givens rotations and the least-squares solve run in
+// float64 on the GPU; the host reads one residual estimate per iteration.
+#include <chrono>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace rbs {
+
+namespace {
+
+constexpr int kDotThreads = 256;
+
+// Incident density of Eq. 19 at every node.
+__global__ void k_incident(long long N, const int* __restrict__ pid, const double4* __restrict__ x,
+                           const double* __restrict__ centre, const double* __restrict__ area,
+                           const double* __restrict__ tauinv, const double* __restrict__ FT, double* __restrict__ rho) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
+    const int i = pid[t];
+    const double* f = FT + 6 * i;
+    const double* Ti = tauinv + 9 * i;
+    const double a0 = Ti[0] * f[3] + Ti[1] * f[4] + Ti[2] * f[5];
+    const double a1 = Ti[3] * f[3] + Ti[4] * f[4] + Ti[5] * f[5];
+    const double a2 = Ti[6] * f[3] + Ti[7] * f[4] + Ti[8] * f[5];
+    const double4 p = x[t];
+    const double rx = p.x - centre[3 * i], ry = p.y - centre[3 * i + 1], rz = p.z - centre[3 * i + 2];
+    const double inva = 1.0 / area[i];
+    rho[3 * t + 0] = f[0] * inva + (a1 * rz - a2 * ry);
+    rho[3 * t + 1] = f[1] * inva + (a2 * rx - a0 * rz);
+    rho[3 * t + 2] = f[2] * inva + (a0 * ry - a1 * rx);
+  }
+}
+
+// Rigid velocities (Eqs. 41-42) from the surface velocity u, one block per particle; the result is
+// divided by the viscosity.
+__global__ void __launch_bounds__(256) k_rigid(const long long* __restrict__ offset, const double4* __restrict__ x,
+                                               const double* __restrict__ centre, const double* __restrict__ area,
+                                               const double* __restrict__ tauinv, const double* __restrict__ u,
+                                               double inv_visc, double* __restrict__ vo) {
+  __shared__ double red[8][6];
+  const int i = blockIdx.x;
+  const double cx = centre[3 * i], cy = centre[3 * i + 1], cz = centre[3 * i + 2];
+  double m[6] = {0, 0, 0, 0, 0, 0};
+  for (long long s = offset[i] + threadIdx.x; s < offset[i + 1]; s += blockDim.x) {
+    const double4 p = x[s];
+    const double rx = p.x - cx, ry = p.y - cy, rz = p.z - cz, w = p.w;
+    const double a = u[3 * s], b = u[3 * s + 1], c = u[3 * s + 2];
+    m[0] += w * a;
+    m[1] += w * b;
+    m[2] += w * c;
+    m[3] += w * (ry * c - rz * b);
+    m[4] += w * (rz * a - rx * c);
+    m[5] += w * (rx * b - ry * a);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 6; ++q)
+    for (int o = 16; o > 0; o >>= 1) m[q] += __shfl_xor_sync(0xffffffffu, m[q], o);
+  if (lane == 0)
+    for (int q = 0; q < 6; ++q) red[warp][q] = m[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      for (int q = 0; q < 6; ++q) s[q] += red[w][q];
+    const double* T = tauinv + 9 * i;
+    const double ia = 1.0 / area[i];
+    vo[6 * i + 0] = s[0] * ia * inv_visc;
+    vo[6 * i + 1] = s[1] * ia * inv_visc;
+    vo[6 * i + 2] = s[2] * ia * inv_visc;
+    vo[6 * i + 3] = (T[0] * s[3] + T[1] * s[4] + T[2] * s[5]) * inv_visc;
+    vo[6 * i + 4] = (T[3] * s[3] + T[4] * s[4] + T[5] * s[5]) * inv_visc;
+    vo[6 * i + 5] = (T[6] * s[3] + T[7] * s[4] + T[8] * s[5]) * inv_visc;
+  }
+}
+
+// partial[i * nchunk + chunk] = sum over the chunk of V_i . w, for i < nv.
+__global__ void __launch_bounds__(kDotThreads) k_multidot(const double* __restrict__ V, long long ldv, int nv,
+                                                          const double* __restrict__ w, long long n, int nchunk,
+                                                          double* __restrict__ partial) {
+  __shared__ double red[kDotThreads / 32];
+  const int i = blockIdx.y;
+  const long long per = (n + nchunk - 1) / nchunk;
+  const long long b = per * blockIdx.x, e = min(n, b + per);
+  const double* v = V + ldv * i;
+  double acc = 0.0;
+  for (long long k = b + threadIdx.x; k < e; k += blockDim.x) acc = fma(v[k], w[k], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < kDotThreads / 32; ++q) s += red[q];
+    partial[(long long)i * nchunk + blockIdx.x] = s;
+  }
+}
+
+// out[i] = sum of the partials of i (fixed order); if accum is not null, accum[i] += out[i].
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nchunk, double* __restrict__ out,
+                                  double* __restrict__ accum) {
+  __shared__ double red[256];
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nchunk; k += blockDim.x) s += partial[(long long)i * nchunk + k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[i] = red[0];
+    if (accum) accum[i] += red[0];
+  }
+}
+
+// w[k] = alpha * (w[k] or 0) + sum_i coef[i] * V_i[k]   (coef from device memory).
+__global__ void k_combine(double* __restrict__ w, double alpha, const double* __restrict__ V, long long ldv, int nv,
+                          const double* __restrict__ coef, double sign, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    double acc = (alpha == 0.0) ? 0.0 : alpha * w[k];
+    for (int i = 0; i < nv; ++i) acc = fma(sign * coef[i], V[ldv * i + k], acc);
+    w[k] = acc;
+  }
+}
+
+// out = in * (*sc) (or in / *sc when divide).
+__global__ void k_scale(double* __restrict__ out, const double* __restrict__ in, const double* __restrict__ sc, int divide,
+                        long long n) {
+  const double f = divide ? 1.0 / *sc : *sc;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    out[k] = in[k] * f;
+}
+
+__global__ void k_axpby(double* __restrict__ y, double a, const double* __restrict__ x, double b, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    y[k] = a * x[k] + b * y[k];
+}
+
+// z = x + y
+__global__ void k_add(double* __restrict__ z, const double* __restrict__ x, const double* __restrict__ y, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    z[k] = x[k] + y[k];
+}
+
+// One Givens step of GMRES on column k of the Hessenberg matrix (stored column-major, leading
+// dimension ld).  On entry col[k + 1] holds ||w||^2; the new basis norm goes to *hnorm.  Writes the
+// least-squares residual |g[k + 1]| to *res.
+__global__ void k_givens(double* H, int ld, int k, double* cs, double* sn, double* g, double* hnorm, double* res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* col = H + (long long)k * ld;
+  const double hn = sqrt(col[k + 1]);
+  *hnorm = hn;
+  col[k + 1] = hn;
+  for (int i = 0; i < k; ++i) {
+    const double a = col[i], b = col[i + 1];
+    col[i] = cs[i] * a + sn[i] * b;
+    col[i + 1] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = col[k], b = col[k + 1];
+  const double den = hypot(a, b);
+  const double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
+  cs[k] = c;
+  sn[k] = s;
+  col[k] = den;
+  col[k + 1] = 0.0;
+  g[k + 1] = -s * g[k];
+  g[k] = c * g[k];
+  *res = fabs(g[k + 1]);
+}
+
+// y = R^{-1} g for the k x k upper-triangular R left in H by the rotations.
+__global__ void k_trisolve(const double* H, int ld, int k, const double* g, double* y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int j = i + 1; j < k; ++j) s -= H[(long long)j * ld + i] * y[j];
+    y[i] = s / H[(long long)i * ld + i];
+  }
+}
+
+__global__ void k_init_g(double* g, int len, const double* beta2) {
+  for (int i = threadIdx.x; i < len; i += blockDim.x) g[i] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) g[0] = sqrt(*beta2);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// Vector helpers on the context stream.
+
+static int vec_blocks(const Context& c, long long n) {
+  return (int)std::min<long long>(std::max(1, 8 * c.sm_count), std::max<long long>(1, (n + 255) / 256));
+}
+
+static int chunks_for(long long n) { return (int)std::min<long long>(1024, std::max<long long>(1, n / 4096)); }
+
+// out[0..nv) = V_i . w (and accum[i] += out[i] if accum).
+static Status multidot(Context& c, const double* V, long long ldv, int nv, const double* w, long long n, double* out,
+                       double* accum) {
+  int nchunk = chunks_for(n);
+  dim3 g(nchunk, nv);
+  k_multidot<<<g, kDotThreads, 0, c.stream>>>(V, ldv, nv, w, n, nchunk, c.d_partials.ptr);
+  k_reduce_partials<<<nv, 256, 0, c.stream>>>(c.d_partials.ptr, nchunk, out, accum);
+  RBS_CUDA_TRY(cudaGetLastError());
+  return Status::Ok();
+}
+
+static Status norm2_dev(Context& c, const double* w, long long n, double* out_sq) {
+  return multidot(c, w, 0, 1, w, n, out_sq, nullptr);
+}
+
+static Status read_scalar(Context& c, const double* dev, double* host) {
+  RBS_CUDA_TRY(cudaMemcpyAsync(c.h_pinned, dev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  RBS_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  *host = *c.h_pinned;
+  return Status::Ok();
+}
+
+// The operator inside GMRES: with the preconditioner, w = (1/2 I + K + L) P v = v + K_off P v
+// (P the exact inverse of the particle-diagonal part), z = P v; without, w = A v.
+static Status gmres_operator(Context& c, int prec, const double* v, double* w, double* z) {
+  if (c.opt.preconditioner) {
+    RBS_TRY(apply_blocks(c, kModePrecond, prec, v, z, w, 1.0));
+    return apply_pairs(c, 0, prec, z, w);
+  }
+  return apply_operator(c, RBS_OP_A, prec, v, w);
+}
+
+// Restarted, right-preconditioned GMRES for A x = b (A in arithmetic `prec`).  x is the initial guess
+// (x_zero: treat it as zero without reading it).  Stops when the residual estimate is <= tol_abs.
+static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zero, double tol_abs, int max_iters,
+                    int* iters, double* res_out, bool* converged) {
+  const long long n3 = 3 * c.N;
+  const int m = c.opt.restart;
+  const int ld = m + 1;
+  double* H = c.d_H.ptr;
+  double* cs = H + (size_t)ld * (m + 1);
+  double* sn = cs + (m + 2);
+  double* g = sn + (m + 2);
+  double* y = g + (m + 2);
+  double* scal = c.d_partials.ptr + (size_t)(m + 1) * 1024;  // 16 scratch scalars after the partials
+  double* hvec = scal + 4;
+  double* V = c.d_V.ptr;
+  double* w = c.d_vec[4].ptr;
+  double* z = c.d_vec[5].ptr;
+  double* r = c.d_vec[6].ptr;
+  const int nbk = vec_blocks(c, n3);
+  *iters = 0;
+  *converged = false;
+  if (x_zero) RBS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n3, c.stream));
+  bool first = true;
+  double res = 0.0;
+  while (true) {
+    // r = b - A x (x = 0 on the first cycle of a zero start)
+    if (first && x_zero) {
+      RBS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+    } else {
+      RBS_TRY(apply_operator(c, RBS_OP_A, prec, x, r));
+      k_axpby<<<nbk, 256, 0, c.stream>>>(r, 1.0, b, -1.0, n3);
+    }
+    first = false;
+    RBS_TRY(norm2_dev(c, r, n3, scal));
+    double beta2;
+    RBS_TRY(read_scalar(c, scal, &beta2));
+    res = std::sqrt(beta2);
+    if (res <= tol_abs) {
+      *converged = true;
+      break;
+    }
+    if (*iters >= max_iters) break;
+    RBS_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(double) * (size_t)ld * (m + 1), c.stream));
+    k_init_g<<<1, 64, 0, c.stream>>>(g, m + 2, scal);
+    k_scale<<<nbk, 256, 0, c.stream>>>(V, r, g, 1, n3);  // V_0 = r / beta
+    int kdone = 0;
+    for (int k = 0; k < m && *iters < max_iters; ++k) {
+      double* vk = V + (size_t)k * n3;
+      RBS_TRY(gmres_operator(c, prec, vk, w, z));
+      double* hcol = H + (size_t)k * ld;
+      for (int pass = 0; pass < 2; ++pass) {
+        RBS_TRY(multidot(c, V, n3, k + 1, w, n3, hvec, hcol));
+        k_combine<<<nbk, 256, 0, c.stream>>>(w, 1.0, V, n3, k + 1, hvec, -1.0, n3);
+      }
+      RBS_TRY(norm2_dev(c, w, n3, hcol + k + 1));
+      k_givens<<<1, 1, 0, c.stream>>>(H, ld, k, cs, sn, g, scal + 1, scal + 2);
+      k_scale<<<nbk, 256, 0, c.stream>>>(V + (size_t)(k + 1) * n3, w, scal + 1, 1, n3);
+      RBS_CUDA_TRY(cudaGetLastError());
+      RBS_TRY(read_scalar(c, scal + 2, &res));
+      ++*iters;
+      kdone = k + 1;
+      if (!(res > tol_abs)) break;  // also stops on NaN
+    }
+    // x += P (V y)
+    k_trisolve<<<1, 1, 0, c.stream>>>(H, ld, kdone, g, y);
+    if (c.opt.preconditioner) {
+      k_combine<<<nbk, 256, 0, c.stream>>>(w, 0.0, V, n3, kdone, y, 1.0, n3);
+      RBS_TRY(apply_blocks(c, kModePrecond, prec, w, z, r, 1.0));
+      k_axpby<<<nbk, 256, 0, c.stream>>>(x, 1.0, z, 1.0, n3);
+    } else {
+      k_combine<<<nbk, 256, 0, c.stream>>>(x, 1.0, V, n3, kdone, y, 1.0, n3);
+    }
+    RBS_CUDA_TRY(cudaGetLastError());
+    if (std::isnan(res)) return Status::Err(RBS_ENOTCONV, "GMRES produced NaN");
+    if (res <= tol_abs) {
+      *converged = true;
+      break;
+    }
+  }
+  *res_out = res;
+  return Status::Ok();
+}
+
+Status incident_density(Context& c, const double* FT_dev, double* rho) {
+  k_incident<<<vec_blocks(c, c.N), 256, 0, c.stream>>>(c.N, c.d_pid.ptr, c.d_x.ptr, c.d_centre.ptr, c.d_area.ptr,
+                                                       c.d_tauinv.ptr, FT_dev, rho);
+  RBS_CUDA_TRY(cudaGetLastError());
+  return Status::Ok();
+}
+
+Status rigid_velocities(Context& c, const double* u, double* vo_dev) {
+  k_rigid<<<c.n, 256, 0, c.stream>>>(c.d_offset.ptr, c.d_x.ptr, c.d_centre.ptr, c.d_area.ptr, c.d_tauinv.ptr, u,
+                                     1.0 / c.opt.viscosity, vo_dev);
+  RBS_CUDA_TRY(cudaGetLastError());
+  return Status::Ok();
+}
+
+// F, T: n x 3 each (host or device); FT interleaved on the device as n x 6.
+__global__ void k_pack_ft(int n, const double* F, const double* T, double* FT) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int q = 0; q < 3; ++q) {
+    FT[6 * i + q] = F[3 * i + q];
+    FT[6 * i + 3 + q] = T[3 * i + q];
+  }
+}
+__global__ void k_unpack_vo(int n, const double* vo, double* v, double* om) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int q = 0; q < 3; ++q) {
+    v[3 * i + q] = vo[6 * i + q];
+    om[3 * i + q] = vo[6 * i + 3 + q];
+  }
+}
+
+Status mobility_solve(Context& c, const double* F, const double* T, double tol, double* v, double* om, double* density,
+                      int* iters_out, bool device_io) {
+  auto t0 = std::chrono::steady_clock::now();
+  const long long n3 = 3 * c.N;
+  const int n = c.n;
+  const int nbk = vec_blocks(c, n3);
+  double* rho = c.d_vec[0].ptr;
+  double* b = c.d_vec[1].ptr;
+  double* x = c.d_vec[2].ptr;
+  double* r = c.d_vec[3].ptr;
+  double* d = c.d_vec[7].ptr;
+  // forces and torques to the device (n x 6)
+  if (device_io) {
+    k_pack_ft<<<cdiv(n, 128), 128, 0, c.stream>>>(n, F, T, c.d_FT.ptr);
+  } else {
+    // staged through the velocity buffer: F then T, then packed
+    RBS_CUDA_TRY(cudaMemcpyAsync(c.d_vo.ptr, F, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c.stream));
+    RBS_CUDA_TRY(cudaMemcpyAsync(c.d_vo.ptr + 3 * n, T, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c.stream));
+    k_pack_ft<<<cdiv(n, 128), 128, 0, c.stream>>>(n, c.d_vo.ptr, c.d_vo.ptr + 3 * n, c.d_FT.ptr);
+  }
+  RBS_CUDA_TRY(cudaGetLastError());
+  // 1. incident density; right-hand side b = -(1/2 I + K) rho in float64
+  RBS_TRY(incident_density(c, c.d_FT.ptr, rho));
+  RBS_TRY(apply_operator(c, RBS_OP_HALF_K, RBS_PREC_FP64, rho, b));
+  k_axpby<<<nbk, 256, 0, c.stream>>>(b, 0.0, b, -1.0, n3);
+  RBS_TRY(norm2_dev(c, b, n3, c.d_partials.ptr + (size_t)(c.opt.restart + 1) * 1024 + 8));
+  double bn2;
+  RBS_TRY(read_scalar(c, c.d_partials.ptr + (size_t)(c.opt.restart + 1) * 1024 + 8, &bn2));
+  const double bnorm = std::sqrt(bn2);
+  int total_iters = 0, refinements = 0;
+  double rel = 0.0;
+  bool converged = true;
+  // 2. the scattered density
+  if (bnorm == 0.0) {
+    RBS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n3, c.stream));
+  } else if (c.opt.precision == RBS_PREC_FP64) {
+    int its = 0;
+    double res = 0.0;
+    RBS_TRY(gmres(c, RBS_PREC_FP64, b, x, true, tol * bnorm, c.opt.max_iters, &its, &res, &converged));
+    total_iters = its;
+    rel = res / bnorm;
+  } else {
+    RBS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n3, c.stream));
+    RBS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+    double rn = bnorm;
+    converged = false;
+    while (refinements < c.opt.max_refinements && total_iters < c.opt.max_iters) {
+      int its = 0;
+      double res = 0.0;
+      bool conv_inner = false;
+      // inner solve of A d = r with the float32 operator
+      RBS_TRY(gmres(c, RBS_PREC_MIXED, r, d, true, c.opt.inner_tol * rn, c.opt.max_iters - total_iters, &its, &res,
+                    &conv_inner));
+      total_iters += its;
+      k_axpby<<<nbk, 256, 0, c.stream>>>(x, 1.0, d, 1.0, n3);
+      // float64 residual r = b - A x
+      RBS_TRY(apply_operator(c, RBS_OP_A, RBS_PREC_FP64, x, r));
+      k_axpby<<<nbk, 256, 0, c.stream>>>(r, 1.0, b, -1.0, n3);
+      double* sc = c.d_partials.ptr + (size_t)(c.opt.restart + 1) * 1024 + 8;
+      RBS_TRY(norm2_dev(c, r, n3, sc));
+      double rn2;
+      RBS_TRY(read_scalar(c, sc, &rn2));
+      rn = std::sqrt(rn2);
+      ++refinements;
+      if (rn <= tol * bnorm) {
+        converged = true;
+        break;
+      }
+      if (its == 0) break;
+    }
+    rel = rn / bnorm;
+  }
+  // 3. u = S[rho + mu] and the rigid velocities
+  double* sigma = c.d_vec[6].ptr;
+  double* u = c.d_vec[4].ptr;
+  k_add<<<nbk, 256, 0, c.stream>>>(sigma, rho, x, n3);
+  RBS_TRY(apply_operator(c, RBS_OP_S, RBS_PREC_FP64, sigma, u));
+  RBS_TRY(rigid_velocities(c, u, c.d_vo.ptr));
+  if (device_io) {
+    k_unpack_vo<<<cdiv(n, 128), 128, 0, c.stream>>>(n, c.d_vo.ptr, v, om);
+    if (density) RBS_CUDA_TRY(cudaMemcpyAsync(density, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+    RBS_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  } else {
+    double* tmp = c.d_FT.ptr;  // reuse: n x 6 -> v (n x 3) then omega (n x 3)
+    k_unpack_vo<<<cdiv(n, 128), 128, 0, c.stream>>>(n, c.d_vo.ptr, tmp, tmp + 3 * n);
+    RBS_CUDA_TRY(cudaMemcpyAsync(v, tmp, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.stream));
+    RBS_CUDA_TRY(cudaMemcpyAsync(om, tmp + 3 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.stream));
+    if (density) RBS_CUDA_TRY(cudaMemcpyAsync(density, x, sizeof(double) * n3, cudaMemcpyDeviceToHost, c.stream));
+    RBS_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  }
+  RBS_CUDA_TRY(cudaGetLastError());
+  if (iters_out) *iters_out = total_iters;
+  c.stats.iterations = total_iters;
+  c.stats.refinements = refinements;
+  c.stats.residual = rel;
+  c.stats.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (!converged)
+    return Status::Err(RBS_ENOTCONV, "GMRES stopped at relative residual " + std::to_string(rel) + " after " +
+                                         std::to_string(total_iters) + " iterations");
+  return Status::Ok();
+}
+
+}  // namespace rbs

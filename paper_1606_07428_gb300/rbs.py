@@ -1,0 +1,286 @@
+"""Thin Python binding of the C ABI in include/rbs.h (argument marshalling only).
+
+Every function named rbs_* calls the C function of the same name in librbs.so; all arithmetic of the
+method runs in the library's CUDA kernels.  Host arrays are numpy float64 / int32; the *_device
+variants take torch CUDA tensors (or raw device addresses).  Loading fails loudly when the library
+has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librbs.so")
+
+RBS_OK = 0
+RBS_EINVAL = -1
+RBS_EOVERLAP = -2
+RBS_ENOTCONV = -3
+RBS_ECUDA = -4
+RBS_ENOMEM = -5
+RBS_ETIMEOUT = -6
+RBS_ESTATE = -7
+
+RBS_PREC_FP64 = 0
+RBS_PREC_MIXED = 1
+
+RBS_OP_A = 0
+RBS_OP_HALF_K = 1
+RBS_OP_S = 2
+RBS_OP_K_OFF = 3
+RBS_OP_K_SELF = 4
+RBS_OP_S_OFF = 5
+RBS_OP_S_SELF = 6
+RBS_OP_L = 7
+
+# every symbol include/rbs.h declares
+EXPORTS = [
+    "rbs_default_options", "rbs_create", "rbs_destroy", "rbs_set_geometry", "rbs_total_nodes",
+    "rbs_get_surface", "rbs_mobility_solve", "rbs_mobility_solve_device", "rbs_incident_density",
+    "rbs_rigid_velocities", "rbs_apply_operator", "rbs_apply_operator_device", "rbs_get_stats",
+    "rbs_last_error",
+]
+
+
+class rbs_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("restart", ctypes.c_int),
+        ("max_iters", ctypes.c_int),
+        ("preconditioner", ctypes.c_int),
+        ("near_delta", ctypes.c_double),
+        ("p_up_factor", ctypes.c_int),
+        ("p_self_factor", ctypes.c_int),
+        ("viscosity", ctypes.c_double),
+        ("inner_tol", ctypes.c_double),
+        ("max_refinements", ctypes.c_int),
+        ("device", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class rbs_stats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int),
+        ("refinements", ctypes.c_int),
+        ("residual", ctypes.c_double),
+        ("setup_ms", ctypes.c_double),
+        ("solve_ms", ctypes.c_double),
+        ("total_nodes", ctypes.c_longlong),
+        ("n_particles", ctypes.c_int),
+        ("n_shapes", ctypes.c_int),
+        ("near_pairs", ctypes.c_longlong),
+        ("far_pairs", ctypes.c_longlong),
+    ]
+
+
+class RbsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rbs error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load librbs.so (built by paper_1606_07428_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (python -m paper_1606_07428_gb300.build)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    sig = {
+        "rbs_default_options": (None, [ctypes.POINTER(rbs_options)]),
+        "rbs_create": (I, [ctypes.POINTER(rbs_options), ctypes.POINTER(P)]),
+        "rbs_destroy": (None, [P]),
+        "rbs_set_geometry": (I, [P, I, P, P, P, P, P, P]),
+        "rbs_total_nodes": (ctypes.c_longlong, [P]),
+        "rbs_get_surface": (I, [P, P, P, P]),
+        "rbs_mobility_solve": (I, [P, P, P, D, P, P, P, P]),
+        "rbs_mobility_solve_device": (I, [P, P, P, D, P, P, P, P]),
+        "rbs_incident_density": (I, [P, P, P, P]),
+        "rbs_rigid_velocities": (I, [P, P, P, P]),
+        "rbs_apply_operator": (I, [P, I, I, P, P]),
+        "rbs_apply_operator_device": (I, [P, I, I, P, P]),
+        "rbs_get_stats": (I, [P, ctypes.POINTER(rbs_stats)]),
+        "rbs_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return int(a)
+
+
+def _f64(a, shape=None) -> np.ndarray:
+    out = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        out = out.reshape(shape)
+    return out
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def rbs_default_options() -> rbs_options:
+    o = rbs_options()
+    load().rbs_default_options(ctypes.byref(o))
+    return o
+
+
+def _check(ctx, rc: int, allow=()):
+    if rc != RBS_OK and rc not in allow:
+        msg = load().rbs_last_error(ctx).decode() if ctx else ""
+        raise RbsError(rc, msg)
+    return rc
+
+
+def rbs_create(options: rbs_options | None = None, **kw) -> int:
+    o = options or rbs_default_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    h = ctypes.c_void_p()
+    rc = load().rbs_create(ctypes.byref(o), ctypes.byref(h))
+    if rc != RBS_OK:
+        raise RbsError(rc, "rbs_create failed")
+    return h.value
+
+
+def rbs_destroy(ctx) -> None:
+    load().rbs_destroy(ctx)
+
+
+def rbs_set_geometry(ctx, semi_axes, p, nphi, centres, quats, suspension_id=None) -> None:
+    semi_axes = _f64(semi_axes, (-1, 3))
+    n = semi_axes.shape[0]
+    p = _i32(np.broadcast_to(p, (n,)))
+    nphi = None if nphi is None else _i32(np.broadcast_to(nphi, (n,)))
+    centres = _f64(centres, (n, 3))
+    quats = _f64(quats, (n, 4))
+    sid = None if suspension_id is None else _i32(suspension_id)
+    _check(ctx, load().rbs_set_geometry(ctx, n, _ptr(semi_axes), _ptr(p), _ptr(nphi), _ptr(centres), _ptr(quats),
+                                        _ptr(sid)))
+
+
+def rbs_total_nodes(ctx) -> int:
+    return int(load().rbs_total_nodes(ctx))
+
+
+def rbs_get_surface(ctx):
+    N = rbs_total_nodes(ctx)
+    x = np.zeros((N, 3))
+    nrm = np.zeros((N, 3))
+    w = np.zeros(N)
+    _check(ctx, load().rbs_get_surface(ctx, _ptr(x), _ptr(nrm), _ptr(w)))
+    return x, nrm, w
+
+
+def rbs_mobility_solve(ctx, F, T, tol, want_density=False, allow_notconv=False):
+    F = _f64(F, (-1, 3))
+    T = _f64(T, F.shape)
+    v = np.zeros_like(F)
+    om = np.zeros_like(F)
+    dens = np.zeros((rbs_total_nodes(ctx), 3)) if want_density else None
+    its = ctypes.c_int(0)
+    rc = load().rbs_mobility_solve(ctx, _ptr(F), _ptr(T), float(tol), _ptr(v), _ptr(om), _ptr(dens),
+                                   ctypes.addressof(its))
+    _check(ctx, rc, (RBS_ENOTCONV,) if allow_notconv else ())
+    return v, om, dens, its.value
+
+
+def rbs_mobility_solve_device(ctx, F_dev, T_dev, tol, v_dev, omega_dev, density_dev=None, allow_notconv=False) -> int:
+    its = ctypes.c_int(0)
+    rc = load().rbs_mobility_solve_device(ctx, _ptr(F_dev), _ptr(T_dev), float(tol), _ptr(v_dev), _ptr(omega_dev),
+                                          _ptr(density_dev), ctypes.addressof(its))
+    _check(ctx, rc, (RBS_ENOTCONV,) if allow_notconv else ())
+    return its.value
+
+
+def rbs_incident_density(ctx, F, T) -> np.ndarray:
+    F = _f64(F, (-1, 3))
+    T = _f64(T, F.shape)
+    rho = np.zeros((rbs_total_nodes(ctx), 3))
+    _check(ctx, load().rbs_incident_density(ctx, _ptr(F), _ptr(T), _ptr(rho)))
+    return rho
+
+
+def rbs_rigid_velocities(ctx, u, n):
+    u = _f64(u, (-1, 3))
+    v = np.zeros((n, 3))
+    om = np.zeros((n, 3))
+    _check(ctx, load().rbs_rigid_velocities(ctx, _ptr(u), _ptr(v), _ptr(om)))
+    return v, om
+
+
+def rbs_apply_operator(ctx, op: int, precision: int, x) -> np.ndarray:
+    x = _f64(x, (-1, 3))
+    y = np.zeros_like(x)
+    _check(ctx, load().rbs_apply_operator(ctx, op, precision, _ptr(x), _ptr(y)))
+    return y
+
+
+def rbs_apply_operator_device(ctx, op: int, precision: int, x_dev, y_dev) -> None:
+    _check(ctx, load().rbs_apply_operator_device(ctx, op, precision, _ptr(x_dev), _ptr(y_dev)))
+
+
+def rbs_get_stats(ctx) -> dict:
+    s = rbs_stats()
+    _check(ctx, load().rbs_get_stats(ctx, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+def rbs_last_error(ctx) -> str:
+    return load().rbs_last_error(ctx).decode()
+
+
+class Context:
+    """Owning wrapper: a context with a geometry, closed on exit."""
+
+    def __init__(self, **options):
+        self.ctx = rbs_create(**options)
+        self.n = 0
+
+    def set_geometry(self, semi_axes, p, nphi, centres, quats, suspension_id=None):
+        rbs_set_geometry(self.ctx, semi_axes, p, nphi, centres, quats, suspension_id)
+        self.n = int(np.asarray(semi_axes).reshape(-1, 3).shape[0])
+        return self
+
+    def set_suspension(self, s):
+        return self.set_geometry(s.semi_axes, s.p, s.nphi, s.centres, s.quats, s.suspension_id)
+
+    def close(self):
+        if self.ctx:
+            rbs_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
