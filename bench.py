@@ -1,0 +1,422 @@
+"""Benchmark of the rigid-particle mobility solve on GB300.
+
+One step = one complete mobility solve (forces and torques in, velocities out) of the chosen
+arithmetic (float32 inner GMRES with float64 refinement, right-hand side and velocity) on a fixed
+suspension, for a fresh seeded (F, T) draw resident in device memory.  The default workload is
+1,000 triaxial ellipsoids at p = 12 (312,000 nodes, 936,000 unknowns), GMRES to 1e-10.
+
+The JSON line carries: device-timed solves/s (value), the same through the host-buffer C ABI call
+(e2e), the plain float64 solve rate on the same suspension, the error of the chosen path against
+the float64 path, Stokeslet and traction pair rates, the dominant kernel's roofline (device time from
+the library's CUDA events on its stream), SM clocks sampled during the timed region, and the
+float64 CPU oracle timed on a bounded sample (cpu_baseline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c2]
+Under torchrun each rank solves its own draws on its own GPU (independent replicas, weak scaling);
+rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import suspensions  # noqa: E402
+
+METRIC = "mobility solves/s at 1e-8 rel. error (chosen vs plain FP64); Stokeslet Gpair/s"
+SMS = 152
+L2_BYTES = 129 * 2 ** 20
+FP64_DFMA_PER_CLK_SM = 2     # float64 FMA lanes per SM per clock (measured 1.19 TFLOP/s at 2.07 GHz)
+FP32_LANES_PER_SM = 128
+# minimal float32-pipe instructions per pair: traction 20, Stokeslet 18; float64 ops
+# per pair (with the float64 reciprocal square root counted as 7): traction 27, Stokeslet 25
+FLOPS_PER_PAIR = {"traction": 30.0, "stokeslet": 28.0}
+FP64_OPS_PER_PAIR = {"traction": 27.0, "stokeslet": 25.0}
+# float32-pipe operations per pair of the double-float kernels, counted from the source of
+# pair_tile_df (separation 24, r^2 28, reciprocal square root 8, r . density 34, powers 8, traction
+# tail 82 / Stokeslet tail 76)
+DF_INSTR_PER_PAIR = {"traction": 184.0, "stokeslet": 178.0}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(suspensions.WORKLOADS))
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain float64 solves (0 skips)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        rows = [r for r in csv.reader(open(self.file.name)) if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(susp, budget_s: float, iterations: int):
+    """Time the float64 oracle on a bounded sample of the workload: rows of the system operator
+    (1/2 I + K + L) at seeded target nodes, each computed in full (every source particle, the near
+    upsampling and a singular-rule row).  Extrapolates to one solve = (iterations + 2) operator
+    applications plus one single-layer application of the same cost.  Returns (solves/s, sample)."""
+    import oracle
+    try:
+        import threadpoolctl
+        threads = max([d.get("num_threads", 1) for d in threadpoolctl.threadpool_info()] or [1])
+    except Exception:
+        threads = 1
+    t0 = time.perf_counter()
+    ref = oracle.System(susp.semi_axes, susp.p, susp.nphi, susp.centres, susp.quats, susp.suspension_id)
+    t_setup = time.perf_counter() - t0
+    mu = suspensions.random_density(9, susp.total_nodes)
+    rng = np.random.default_rng(9)
+    rows = 0
+    t1 = time.perf_counter()
+    while True:
+        node = int(rng.integers(susp.total_nodes))
+        ref.apply_rows("K", mu, [node], half=0.5, with_L=True)
+        rows += 1
+        el = time.perf_counter() - t1
+        if el > budget_s or rows >= 4096:
+            break
+    per_row = el / rows
+    matvec_s = per_row * susp.total_nodes
+    solve_s = matvec_s * (iterations + 3)
+    sample = (f"{rows} rows of the float64 operator at random nodes of the {susp.name} workload "
+              f"({el:.1f} s, {per_row * 1e3:.1f} ms per row; oracle set-up {t_setup:.1f} s excluded); "
+              f"one solve extrapolated as {iterations} GMRES + 3 operator applications")
+    return 1.0 / solve_s, sample, threads, el
+
+
+# ---------------------------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    susp = suspensions.WORKLOADS[args.workload]()
+    iters = 12
+    vals = []
+    sample = ""
+    threads = 1
+    per_step = max(2.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    for k in range(args.warmup + args.steps):
+        v, sample, threads, el = oracle_sample(susp, per_step, iters)
+        if k >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": susp.name, "n_particles": susp.n, "unknowns": 3 * susp.total_nodes,
+                       "tol": args.tol},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------- our arm
+
+def kernel_table(stats):
+    from paper_1606_07428_gb300 import rbs
+    out = {}
+    for k, name in enumerate(rbs.KERNEL_CLASSES):
+        if stats["kernel_count"][k]:
+            out[name] = {"ms": stats["kernel_ms"][k], "launches": stats["kernel_count"][k],
+                         "units": stats["kernel_units"][k]}
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1606_07428_gb300 import rbs
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    susp = suspensions.WORKLOADS[args.workload]()
+    n = susp.n
+    stream = torch.cuda.current_stream()
+    ctx = rbs.Context(device=local, precision=rbs.RBS_PREC_MIXED, timing=1, stream=stream.cuda_stream)
+    ctx.set_suspension(susp)
+    setup_ms = rbs.rbs_get_stats(ctx.ctx)["setup_ms"]
+
+    draws = [suspensions.forces(100 + rank, n, k) for k in range(args.warmup + args.steps)]
+    F_dev = torch.tensor(np.stack([d[0] for d in draws]), device="cuda")
+    T_dev = torch.tensor(np.stack([d[1] for d in draws]), device="cuda")
+    v_dev = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    om_dev = torch.zeros_like(v_dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    for k in range(args.warmup):
+        rbs.rbs_mobility_solve_device(ctx.ctx, F_dev[k], T_dev[k], args.tol, v_dev, om_dev)
+    barrier()
+    rbs.rbs_reset_stats(ctx.ctx)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    iters = []
+    barrier()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))                      # L2 flush between timed solves
+            starts[k].record(stream)
+            its = rbs.rbs_mobility_solve_device(ctx.ctx, F_dev[args.warmup + k], T_dev[args.warmup + k], args.tol,
+                                                v_dev, om_dev)
+            ends[k].record(stream)
+            iters.append(its)
+        torch.cuda.synchronize()
+    times = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(times)
+    stats = rbs.rbs_get_stats(ctx.ctx)
+    refinements = stats["refinements"]
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = args.steps * world / (total_ms / 1e3)
+    kernels = kernel_table(stats)
+    launches = stats["launches"]
+    clocks = clk.summary()
+
+    # accuracy of the chosen path against the plain float64 path, and the float64 solve rate
+    F0 = draws[args.warmup][0]
+    T0 = draws[args.warmup][1]
+    v_mix, om_mix, _, _ = rbs.rbs_mobility_solve(ctx.ctx, F0, T0, args.tol)
+    ctx64 = rbs.Context(device=local, precision=rbs.RBS_PREC_FP64, timing=1, stream=stream.cuda_stream)
+    ctx64.set_suspension(susp)
+    plain = None
+    err = None
+    if args.fp64_steps > 0:
+        barrier()
+        rbs.rbs_reset_stats(ctx64.ctx)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its64 = 0
+        for k in range(args.fp64_steps):
+            Fk = F_dev[args.warmup + k]
+            Tk = T_dev[args.warmup + k]
+            its64 = rbs.rbs_mobility_solve_device(ctx64.ctx, Fk, Tk, args.tol, v_dev, om_dev)
+            if k == 0:
+                v64 = v_dev.cpu().numpy().copy()
+                om64 = om_dev.cpu().numpy().copy()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        st64 = rbs.rbs_get_stats(ctx64.ctx)
+        V = np.concatenate([v_mix, om_mix], 1)
+        V64 = np.concatenate([v64, om64], 1)
+        err = float(np.linalg.norm(V - V64) / np.linalg.norm(V64))
+        k64 = kernel_table(st64)
+        plain = {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "steps": args.fp64_steps, "warmup": 0,
+                 "gmres_iterations": its64, "kernels": k64}
+
+    # end to end through the host-buffer entry point (pinned host arrays, copies inside the timing)
+    e2e = None
+    if args.e2e_steps > 0:
+        Fh = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+        Th = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+        vh = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+        omh = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+        lib = rbs.load()
+        import ctypes
+        its_c = ctypes.c_int(0)
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            Fh[:] = draws[(args.warmup + k) % len(draws)][0]
+            Th[:] = draws[(args.warmup + k) % len(draws)][1]
+            rc = lib.rbs_mobility_solve(ctx.ctx, Fh.ctypes.data, Th.ctypes.data, args.tol, vh.ctypes.data,
+                                        omh.ctypes.data, None, ctypes.addressof(its_c))
+            if rc != 0:
+                raise RuntimeError(rbs.rbs_last_error(ctx.ctx))
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": args.e2e_steps * world / el, "unit": "solves/s", "h2d_bytes_per_step": 2 * 3 * 8 * n,
+               "d2h_bytes_per_step": 2 * 3 * 8 * n}
+
+    # Stokeslet pair rates in each arithmetic (one application of the off-diagonal single layer)
+    x_dev = torch.tensor(suspensions.random_density(3, susp.total_nodes), device="cuda")
+    y_dev = torch.zeros_like(x_dev)
+    rbs.rbs_reset_stats(ctx.ctx)
+    for prec in (rbs.RBS_PREC_MIXED, rbs.RBS_PREC_MIXED, rbs.RBS_PREC_DF):
+        rbs.rbs_apply_operator_device(ctx.ctx, rbs.RBS_OP_S_OFF, prec, x_dev, y_dev)
+    srates = kernel_table(rbs.rbs_get_stats(ctx.ctx))
+
+    # pair rates and the roofline of the dominant kernel of the chosen path
+    f_mhz = clocks.get("sm_mhz") or 2070.0
+    fp32_peak_tflops = SMS * FP32_LANES_PER_SM * 2 * f_mhz * 1e6 / 1e12
+    fp64_peak_tflops = SMS * FP64_DFMA_PER_CLK_SM * 2 * f_mhz * 1e6 / 1e12
+
+    def rate(tab, name):
+        e = tab.get(name)
+        return None if not e or e["ms"] <= 0 else e["units"] / (e["ms"] / 1e3) / 1e9
+
+    gpairs = {"stokeslet_f32": rate(srates, "pair_stokeslet_f32"),
+              "stokeslet_df": rate(srates, "pair_stokeslet_df"),
+              "traction_f32": rate(kernels, "pair_traction_f32"),
+              "traction_df": rate(kernels, "pair_traction_df"),
+              "traction_f64": rate(kernels, "pair_traction_f64")}
+    if plain:
+        gpairs["stokeslet_f64_plain"] = rate(plain["kernels"], "pair_stokeslet_f64")
+        gpairs["traction_f64_plain"] = rate(plain["kernels"], "pair_traction_f64")
+    dom = max(kernels.items(), key=lambda kv: kv[1]["ms"])
+    name, e = dom
+    per_launch_ms = e["ms"] / e["launches"]
+    units_per_launch = e["units"] / e["launches"]
+    if name.startswith("pair_"):
+        kind = "traction" if "traction" in name else "stokeslet"
+        if name.endswith("_df"):
+            # double-float: reported as the float64-equivalent pair rate against the float32 issue rate
+            # at the kernel's own instruction count per pair (DF_INSTR_PER_PAIR)
+            achieved = units_per_launch / (per_launch_ms / 1e3) / 1e9
+            peak = SMS * FP32_LANES_PER_SM * f_mhz * 1e6 / DF_INSTR_PER_PAIR[kind] / 1e9
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": name,
+                    "peak_basis": f"float32 issue: {SMS} SMs x 128 lanes x {f_mhz:.0f} MHz / "
+                                  f"{DF_INSTR_PER_PAIR[kind]} double-float instructions per pair"}
+        elif name.endswith("f32"):
+            achieved = units_per_launch * FLOPS_PER_PAIR[kind] / (per_launch_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak_tflops, "traffic": None, "kernel": name,
+                    "peak_basis": f"float32 FMA: {SMS} SMs x 128 lanes x 2 flop x {f_mhz:.0f} MHz (median under load)"}
+        else:
+            achieved = units_per_launch * FP64_OPS_PER_PAIR[kind] * 2 / (per_launch_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_peak_tflops, "traffic": None, "kernel": name,
+                    "peak_basis": f"float64 FMA: {SMS} SMs x 2 lanes x 2 flop x {f_mhz:.0f} MHz"}
+    else:
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        achieved = units_per_launch / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": name,
+                "peak_basis": "measured copy bandwidth" if peaks else "fallback 6.8 TB/s"}
+    roof["ms_per_launch"] = per_launch_ms
+    roof["share_of_step"] = e["ms"] / total_ms if world == 1 else None
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        cpu_val, sample, threads, _ = oracle_sample(susp, args.cpu_seconds, int(np.mean(iters)) if iters else 12)
+        cpu = {"value": cpu_val, "unit": "solves/s", "cores": threads, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": susp.name, "n_particles": n, "p": int(susp.p[0]), "nodes": susp.total_nodes,
+                       "unknowns": 3 * susp.total_nodes, "tol": args.tol, "precision": "mixed",
+                       "preconditioner": "block-diagonal", "gmres_iterations": iters,
+                       "refinements_last": refinements, "setup_ms": setup_ms,
+                       "l2": "flushed before every timed solve (258 MB write); working set > L2",
+                       "parallelism": f"replicas x{world}"},
+            "error_vs_fp64": err,
+            "plain_fp64": plain,
+            "speedup_vs_plain_fp64": (value / world) / plain["solves_per_s"] if plain else None,
+            "gpair_per_s": gpairs,
+            "kernels": kernels,
+            "roofline": roof,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    ctx64.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

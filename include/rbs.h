@@ -44,8 +44,12 @@ extern "C" {
 
 /* Arithmetic of a solve. */
 #define RBS_PREC_FP64 0  /* every step in float64 */
-#define RBS_PREC_MIXED 1 /* float32 inner GMRES, float64 right-hand side, residuals, refinement
-                            updates, projection and velocity extraction */
+#define RBS_PREC_MIXED 1 /* float32 inner GMRES; right-hand side, refinement residuals and velocity
+                            in the arithmetic of rbs_options.refine_precision; float64 vectors,
+                            Arnoldi, refinement updates, projection and velocity extraction */
+#define RBS_PREC_DF 2    /* float64-class operator: pair sums in double-float arithmetic (unevaluated
+                            sums of two float32 numbers, ~1e-12 relative), blocks and vectors in
+                            float64 (rbs_apply_operator and rbs_options.refine_precision only) */
 
 /* Operators for rbs_apply_operator (each acts on a surface field, Section 2). */
 #define RBS_OP_A 0        /* (1/2 I + K + L), the system operator of Eq. 25 */
@@ -74,7 +78,22 @@ typedef struct {
   int max_refinements; /* RBS_PREC_MIXED: cap on float64 refinement steps (default 20) */
   int device;          /* CUDA device ordinal (default 0) */
   void* stream;        /* cudaStream_t for all device work, NULL = legacy default stream */
+  int timing;          /* 1: time the kernel classes below with CUDA events on the context stream
+                          (default 0); results in rbs_stats.kernel_ms */
+  int refine_precision; /* RBS_PREC_MIXED: arithmetic of the right-hand side, refinement residuals
+                          and velocity evaluation, RBS_PREC_DF (default) or RBS_PREC_FP64 */
 } rbs_options;
+
+/* Kernel classes timed when rbs_options.timing is set (indices into rbs_stats.kernel_*). */
+#define RBS_KC_PAIR_K32 0 /* smooth traction pair sum, float32 */
+#define RBS_KC_PAIR_S32 1 /* smooth Stokeslet pair sum, float32 */
+#define RBS_KC_PAIR_K64 2 /* smooth traction pair sum, float64 */
+#define RBS_KC_PAIR_S64 3 /* smooth Stokeslet pair sum, float64 */
+#define RBS_KC_BLOCKS 4   /* particle-block kernel (self blocks, projection, preconditioner) */
+#define RBS_KC_NEAR 5     /* near correction (upsampling and upsampled pair sums) */
+#define RBS_KC_PAIR_KDF 6 /* smooth traction pair sum, double-float */
+#define RBS_KC_PAIR_SDF 7 /* smooth Stokeslet pair sum, double-float */
+#define RBS_KC_COUNT 8
 
 typedef struct {
   int iterations;        /* total GMRES iterations of the last solve (inner iterations for mixed) */
@@ -87,6 +106,11 @@ typedef struct {
   int n_shapes;          /* distinct (semi-axes, p, n_phi) body shapes */
   long long near_pairs;  /* ordered (target, source) particle pairs treated as near */
   long long far_pairs;   /* (target node, source node) pairs of the smooth pair sum per apply */
+  long long launches;    /* kernels launched by the context since creation or rbs_reset_stats */
+  double kernel_ms[RBS_KC_COUNT];        /* summed device time per class (rbs_options.timing) */
+  long long kernel_count[RBS_KC_COUNT];  /* launches per class */
+  double kernel_units[RBS_KC_COUNT];     /* work per class: node pairs (pair sums, near), bytes of
+                                            block entries read (particle blocks) */
 } rbs_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -109,7 +133,8 @@ void rbs_destroy(rbs_ctx* ctx);
  *  quats        n x 4, orientations as quaternions (w, x, y, z); normalised here
  *  suspension_id  n (NULL: all particles in one suspension); particles with different ids do not
  *               interact.  Particles of one suspension must be contiguous.
- * Returns RBS_EOVERLAP when two interacting particles' bounding spheres intersect.
+ * Returns RBS_EOVERLAP when two interacting particles certainly overlap (their inscribed spheres,
+ * of radius the smallest semi-axis, intersect).
  */
 int rbs_set_geometry(rbs_ctx* ctx, int n, const double* semi_axes, const int* p, const int* nphi,
                      const double* centres, const double* quats, const int* suspension_id);
@@ -149,15 +174,20 @@ int rbs_rigid_velocities(rbs_ctx* ctx, const double* u, double* v, double* omega
 /*
  * Apply one discrete operator (RBS_OP_*) to a surface field: y = op(x), x and y total_nodes x 3 host
  * arrays.  precision RBS_PREC_FP64 applies it in float64; RBS_PREC_MIXED in the float32 arithmetic of
- * the inner solve (pair sums with compensated accumulation, float32 self blocks).
+ * the inner solve (pair sums with compensated accumulation, float32 self blocks); RBS_PREC_DF with
+ * double-float pair sums and float64 blocks.
  */
 int rbs_apply_operator(rbs_ctx* ctx, int op, int precision, const double* x, double* y);
 
 /* The same with device buffers (x_dev, y_dev: total_nodes x 3 float64). */
 int rbs_apply_operator_device(rbs_ctx* ctx, int op, int precision, const double* x_dev, double* y_dev);
 
-/* Statistics of the last rbs_set_geometry / rbs_mobility_solve. */
-int rbs_get_stats(const rbs_ctx* ctx, rbs_stats* out);
+/* Statistics of the last rbs_set_geometry / rbs_mobility_solve, and the launch and kernel-time
+ * counters accumulated since creation or the last rbs_reset_stats (waits for pending timing events). */
+int rbs_get_stats(rbs_ctx* ctx, rbs_stats* out);
+
+/* Zero the launch and kernel-time counters. */
+int rbs_reset_stats(rbs_ctx* ctx);
 
 /* Message describing the last error of the context (empty when none); valid until the next call. */
 const char* rbs_last_error(const rbs_ctx* ctx);

@@ -28,7 +28,48 @@ bool finite_all(const double* a, long long n) {
 }  // namespace
 
 namespace rbs {
+
+Status Context::time_begin(int cls, Timed* t) {
+  t->cls = cls;
+  for (cudaEvent_t* e : {&t->a, &t->b}) {
+    if (!free_events.empty()) {
+      *e = free_events.back();
+      free_events.pop_back();
+    } else {
+      RBS_CUDA_TRY(cudaEventCreate(e));
+    }
+  }
+  RBS_CUDA_TRY(cudaEventRecord(t->a, stream));
+  return Status::Ok();
+}
+
+Status Context::time_end(Timed* t, double units) {
+  RBS_CUDA_TRY(cudaEventRecord(t->b, stream));
+  t->units = units;
+  pending.push_back(*t);
+  if (pending.size() > 4096) return harvest();
+  return Status::Ok();
+}
+
+Status Context::harvest() {
+  for (const Timed& t : pending) {
+    RBS_CUDA_TRY(cudaEventSynchronize(t.b));
+    float ms = 0.0f;
+    RBS_CUDA_TRY(cudaEventElapsedTime(&ms, t.a, t.b));
+    stats.kernel_ms[t.cls] += ms;
+    free_events.push_back(t.a);
+    free_events.push_back(t.b);
+  }
+  pending.clear();
+  return Status::Ok();
+}
+
 Context::~Context() {
+  for (const Timed& t : pending) {
+    free_events.push_back(t.a);
+    free_events.push_back(t.b);
+  }
+  for (cudaEvent_t e : free_events) cudaEventDestroy(e);
   for (Grid* g : grids) delete g;
   grids.clear();
   if (h_pinned) cudaFreeHost(h_pinned);
@@ -53,6 +94,8 @@ void rbs_default_options(rbs_options* o) {
   o->max_refinements = 20;
   o->device = 0;
   o->stream = nullptr;
+  o->timing = 0;
+  o->refine_precision = RBS_PREC_DF;
 }
 
 int rbs_create(const rbs_options* opt, rbs_ctx** out) {
@@ -66,7 +109,8 @@ int rbs_create(const rbs_options* opt, rbs_ctx** out) {
   if (o.restart < 1 || o.restart > 500 || o.max_iters < 1 || o.p_up_factor < 1 || o.p_up_factor > 4 ||
       o.p_self_factor < 1 || o.p_self_factor > 4 || !(o.viscosity > 0) || !(o.near_delta >= 0) ||
       !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_refinements < 1 ||
-      (o.precision != RBS_PREC_FP64 && o.precision != RBS_PREC_MIXED))
+      (o.precision != RBS_PREC_FP64 && o.precision != RBS_PREC_MIXED) ||
+      (o.refine_precision != RBS_PREC_FP64 && o.refine_precision != RBS_PREC_DF))
     return RBS_EINVAL;
   rbs_ctx* h = new rbs_ctx();
   Context& c = h->c;
@@ -237,7 +281,7 @@ int rbs_apply_operator_device(rbs_ctx* h, int op, int precision, const double* x
   Context& c = h->c;
   if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
   if (!x_dev || !y_dev || x_dev == y_dev) return finish(c, Status::Err(RBS_EINVAL, "apply_operator: bad buffers"));
-  if (precision != RBS_PREC_FP64 && precision != RBS_PREC_MIXED)
+  if (precision != RBS_PREC_FP64 && precision != RBS_PREC_MIXED && precision != RBS_PREC_DF)
     return finish(c, Status::Err(RBS_EINVAL, "apply_operator: bad precision"));
   Status s = enter(c);
   if (!s.ok()) return finish(c, s);
@@ -266,9 +310,28 @@ int rbs_apply_operator(rbs_ctx* h, int op, int precision, const double* x, doubl
   return finish(c, Status::Ok());
 }
 
-int rbs_get_stats(const rbs_ctx* h, rbs_stats* out) {
+int rbs_get_stats(rbs_ctx* h, rbs_stats* out) {
   if (!h || !out) return RBS_EINVAL;
-  *out = h->c.stats;
+  Context& c = h->c;
+  Status s = enter(c);
+  if (s.ok()) s = c.harvest();
+  if (!s.ok()) return finish(c, s);
+  *out = c.stats;
+  return RBS_OK;
+}
+
+int rbs_reset_stats(rbs_ctx* h) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  Status s = enter(c);
+  if (s.ok()) s = c.harvest();
+  if (!s.ok()) return finish(c, s);
+  c.stats.launches = 0;
+  for (int k = 0; k < RBS_KC_COUNT; ++k) {
+    c.stats.kernel_ms[k] = 0.0;
+    c.stats.kernel_count[k] = 0;
+    c.stats.kernel_units[k] = 0.0;
+  }
   return RBS_OK;
 }
 

@@ -105,6 +105,8 @@ struct Context {
   std::vector<Grid*> grids;
   std::vector<Shape> shapes;
   size_t block_elems = 0;  // sum over shapes of (3 np)^2
+  double particle_block_entries = 0;  // sum over particles of (3 np)^2 (entries read per block apply)
+  double near_pair_nodes = 0;         // sum over near pairs of np_i (nup_j + np_j)
   bool have_geometry = false;
 
   // per-particle device data
@@ -154,6 +156,17 @@ struct Context {
   double* h_pinned = nullptr;
 
   rbs_stats stats{};
+  // kernel timing: (class, start, stop, units) of launches not yet harvested
+  struct Timed {
+    int cls;
+    cudaEvent_t a, b;
+    double units;
+  };
+  std::vector<Timed> pending;
+  std::vector<cudaEvent_t> free_events;
+  Status time_begin(int cls, Timed* t);
+  Status time_end(Timed* t, double units);
+  Status harvest();
 
   Context() = default;
   ~Context();
@@ -193,6 +206,23 @@ Status incident_density(Context& c, const double* FT_dev, double* rho);
 Status rigid_velocities(Context& c, const double* u, double* vo_dev);
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Brackets one timed launch: records events only when timing is on; always counts the launch.
+struct KernelTimer {
+  Context& c;
+  Context::Timed t{};
+  bool on;
+  KernelTimer(Context& ctx, int cls) : c(ctx), on(ctx.opt.timing != 0) {
+    t.cls = cls;
+    if (on && !c.time_begin(cls, &t).ok()) on = false;
+  }
+  void done(double units, int launches = 1) {
+    c.stats.launches += launches;
+    c.stats.kernel_count[t.cls] += launches;
+    c.stats.kernel_units[t.cls] += units;
+    if (on) c.time_end(&t, units);
+  }
+};
 
 }  // namespace rbs
 

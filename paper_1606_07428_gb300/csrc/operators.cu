@@ -305,6 +305,161 @@ __global__ void __launch_bounds__(128) k_pairs32(const longlong4* __restrict__ w
 }
 
 // ------------------------------------------------------------------------------------------
+// Smooth pair sums in double-float arithmetic: each value is an unevaluated sum hi + lo of two
+// float32 numbers (Dekker's and Knuth's error-free transformations with fused multiply-add), so the
+// float32 pipes deliver about 44 bits per operation.  The reciprocal square root is one Newton step
+// from rsqrtf, with the residual 1 - r^2 y0^2 formed by fused multiply-adds.  Each 128-source tile
+// is summed in double-float and added into a float64 accumulator, so the sum keeps ~1e-12 relative
+// accuracy.  Coordinates are relative to the block's first target as in the float32 kernel.
+struct dflt {
+  float h, l;
+};
+__device__ __forceinline__ dflt df_split(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ dflt df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dflt df_mul(dflt a, dflt b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return {p, e};
+}
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+  dflt s = df_two_sum(a.h, b.h);
+  s.l += a.l + b.l;
+  const float h = s.h + s.l;
+  return {h, s.l - (h - s.h)};
+}
+// acc += v with the low parts carried unnormalised (renormalised when the tile is flushed)
+__device__ __forceinline__ void df_acc(dflt& acc, dflt v) {
+  const dflt s = df_two_sum(acc.h, v.h);
+  acc.h = s.h;
+  acc.l += s.l + v.l;
+}
+
+template <int KIND, bool MASK>
+__device__ __forceinline__ void pair_tile_df(const float4* __restrict__ sph, const float4* __restrict__ spl,
+                                             const float4* __restrict__ sdh, const float4* __restrict__ sdl, int cnt,
+                                             const dflt* xt, const dflt* nt, int pt, dflt* acc) {
+  for (int l = 0; l < cnt; ++l) {
+    const float4 yh = sph[l], yl = spl[l], dh = sdh[l], dl = sdl[l];
+    dflt d[3];
+    d[0] = df_two_sum(xt[0].h, -yh.x);
+    d[0].l += xt[0].l - yl.x;
+    d[1] = df_two_sum(xt[1].h, -yh.y);
+    d[1].l += xt[1].l - yl.y;
+    d[2] = df_two_sum(xt[2].h, -yh.z);
+    d[2].l += xt[2].l - yl.z;
+    // r^2 = sum of d_c^2
+    float p[3], e[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      p[c] = d[c].h * d[c].h;
+      e[c] = fmaf(d[c].h, d[c].h, -p[c]);
+      e[c] = fmaf(d[c].h + d[c].h, d[c].l, e[c]);
+    }
+    dflt s1 = df_two_sum(p[0], p[1]);
+    dflt s2 = df_two_sum(s1.h, p[2]);
+    const float r2l = s1.l + s2.l + e[0] + e[1] + e[2];
+    const float r2h = s2.h;
+    // 1 / sqrt(r^2): y0 = rsqrtf, one Newton step
+    const float y0 = rsqrtf(r2h);
+    const float q = y0 * y0;
+    const float qe = fmaf(y0, y0, -q);
+    float t = fmaf(r2h, q, -1.0f);
+    t = fmaf(r2h, qe, t);
+    t = fmaf(r2l, q, t);
+    dflt inv = {y0, -0.5f * t * y0};
+    if (MASK && __float_as_int(yh.w) == pt) inv = {0.0f, 0.0f};
+    const dflt den[3] = {{dh.x, dl.x}, {dh.y, dl.y}, {dh.z, dl.z}};
+    dflt rr = df_mul(d[0], den[0]);
+    rr = df_add(rr, df_mul(d[1], den[1]));
+    rr = df_add(rr, df_mul(d[2], den[2]));
+    const dflt inv2 = df_mul(inv, inv);
+    const dflt inv3 = df_mul(inv2, inv);
+    if (KIND == 0) {
+      const dflt inv5 = df_mul(inv3, inv2);
+      dflt rn = df_mul(d[0], nt[0]);
+      rn = df_add(rn, df_mul(d[1], nt[1]));
+      rn = df_add(rn, df_mul(d[2], nt[2]));
+      const dflt cc = df_mul(df_mul(rn, rr), inv5);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) df_acc(acc[c], df_mul(cc, d[c]));
+    } else {
+      const dflt cc = df_mul(rr, inv3);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        df_acc(acc[c], df_mul(den[c], inv));
+        df_acc(acc[c], df_mul(cc, d[c]));
+      }
+    }
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(128) k_pairs_df(const longlong4* __restrict__ work, const double4* __restrict__ x,
+                                                  const double4* __restrict__ nrm, const int* __restrict__ pid,
+                                                  const double* __restrict__ dens, double* __restrict__ y) {
+  constexpr int TS = 128;
+  __shared__ float4 sph[TS], spl[TS], sdh[TS], sdl[TS];
+  const longlong4 w = work[blockIdx.x];
+  const long long t = w.x + threadIdx.x;
+  const bool valid = t < w.y;
+  const double4 org = x[w.x];
+  dflt xt[3] = {{0, 0}, {0, 0}, {0, 0}}, nt[3] = {{0, 0}, {0, 0}, {0, 0}};
+  int pt = -1;
+  if (valid) {
+    const double4 a = x[t], nn = nrm[t];
+    xt[0] = df_split(a.x - org.x);
+    xt[1] = df_split(a.y - org.y);
+    xt[2] = df_split(a.z - org.z);
+    nt[0] = df_split(nn.x);
+    nt[1] = df_split(nn.y);
+    nt[2] = df_split(nn.z);
+    pt = pid[t];
+  }
+  const int pid_lo = pid[w.x], pid_hi = pid[w.y - 1];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (long long s0 = w.z; s0 < w.w; s0 += TS) {
+    const int cnt = (int)min((long long)TS, w.w - s0);
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+      const long long s = s0 + threadIdx.x;
+      const double4 ps = x[s];
+      const double* dd = dens + 3 * s;
+      const dflt px = df_split(ps.x - org.x), py = df_split(ps.y - org.y), pz = df_split(ps.z - org.z);
+      const dflt d0 = df_split(ps.w * dd[0]), d1 = df_split(ps.w * dd[1]), d2 = df_split(ps.w * dd[2]);
+      sph[threadIdx.x] = make_float4(px.h, py.h, pz.h, __int_as_float(pid[s]));
+      spl[threadIdx.x] = make_float4(px.l, py.l, pz.l, 0.0f);
+      sdh[threadIdx.x] = make_float4(d0.h, d1.h, d2.h, 0.0f);
+      sdl[threadIdx.x] = make_float4(d0.l, d1.l, d2.l, 0.0f);
+    }
+    __syncthreads();
+    const int tlo = pid[s0], thi = pid[s0 + cnt - 1];
+    dflt acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    if (thi < pid_lo || tlo > pid_hi)
+      pair_tile_df<KIND, false>(sph, spl, sdh, sdl, cnt, xt, nt, pt, acc);
+    else
+      pair_tile_df<KIND, true>(sph, spl, sdh, sdl, cnt, xt, nt, pt, acc);
+    a0 += (double)acc[0].h + (double)acc[0].l;
+    a1 += (double)acc[1].h + (double)acc[1].l;
+    a2 += (double)acc[2].h + (double)acc[2].l;
+  }
+  if (valid) {
+    const double sc = KIND == 0 ? kTractionScale : kStokesletScale;
+    atomicAdd(y + 3 * t + 0, sc * a0);
+    atomicAdd(y + 3 * t + 1, sc * a1);
+    atomicAdd(y + 3 * t + 2, sc * a2);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Upsampled densities of the near-source particles: mu_up = U mu_j, one warp per upsampled node.
 template <typename TU>
 __global__ void __launch_bounds__(256) k_upsample(int n_up, const int* __restrict__ up_particle, const long long* __restrict__ up_off,
@@ -445,6 +600,7 @@ __global__ void __launch_bounds__(256) k_near(const int2* __restrict__ near, con
 
 Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, double* aux, double scale) {
   if (mode == kModeZero) {
+    c.stats.launches += 1;
     RBS_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * 3 * c.N, c.stream));
     return Status::Ok();
   }
@@ -452,6 +608,8 @@ Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, 
   const int nb = (int)c.bwork.size();
   bool use32 = (prec == RBS_PREC_MIXED) && (mode == kModeSelfK || mode == kModeSelfKNoL || mode == kModeKOnlySelf ||
                                              mode == kModePrecond);
+  const double bytes = (mode == kModeL) ? 0.0 : (double)c.particle_block_entries * (use32 ? 4.0 : 8.0);
+  KernelTimer timer(c, RBS_KC_BLOCKS);
   if (use32) {
     const float* B = (mode == kModePrecond) ? c.d_precond32.ptr : c.d_blockK32.ptr;
     if (smem > 48 * 1024)
@@ -468,6 +626,7 @@ Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, 
                                                   aux, scale);
   }
   RBS_CUDA_TRY(cudaGetLastError());
+  timer.done(bytes);
   return Status::Ok();
 }
 
@@ -475,7 +634,15 @@ Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y) {
   const int nw = (int)c.work.size();
   const bool f32 = (prec == RBS_PREC_MIXED);
   if (nw > 0) {
-    if (f32) {
+    int cls = f32 ? (kind == 0 ? RBS_KC_PAIR_K32 : RBS_KC_PAIR_S32) : (kind == 0 ? RBS_KC_PAIR_K64 : RBS_KC_PAIR_S64);
+    if (prec == RBS_PREC_DF) cls = kind == 0 ? RBS_KC_PAIR_KDF : RBS_KC_PAIR_SDF;
+    KernelTimer timer(c, cls);
+    if (prec == RBS_PREC_DF) {
+      if (kind == 0)
+        k_pairs_df<0><<<nw, 128, 0, c.stream>>>(c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
+      else
+        k_pairs_df<1><<<nw, 128, 0, c.stream>>>(c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
+    } else if (f32) {
       if (kind == 0)
         k_pairs32<0><<<nw, 128, 0, c.stream>>>(c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
       else
@@ -487,9 +654,11 @@ Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y) {
         k_pairs64<1><<<nw, 128, 0, c.stream>>>(c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
     }
     RBS_CUDA_TRY(cudaGetLastError());
+    timer.done((double)c.stats.far_pairs);
   }
   const int nn = (int)c.near_pairs.size();
   if (nn > 0) {
+    KernelTimer timer(c, RBS_KC_NEAR);
     size_t smem = sizeof(double) * 3 * (size_t)c.max_np;
     if (smem > 48 * 1024) {
       RBS_CUDA_TRY(cudaFuncSetAttribute(k_upsample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -522,6 +691,7 @@ Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y) {
     }
 #undef RBS_NEAR_ARGS
     RBS_CUDA_TRY(cudaGetLastError());
+    timer.done((double)c.near_pair_nodes, 2);
   }
   return Status::Ok();
 }

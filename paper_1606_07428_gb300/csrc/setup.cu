@@ -802,6 +802,11 @@ Status build_geometry(Context& c) {
     }
   }
   c.stats.far_pairs = fp;
+  c.particle_block_entries = 0;
+  for (int k = 0; k < n; ++k) c.particle_block_entries += 9.0 * nodes[k] * nodes[k];
+  c.near_pair_nodes = 0;
+  for (const int2& pr : c.near_pairs)
+    c.near_pair_nodes += (double)nodes[pr.x] * (c.grids[grid_of[pr.y]]->nup + nodes[pr.y]);
   c.stats.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   c.have_geometry = true;
   return Status::Ok();

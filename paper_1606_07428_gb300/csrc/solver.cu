@@ -207,6 +207,7 @@ static Status multidot(Context& c, const double* V, long long ldv, int nv, const
                        double* accum) {
   int nchunk = chunks_for(n);
   dim3 g(nchunk, nv);
+  c.stats.launches += 2;
   k_multidot<<<g, kDotThreads, 0, c.stream>>>(V, ldv, nv, w, n, nchunk, c.d_partials.ptr);
   k_reduce_partials<<<nv, 256, 0, c.stream>>>(c.d_partials.ptr, nchunk, out, accum);
   RBS_CUDA_TRY(cudaGetLastError());
@@ -264,6 +265,7 @@ static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zer
       RBS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
     } else {
       RBS_TRY(apply_operator(c, RBS_OP_A, prec, x, r));
+      c.stats.launches++;
       k_axpby<<<nbk, 256, 0, c.stream>>>(r, 1.0, b, -1.0, n3);
     }
     first = false;
@@ -277,7 +279,9 @@ static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zer
     }
     if (*iters >= max_iters) break;
     RBS_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(double) * (size_t)ld * (m + 1), c.stream));
+    c.stats.launches++;
     k_init_g<<<1, 64, 0, c.stream>>>(g, m + 2, scal);
+    c.stats.launches++;
     k_scale<<<nbk, 256, 0, c.stream>>>(V, r, g, 1, n3);  // V_0 = r / beta
     int kdone = 0;
     for (int k = 0; k < m && *iters < max_iters; ++k) {
@@ -286,10 +290,13 @@ static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zer
       double* hcol = H + (size_t)k * ld;
       for (int pass = 0; pass < 2; ++pass) {
         RBS_TRY(multidot(c, V, n3, k + 1, w, n3, hvec, hcol));
+        c.stats.launches++;
         k_combine<<<nbk, 256, 0, c.stream>>>(w, 1.0, V, n3, k + 1, hvec, -1.0, n3);
       }
       RBS_TRY(norm2_dev(c, w, n3, hcol + k + 1));
+      c.stats.launches++;
       k_givens<<<1, 1, 0, c.stream>>>(H, ld, k, cs, sn, g, scal + 1, scal + 2);
+      c.stats.launches++;
       k_scale<<<nbk, 256, 0, c.stream>>>(V + (size_t)(k + 1) * n3, w, scal + 1, 1, n3);
       RBS_CUDA_TRY(cudaGetLastError());
       RBS_TRY(read_scalar(c, scal + 2, &res));
@@ -298,12 +305,16 @@ static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zer
       if (!(res > tol_abs)) break;  // also stops on NaN
     }
     // x += P (V y)
+    c.stats.launches++;
     k_trisolve<<<1, 1, 0, c.stream>>>(H, ld, kdone, g, y);
     if (c.opt.preconditioner) {
+      c.stats.launches++;
       k_combine<<<nbk, 256, 0, c.stream>>>(w, 0.0, V, n3, kdone, y, 1.0, n3);
       RBS_TRY(apply_blocks(c, kModePrecond, prec, w, z, r, 1.0));
+      c.stats.launches++;
       k_axpby<<<nbk, 256, 0, c.stream>>>(x, 1.0, z, 1.0, n3);
     } else {
+      c.stats.launches++;
       k_combine<<<nbk, 256, 0, c.stream>>>(x, 1.0, V, n3, kdone, y, 1.0, n3);
     }
     RBS_CUDA_TRY(cudaGetLastError());
@@ -318,6 +329,7 @@ static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zer
 }
 
 Status incident_density(Context& c, const double* FT_dev, double* rho) {
+  c.stats.launches++;
   k_incident<<<vec_blocks(c, c.N), 256, 0, c.stream>>>(c.N, c.d_pid.ptr, c.d_x.ptr, c.d_centre.ptr, c.d_area.ptr,
                                                        c.d_tauinv.ptr, FT_dev, rho);
   RBS_CUDA_TRY(cudaGetLastError());
@@ -325,6 +337,7 @@ Status incident_density(Context& c, const double* FT_dev, double* rho) {
 }
 
 Status rigid_velocities(Context& c, const double* u, double* vo_dev) {
+  c.stats.launches++;
   k_rigid<<<c.n, 256, 0, c.stream>>>(c.d_offset.ptr, c.d_x.ptr, c.d_centre.ptr, c.d_area.ptr, c.d_tauinv.ptr, u,
                                      1.0 / c.opt.viscosity, vo_dev);
   RBS_CUDA_TRY(cudaGetLastError());
@@ -362,17 +375,21 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
   double* d = c.d_vec[7].ptr;
   // forces and torques to the device (n x 6)
   if (device_io) {
+    c.stats.launches++;
     k_pack_ft<<<cdiv(n, 128), 128, 0, c.stream>>>(n, F, T, c.d_FT.ptr);
   } else {
     // staged through the velocity buffer: F then T, then packed
     RBS_CUDA_TRY(cudaMemcpyAsync(c.d_vo.ptr, F, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c.stream));
     RBS_CUDA_TRY(cudaMemcpyAsync(c.d_vo.ptr + 3 * n, T, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c.stream));
+    c.stats.launches++;
     k_pack_ft<<<cdiv(n, 128), 128, 0, c.stream>>>(n, c.d_vo.ptr, c.d_vo.ptr + 3 * n, c.d_FT.ptr);
   }
   RBS_CUDA_TRY(cudaGetLastError());
   // 1. incident density; right-hand side b = -(1/2 I + K) rho in float64
   RBS_TRY(incident_density(c, c.d_FT.ptr, rho));
-  RBS_TRY(apply_operator(c, RBS_OP_HALF_K, RBS_PREC_FP64, rho, b));
+  const int hi = (c.opt.precision == RBS_PREC_MIXED) ? c.opt.refine_precision : RBS_PREC_FP64;
+  RBS_TRY(apply_operator(c, RBS_OP_HALF_K, hi, rho, b));
+  c.stats.launches++;
   k_axpby<<<nbk, 256, 0, c.stream>>>(b, 0.0, b, -1.0, n3);
   RBS_TRY(norm2_dev(c, b, n3, c.d_partials.ptr + (size_t)(c.opt.restart + 1) * 1024 + 8));
   double bn2;
@@ -403,9 +420,11 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
       RBS_TRY(gmres(c, RBS_PREC_MIXED, r, d, true, c.opt.inner_tol * rn, c.opt.max_iters - total_iters, &its, &res,
                     &conv_inner));
       total_iters += its;
+      c.stats.launches++;
       k_axpby<<<nbk, 256, 0, c.stream>>>(x, 1.0, d, 1.0, n3);
       // float64 residual r = b - A x
-      RBS_TRY(apply_operator(c, RBS_OP_A, RBS_PREC_FP64, x, r));
+      RBS_TRY(apply_operator(c, RBS_OP_A, hi, x, r));
+      c.stats.launches++;
       k_axpby<<<nbk, 256, 0, c.stream>>>(r, 1.0, b, -1.0, n3);
       double* sc = c.d_partials.ptr + (size_t)(c.opt.restart + 1) * 1024 + 8;
       RBS_TRY(norm2_dev(c, r, n3, sc));
@@ -424,15 +443,18 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
   // 3. u = S[rho + mu] and the rigid velocities
   double* sigma = c.d_vec[6].ptr;
   double* u = c.d_vec[4].ptr;
+  c.stats.launches++;
   k_add<<<nbk, 256, 0, c.stream>>>(sigma, rho, x, n3);
-  RBS_TRY(apply_operator(c, RBS_OP_S, RBS_PREC_FP64, sigma, u));
+  RBS_TRY(apply_operator(c, RBS_OP_S, hi, sigma, u));
   RBS_TRY(rigid_velocities(c, u, c.d_vo.ptr));
   if (device_io) {
+    c.stats.launches++;
     k_unpack_vo<<<cdiv(n, 128), 128, 0, c.stream>>>(n, c.d_vo.ptr, v, om);
     if (density) RBS_CUDA_TRY(cudaMemcpyAsync(density, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
     RBS_CUDA_TRY(cudaStreamSynchronize(c.stream));
   } else {
     double* tmp = c.d_FT.ptr;  // reuse: n x 6 -> v (n x 3) then omega (n x 3)
+    c.stats.launches++;
     k_unpack_vo<<<cdiv(n, 128), 128, 0, c.stream>>>(n, c.d_vo.ptr, tmp, tmp + 3 * n);
     RBS_CUDA_TRY(cudaMemcpyAsync(v, tmp, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.stream));
     RBS_CUDA_TRY(cudaMemcpyAsync(om, tmp + 3 * n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c.stream));

@@ -26,6 +26,7 @@ RBS_ESTATE = -7
 
 RBS_PREC_FP64 = 0
 RBS_PREC_MIXED = 1
+RBS_PREC_DF = 2
 
 RBS_OP_A = 0
 RBS_OP_HALF_K = 1
@@ -41,7 +42,7 @@ EXPORTS = [
     "rbs_default_options", "rbs_create", "rbs_destroy", "rbs_set_geometry", "rbs_total_nodes",
     "rbs_get_surface", "rbs_mobility_solve", "rbs_mobility_solve_device", "rbs_incident_density",
     "rbs_rigid_velocities", "rbs_apply_operator", "rbs_apply_operator_device", "rbs_get_stats",
-    "rbs_last_error",
+    "rbs_reset_stats", "rbs_last_error",
 ]
 
 
@@ -59,7 +60,22 @@ class rbs_options(ctypes.Structure):
         ("max_refinements", ctypes.c_int),
         ("device", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("timing", ctypes.c_int),
+        ("refine_precision", ctypes.c_int),
     ]
+
+
+RBS_KC_PAIR_K32 = 0
+RBS_KC_PAIR_S32 = 1
+RBS_KC_PAIR_K64 = 2
+RBS_KC_PAIR_S64 = 3
+RBS_KC_BLOCKS = 4
+RBS_KC_NEAR = 5
+RBS_KC_PAIR_KDF = 6
+RBS_KC_PAIR_SDF = 7
+RBS_KC_COUNT = 8
+KERNEL_CLASSES = ["pair_traction_f32", "pair_stokeslet_f32", "pair_traction_f64", "pair_stokeslet_f64",
+                  "particle_blocks", "near_correction", "pair_traction_df", "pair_stokeslet_df"]
 
 
 class rbs_stats(ctypes.Structure):
@@ -74,6 +90,10 @@ class rbs_stats(ctypes.Structure):
         ("n_shapes", ctypes.c_int),
         ("near_pairs", ctypes.c_longlong),
         ("far_pairs", ctypes.c_longlong),
+        ("launches", ctypes.c_longlong),
+        ("kernel_ms", ctypes.c_double * 8),
+        ("kernel_count", ctypes.c_longlong * 8),
+        ("kernel_units", ctypes.c_double * 8),
     ]
 
 
@@ -111,6 +131,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rbs_apply_operator": (I, [P, I, I, P, P]),
         "rbs_apply_operator_device": (I, [P, I, I, P, P]),
         "rbs_get_stats": (I, [P, ctypes.POINTER(rbs_stats)]),
+        "rbs_reset_stats": (I, [P]),
         "rbs_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
@@ -246,7 +267,15 @@ def rbs_apply_operator_device(ctx, op: int, precision: int, x_dev, y_dev) -> Non
 def rbs_get_stats(ctx) -> dict:
     s = rbs_stats()
     _check(ctx, load().rbs_get_stats(ctx, ctypes.byref(s)))
-    return {name: getattr(s, name) for name, _ in s._fields_}
+    out = {}
+    for name, _ in s._fields_:
+        val = getattr(s, name)
+        out[name] = list(val) if name.startswith("kernel_") else val
+    return out
+
+
+def rbs_reset_stats(ctx) -> None:
+    _check(ctx, load().rbs_reset_stats(ctx))
 
 
 def rbs_last_error(ctx) -> str:

@@ -4,6 +4,8 @@ Tolerances (relative L2 over the stacked outputs):
 * float64 operators: 1e-12 (both sides evaluate the same sums in float64; only the summation order
   differs, so the gap is a few hundred units in the last place);
 * float64 solve, (v, omega): 1e-11;
+* double-float operator (float64-class steps of the mixed solve): 1e-11 (double-float carries about
+  44 bits per operation; tiles of 128 terms are summed in double-float, then in float64);
 * float32 operator (inner-solve arithmetic): 2e-5 (float32 unit roundoff 6e-8 per pair, rsqrtf within
   2 ulp, blocks rounded to float32, sums of up to 10^5 terms with per-tile compensation);
 * mixed-precision solve, (v, omega): 1e-8.
@@ -36,7 +38,7 @@ def rbs():
 
 
 def mixed_system():
-    """7 ellipsoids, p in {4, 5, 6}, n_phi = 2p or 2p + 2, near pairs present, 370 nodes (a ragged
+    """7 ellipsoids, p in {4, 5, 6}, n_phi = 2p or 2p + 2, near pairs present, 502 nodes (a ragged
     tail of the 128-node tiles)."""
     s = suspensions.random_ellipsoids(7, 4, None, 0.12, 0.2, seed=21)
     s.p = np.array([4, 6, 5, 6, 4, 5, 6], np.int32)
@@ -121,6 +123,14 @@ def test_projection_operator_matches_oracle(rbs, small):
     assert rel(y, yr) < 1e-13
 
 
+@pytest.mark.parametrize("name", ["A", "K_OFF", "S_OFF", "HALF_K", "S"])
+def test_double_float_operators_match_oracle(rbs, small, name):
+    s, ref, ctx = small
+    x = suspensions.random_density(6, s.total_nodes)
+    y = rbs.rbs_apply_operator(ctx.ctx, getattr(rbs, "RBS_OP_" + name), rbs.RBS_PREC_DF, x)
+    assert rel(y, oracle_op(ref, name, x)) < 1e-11
+
+
 @pytest.mark.parametrize("name", ["A", "K_OFF", "S_OFF", "HALF_K"])
 def test_float32_operators_within_float32_bound(rbs, small, name):
     s, ref, ctx = small
@@ -138,9 +148,11 @@ def test_float64_solve_matches_oracle_lu(rbs, small):
     assert 0 < its < 40
 
 
-def test_mixed_solve_matches_oracle(rbs, small):
+@pytest.mark.parametrize("refine", ["DF", "FP64"])
+def test_mixed_solve_matches_oracle(rbs, small, refine):
     s, ref, _ = small
-    with rbs.Context(device=0, precision=rbs.RBS_PREC_MIXED) as ctx:
+    with rbs.Context(device=0, precision=rbs.RBS_PREC_MIXED,
+                     refine_precision=getattr(rbs, "RBS_PREC_" + refine)) as ctx:
         ctx.set_suspension(s)
         v, om, _, its = rbs.rbs_mobility_solve(ctx.ctx, s.F, s.T, 1e-10)
         st = rbs.rbs_get_stats(ctx.ctx)
