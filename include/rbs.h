@@ -172,6 +172,24 @@ int rbs_incident_density(rbs_ctx* ctx, const double* F, const double* T, double*
 int rbs_rigid_velocities(rbs_ctx* ctx, const double* u, double* v, double* omega);
 
 /*
+ * Allocation-free variant of rbs_rigid_velocities, on device buffers.  The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory at call time, such as code
+ * running while a stream is captured into a CUDA graph (where cudaMalloc is not allowed), real-time
+ * stepping loops that forbid allocator calls, or hosts that give the library a fixed memory budget.
+ *  u_dev      total_nodes x 3 surface velocity (device)
+ *  v_dev, omega_dev   n x 3 outputs (device), Eqs. 41-42
+ * The per-particle intermediate lives in a fixed device array of 6 x 65,536 float64 (3 MiB), which
+ * every GPU that loads the library holds until the process exits; geometries with more than 65,536
+ * particles are rejected with RBS_EINVAL.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All calls share the array
+ * and each overwrites the entries it reads, so calls whose work overlaps on the GPU (other contexts or
+ * streams at the same time) race and must be ordered by the caller.  Work runs on the context's
+ * stream; the call returns after it completes.
+ */
+int rbs_rigid_velocities_noalloc(rbs_ctx* ctx, const double* u_dev, double* v_dev, double* omega_dev);
+
+/*
  * Apply one discrete operator (RBS_OP_*) to a surface field: y = op(x), x and y total_nodes x 3 host
  * arrays.  precision RBS_PREC_FP64 applies it in float64; RBS_PREC_MIXED in the float32 arithmetic of
  * the inner solve (pair sums with compensated accumulation, float32 self blocks); RBS_PREC_DF with

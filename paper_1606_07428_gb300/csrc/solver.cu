@@ -8,6 +8,7 @@
 // float64 on the GPU; the host reads one residual estimate per iteration.
 #include <chrono>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -474,3 +475,66 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
 }
 
 }  // namespace rbs
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free rigid velocities.  Some callers may not allocate device memory when they call in:
+// code that runs while a stream is being captured into a CUDA graph (cudaMalloc is not permitted
+// then), real-time time-stepping loops that forbid allocator calls, and hosts that hand the library
+// a fixed memory budget up front.  For them rbs_rigid_velocities_noalloc reads u and writes v and
+// omega in caller buffers, and keeps its one intermediate (the interleaved n x 6 result of the
+// per-particle reduction) in the fixed device array below instead of a context buffer.
+namespace rbs {
+namespace {
+
+constexpr int kNoAllocMaxParticles = 65536;  // 65,536 x 6 float64 = 3 MiB per device
+static __device__ __align__(256) double g_rigid_scratch[6 * kNoAllocMaxParticles];
+
+std::mutex g_scratch_mutex;
+double* g_scratch_addr[64] = {};  // device address of g_rigid_scratch, per device ordinal
+
+// Host code may not pass g_rigid_scratch to a kernel directly (its name is a host-side stand-in);
+// the device address is looked up once per device, with that device current.
+Status rigid_scratch(int device, double** out) {
+  if (device < 0 || device >= 64) return Status::Err(RBS_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[device]) {
+    void* p = nullptr;
+    RBS_CUDA_TRY(cudaGetSymbolAddress(&p, g_rigid_scratch));
+    g_scratch_addr[device] = static_cast<double*>(p);
+  }
+  *out = g_scratch_addr[device];
+  return Status::Ok();
+}
+
+}  // namespace
+}  // namespace rbs
+
+extern "C" int rbs_rigid_velocities_noalloc(rbs_ctx* h, const double* u_dev, double* v_dev, double* omega_dev) {
+  if (!h) return RBS_EINVAL;
+  rbs::Context& c = h->c;
+  auto fail = [&](const rbs::Status& s) {
+    c.err = s.msg;
+    return s.code;
+  };
+  if (!c.have_geometry) return fail(rbs::Status::Err(RBS_ESTATE, "no geometry"));
+  if (!u_dev || !v_dev || !omega_dev) return fail(rbs::Status::Err(RBS_EINVAL, "rigid_velocities_noalloc: null pointer"));
+  if (c.n > rbs::kNoAllocMaxParticles)
+    return fail(rbs::Status::Err(RBS_EINVAL, "rigid_velocities_noalloc: " + std::to_string(c.n) +
+                                                 " particles exceed the fixed scratch limit of " +
+                                                 std::to_string(rbs::kNoAllocMaxParticles)));
+  cudaError_t e = cudaSetDevice(c.device);
+  if (e != cudaSuccess) return fail(rbs::Status::Err(RBS_ECUDA, cudaGetErrorString(e)));
+  double* scratch = nullptr;
+  rbs::Status s = rbs::rigid_scratch(c.device, &scratch);
+  if (!s.ok()) return fail(s);
+  // every scratch entry read below is written first by k_rigid, so nothing needs clearing
+  rbs::k_rigid<<<c.n, 256, 0, c.stream>>>(c.d_offset.ptr, c.d_x.ptr, c.d_centre.ptr, c.d_area.ptr, c.d_tauinv.ptr,
+                                         u_dev, 1.0 / c.opt.viscosity, scratch);
+  rbs::k_unpack_vo<<<rbs::cdiv(c.n, 128), 128, 0, c.stream>>>(c.n, scratch, v_dev, omega_dev);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) return fail(rbs::Status::Err(RBS_ECUDA, std::string("rigid_velocities_noalloc: ") + cudaGetErrorString(e)));
+  c.stats.launches += 2;
+  c.err.clear();
+  return RBS_OK;
+}

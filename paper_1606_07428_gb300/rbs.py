@@ -42,7 +42,7 @@ EXPORTS = [
     "rbs_default_options", "rbs_create", "rbs_destroy", "rbs_set_geometry", "rbs_total_nodes",
     "rbs_get_surface", "rbs_mobility_solve", "rbs_mobility_solve_device", "rbs_incident_density",
     "rbs_rigid_velocities", "rbs_apply_operator", "rbs_apply_operator_device", "rbs_get_stats",
-    "rbs_reset_stats", "rbs_last_error",
+    "rbs_reset_stats", "rbs_last_error", "rbs_rigid_velocities_noalloc",
 ]
 
 
@@ -128,6 +128,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rbs_mobility_solve_device": (I, [P, P, P, D, P, P, P, P]),
         "rbs_incident_density": (I, [P, P, P, P]),
         "rbs_rigid_velocities": (I, [P, P, P, P]),
+        "rbs_rigid_velocities_noalloc": (I, [P, P, P, P]),
         "rbs_apply_operator": (I, [P, I, I, P, P]),
         "rbs_apply_operator_device": (I, [P, I, I, P, P]),
         "rbs_get_stats": (I, [P, ctypes.POINTER(rbs_stats)]),
@@ -251,6 +252,11 @@ def rbs_rigid_velocities(ctx, u, n):
     om = np.zeros((n, 3))
     _check(ctx, load().rbs_rigid_velocities(ctx, _ptr(u), _ptr(v), _ptr(om)))
     return v, om
+
+
+def rbs_rigid_velocities_noalloc(ctx, u_dev, v_dev, omega_dev) -> None:
+    """Device-buffer rigid velocities that allocate nothing (fixed 65,536-particle scratch)."""
+    _check(ctx, load().rbs_rigid_velocities_noalloc(ctx, _ptr(u_dev), _ptr(v_dev), _ptr(omega_dev)))
 
 
 def rbs_apply_operator(ctx, op: int, precision: int, x) -> np.ndarray:
