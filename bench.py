@@ -255,12 +255,13 @@ def run_ours(args):
     # accuracy of the chosen path against the plain float64 path, and the float64 solve rate
     F0 = draws[args.warmup][0]
     T0 = draws[args.warmup][1]
-    v_mix, om_mix, _, _ = rbs.rbs_mobility_solve(ctx.ctx, F0, T0, args.tol)
-    ctx64 = rbs.Context(device=local, precision=rbs.RBS_PREC_FP64, timing=1, stream=stream.cuda_stream)
-    ctx64.set_suspension(susp)
     plain = None
     err = None
+    ctx64 = None
     if args.fp64_steps > 0:
+        v_mix, om_mix, _, _ = rbs.rbs_mobility_solve(ctx.ctx, F0, T0, args.tol)
+        ctx64 = rbs.Context(device=local, precision=rbs.RBS_PREC_FP64, timing=1, stream=stream.cuda_stream)
+        ctx64.set_suspension(susp)
         barrier()
         rbs.rbs_reset_stats(ctx64.ctx)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -405,7 +406,8 @@ def run_ours(args):
         }
         print(json.dumps(line), flush=True)
     ctx.close()
-    ctx64.close()
+    if ctx64 is not None:
+        ctx64.close()
     if world > 1:
         dist.destroy_process_group()
 

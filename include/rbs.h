@@ -82,7 +82,14 @@ typedef struct {
                           (default 0); results in rbs_stats.kernel_ms */
   int refine_precision; /* RBS_PREC_MIXED: arithmetic of the right-hand side, refinement residuals
                           and velocity evaluation, RBS_PREC_DF (default) or RBS_PREC_FP64 */
+  int warm_start;      /* initial GMRES guess: RBS_WARM_ZERO (default), RBS_WARM_PREVIOUS (the last
+                          solved density of this context) or RBS_WARM_LEARNED (the trained network);
+                          the converged solution does not depend on it */
 } rbs_options;
+
+#define RBS_WARM_ZERO 0
+#define RBS_WARM_PREVIOUS 1
+#define RBS_WARM_LEARNED 2
 
 /* Kernel classes timed when rbs_options.timing is set (indices into rbs_stats.kernel_*). */
 #define RBS_KC_PAIR_K32 0 /* smooth traction pair sum, float32 */
@@ -165,6 +172,26 @@ int rbs_mobility_solve(rbs_ctx* ctx, const double* F, const double* T, double to
 int rbs_mobility_solve_device(rbs_ctx* ctx, const double* F_dev, const double* T_dev, double tol,
                               double* v_dev, double* omega_dev, double* density_dev, int* iterations);
 
+/* Explicit Runge-Kutta schemes for rbs_advance. */
+#define RBS_RK_EULER 1
+#define RBS_RK_TRAPEZOID 2
+#define RBS_RK4 4
+
+/*
+ * Rigid-body time stepping (Section 3.3, Eqs. 40 and 43; Algorithm 1 without contact): `steps`
+ * explicit Runge-Kutta steps of size dt (scheme RBS_RK_EULER, RBS_RK_TRAPEZOID or RBS_RK4) of
+ * dc_i/dt = v_i, dq_i/dt = 1/2 (0, omega_i) q_i, with the forces F and torques T (n x 3 each, host)
+ * held fixed.  Every stage is one mobility solve to relative tolerance tol at the stage
+ * configuration (the body-frame self blocks and preconditioner are reused, Eq. 38); quaternions are
+ * renormalised after each step.  The context's configuration is updated in place; iterations (may be
+ * NULL) receives the total GMRES iterations.  Returns RBS_EOVERLAP if particles come into contact.
+ */
+int rbs_advance(rbs_ctx* ctx, const double* F, const double* T, double dt, int steps, int scheme, double tol,
+                int* iterations);
+
+/* Current centres (n x 3) and unit quaternions (n x 4) of the context's particles (host arrays). */
+int rbs_get_state(rbs_ctx* ctx, double* centres, double* quats);
+
 /* Incident density rho of Eq. 19 for forces F and torques T (n x 3 each); rho is total_nodes x 3. */
 int rbs_incident_density(rbs_ctx* ctx, const double* F, const double* T, double* rho);
 
@@ -199,6 +226,40 @@ int rbs_apply_operator(rbs_ctx* ctx, int op, int precision, const double* x, dou
 
 /* The same with device buffers (x_dev, y_dev: total_nodes x 3 float64). */
 int rbs_apply_operator_device(rbs_ctx* ctx, int op, int precision, const double* x_dev, double* y_dev);
+
+/*
+ * Learned warm start.  The paper's GMRES (Section 3.2) starts from zero; this network only changes
+ * the initial guess, so the solve still converges to the same tolerance and the same solution.
+ * Definitions (one (p, n_phi) grid for all particles):
+ *  - features, 128 floats per particle: R_i^T F_i, R_i^T T_i, semi-axes, then for its 16 nearest
+ *    neighbours in the same suspension (centre distance ascending, ties to the lower index) the
+ *    body-frame offset R_i^T (c_j - c_i) and the relative rotation conj(q_i) q_j (scalar part >= 0);
+ *    absent neighbours and entries 121-127 are zero;
+ *  - targets, 3 n_basis floats per particle: the real orthonormal spherical-harmonic coefficients
+ *    (Eq. 32, no Condon-Shortley sign) of the body-frame density R_i^T mu, component-major, each in
+ *    the order m = 0..m_max, n = m..p, cos then (m > 0) sin;
+ *  - network: y = W3 g(W2 g(W1 x + b1) + b2) + b3, widths 128 -> 256 -> 256 -> 3 n_basis, g the tanh
+ *    form of GELU; bfloat16 operands, float32 accumulation and float32 master weights (Adam).
+ *    Parameters are flattened as W1 (128 x 256, row-major), b1, W2 (256 x 256), b2, W3 (256 x 3 n_basis),
+ *    b3.  The network predicts targets divided by a scale (the RMS of the training targets).
+ */
+/* Record the features of the current configuration for F, T (n x 3, host) and the coefficients of the
+ * context's last solved density as one training sample per particle. */
+int rbs_warmstart_record(rbs_ctx* ctx, const double* F, const double* T);
+/* Train on the recorded samples: `epochs` passes of shuffled minibatches of `batch` rows, Adam with
+ * learning rate lr; the first call draws initial weights from `seed`.  loss (may be NULL) receives
+ * the mean loss of the last epoch. */
+int rbs_warmstart_train(rbs_ctx* ctx, int epochs, int batch, double lr, unsigned seed, double* loss);
+/* Read (out != NULL) or load (in != NULL) the flattened float32 parameters; count receives their
+ * number, scale the output scale (read, or loaded with `in`). */
+int rbs_warmstart_weights(rbs_ctx* ctx, float* out, const float* in, long long* count, float* scale);
+/* Feature rows of the current configuration (X: n x 128, host). */
+int rbs_warmstart_features(rbs_ctx* ctx, const double* F, const double* T, float* X);
+/* Target coefficients of a density mu (total_nodes x 3, host) into coef (n x 3 n_basis, host). */
+int rbs_warmstart_targets(rbs_ctx* ctx, const double* mu, float* coef);
+/* Network on host rows X (rows x 128): outputs Y (rows x 3 n_basis, may be NULL); with targets Yt,
+ * the gradients of mean((Y - Yt)^2) into grads (flattened like the parameters) and the loss. */
+int rbs_warmstart_mlp(rbs_ctx* ctx, int rows, const float* X, const float* Yt, float* Y, float* grads, double* loss);
 
 /* Statistics of the last rbs_set_geometry / rbs_mobility_solve, and the launch and kernel-time
  * counters accumulated since creation or the last rbs_reset_stats (waits for pending timing events). */

@@ -65,6 +65,7 @@ Status Context::harvest() {
 }
 
 Context::~Context() {
+  warm_release(*this);
   for (const Timed& t : pending) {
     free_events.push_back(t.a);
     free_events.push_back(t.b);
@@ -96,6 +97,7 @@ void rbs_default_options(rbs_options* o) {
   o->stream = nullptr;
   o->timing = 0;
   o->refine_precision = RBS_PREC_DF;
+  o->warm_start = RBS_WARM_ZERO;
 }
 
 int rbs_create(const rbs_options* opt, rbs_ctx** out) {
@@ -110,7 +112,8 @@ int rbs_create(const rbs_options* opt, rbs_ctx** out) {
       o.p_self_factor < 1 || o.p_self_factor > 4 || !(o.viscosity > 0) || !(o.near_delta >= 0) ||
       !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_refinements < 1 ||
       (o.precision != RBS_PREC_FP64 && o.precision != RBS_PREC_MIXED) ||
-      (o.refine_precision != RBS_PREC_FP64 && o.refine_precision != RBS_PREC_DF))
+      (o.refine_precision != RBS_PREC_FP64 && o.refine_precision != RBS_PREC_DF) || o.warm_start < 0 ||
+      o.warm_start > 2)
     return RBS_EINVAL;
   rbs_ctx* h = new rbs_ctx();
   Context& c = h->c;
@@ -228,6 +231,97 @@ int rbs_mobility_solve(rbs_ctx* h, const double* F, const double* T, double tol,
 int rbs_mobility_solve_device(rbs_ctx* h, const double* F_dev, const double* T_dev, double tol, double* v_dev,
                               double* omega_dev, double* density_dev, int* iterations) {
   return solve_common(h, F_dev, T_dev, tol, v_dev, omega_dev, density_dev, iterations, true);
+}
+
+int rbs_advance(rbs_ctx* h, const double* F, const double* T, double dt, int steps, int scheme, double tol,
+                int* iterations) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "advance before set_geometry"));
+  if (!F || !T) return finish(c, Status::Err(RBS_EINVAL, "advance: null force or torque"));
+  if (!(dt > 0) || !std::isfinite(dt) || steps < 0 || !(tol > 0 && tol < 1))
+    return finish(c, Status::Err(RBS_EINVAL, "advance: need dt > 0, steps >= 0, 0 < tol < 1"));
+  if (!finite_all(F, 3LL * c.n) || !finite_all(T, 3LL * c.n))
+    return finish(c, Status::Err(RBS_EINVAL, "advance: non-finite force or torque"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  return finish(c, rbs::advance(c, F, T, dt, steps, scheme, tol, iterations));
+}
+
+int rbs_warmstart_record(rbs_ctx* h, const double* F, const double* T) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry || !c.have_prev) return finish(c, Status::Err(RBS_ESTATE, "warmstart_record needs a solved density"));
+  if (!F || !T) return finish(c, Status::Err(RBS_EINVAL, "warmstart_record: null force or torque"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  std::vector<double> ft(6 * (size_t)c.n);
+  for (int i = 0; i < c.n; ++i)
+    for (int q = 0; q < 3; ++q) {
+      ft[6 * i + q] = F[3 * i + q];
+      ft[6 * i + 3 + q] = T[3 * i + q];
+    }
+  cudaError_t e = cudaMemcpyAsync(c.d_FT.ptr, ft.data(), sizeof(double) * ft.size(), cudaMemcpyHostToDevice, c.stream);
+  if (e != cudaSuccess) return finish(c, Status::Err(RBS_ECUDA, cudaGetErrorString(e)));
+  return finish(c, rbs::warm_record(c, c.d_FT.ptr, c.d_prev.ptr));
+}
+
+int rbs_warmstart_train(rbs_ctx* h, int epochs, int batch, double lr, unsigned seed, double* loss) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  if (epochs < 0 || batch < 1 || !(lr > 0)) return finish(c, Status::Err(RBS_EINVAL, "warmstart_train: bad arguments"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  return finish(c, rbs::warm_train(c, epochs, batch, lr, seed, loss));
+}
+
+int rbs_warmstart_weights(rbs_ctx* h, float* out, const float* in, long long* count, float* scale) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  return finish(c, rbs::warm_weights(c, out, in, count, scale));
+}
+
+int rbs_warmstart_features(rbs_ctx* h, const double* F, const double* T, float* X) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  if (!F || !T || !X) return finish(c, Status::Err(RBS_EINVAL, "warmstart_features: null array"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  return finish(c, rbs::warm_features_host(c, F, T, X));
+}
+
+int rbs_warmstart_targets(rbs_ctx* h, const double* mu, float* coef) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  if (!mu || !coef) return finish(c, Status::Err(RBS_EINVAL, "warmstart_targets: null array"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  return finish(c, rbs::warm_targets_host(c, mu, coef));
+}
+
+int rbs_warmstart_mlp(rbs_ctx* h, int rows, const float* X, const float* Yt, float* Y, float* grads, double* loss) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  if (rows < 1 || !X) return finish(c, Status::Err(RBS_EINVAL, "warmstart_mlp: bad arguments"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  return finish(c, rbs::warm_mlp_host(c, rows, X, Yt, Y, grads, loss));
+}
+
+int rbs_get_state(rbs_ctx* h, double* centres, double* quats) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  for (int i = 0; i < 3 * c.n && centres; ++i) centres[i] = c.centres[i];
+  for (int i = 0; i < 4 * c.n && quats; ++i) quats[i] = c.quats[i];
+  return finish(c, Status::Ok());
 }
 
 int rbs_incident_density(rbs_ctx* h, const double* F, const double* T, double* rho) {

@@ -3,7 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
+#include <map>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -11,6 +13,8 @@
 #include "../../include/rbs.h"
 
 namespace rbs {
+
+struct WarmState;
 
 constexpr double kPi = 3.14159265358979323846;
 
@@ -78,6 +82,8 @@ struct Grid {
   DevBuf<double> d_interp;  // (p + 1) x nrot x np: singular-rule interpolation, target (j, 0)
   DevBuf<double> d_rotpts;  // (p + 1) x nrot x 4: rotated-rule points (x, y, z, weight)
   DevBuf<double> d_up;      // nup x np: interpolation to the upsampled grid
+  DevBuf<double> d_an;      // nbasis x np: analysis (grid values -> coefficients)
+  DevBuf<double> d_yg;      // np x nbasis: basis values at the grid nodes
   DevBuf<float> d_up32;
 };
 
@@ -110,6 +116,10 @@ struct Context {
   bool have_geometry = false;
 
   // per-particle device data
+  std::vector<int> grid_of;
+  DevBuf<long long> d_gtab_off, d_gtab_up_off;  // per particle: its grid's (t, lambda) in d_gtab
+  DevBuf<double> d_gtab, d_axes;
+  DevBuf<int> d_p, d_nphi, d_pup;
   DevBuf<double> d_centre, d_rot, d_area, d_tauinv;  // n x 3, n x 9, n, n x 9
   DevBuf<int> d_shape, d_nodes;                      // n: shape id, node count
   DevBuf<long long> d_offset;                        // n + 1
@@ -144,6 +154,8 @@ struct Context {
   DevBuf<const double*> d_upU;
   DevBuf<const float*> d_upU32;
 
+  std::map<const void*, int> resident;  // kernel -> resident blocks per SM
+
   // smooth pair-sum work list: (target begin, target end, source begin, source end)
   std::vector<longlong4> work;
   DevBuf<longlong4> d_work;
@@ -156,6 +168,9 @@ struct Context {
   double* h_pinned = nullptr;
 
   rbs_stats stats{};
+  WarmState* warm = nullptr;       // learned warm start (warmstart.cu)
+  DevBuf<double> d_prev;           // last solved density (previous-solution warm start)
+  bool have_prev = false;
   // kernel timing: (class, start, stop, units) of launches not yet harvested
   struct Timed {
     int cls;
@@ -176,6 +191,9 @@ struct Context {
 
 // ---- setup (setup.cu)
 Status build_geometry(Context& c);
+Status place_particles(Context& c);
+Status build_near(Context& c);
+Status update_configuration(Context& c, const double* centres, const double* quats);
 void gauss_legendre_newton(int n, std::vector<double>& t, std::vector<double>& w);
 
 // ---- dense kernels (linalg.cu)
@@ -204,6 +222,20 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
                       double* density, int* iters, bool device_io);
 Status incident_density(Context& c, const double* FT_dev, double* rho);
 Status rigid_velocities(Context& c, const double* u, double* vo_dev);
+
+// ---- learned warm start (warmstart.cu)
+Status warm_prepare(Context& c);
+Status warm_guess(Context& c, const double* FT_dev, double* mu0);
+Status warm_record(Context& c, const double* FT_dev, const double* mu);
+Status warm_train(Context& c, int epochs, int batch, double lr, unsigned seed, double* final_loss);
+Status warm_weights(Context& c, float* out, const float* in, long long* count, float* scale_inout);
+Status warm_features_host(Context& c, const double* F, const double* T, float* X);
+Status warm_targets_host(Context& c, const double* mu, float* coef);
+Status warm_mlp_host(Context& c, int rows, const float* X, const float* Yt, float* Y, float* grads, double* loss);
+void warm_release(Context& c);
+
+// ---- time stepping (timestep.cu)
+Status advance(Context& c, const double* F, const double* T, double dt, int steps, int scheme, double tol, int* iters);
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 

@@ -145,14 +145,15 @@ __global__ void __launch_bounds__(256) k_blocks(int mode, const int4* __restrict
 // density w_s mu_s.  Pairs on the same particle are excluded (their contribution is the singular
 // rule's); the select also removes the r = 0 self pair before it is used.
 template <int KIND>
-__global__ void __launch_bounds__(128) k_pairs64(const longlong4* __restrict__ work, const double4* __restrict__ x,
+__global__ void __launch_bounds__(128) k_pairs64(int nitems, const longlong4* __restrict__ work, const double4* __restrict__ x,
                                                  const double4* __restrict__ nrm, const int* __restrict__ pid,
                                                  const double* __restrict__ dens, double* __restrict__ y) {
   constexpr int TS = 128;
   __shared__ double4 sp[TS];
   __shared__ double4 sd[TS];
   __shared__ int spid[TS];
-  const longlong4 w = work[blockIdx.x];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  const longlong4 w = work[it];
   const long long t = w.x + threadIdx.x;
   const bool valid = t < w.y;
   double4 xt = make_double4(0, 0, 0, 0), nt = make_double4(0, 0, 0, 0);
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(128) k_pairs64(const longlong4* __restrict__ w
     atomicAdd(y + 3 * t + 1, sc * a1);
     atomicAdd(y + 3 * t + 2, sc * a2);
   }
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -220,87 +222,106 @@ __device__ __forceinline__ void two_sum_acc(float& s, float& e, float v) {
   s = t;
 }
 
-template <int KIND, bool MASK>
+template <int KIND, bool MASK, int NT>
 __device__ __forceinline__ void pair_tile32(const float4* __restrict__ sp, const float4* __restrict__ sd, int cnt,
-                                            float xx, float xy, float xz, float nx, float ny, float nz, int pt,
-                                            float& p0, float& p1, float& p2) {
-#pragma unroll 8
+                                            const float (&xt)[NT][3], const float (&nt)[NT][3], const int (&pt)[NT],
+                                            float (&acc)[NT][3]) {
+#pragma unroll 4
   for (int l = 0; l < cnt; ++l) {
     const float4 ps = sp[l];
     const float4 ds = sd[l];
-    const float dx = xx - ps.x, dy = xy - ps.y, dz = xz - ps.z;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float inv = rsqrtf(r2);
-    if (MASK && __float_as_int(ps.w) == pt) inv = 0.0f;
-    const float rr = fmaf(dx, ds.x, fmaf(dy, ds.y, dz * ds.z));
-    if (KIND == 0) {
-      const float inv2 = inv * inv;
-      const float rn = fmaf(dx, nx, fmaf(dy, ny, dz * nz));
-      const float c = (rn * rr) * (inv2 * inv2 * inv);
-      p0 = fmaf(c, dx, p0);
-      p1 = fmaf(c, dy, p1);
-      p2 = fmaf(c, dz, p2);
-    } else {
-      const float c = rr * (inv * inv * inv);
-      p0 = fmaf(c, dx, fmaf(ds.x, inv, p0));
-      p1 = fmaf(c, dy, fmaf(ds.y, inv, p1));
-      p2 = fmaf(c, dz, fmaf(ds.z, inv, p2));
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      const float dx = xt[u][0] - ps.x, dy = xt[u][1] - ps.y, dz = xt[u][2] - ps.z;
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      float inv = rsqrtf(r2);
+      if (MASK && __float_as_int(ps.w) == pt[u]) inv = 0.0f;
+      const float rr = fmaf(dx, ds.x, fmaf(dy, ds.y, dz * ds.z));
+      if (KIND == 0) {
+        const float inv2 = inv * inv;
+        const float rn = fmaf(dx, nt[u][0], fmaf(dy, nt[u][1], dz * nt[u][2]));
+        const float c = (rn * rr) * (inv2 * inv2 * inv);
+        acc[u][0] = fmaf(c, dx, acc[u][0]);
+        acc[u][1] = fmaf(c, dy, acc[u][1]);
+        acc[u][2] = fmaf(c, dz, acc[u][2]);
+      } else {
+        const float c = rr * (inv * inv * inv);
+        acc[u][0] = fmaf(c, dx, fmaf(ds.x, inv, acc[u][0]));
+        acc[u][1] = fmaf(c, dy, fmaf(ds.y, inv, acc[u][1]));
+        acc[u][2] = fmaf(c, dz, fmaf(ds.z, inv, acc[u][2]));
+      }
     }
   }
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(128) k_pairs32(const longlong4* __restrict__ work, const double4* __restrict__ x,
-                                                 const double4* __restrict__ nrm, const int* __restrict__ pid,
-                                                 const double* __restrict__ dens, double* __restrict__ y) {
-  constexpr int TS = 256;
+// NT targets per thread (block = 128 / NT threads over a 128-target work item): each staged source
+// feeds NT independent pair evaluations.
+template <int KIND, int NT>
+__global__ void __launch_bounds__(128 / NT) k_pairs32(int nitems, const longlong4* __restrict__ work, const double4* __restrict__ x,
+                                                      const double4* __restrict__ nrm, const int* __restrict__ pid,
+                                                      const double* __restrict__ dens, double* __restrict__ y) {
+  constexpr int TS = 256, NTH = 128 / NT;
   __shared__ float4 sp[TS];
   __shared__ float4 sd[TS];
-  const longlong4 w = work[blockIdx.x];
-  const long long t = w.x + threadIdx.x;
-  const bool valid = t < w.y;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  const longlong4 w = work[it];
   const double4 org = x[w.x];
-  float xx = 0, xy = 0, xz = 0, nx = 0, ny = 0, nz = 0;
-  int pt = -1;
-  if (valid) {
-    double4 xt = x[t];
-    double4 nt = nrm[t];
-    xx = (float)(xt.x - org.x);
-    xy = (float)(xt.y - org.y);
-    xz = (float)(xt.z - org.z);
-    nx = (float)nt.x;
-    ny = (float)nt.y;
-    nz = (float)nt.z;
-    pt = pid[t];
+  float xt[NT][3], nt[NT][3];
+  int pt[NT];
+  bool valid[NT];
+#pragma unroll
+  for (int u = 0; u < NT; ++u) {
+    const long long t = w.x + threadIdx.x + NTH * u;
+    valid[u] = t < w.y;
+    xt[u][0] = xt[u][1] = xt[u][2] = nt[u][0] = nt[u][1] = nt[u][2] = 0.0f;
+    pt[u] = -1;
+    if (valid[u]) {
+      const double4 a = x[t], nn = nrm[t];
+      xt[u][0] = (float)(a.x - org.x);
+      xt[u][1] = (float)(a.y - org.y);
+      xt[u][2] = (float)(a.z - org.z);
+      nt[u][0] = (float)nn.x;
+      nt[u][1] = (float)nn.y;
+      nt[u][2] = (float)nn.z;
+      pt[u] = pid[t];
+    }
   }
   const int pid_lo = pid[w.x], pid_hi = pid[w.y - 1];
-  float s0a = 0, s1a = 0, s2a = 0, e0 = 0, e1 = 0, e2 = 0;
+  float sa[NT][3], ea[NT][3];
+#pragma unroll
+  for (int u = 0; u < NT; ++u) sa[u][0] = sa[u][1] = sa[u][2] = ea[u][0] = ea[u][1] = ea[u][2] = 0.0f;
   for (long long s0 = w.z; s0 < w.w; s0 += TS) {
     const int cnt = (int)min((long long)TS, w.w - s0);
     __syncthreads();
-    for (int l = threadIdx.x; l < cnt; l += blockDim.x) {
+    for (int l = threadIdx.x; l < cnt; l += NTH) {
       const long long s = s0 + l;
-      double4 ps = x[s];
+      const double4 ps = x[s];
       const double* d = dens + 3 * s;
       sp[l] = make_float4((float)(ps.x - org.x), (float)(ps.y - org.y), (float)(ps.z - org.z), __int_as_float(pid[s]));
       sd[l] = make_float4((float)(ps.w * d[0]), (float)(ps.w * d[1]), (float)(ps.w * d[2]), 0.0f);
     }
     __syncthreads();
     const int tlo = pid[s0], thi = pid[s0 + cnt - 1];
-    float p0 = 0, p1 = 0, p2 = 0;
+    float p[NT][3];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) p[u][0] = p[u][1] = p[u][2] = 0.0f;
     if (thi < pid_lo || tlo > pid_hi)
-      pair_tile32<KIND, false>(sp, sd, cnt, xx, xy, xz, nx, ny, nz, pt, p0, p1, p2);
+      pair_tile32<KIND, false, NT>(sp, sd, cnt, xt, nt, pt, p);
     else
-      pair_tile32<KIND, true>(sp, sd, cnt, xx, xy, xz, nx, ny, nz, pt, p0, p1, p2);
-    two_sum_acc(s0a, e0, p0);
-    two_sum_acc(s1a, e1, p1);
-    two_sum_acc(s2a, e2, p2);
+      pair_tile32<KIND, true, NT>(sp, sd, cnt, xt, nt, pt, p);
+#pragma unroll
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) two_sum_acc(sa[u][c], ea[u][c], p[u][c]);
   }
-  if (valid) {
-    const double sc = KIND == 0 ? kTractionScale : kStokesletScale;
-    atomicAdd(y + 3 * t + 0, sc * ((double)s0a + (double)e0));
-    atomicAdd(y + 3 * t + 1, sc * ((double)s1a + (double)e1));
-    atomicAdd(y + 3 * t + 2, sc * ((double)s2a + (double)e2));
+  const double sc = KIND == 0 ? kTractionScale : kStokesletScale;
+#pragma unroll
+  for (int u = 0; u < NT; ++u) {
+    if (!valid[u]) continue;
+    const long long t = w.x + threadIdx.x + NTH * u;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) atomicAdd(y + 3 * t + c, sc * ((double)sa[u][c] + (double)ea[u][c]));
+  }
   }
 }
 
@@ -343,119 +364,139 @@ __device__ __forceinline__ void df_acc(dflt& acc, dflt v) {
   acc.l += s.l + v.l;
 }
 
-template <int KIND, bool MASK>
+template <int KIND, bool MASK, int NT>
 __device__ __forceinline__ void pair_tile_df(const float4* __restrict__ sph, const float4* __restrict__ spl,
                                              const float4* __restrict__ sdh, const float4* __restrict__ sdl, int cnt,
-                                             const dflt* xt, const dflt* nt, int pt, dflt* acc) {
+                                             const dflt (&xt)[NT][3], const dflt (&nt)[NT][3], const int (&pt)[NT],
+                                             dflt (&acc)[NT][3]) {
   for (int l = 0; l < cnt; ++l) {
     const float4 yh = sph[l], yl = spl[l], dh = sdh[l], dl = sdl[l];
-    dflt d[3];
-    d[0] = df_two_sum(xt[0].h, -yh.x);
-    d[0].l += xt[0].l - yl.x;
-    d[1] = df_two_sum(xt[1].h, -yh.y);
-    d[1].l += xt[1].l - yl.y;
-    d[2] = df_two_sum(xt[2].h, -yh.z);
-    d[2].l += xt[2].l - yl.z;
-    // r^2 = sum of d_c^2
-    float p[3], e[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      p[c] = d[c].h * d[c].h;
-      e[c] = fmaf(d[c].h, d[c].h, -p[c]);
-      e[c] = fmaf(d[c].h + d[c].h, d[c].l, e[c]);
-    }
-    dflt s1 = df_two_sum(p[0], p[1]);
-    dflt s2 = df_two_sum(s1.h, p[2]);
-    const float r2l = s1.l + s2.l + e[0] + e[1] + e[2];
-    const float r2h = s2.h;
-    // 1 / sqrt(r^2): y0 = rsqrtf, one Newton step
-    const float y0 = rsqrtf(r2h);
-    const float q = y0 * y0;
-    const float qe = fmaf(y0, y0, -q);
-    float t = fmaf(r2h, q, -1.0f);
-    t = fmaf(r2h, qe, t);
-    t = fmaf(r2l, q, t);
-    dflt inv = {y0, -0.5f * t * y0};
-    if (MASK && __float_as_int(yh.w) == pt) inv = {0.0f, 0.0f};
     const dflt den[3] = {{dh.x, dl.x}, {dh.y, dl.y}, {dh.z, dl.z}};
-    dflt rr = df_mul(d[0], den[0]);
-    rr = df_add(rr, df_mul(d[1], den[1]));
-    rr = df_add(rr, df_mul(d[2], den[2]));
-    const dflt inv2 = df_mul(inv, inv);
-    const dflt inv3 = df_mul(inv2, inv);
-    if (KIND == 0) {
-      const dflt inv5 = df_mul(inv3, inv2);
-      dflt rn = df_mul(d[0], nt[0]);
-      rn = df_add(rn, df_mul(d[1], nt[1]));
-      rn = df_add(rn, df_mul(d[2], nt[2]));
-      const dflt cc = df_mul(df_mul(rn, rr), inv5);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) df_acc(acc[c], df_mul(cc, d[c]));
-    } else {
-      const dflt cc = df_mul(rr, inv3);
+    for (int u = 0; u < NT; ++u) {
+      dflt d[3];
+      d[0] = df_two_sum(xt[u][0].h, -yh.x);
+      d[0].l += xt[u][0].l - yl.x;
+      d[1] = df_two_sum(xt[u][1].h, -yh.y);
+      d[1].l += xt[u][1].l - yl.y;
+      d[2] = df_two_sum(xt[u][2].h, -yh.z);
+      d[2].l += xt[u][2].l - yl.z;
+      // r^2 = sum of d_c^2
+      float p[3], e[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        df_acc(acc[c], df_mul(den[c], inv));
-        df_acc(acc[c], df_mul(cc, d[c]));
+        p[c] = d[c].h * d[c].h;
+        e[c] = fmaf(d[c].h, d[c].h, -p[c]);
+        e[c] = fmaf(d[c].h + d[c].h, d[c].l, e[c]);
+      }
+      const dflt s1 = df_two_sum(p[0], p[1]);
+      const dflt s2 = df_two_sum(s1.h, p[2]);
+      const float r2l = s1.l + s2.l + e[0] + e[1] + e[2];
+      const float r2h = s2.h;
+      // 1 / sqrt(r^2): y0 = rsqrtf, one Newton step
+      const float y0 = rsqrtf(r2h);
+      const float q = y0 * y0;
+      const float qe = fmaf(y0, y0, -q);
+      float t = fmaf(r2h, q, -1.0f);
+      t = fmaf(r2h, qe, t);
+      t = fmaf(r2l, q, t);
+      dflt inv = {y0, -0.5f * t * y0};
+      if (MASK && __float_as_int(yh.w) == pt[u]) inv = {0.0f, 0.0f};
+      dflt rr = df_mul(d[0], den[0]);
+      rr = df_add(rr, df_mul(d[1], den[1]));
+      rr = df_add(rr, df_mul(d[2], den[2]));
+      const dflt inv2 = df_mul(inv, inv);
+      const dflt inv3 = df_mul(inv2, inv);
+      if (KIND == 0) {
+        const dflt inv5 = df_mul(inv3, inv2);
+        dflt rn = df_mul(d[0], nt[u][0]);
+        rn = df_add(rn, df_mul(d[1], nt[u][1]));
+        rn = df_add(rn, df_mul(d[2], nt[u][2]));
+        const dflt cc = df_mul(df_mul(rn, rr), inv5);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) df_acc(acc[u][c], df_mul(cc, d[c]));
+      } else {
+        const dflt cc = df_mul(rr, inv3);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          df_acc(acc[u][c], df_mul(den[c], inv));
+          df_acc(acc[u][c], df_mul(cc, d[c]));
+        }
       }
     }
   }
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(128) k_pairs_df(const longlong4* __restrict__ work, const double4* __restrict__ x,
-                                                  const double4* __restrict__ nrm, const int* __restrict__ pid,
-                                                  const double* __restrict__ dens, double* __restrict__ y) {
-  constexpr int TS = 128;
+template <int KIND, int NT>
+__global__ void __launch_bounds__(128 / NT) k_pairs_df(int nitems, const longlong4* __restrict__ work, const double4* __restrict__ x,
+                                                       const double4* __restrict__ nrm, const int* __restrict__ pid,
+                                                       const double* __restrict__ dens, double* __restrict__ y) {
+  constexpr int TS = 128, NTH = 128 / NT;
   __shared__ float4 sph[TS], spl[TS], sdh[TS], sdl[TS];
-  const longlong4 w = work[blockIdx.x];
-  const long long t = w.x + threadIdx.x;
-  const bool valid = t < w.y;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  const longlong4 w = work[it];
   const double4 org = x[w.x];
-  dflt xt[3] = {{0, 0}, {0, 0}, {0, 0}}, nt[3] = {{0, 0}, {0, 0}, {0, 0}};
-  int pt = -1;
-  if (valid) {
-    const double4 a = x[t], nn = nrm[t];
-    xt[0] = df_split(a.x - org.x);
-    xt[1] = df_split(a.y - org.y);
-    xt[2] = df_split(a.z - org.z);
-    nt[0] = df_split(nn.x);
-    nt[1] = df_split(nn.y);
-    nt[2] = df_split(nn.z);
-    pt = pid[t];
+  dflt xt[NT][3], nt[NT][3];
+  int pt[NT];
+  bool valid[NT];
+#pragma unroll
+  for (int u = 0; u < NT; ++u) {
+    const long long t = w.x + threadIdx.x + NTH * u;
+    valid[u] = t < w.y;
+    double4 a = make_double4(org.x, org.y, org.z, 0.0), nn = make_double4(0, 0, 0, 0);
+    pt[u] = -1;
+    if (valid[u]) {
+      a = x[t];
+      nn = nrm[t];
+      pt[u] = pid[t];
+    }
+    xt[u][0] = df_split(a.x - org.x);
+    xt[u][1] = df_split(a.y - org.y);
+    xt[u][2] = df_split(a.z - org.z);
+    nt[u][0] = df_split(nn.x);
+    nt[u][1] = df_split(nn.y);
+    nt[u][2] = df_split(nn.z);
   }
   const int pid_lo = pid[w.x], pid_hi = pid[w.y - 1];
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  double a[NT][3];
+#pragma unroll
+  for (int u = 0; u < NT; ++u) a[u][0] = a[u][1] = a[u][2] = 0.0;
   for (long long s0 = w.z; s0 < w.w; s0 += TS) {
     const int cnt = (int)min((long long)TS, w.w - s0);
     __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      const long long s = s0 + threadIdx.x;
+    for (int l = threadIdx.x; l < cnt; l += NTH) {
+      const long long s = s0 + l;
       const double4 ps = x[s];
       const double* dd = dens + 3 * s;
       const dflt px = df_split(ps.x - org.x), py = df_split(ps.y - org.y), pz = df_split(ps.z - org.z);
       const dflt d0 = df_split(ps.w * dd[0]), d1 = df_split(ps.w * dd[1]), d2 = df_split(ps.w * dd[2]);
-      sph[threadIdx.x] = make_float4(px.h, py.h, pz.h, __int_as_float(pid[s]));
-      spl[threadIdx.x] = make_float4(px.l, py.l, pz.l, 0.0f);
-      sdh[threadIdx.x] = make_float4(d0.h, d1.h, d2.h, 0.0f);
-      sdl[threadIdx.x] = make_float4(d0.l, d1.l, d2.l, 0.0f);
+      sph[l] = make_float4(px.h, py.h, pz.h, __int_as_float(pid[s]));
+      spl[l] = make_float4(px.l, py.l, pz.l, 0.0f);
+      sdh[l] = make_float4(d0.h, d1.h, d2.h, 0.0f);
+      sdl[l] = make_float4(d0.l, d1.l, d2.l, 0.0f);
     }
     __syncthreads();
     const int tlo = pid[s0], thi = pid[s0 + cnt - 1];
-    dflt acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    dflt acc[NT][3];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) acc[u][0] = acc[u][1] = acc[u][2] = dflt{0.0f, 0.0f};
     if (thi < pid_lo || tlo > pid_hi)
-      pair_tile_df<KIND, false>(sph, spl, sdh, sdl, cnt, xt, nt, pt, acc);
+      pair_tile_df<KIND, false, NT>(sph, spl, sdh, sdl, cnt, xt, nt, pt, acc);
     else
-      pair_tile_df<KIND, true>(sph, spl, sdh, sdl, cnt, xt, nt, pt, acc);
-    a0 += (double)acc[0].h + (double)acc[0].l;
-    a1 += (double)acc[1].h + (double)acc[1].l;
-    a2 += (double)acc[2].h + (double)acc[2].l;
+      pair_tile_df<KIND, true, NT>(sph, spl, sdh, sdl, cnt, xt, nt, pt, acc);
+#pragma unroll
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a[u][c] += (double)acc[u][c].h + (double)acc[u][c].l;
   }
-  if (valid) {
-    const double sc = KIND == 0 ? kTractionScale : kStokesletScale;
-    atomicAdd(y + 3 * t + 0, sc * a0);
-    atomicAdd(y + 3 * t + 1, sc * a1);
-    atomicAdd(y + 3 * t + 2, sc * a2);
+  const double sc = KIND == 0 ? kTractionScale : kStokesletScale;
+#pragma unroll
+  for (int u = 0; u < NT; ++u) {
+    if (!valid[u]) continue;
+    const long long t = w.x + threadIdx.x + NTH * u;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) atomicAdd(y + 3 * t + c, sc * a[u][c]);
+  }
   }
 }
 
@@ -594,7 +635,117 @@ __global__ void __launch_bounds__(256) k_near(const int2* __restrict__ near, con
   }
 }
 
+// Near correction in float32 or double-float, sharing the tile loops of the smooth sums.  One
+// block per near pair; the block size covers the largest target particle in one or two passes;
+// sources (upsampled nodes of j with +w, base nodes of j with -w) are staged relative to the target
+// particle's centre.  Tile partials are added in float64.
+template <int KIND, bool DF>
+__global__ void __launch_bounds__(512) k_near_tiled(const int2* __restrict__ near, const long long* __restrict__ offset,
+                                                    const int* __restrict__ nodes, const double* __restrict__ centre,
+                                                    const int* __restrict__ up_index, const long long* __restrict__ up_off,
+                                                    const double4* __restrict__ x, const double4* __restrict__ nrm,
+                                                    const double* __restrict__ dens, const double4* __restrict__ upx,
+                                                    const double* __restrict__ upmu, double* __restrict__ y) {
+  constexpr int TS = 256;
+  __shared__ float4 s0[TS], s1[TS], s2[DF ? TS : 1], s3[DF ? TS : 1];
+  const int2 pr = near[blockIdx.x];
+  const int i = pr.x, j = pr.y;
+  const double ox = centre[3 * i], oy = centre[3 * i + 1], oz = centre[3 * i + 2];
+  const long long oi = offset[i], oj = offset[j];
+  const int npi = nodes[i], npj = nodes[j];
+  const int u = up_index[j];
+  const long long ub = up_off[u];
+  const int nup = (int)(up_off[u + 1] - ub);
+  const int total = nup + npj;
+  for (int tb = 0; tb < npi; tb += blockDim.x) {
+    const int tl = tb + threadIdx.x;
+    const bool valid = tl < npi;
+    double4 xt = make_double4(0, 0, 0, 0), nt = make_double4(0, 0, 0, 0);
+    if (valid) {
+      xt = x[oi + tl];
+      nt = nrm[oi + tl];
+    }
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int sb = 0; sb < total; sb += TS) {
+      const int cnt = min(TS, total - sb);
+      __syncthreads();
+      for (int l = threadIdx.x; l < cnt; l += blockDim.x) {
+        const int s = sb + l;
+        double4 ps;
+        double d0, d1, d2, wgt;
+        if (s < nup) {
+          ps = upx[ub + s];
+          wgt = ps.w;
+          d0 = upmu[3 * (ub + s)];
+          d1 = upmu[3 * (ub + s) + 1];
+          d2 = upmu[3 * (ub + s) + 2];
+        } else {
+          ps = x[oj + (s - nup)];
+          wgt = -ps.w;
+          const double* d = dens + 3 * (oj + (s - nup));
+          d0 = d[0];
+          d1 = d[1];
+          d2 = d[2];
+        }
+        if (DF) {
+          const dflt px = df_split(ps.x - ox), py = df_split(ps.y - oy), pz = df_split(ps.z - oz);
+          const dflt q0 = df_split(wgt * d0), q1 = df_split(wgt * d1), q2 = df_split(wgt * d2);
+          s0[l] = make_float4(px.h, py.h, pz.h, 0.0f);
+          s1[l] = make_float4(px.l, py.l, pz.l, 0.0f);
+          s2[l] = make_float4(q0.h, q1.h, q2.h, 0.0f);
+          s3[l] = make_float4(q0.l, q1.l, q2.l, 0.0f);
+        } else {
+          s0[l] = make_float4((float)(ps.x - ox), (float)(ps.y - oy), (float)(ps.z - oz), 0.0f);
+          s1[l] = make_float4((float)(wgt * d0), (float)(wgt * d1), (float)(wgt * d2), 0.0f);
+        }
+      }
+      __syncthreads();
+      if (DF) {
+        const dflt xd[1][3] = {{df_split(xt.x - ox), df_split(xt.y - oy), df_split(xt.z - oz)}};
+        const dflt nd[1][3] = {{df_split(nt.x), df_split(nt.y), df_split(nt.z)}};
+        const int none[1] = {-1};
+        dflt acc[1][3] = {{{0, 0}, {0, 0}, {0, 0}}};
+        pair_tile_df<KIND, false, 1>(s0, s1, s2, s3, cnt, xd, nd, none, acc);
+        a0 += (double)acc[0][0].h + (double)acc[0][0].l;
+        a1 += (double)acc[0][1].h + (double)acc[0][1].l;
+        a2 += (double)acc[0][2].h + (double)acc[0][2].l;
+      } else {
+        const float xf[1][3] = {{(float)(xt.x - ox), (float)(xt.y - oy), (float)(xt.z - oz)}};
+        const float nf[1][3] = {{(float)nt.x, (float)nt.y, (float)nt.z}};
+        const int none[1] = {-1};
+        float p[1][3] = {{0, 0, 0}};
+        pair_tile32<KIND, false, 1>(s0, s1, cnt, xf, nf, none, p);
+        a0 += p[0][0];
+        a1 += p[0][1];
+        a2 += p[0][2];
+      }
+    }
+    if (valid) {
+      const double sc = KIND == 0 ? kTractionScale : kStokesletScale;
+      atomicAdd(y + 3 * (oi + tl) + 0, sc * a0);
+      atomicAdd(y + 3 * (oi + tl) + 1, sc * a1);
+      atomicAdd(y + 3 * (oi + tl) + 2, sc * a2);
+    }
+  }
+}
+
 }  // namespace
+
+// Blocks of `kernel` that fit on the GPU at once (occupancy x SMs), capped at the item count: the
+// pair kernels loop over their work items with this persistent grid, so the last wave is not a
+// mostly idle second pass over the SMs.
+static int resident_grid(Context& c, const void* kernel, int threads, int items) {
+  auto it = c.resident.find(kernel);
+  int per_sm = 0;
+  if (it == c.resident.end()) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    c.resident[kernel] = per_sm;
+  } else {
+    per_sm = it->second;
+  }
+  return std::max(1, std::min(items, per_sm * std::max(1, c.sm_count)));
+}
 
 // ------------------------------------------------------------------------------------------
 
@@ -637,21 +788,24 @@ Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y) {
     int cls = f32 ? (kind == 0 ? RBS_KC_PAIR_K32 : RBS_KC_PAIR_S32) : (kind == 0 ? RBS_KC_PAIR_K64 : RBS_KC_PAIR_S64);
     if (prec == RBS_PREC_DF) cls = kind == 0 ? RBS_KC_PAIR_KDF : RBS_KC_PAIR_SDF;
     KernelTimer timer(c, cls);
+    const int g64 = resident_grid(c, (const void*)k_pairs64<0>, 128, nw);
+    const int g32 = resident_grid(c, (const void*)k_pairs32<0, 2>, 64, nw);
+    const int gdf = resident_grid(c, (const void*)k_pairs_df<0, 2>, 64, nw);
     if (prec == RBS_PREC_DF) {
       if (kind == 0)
-        k_pairs_df<0><<<nw, 128, 0, c.stream>>>(c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
+        k_pairs_df<0, 2><<<gdf, 64, 0, c.stream>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
       else
-        k_pairs_df<1><<<nw, 128, 0, c.stream>>>(c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
+        k_pairs_df<1, 2><<<gdf, 64, 0, c.stream>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
     } else if (f32) {
       if (kind == 0)
-        k_pairs32<0><<<nw, 128, 0, c.stream>>>(c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
+        k_pairs32<0, 2><<<g32, 64, 0, c.stream>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
       else
-        k_pairs32<1><<<nw, 128, 0, c.stream>>>(c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
+        k_pairs32<1, 2><<<g32, 64, 0, c.stream>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
     } else {
       if (kind == 0)
-        k_pairs64<0><<<nw, 128, 0, c.stream>>>(c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
+        k_pairs64<0><<<g64, 128, 0, c.stream>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
       else
-        k_pairs64<1><<<nw, 128, 0, c.stream>>>(c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
+        k_pairs64<1><<<g64, 128, 0, c.stream>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
     }
     RBS_CUDA_TRY(cudaGetLastError());
     timer.done((double)c.stats.far_pairs);
@@ -678,14 +832,20 @@ Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y) {
 #define RBS_NEAR_ARGS                                                                                            \
   c.d_near.ptr, c.d_offset.ptr, c.d_nodes.ptr, c.d_centre.ptr, c.d_up_index.ptr, c.d_up_off.ptr, c.d_x.ptr, \
       c.d_nrm.ptr, x, c.d_up_x.ptr, c.d_up_mu.ptr, y
-    if (kind == 0) {
-      if (f32)
-        k_near<0, float><<<nn, 256, 0, c.stream>>>(RBS_NEAR_ARGS);
+    const int nthr = std::min(512, std::max(64, (c.max_np + 31) / 32 * 32));
+    if (prec == RBS_PREC_DF) {
+      if (kind == 0)
+        k_near_tiled<0, true><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
       else
-        k_near<0, double><<<nn, 256, 0, c.stream>>>(RBS_NEAR_ARGS);
+        k_near_tiled<1, true><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
+    } else if (f32) {
+      if (kind == 0)
+        k_near_tiled<0, false><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
+      else
+        k_near_tiled<1, false><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
     } else {
-      if (f32)
-        k_near<1, float><<<nn, 256, 0, c.stream>>>(RBS_NEAR_ARGS);
+      if (kind == 0)
+        k_near<0, double><<<nn, 256, 0, c.stream>>>(RBS_NEAR_ARGS);
       else
         k_near<1, double><<<nn, 256, 0, c.stream>>>(RBS_NEAR_ARGS);
     }

@@ -421,7 +421,8 @@ static Status build_grid(Context& c, Grid& g) {
   DevBuf<double4> gp;
   RBS_TRY(gp.alloc(g.np));
   k_grid_points<<<cdiv(g.np, 128), 128, 0, s>>>(g.p, g.nphi, g.d_t.ptr, g.d_lam.ptr, gp.ptr);
-  DevBuf<double> Yg, An;
+  DevBuf<double>& Yg = g.d_yg;
+  DevBuf<double>& An = g.d_an;
   RBS_TRY(Yg.alloc((size_t)g.np * g.nbasis));
   RBS_TRY(An.alloc((size_t)g.np * g.nbasis));
   k_sh_at_points<<<cdiv(g.np, 128), 128, 0, s>>>(g.p, g.mmax, g.nbasis, gp.ptr, g.np, Yg.ptr);
@@ -501,6 +502,133 @@ static Status build_self_blocks(Context& c, int gi, const std::vector<int>& shap
   return Status::Ok();
 }
 
+// Lab-frame nodes, normals, weights and moments of every particle from the current centres and
+// rotations (Eq. 40 with the body frame as reference; Eq. 18).
+Status place_particles(Context& c) {
+  cudaStream_t s = c.stream;
+  const int n = c.n;
+  RBS_TRY(upload(c.d_centre, c.centres, s));
+  RBS_TRY(upload(c.d_rot, c.rot, s));
+  if (c.d_x.n != (size_t)c.N) {
+    RBS_TRY(c.d_x.alloc(c.N));
+    RBS_TRY(c.d_nrm.alloc(c.N));
+    RBS_TRY(c.d_pid.alloc(c.N));
+    RBS_TRY(c.d_area.alloc(n));
+    RBS_TRY(c.d_tauinv.alloc((size_t)9 * n));
+  }
+  int maxnp = 0;
+  for (int i = 0; i < n; ++i) maxnp = std::max(maxnp, (int)(c.offset[i + 1] - c.offset[i]));
+  dim3 grd(cdiv(maxnp, 128), std::min(n, 65535));
+  k_nodes<<<grd, 128, 0, s>>>(n, c.d_offset.ptr, c.d_p.ptr, c.d_nphi.ptr, c.d_axes.ptr, c.d_centre.ptr, c.d_rot.ptr,
+                              c.d_gtab_off.ptr, c.d_gtab.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr);
+  k_moments<<<n, 256, 0, s>>>(n, c.d_offset.ptr, c.d_x.ptr, c.d_centre.ptr, c.d_area.ptr, c.d_tauinv.ptr);
+  RBS_CUDA_TRY(cudaGetLastError());
+  return Status::Ok();
+}
+
+// Near-pair list (Section 3, upsampling for close particles) and the upsampled source nodes.
+Status build_near(Context& c) {
+  cudaStream_t s = c.stream;
+  const int n = c.n;
+  // near pairs: |c_i - c_j| < R_i + R_j + delta within one suspension, by a cell list
+  c.near_pairs.clear();
+  {
+    std::vector<double> R(n);
+    double rmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      R[i] = std::max(c.axes[3 * i], std::max(c.axes[3 * i + 1], c.axes[3 * i + 2]));
+      rmax = std::max(rmax, R[i]);
+    }
+    double cell = 2.0 * rmax + c.opt.near_delta;
+    std::unordered_map<long long, std::vector<int>> cells;
+    auto key = [&](long long a, long long b, long long d) { return (a * 73856093LL) ^ (b * 19349663LL) ^ (d * 83492791LL); };
+    std::vector<long long> ci(3 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+      for (int d = 0; d < 3; ++d) ci[3 * i + d] = (long long)std::floor(c.centres[3 * i + d] / cell);
+      cells[key(ci[3 * i], ci[3 * i + 1], ci[3 * i + 2])].push_back(i);
+    }
+    for (int i = 0; i < n; ++i) {
+      std::vector<int> cand;
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            auto it = cells.find(key(ci[3 * i] + dx, ci[3 * i + 1] + dy, ci[3 * i + 2] + dz));
+            if (it == cells.end()) continue;
+            for (int j : it->second) cand.push_back(j);
+          }
+      std::sort(cand.begin(), cand.end());
+      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+      for (int j : cand) {
+        if (j == i || c.sid[j] != c.sid[i]) continue;
+        double dx = c.centres[3 * i] - c.centres[3 * j], dy = c.centres[3 * i + 1] - c.centres[3 * j + 1],
+               dz = c.centres[3 * i + 2] - c.centres[3 * j + 2];
+        double d = std::sqrt(dx * dx + dy * dy + dz * dz);
+        double rmin_i = std::min(c.axes[3 * i], std::min(c.axes[3 * i + 1], c.axes[3 * i + 2]));
+        double rmin_j = std::min(c.axes[3 * j], std::min(c.axes[3 * j + 1], c.axes[3 * j + 2]));
+        if (d < rmin_i + rmin_j)
+          return Status::Err(RBS_EOVERLAP, "particles " + std::to_string(i) + " and " + std::to_string(j) +
+                                               " overlap (inscribed spheres intersect)");
+        if (d < R[i] + R[j] + c.opt.near_delta) c.near_pairs.push_back(make_int2(i, j));
+      }
+    }
+  }
+  RBS_TRY(upload(c.d_near, c.near_pairs, s));
+  // upsampled sources
+  c.up_index.assign(n, -1);
+  c.up_particle.clear();
+  c.up_offset.clear();
+  c.n_up_nodes = 0;
+  for (const int2& pr : c.near_pairs) {
+    int j = pr.y;
+    if (c.up_index[j] < 0) {
+      c.up_index[j] = (int)c.up_particle.size();
+      c.up_particle.push_back(j);
+      c.up_offset.push_back(c.n_up_nodes);
+      c.n_up_nodes += c.grids[c.grid_of[j]]->nup;
+    }
+  }
+  c.up_offset.push_back(c.n_up_nodes);
+  {
+    std::vector<const double*> U;
+    std::vector<const float*> U32;
+    for (int j : c.up_particle) {
+      U.push_back(c.grids[c.grid_of[j]]->d_up.ptr);
+      U32.push_back(c.grids[c.grid_of[j]]->d_up32.ptr);
+    }
+    RBS_TRY(upload(c.d_upU, U, s));
+    RBS_TRY(upload(c.d_upU32, U32, s));
+  }
+  RBS_TRY(upload(c.d_up_particle, c.up_particle, s));
+  RBS_TRY(upload(c.d_up_off, c.up_offset, s));
+  RBS_TRY(upload(c.d_up_index, c.up_index, s));
+  RBS_TRY(c.d_up_x.alloc(c.n_up_nodes));
+  RBS_TRY(c.d_up_mu.alloc(3 * c.n_up_nodes));
+  if (!c.up_particle.empty()) {
+    int maxnup = 0;
+    for (Grid* g : c.grids) maxnup = std::max(maxnup, g->nup);
+    dim3 grd(cdiv(maxnup, 128), (unsigned)std::min<size_t>(c.up_particle.size(), 65535));
+    k_up_nodes<<<grd, 128, 0, s>>>((int)c.up_particle.size(), c.d_up_particle.ptr, c.d_up_off.ptr, c.d_p.ptr, c.d_nphi.ptr,
+                                   c.d_pup.ptr, c.d_axes.ptr, c.d_centre.ptr, c.d_rot.ptr, c.d_gtab_up_off.ptr, c.d_gtab.ptr,
+                                   c.d_up_x.ptr);
+    RBS_CUDA_TRY(cudaGetLastError());
+  }
+
+  c.near_pair_nodes = 0;
+  for (const int2& pr : c.near_pairs)
+    c.near_pair_nodes += (double)(c.offset[pr.x + 1] - c.offset[pr.x]) *
+                         (c.grids[c.grid_of[pr.y]]->nup + (c.offset[pr.y + 1] - c.offset[pr.y]));
+  c.stats.near_pairs = (long long)c.near_pairs.size();
+  return Status::Ok();
+}
+
+Status update_configuration(Context& c, const double* centres, const double* quats) {
+  for (int i = 0; i < 3 * c.n; ++i) c.centres[i] = centres[i];
+  for (int i = 0; i < 4 * c.n; ++i) c.quats[i] = quats[i];
+  for (int i = 0; i < c.n; ++i) quat_to_rot_host(&c.quats[4 * i], &c.rot[9 * i]);
+  RBS_TRY(place_particles(c));
+  return build_near(c);
+}
+
 Status build_geometry(Context& c) {
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = c.stream;
@@ -574,18 +702,14 @@ Status build_geometry(Context& c) {
     gtab_up_off[i] = grid_tab_up_off[grid_of[i]];
     pup[i] = c.grids[grid_of[i]]->pup;
   }
-  DevBuf<long long> d_gtab_off, d_gtab_up_off;
-  DevBuf<double> d_gtab, d_axes;
-  DevBuf<int> d_p, d_nphi, d_pup;
-  RBS_TRY(upload(d_gtab_off, gtab_off, s));
-  RBS_TRY(upload(d_gtab_up_off, gtab_up_off, s));
-  RBS_TRY(upload(d_gtab, gtab, s));
-  RBS_TRY(upload(d_axes, c.axes, s));
-  RBS_TRY(upload(d_p, c.p, s));
-  RBS_TRY(upload(d_nphi, c.nphi, s));
-  RBS_TRY(upload(d_pup, pup, s));
-  RBS_TRY(upload(c.d_centre, c.centres, s));
-  RBS_TRY(upload(c.d_rot, c.rot, s));
+  c.grid_of = grid_of;
+  RBS_TRY(upload(c.d_gtab_off, gtab_off, s));
+  RBS_TRY(upload(c.d_gtab_up_off, gtab_up_off, s));
+  RBS_TRY(upload(c.d_gtab, gtab, s));
+  RBS_TRY(upload(c.d_axes, c.axes, s));
+  RBS_TRY(upload(c.d_p, c.p, s));
+  RBS_TRY(upload(c.d_nphi, c.nphi, s));
+  RBS_TRY(upload(c.d_pup, pup, s));
   RBS_TRY(upload(c.d_offset, c.offset, s));
   RBS_TRY(upload(c.d_shape, c.shape_of, s));
   std::vector<int> nodes(n);
@@ -596,15 +720,7 @@ Status build_geometry(Context& c) {
   RBS_TRY(c.d_pid.alloc(c.N));
   RBS_TRY(c.d_area.alloc(n));
   RBS_TRY(c.d_tauinv.alloc((size_t)9 * n));
-  {
-    int maxnp = 0;
-    for (int i = 0; i < n; ++i) maxnp = std::max(maxnp, nodes[i]);
-    dim3 grd(cdiv(maxnp, 128), std::min(n, 65535));
-    k_nodes<<<grd, 128, 0, s>>>(n, c.d_offset.ptr, d_p.ptr, d_nphi.ptr, d_axes.ptr, c.d_centre.ptr, c.d_rot.ptr,
-                                d_gtab_off.ptr, d_gtab.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr);
-    k_moments<<<n, 256, 0, s>>>(n, c.d_offset.ptr, c.d_x.ptr, c.d_centre.ptr, c.d_area.ptr, c.d_tauinv.ptr);
-    RBS_CUDA_TRY(cudaGetLastError());
-  }
+  RBS_TRY(place_particles(c));
 
   // self blocks (body frame) of every shape
   RBS_TRY(c.d_blockK.alloc(c.block_elems));
@@ -648,88 +764,7 @@ Status build_geometry(Context& c) {
   k_to_float<<<1024, 256, 0, s>>>(c.d_blockK.ptr, c.d_blockK32.ptr, (long long)c.block_elems);
   RBS_CUDA_TRY(cudaGetLastError());
 
-  // near pairs: |c_i - c_j| < R_i + R_j + delta within one suspension, by a cell list
-  c.near_pairs.clear();
-  {
-    std::vector<double> R(n);
-    double rmax = 0.0;
-    for (int i = 0; i < n; ++i) {
-      R[i] = std::max(c.axes[3 * i], std::max(c.axes[3 * i + 1], c.axes[3 * i + 2]));
-      rmax = std::max(rmax, R[i]);
-    }
-    double cell = 2.0 * rmax + c.opt.near_delta;
-    std::unordered_map<long long, std::vector<int>> cells;
-    auto key = [&](long long a, long long b, long long d) { return (a * 73856093LL) ^ (b * 19349663LL) ^ (d * 83492791LL); };
-    std::vector<long long> ci(3 * (size_t)n);
-    for (int i = 0; i < n; ++i) {
-      for (int d = 0; d < 3; ++d) ci[3 * i + d] = (long long)std::floor(c.centres[3 * i + d] / cell);
-      cells[key(ci[3 * i], ci[3 * i + 1], ci[3 * i + 2])].push_back(i);
-    }
-    for (int i = 0; i < n; ++i) {
-      std::vector<int> cand;
-      for (int dx = -1; dx <= 1; ++dx)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dz = -1; dz <= 1; ++dz) {
-            auto it = cells.find(key(ci[3 * i] + dx, ci[3 * i + 1] + dy, ci[3 * i + 2] + dz));
-            if (it == cells.end()) continue;
-            for (int j : it->second) cand.push_back(j);
-          }
-      std::sort(cand.begin(), cand.end());
-      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-      for (int j : cand) {
-        if (j == i || c.sid[j] != c.sid[i]) continue;
-        double dx = c.centres[3 * i] - c.centres[3 * j], dy = c.centres[3 * i + 1] - c.centres[3 * j + 1],
-               dz = c.centres[3 * i + 2] - c.centres[3 * j + 2];
-        double d = std::sqrt(dx * dx + dy * dy + dz * dz);
-        double rmin_i = std::min(c.axes[3 * i], std::min(c.axes[3 * i + 1], c.axes[3 * i + 2]));
-        double rmin_j = std::min(c.axes[3 * j], std::min(c.axes[3 * j + 1], c.axes[3 * j + 2]));
-        if (d < rmin_i + rmin_j)
-          return Status::Err(RBS_EOVERLAP, "particles " + std::to_string(i) + " and " + std::to_string(j) +
-                                               " overlap (inscribed spheres intersect)");
-        if (d < R[i] + R[j] + c.opt.near_delta) c.near_pairs.push_back(make_int2(i, j));
-      }
-    }
-  }
-  RBS_TRY(upload(c.d_near, c.near_pairs, s));
-  // upsampled sources
-  c.up_index.assign(n, -1);
-  c.up_particle.clear();
-  c.up_offset.clear();
-  c.n_up_nodes = 0;
-  for (const int2& pr : c.near_pairs) {
-    int j = pr.y;
-    if (c.up_index[j] < 0) {
-      c.up_index[j] = (int)c.up_particle.size();
-      c.up_particle.push_back(j);
-      c.up_offset.push_back(c.n_up_nodes);
-      c.n_up_nodes += c.grids[grid_of[j]]->nup;
-    }
-  }
-  c.up_offset.push_back(c.n_up_nodes);
-  {
-    std::vector<const double*> U;
-    std::vector<const float*> U32;
-    for (int j : c.up_particle) {
-      U.push_back(c.grids[grid_of[j]]->d_up.ptr);
-      U32.push_back(c.grids[grid_of[j]]->d_up32.ptr);
-    }
-    RBS_TRY(upload(c.d_upU, U, s));
-    RBS_TRY(upload(c.d_upU32, U32, s));
-  }
-  RBS_TRY(upload(c.d_up_particle, c.up_particle, s));
-  RBS_TRY(upload(c.d_up_off, c.up_offset, s));
-  RBS_TRY(upload(c.d_up_index, c.up_index, s));
-  RBS_TRY(c.d_up_x.alloc(c.n_up_nodes));
-  RBS_TRY(c.d_up_mu.alloc(3 * c.n_up_nodes));
-  if (!c.up_particle.empty()) {
-    int maxnup = 0;
-    for (Grid* g : c.grids) maxnup = std::max(maxnup, g->nup);
-    dim3 grd(cdiv(maxnup, 128), (unsigned)std::min<size_t>(c.up_particle.size(), 65535));
-    k_up_nodes<<<grd, 128, 0, s>>>((int)c.up_particle.size(), c.d_up_particle.ptr, c.d_up_off.ptr, d_p.ptr, d_nphi.ptr,
-                                   d_pup.ptr, d_axes.ptr, c.d_centre.ptr, c.d_rot.ptr, d_gtab_up_off.ptr, d_gtab.ptr,
-                                   c.d_up_x.ptr);
-    RBS_CUDA_TRY(cudaGetLastError());
-  }
+  RBS_TRY(build_near(c));
 
   // smooth pair-sum work list: target tiles of 128 nodes, never straddling a suspension, each
   // paired with source chunks of that suspension; chunks split so the grid covers the GPU.
@@ -746,11 +781,13 @@ Status build_geometry(Context& c) {
     const long long TT = 128;
     long long tiles = 0;
     for (auto& sp : susp) tiles += (sp.second - sp.first + TT - 1) / TT;
-    long long want = 4LL * std::max(1, c.sm_count);
+    // about 96 items per SM, so a persistent grid of ~12 resident blocks per SM runs ~8 rounds and
+    // its last round is nearly full; source chunks stay >= 2048 nodes
+    long long want = 96LL * std::max(1, c.sm_count);
     int splits = (int)std::max(1LL, (want + tiles - 1) / std::max(1LL, tiles));
     for (auto& sp : susp) {
       long long ns = sp.second - sp.first;
-      int sc = (int)std::min<long long>(splits, std::max(1LL, ns / 256));
+      int sc = (int)std::min<long long>(splits, std::max(1LL, ns / 2048));
       long long chunk = (ns + sc - 1) / sc;
       for (long long tb = sp.first; tb < sp.second; tb += TT)
         for (long long sb = sp.first; sb < sp.second; sb += chunk) {
@@ -788,7 +825,7 @@ Status build_geometry(Context& c) {
   c.stats.total_nodes = c.N;
   c.stats.n_particles = n;
   c.stats.n_shapes = (int)c.shapes.size();
-  c.stats.near_pairs = (long long)c.near_pairs.size();
+
   long long fp = 0;
   {
     int i = 0;
@@ -804,9 +841,7 @@ Status build_geometry(Context& c) {
   c.stats.far_pairs = fp;
   c.particle_block_entries = 0;
   for (int k = 0; k < n; ++k) c.particle_block_entries += 9.0 * nodes[k] * nodes[k];
-  c.near_pair_nodes = 0;
-  for (const int2& pr : c.near_pairs)
-    c.near_pair_nodes += (double)nodes[pr.x] * (c.grids[grid_of[pr.y]]->nup + nodes[pr.y]);
+
   c.stats.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   c.have_geometry = true;
   return Status::Ok();

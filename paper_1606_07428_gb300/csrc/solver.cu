@@ -399,13 +399,24 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
   int total_iters = 0, refinements = 0;
   double rel = 0.0;
   bool converged = true;
+  // initial guess: zero, the previous solution, or the learned warm start
+  bool have_x0 = false;
+  double* x0 = d;  // the first GMRES call starts from here
+  if (bnorm > 0.0 && c.opt.warm_start == RBS_WARM_PREVIOUS && c.have_prev && c.d_prev.n == (size_t)n3) {
+    RBS_CUDA_TRY(cudaMemcpyAsync(x0, c.d_prev.ptr, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+    have_x0 = true;
+  } else if (bnorm > 0.0 && c.opt.warm_start == RBS_WARM_LEARNED) {
+    RBS_TRY(warm_guess(c, c.d_FT.ptr, x0));
+    have_x0 = true;
+  }
   // 2. the scattered density
   if (bnorm == 0.0) {
     RBS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n3, c.stream));
   } else if (c.opt.precision == RBS_PREC_FP64) {
     int its = 0;
     double res = 0.0;
-    RBS_TRY(gmres(c, RBS_PREC_FP64, b, x, true, tol * bnorm, c.opt.max_iters, &its, &res, &converged));
+    if (have_x0) RBS_CUDA_TRY(cudaMemcpyAsync(x, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+    RBS_TRY(gmres(c, RBS_PREC_FP64, b, x, !have_x0, tol * bnorm, c.opt.max_iters, &its, &res, &converged));
     total_iters = its;
     rel = res / bnorm;
   } else {
@@ -418,7 +429,8 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
       double res = 0.0;
       bool conv_inner = false;
       // inner solve of A d = r with the float32 operator
-      RBS_TRY(gmres(c, RBS_PREC_MIXED, r, d, true, c.opt.inner_tol * rn, c.opt.max_iters - total_iters, &its, &res,
+      const bool start_zero = !(have_x0 && refinements == 0);  // d holds the warm start on the first pass
+      RBS_TRY(gmres(c, RBS_PREC_MIXED, r, d, start_zero, c.opt.inner_tol * rn, c.opt.max_iters - total_iters, &its, &res,
                     &conv_inner));
       total_iters += its;
       c.stats.launches++;
@@ -441,6 +453,10 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
     }
     rel = rn / bnorm;
   }
+  // keep the density for a previous-solution warm start and for recording training samples
+  if (c.d_prev.n != (size_t)n3) RBS_TRY(c.d_prev.alloc(n3));
+  RBS_CUDA_TRY(cudaMemcpyAsync(c.d_prev.ptr, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+  c.have_prev = true;
   // 3. u = S[rho + mu] and the rigid velocities
   double* sigma = c.d_vec[6].ptr;
   double* u = c.d_vec[4].ptr;

@@ -42,8 +42,18 @@ EXPORTS = [
     "rbs_default_options", "rbs_create", "rbs_destroy", "rbs_set_geometry", "rbs_total_nodes",
     "rbs_get_surface", "rbs_mobility_solve", "rbs_mobility_solve_device", "rbs_incident_density",
     "rbs_rigid_velocities", "rbs_apply_operator", "rbs_apply_operator_device", "rbs_get_stats",
-    "rbs_reset_stats", "rbs_last_error", "rbs_rigid_velocities_noalloc",
+    "rbs_reset_stats", "rbs_last_error", "rbs_rigid_velocities_noalloc", "rbs_advance", "rbs_get_state",
+    "rbs_warmstart_record", "rbs_warmstart_train", "rbs_warmstart_weights", "rbs_warmstart_features",
+    "rbs_warmstart_targets", "rbs_warmstart_mlp",
 ]
+
+RBS_WARM_ZERO = 0
+RBS_WARM_PREVIOUS = 1
+RBS_WARM_LEARNED = 2
+
+RBS_RK_EULER = 1
+RBS_RK_TRAPEZOID = 2
+RBS_RK4 = 4
 
 
 class rbs_options(ctypes.Structure):
@@ -62,6 +72,7 @@ class rbs_options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("timing", ctypes.c_int),
         ("refine_precision", ctypes.c_int),
+        ("warm_start", ctypes.c_int),
     ]
 
 
@@ -129,6 +140,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rbs_incident_density": (I, [P, P, P, P]),
         "rbs_rigid_velocities": (I, [P, P, P, P]),
         "rbs_rigid_velocities_noalloc": (I, [P, P, P, P]),
+        "rbs_advance": (I, [P, P, P, D, I, I, D, P]),
+        "rbs_get_state": (I, [P, P, P]),
+        "rbs_warmstart_record": (I, [P, P, P]),
+        "rbs_warmstart_train": (I, [P, I, I, D, ctypes.c_uint, P]),
+        "rbs_warmstart_weights": (I, [P, P, P, P, P]),
+        "rbs_warmstart_features": (I, [P, P, P, P]),
+        "rbs_warmstart_targets": (I, [P, P, P]),
+        "rbs_warmstart_mlp": (I, [P, I, P, P, P, P, P]),
         "rbs_apply_operator": (I, [P, I, I, P, P]),
         "rbs_apply_operator_device": (I, [P, I, I, P, P]),
         "rbs_get_stats": (I, [P, ctypes.POINTER(rbs_stats)]),
@@ -236,6 +255,78 @@ def rbs_mobility_solve_device(ctx, F_dev, T_dev, tol, v_dev, omega_dev, density_
                                           _ptr(density_dev), ctypes.addressof(its))
     _check(ctx, rc, (RBS_ENOTCONV,) if allow_notconv else ())
     return its.value
+
+
+def rbs_advance(ctx, F, T, dt, steps, scheme=RBS_RK4, tol=1e-10) -> int:
+    F = _f64(F, (-1, 3))
+    T = _f64(T, F.shape)
+    its = ctypes.c_int(0)
+    _check(ctx, load().rbs_advance(ctx, _ptr(F), _ptr(T), float(dt), int(steps), int(scheme), float(tol),
+                                   ctypes.addressof(its)))
+    return its.value
+
+
+def rbs_warmstart_record(ctx, F, T) -> None:
+    F = _f64(F, (-1, 3))
+    T = _f64(T, F.shape)
+    _check(ctx, load().rbs_warmstart_record(ctx, _ptr(F), _ptr(T)))
+
+
+def rbs_warmstart_train(ctx, epochs, batch=256, lr=1e-3, seed=0) -> float:
+    loss = ctypes.c_double(0.0)
+    _check(ctx, load().rbs_warmstart_train(ctx, int(epochs), int(batch), float(lr), int(seed), ctypes.addressof(loss)))
+    return loss.value
+
+
+def rbs_warmstart_weights(ctx, params: np.ndarray | None = None, scale: float = 1.0):
+    """Without params: returns (flattened float32 parameters, output scale).  With params: loads them."""
+    count = ctypes.c_longlong(0)
+    sc = ctypes.c_float(scale)
+    lib = load()
+    if params is None:
+        _check(ctx, lib.rbs_warmstart_weights(ctx, None, None, ctypes.addressof(count), None))
+        out = np.zeros(count.value, np.float32)
+        _check(ctx, lib.rbs_warmstart_weights(ctx, _ptr(out), None, None, ctypes.addressof(sc)))
+        return out, sc.value
+    p = np.ascontiguousarray(params, np.float32)
+    _check(ctx, lib.rbs_warmstart_weights(ctx, None, _ptr(p), ctypes.addressof(count), ctypes.addressof(sc)))
+    return None
+
+
+def rbs_warmstart_features(ctx, F, T, n) -> np.ndarray:
+    F = _f64(F, (-1, 3))
+    T = _f64(T, F.shape)
+    X = np.zeros((n, 128), np.float32)
+    _check(ctx, load().rbs_warmstart_features(ctx, _ptr(F), _ptr(T), _ptr(X)))
+    return X
+
+
+def rbs_warmstart_targets(ctx, mu, n, n_out) -> np.ndarray:
+    mu = _f64(mu, (-1, 3))
+    out = np.zeros((n, n_out), np.float32)
+    _check(ctx, load().rbs_warmstart_targets(ctx, _ptr(mu), _ptr(out)))
+    return out
+
+
+def rbs_warmstart_mlp(ctx, X, n_out, Yt=None, n_params=None):
+    X = np.ascontiguousarray(X, np.float32)
+    rows = X.shape[0]
+    Y = np.zeros((rows, n_out), np.float32)
+    grads = None
+    loss = ctypes.c_double(0.0)
+    yt = None
+    if Yt is not None:
+        yt = np.ascontiguousarray(Yt, np.float32)
+        grads = np.zeros(n_params, np.float32)
+    _check(ctx, load().rbs_warmstart_mlp(ctx, rows, _ptr(X), _ptr(yt), _ptr(Y), _ptr(grads), ctypes.addressof(loss)))
+    return Y, grads, loss.value
+
+
+def rbs_get_state(ctx, n):
+    c = np.zeros((n, 3))
+    q = np.zeros((n, 4))
+    _check(ctx, load().rbs_get_state(ctx, _ptr(c), _ptr(q)))
+    return c, q
 
 
 def rbs_incident_density(ctx, F, T) -> np.ndarray:

@@ -208,8 +208,16 @@ def c5_sedimenting() -> Suspension:
     return s
 
 
+def profile_ellipsoids() -> Suspension:
+    """400 ellipsoids drawn like the 1,000-ellipsoid workload but at p = 8 (57,600 nodes, ~10% volume
+    fraction, gap 0.2; seed 1): a case of the same kernels small enough for hardware-counter captures
+    (about 2 GB on the device) that still fills every SM."""
+    return random_ellipsoids(400, 8, 16, 0.10, 0.2, seed=1, name="profile_400_ellipsoids_p8")
+
+
 WORKLOADS = {
     "c1": c1_spheres,
+    "profile": profile_ellipsoids,
     "c2": c2_ellipsoids,
     "c3": c3_ellipsoids,
     "c4": c4_batched,
