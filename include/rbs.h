@@ -82,6 +82,8 @@ typedef struct {
                           (default 0); results in rbs_stats.kernel_ms */
   int refine_precision; /* RBS_PREC_MIXED: arithmetic of the right-hand side, refinement residuals
                           and velocity evaluation, RBS_PREC_DF (default) or RBS_PREC_FP64 */
+  int pair_variant;    /* targets per thread of the float32 and double-float pair kernels: 1, 2 or 4;
+                          0 (default) times the three once per context and keeps the fastest */
   int warm_start;      /* initial GMRES guess: RBS_WARM_ZERO (default), RBS_WARM_PREVIOUS (the last
                           solved density of this context) or RBS_WARM_LEARNED (the trained network);
                           the converged solution does not depend on it */
@@ -118,6 +120,8 @@ typedef struct {
   long long kernel_count[RBS_KC_COUNT];  /* launches per class */
   double kernel_units[RBS_KC_COUNT];     /* work per class: node pairs (pair sums, near), bytes of
                                             block entries read (particle blocks) */
+  int pair_variant[4];   /* targets per thread in use: float32 traction, float32 Stokeslet,
+                            double-float traction, double-float Stokeslet (0 = not yet chosen) */
 } rbs_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -98,6 +98,7 @@ void rbs_default_options(rbs_options* o) {
   o->timing = 0;
   o->refine_precision = RBS_PREC_DF;
   o->warm_start = RBS_WARM_ZERO;
+  o->pair_variant = 0;
 }
 
 int rbs_create(const rbs_options* opt, rbs_ctx** out) {
@@ -113,6 +114,7 @@ int rbs_create(const rbs_options* opt, rbs_ctx** out) {
       !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_refinements < 1 ||
       (o.precision != RBS_PREC_FP64 && o.precision != RBS_PREC_MIXED) ||
       (o.refine_precision != RBS_PREC_FP64 && o.refine_precision != RBS_PREC_DF) || o.warm_start < 0 ||
+      (o.pair_variant != 0 && o.pair_variant != 1 && o.pair_variant != 2 && o.pair_variant != 4) ||
       o.warm_start > 2)
     return RBS_EINVAL;
   rbs_ctx* h = new rbs_ctx();
@@ -411,6 +413,7 @@ int rbs_get_stats(rbs_ctx* h, rbs_stats* out) {
   if (s.ok()) s = c.harvest();
   if (!s.ok()) return finish(c, s);
   *out = c.stats;
+  for (int k = 0; k < 4; ++k) out->pair_variant[k] = c.tuned[k];
   return RBS_OK;
 }
 

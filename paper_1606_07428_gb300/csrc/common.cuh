@@ -155,6 +155,8 @@ struct Context {
   DevBuf<const float*> d_upU32;
 
   std::map<const void*, int> resident;  // kernel -> resident blocks per SM
+  int tuned[4] = {0, 0, 0, 0};          // chosen targets per thread: (float32, double-float) x (K, S)
+  float tune_ms[4] = {0, 0, 0, 0};
 
   // smooth pair-sum work list: (target begin, target end, source begin, source end)
   std::vector<longlong4> work;

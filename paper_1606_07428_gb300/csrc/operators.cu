@@ -24,6 +24,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
+__device__ __forceinline__ double2 load2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
+__device__ __forceinline__ double2 load2(const float* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return make_double2((double)v.x, (double)v.y);
+}
 __device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
@@ -90,25 +95,30 @@ __global__ void __launch_bounds__(256) k_blocks(int mode, const int4* __restrict
     mom[threadIdx.x] = acc;
   }
   __syncthreads();
-  const int dim = 3 * np;
+  const int dim = 3 * np;  // even: n_phi is even, so N_p is
   const TB* A = blocks + (has_block ? block_off[shape_of[i]] : 0);
-  for (int t = wk.y + warp; t < wk.z; t += (blockDim.x >> 5)) {
-    double y0 = 0.0, y1 = 0.0, y2 = 0.0;
+  // two nodes (six consecutive rows) per warp pass, two columns per lane per load
+  for (int t0 = wk.y + 2 * warp; t0 < wk.z; t0 += 2 * (int)(blockDim.x >> 5)) {
+    const int nn = (t0 + 1 < wk.z) ? 2 : 1;
+    double y[6] = {0, 0, 0, 0, 0, 0};
     if (has_block) {
-      const TB* r0 = A + (long long)(3 * t) * dim;
-      const TB* r1 = r0 + dim;
-      const TB* r2 = r1 + dim;
-      for (int col = lane; col < dim; col += 32) {
-        double z = zs[col];
-        y0 = fma((double)r0[col], z, y0);
-        y1 = fma((double)r1[col], z, y1);
-        y2 = fma((double)r2[col], z, y2);
+      const TB* base = A + (long long)(3 * t0) * dim;
+      for (int col = 2 * lane; col < dim; col += 64) {
+        const double z0 = zs[col], z1 = zs[col + 1];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+          if (r < 3 * nn) {
+            const double2 v = load2(base + (long long)r * dim + col);
+            y[r] = fma(v.x, z0, fma(v.y, z1, y[r]));
+          }
+        }
       }
-      y0 = warp_sum(y0);
-      y1 = warp_sum(y1);
-      y2 = warp_sum(y2);
+#pragma unroll
+      for (int r = 0; r < 6; ++r) y[r] = warp_sum(y[r]);
     }
-    if (lane == 0) {
+    if (lane < nn) {
+      const int t = t0 + lane;
+      const double y0 = y[3 * lane], y1 = y[3 * lane + 1], y2 = y[3 * lane + 2];
       const long long g = o + t;
       double l0 = R0 * y0 + R1 * y1 + R2 * y2;
       double l1 = R3 * y0 + R4 * y1 + R5 * y2;
@@ -257,7 +267,7 @@ __device__ __forceinline__ void pair_tile32(const float4* __restrict__ sp, const
 // NT targets per thread (block = 128 / NT threads over a 128-target work item): each staged source
 // feeds NT independent pair evaluations.
 template <int KIND, int NT>
-__global__ void __launch_bounds__(128 / NT) k_pairs32(int nitems, const longlong4* __restrict__ work, const double4* __restrict__ x,
+__global__ void __launch_bounds__(128 / NT, NT == 1 ? 6 : (NT == 2 ? 16 : 12)) k_pairs32(int nitems, const longlong4* __restrict__ work, const double4* __restrict__ x,
                                                       const double4* __restrict__ nrm, const int* __restrict__ pid,
                                                       const double* __restrict__ dens, double* __restrict__ y) {
   constexpr int TS = 256, NTH = 128 / NT;
@@ -357,6 +367,14 @@ __device__ __forceinline__ dflt df_add(dflt a, dflt b) {
   const float h = s.h + s.l;
   return {h, s.l - (h - s.h)};
 }
+// a0 b0 + a1 b1 + a2 b2: products exact to the low part, the three high parts added with two-sums
+// and every low part folded into one float32 sum (unnormalised result)
+__device__ __forceinline__ dflt df_dot3(dflt a0, dflt b0, dflt a1, dflt b1, dflt a2, dflt b2) {
+  const dflt p0 = df_mul(a0, b0), p1 = df_mul(a1, b1), p2 = df_mul(a2, b2);
+  const dflt s1 = df_two_sum(p0.h, p1.h);
+  const dflt s2 = df_two_sum(s1.h, p2.h);
+  return {s2.h, ((s1.l + s2.l) + (p0.l + p1.l)) + p2.l};
+}
 // acc += v with the low parts carried unnormalised (renormalised when the tile is flushed)
 __device__ __forceinline__ void df_acc(dflt& acc, dflt v) {
   const dflt s = df_two_sum(acc.h, v.h);
@@ -402,16 +420,12 @@ __device__ __forceinline__ void pair_tile_df(const float4* __restrict__ sph, con
       t = fmaf(r2l, q, t);
       dflt inv = {y0, -0.5f * t * y0};
       if (MASK && __float_as_int(yh.w) == pt[u]) inv = {0.0f, 0.0f};
-      dflt rr = df_mul(d[0], den[0]);
-      rr = df_add(rr, df_mul(d[1], den[1]));
-      rr = df_add(rr, df_mul(d[2], den[2]));
+      const dflt rr = df_dot3(d[0], den[0], d[1], den[1], d[2], den[2]);
       const dflt inv2 = df_mul(inv, inv);
       const dflt inv3 = df_mul(inv2, inv);
       if (KIND == 0) {
         const dflt inv5 = df_mul(inv3, inv2);
-        dflt rn = df_mul(d[0], nt[u][0]);
-        rn = df_add(rn, df_mul(d[1], nt[u][1]));
-        rn = df_add(rn, df_mul(d[2], nt[u][2]));
+        const dflt rn = df_dot3(d[0], nt[u][0], d[1], nt[u][1], d[2], nt[u][2]);
         const dflt cc = df_mul(df_mul(rn, rr), inv5);
 #pragma unroll
         for (int c = 0; c < 3; ++c) df_acc(acc[u][c], df_mul(cc, d[c]));
@@ -428,7 +442,7 @@ __device__ __forceinline__ void pair_tile_df(const float4* __restrict__ sph, con
 }
 
 template <int KIND, int NT>
-__global__ void __launch_bounds__(128 / NT) k_pairs_df(int nitems, const longlong4* __restrict__ work, const double4* __restrict__ x,
+__global__ void __launch_bounds__(128 / NT, 8) k_pairs_df(int nitems, const longlong4* __restrict__ work, const double4* __restrict__ x,
                                                        const double4* __restrict__ nrm, const int* __restrict__ pid,
                                                        const double* __restrict__ dens, double* __restrict__ y) {
   constexpr int TS = 128, NTH = 128 / NT;
@@ -501,43 +515,37 @@ __global__ void __launch_bounds__(128 / NT) k_pairs_df(int nitems, const longlon
 }
 
 // ------------------------------------------------------------------------------------------
-// Upsampled densities of the near-source particles: mu_up = U mu_j, one warp per upsampled node.
+// Upsampled densities of the near-source particles: mu_up = U mu_j with U stored transposed
+// (N_p x N_up), one thread per upsampled node reading U coalesced and mu_j from shared memory.
 template <typename TU>
-__global__ void __launch_bounds__(256) k_upsample(int n_up, const int* __restrict__ up_particle, const long long* __restrict__ up_off,
+__global__ void __launch_bounds__(128) k_upsample(int n_up, const int* __restrict__ up_particle,
+                                                  const long long* __restrict__ up_off,
                                                   const long long* __restrict__ offset, const int* __restrict__ nodes,
                                                   const TU* const* __restrict__ Umats, const double* __restrict__ dens,
                                                   double* __restrict__ upmu) {
   extern __shared__ double mus[];  // 3 N_p
   for (int u = blockIdx.y; u < n_up; u += gridDim.y) {
-  const int j = up_particle[u];
-  const int np = nodes[j];
-  const long long o = offset[j];
-  __syncthreads();
-  for (int l = threadIdx.x; l < 3 * np; l += blockDim.x) mus[l] = dens[3 * o + l];
-  __syncthreads();
-  const long long base = up_off[u];
-  const int nup = (int)(up_off[u + 1] - base);
-  const TU* U = Umats[u];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = blockIdx.x * 8 + warp; r < nup; r += gridDim.x * 8) {
-    const TU* row = U + (long long)r * np;
-    double a0 = 0, a1 = 0, a2 = 0;
-    for (int s = lane; s < np; s += 32) {
-      double uv = (double)row[s];
-      a0 = fma(uv, mus[3 * s], a0);
-      a1 = fma(uv, mus[3 * s + 1], a1);
-      a2 = fma(uv, mus[3 * s + 2], a2);
-    }
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
-    a2 = warp_sum(a2);
-    if (lane == 0) {
+    const int j = up_particle[u];
+    const int np = nodes[j];
+    const long long o = offset[j];
+    __syncthreads();
+    for (int l = threadIdx.x; l < 3 * np; l += blockDim.x) mus[l] = dens[3 * o + l];
+    __syncthreads();
+    const long long base = up_off[u];
+    const int nup = (int)(up_off[u + 1] - base);
+    const TU* Ut = Umats[u];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nup; r += gridDim.x * blockDim.x) {
+      double a0 = 0, a1 = 0, a2 = 0;
+      for (int s = 0; s < np; ++s) {
+        const double uv = (double)Ut[(long long)s * nup + r];
+        a0 = fma(uv, mus[3 * s], a0);
+        a1 = fma(uv, mus[3 * s + 1], a1);
+        a2 = fma(uv, mus[3 * s + 2], a2);
+      }
       upmu[3 * (base + r) + 0] = a0;
       upmu[3 * (base + r) + 1] = a1;
       upmu[3 * (base + r) + 2] = a2;
     }
-  }
-  __syncthreads();
   }
 }
 
@@ -747,6 +755,75 @@ static int resident_grid(Context& c, const void* kernel, int threads, int items)
   return std::max(1, std::min(items, per_sm * std::max(1, c.sm_count)));
 }
 
+// Launch of the smooth pair sum over the first `items` work items with NT targets per thread.
+template <int KIND>
+static void launch_pairs_kind(Context& c, int prec, int nt, int items, const double* x, double* y) {
+#define RBS_PAIR_ARGS items, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y
+  if (prec == RBS_PREC_FP64) {
+    k_pairs64<KIND><<<resident_grid(c, (const void*)k_pairs64<KIND>, 128, items), 128, 0, c.stream>>>(RBS_PAIR_ARGS);
+  } else if (prec == RBS_PREC_DF) {
+    if (nt == 1)
+      k_pairs_df<KIND, 1><<<resident_grid(c, (const void*)k_pairs_df<KIND, 1>, 128, items), 128, 0, c.stream>>>(RBS_PAIR_ARGS);
+    else if (nt == 2)
+      k_pairs_df<KIND, 2><<<resident_grid(c, (const void*)k_pairs_df<KIND, 2>, 64, items), 64, 0, c.stream>>>(RBS_PAIR_ARGS);
+    else
+      k_pairs_df<KIND, 4><<<resident_grid(c, (const void*)k_pairs_df<KIND, 4>, 32, items), 32, 0, c.stream>>>(RBS_PAIR_ARGS);
+  } else {
+    if (nt == 1)
+      k_pairs32<KIND, 1><<<resident_grid(c, (const void*)k_pairs32<KIND, 1>, 128, items), 128, 0, c.stream>>>(RBS_PAIR_ARGS);
+    else if (nt == 2)
+      k_pairs32<KIND, 2><<<resident_grid(c, (const void*)k_pairs32<KIND, 2>, 64, items), 64, 0, c.stream>>>(RBS_PAIR_ARGS);
+    else
+      k_pairs32<KIND, 4><<<resident_grid(c, (const void*)k_pairs32<KIND, 4>, 32, items), 32, 0, c.stream>>>(RBS_PAIR_ARGS);
+  }
+#undef RBS_PAIR_ARGS
+}
+
+static Status launch_pairs(Context& c, int kind, int prec, int nt, int items, const double* x, double* y) {
+  if (kind == 0)
+    launch_pairs_kind<0>(c, prec, nt, items, x, y);
+  else
+    launch_pairs_kind<1>(c, prec, nt, items, x, y);
+  RBS_CUDA_TRY(cudaGetLastError());
+  return Status::Ok();
+}
+
+// Targets per thread of the float32 and double-float pair kernels: rbs_options.pair_variant when set,
+// otherwise the fastest of 1, 2 and 4 timed once per (kernel, arithmetic) on a prefix of the work
+// list (the same items for every variant, into a scratch output).
+static int pair_variant(Context& c, int kind, int prec, const double* x) {
+  if (c.opt.pair_variant == 1 || c.opt.pair_variant == 2 || c.opt.pair_variant == 4) return c.opt.pair_variant;
+  const int key = 2 * (prec == RBS_PREC_DF ? 1 : 0) + kind;
+  if (c.tuned[key]) return c.tuned[key];
+  int best = 2;
+  const int items = std::min<int>((int)c.work.size(), 2 * 32 * std::max(1, c.sm_count));
+  double* scratch = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaMalloc(&scratch, sizeof(double) * 3 * c.N) == cudaSuccess && cudaEventCreate(&a) == cudaSuccess &&
+      cudaEventCreate(&b) == cudaSuccess) {
+    float best_ms = 1e30f;
+    for (int nt : {1, 2, 4}) {
+      launch_pairs(c, kind, prec, nt, items, x, scratch);  // warm (first launch of this variant)
+      cudaEventRecord(a, c.stream);
+      launch_pairs(c, kind, prec, nt, items, x, scratch);
+      cudaEventRecord(b, c.stream);
+      float ms = 0.0f;
+      if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = nt;
+      }
+      c.stats.launches += 2;
+    }
+    c.tune_ms[key] = best_ms;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (scratch) cudaFree(scratch);
+  cudaGetLastError();
+  c.tuned[key] = best;
+  return best;
+}
+
 // ------------------------------------------------------------------------------------------
 
 Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, double* aux, double scale) {
@@ -787,26 +864,9 @@ Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y) {
   if (nw > 0) {
     int cls = f32 ? (kind == 0 ? RBS_KC_PAIR_K32 : RBS_KC_PAIR_S32) : (kind == 0 ? RBS_KC_PAIR_K64 : RBS_KC_PAIR_S64);
     if (prec == RBS_PREC_DF) cls = kind == 0 ? RBS_KC_PAIR_KDF : RBS_KC_PAIR_SDF;
+    const int nt = (prec == RBS_PREC_FP64) ? 1 : pair_variant(c, kind, prec, x);
     KernelTimer timer(c, cls);
-    const int g64 = resident_grid(c, (const void*)k_pairs64<0>, 128, nw);
-    const int g32 = resident_grid(c, (const void*)k_pairs32<0, 2>, 64, nw);
-    const int gdf = resident_grid(c, (const void*)k_pairs_df<0, 2>, 64, nw);
-    if (prec == RBS_PREC_DF) {
-      if (kind == 0)
-        k_pairs_df<0, 2><<<gdf, 64, 0, c.stream>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
-      else
-        k_pairs_df<1, 2><<<gdf, 64, 0, c.stream>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
-    } else if (f32) {
-      if (kind == 0)
-        k_pairs32<0, 2><<<g32, 64, 0, c.stream>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
-      else
-        k_pairs32<1, 2><<<g32, 64, 0, c.stream>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
-    } else {
-      if (kind == 0)
-        k_pairs64<0><<<g64, 128, 0, c.stream>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
-      else
-        k_pairs64<1><<<g64, 128, 0, c.stream>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y);
-    }
+    RBS_TRY(launch_pairs(c, kind, prec, nt, nw, x, y));
     RBS_CUDA_TRY(cudaGetLastError());
     timer.done((double)c.stats.far_pairs);
   }
@@ -821,12 +881,12 @@ Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y) {
     int maxup = 0;
     for (Grid* g : c.grids) maxup = std::max(maxup, g->nup);
     const int nup_p = (int)c.up_particle.size();
-    dim3 gu(cdiv(maxup, 8), (unsigned)std::min(nup_p, 65535));
+    dim3 gu(cdiv(maxup, 128), (unsigned)std::min(nup_p, 65535));
     if (f32)
-      k_upsample<float><<<gu, 256, smem, c.stream>>>(nup_p, c.d_up_particle.ptr, c.d_up_off.ptr, c.d_offset.ptr, c.d_nodes.ptr,
+      k_upsample<float><<<gu, 128, smem, c.stream>>>(nup_p, c.d_up_particle.ptr, c.d_up_off.ptr, c.d_offset.ptr, c.d_nodes.ptr,
                                                      c.d_upU32.ptr, x, c.d_up_mu.ptr);
     else
-      k_upsample<double><<<gu, 256, smem, c.stream>>>(nup_p, c.d_up_particle.ptr, c.d_up_off.ptr, c.d_offset.ptr,
+      k_upsample<double><<<gu, 128, smem, c.stream>>>(nup_p, c.d_up_particle.ptr, c.d_up_off.ptr, c.d_offset.ptr,
                                                       c.d_nodes.ptr, c.d_upU.ptr, x, c.d_up_mu.ptr);
     RBS_CUDA_TRY(cudaGetLastError());
 #define RBS_NEAR_ARGS                                                                                            \

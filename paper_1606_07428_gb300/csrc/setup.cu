@@ -304,6 +304,14 @@ __global__ void k_precond_matrix(int np, int nphi, const double* t, const double
   M[i] = BK[i] + Lv + (row == col ? 0.5 : 0.0);
 }
 
+// out (cols x rows) = in (rows x cols)^T
+__global__ void k_transpose(const double* in, int rows, int cols, double* out) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)rows * cols) return;
+  int r = (int)(i / cols), c = (int)(i % cols);
+  out[(long long)c * rows + r] = in[i];
+}
+
 __global__ void k_to_float(const double* in, float* out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
@@ -445,10 +453,19 @@ static Status build_grid(Context& c, Grid& g) {
   DevBuf<double> Yu;
   RBS_TRY(Yu.alloc((size_t)g.nup * g.nbasis));
   k_sh_at_points<<<cdiv(g.nup, 128), 128, 0, s>>>(g.p, g.mmax, g.nbasis, gup.ptr, g.nup, Yu.ptr);
-  RBS_TRY(g.d_up.alloc((size_t)g.nup * g.np));
-  RBS_TRY(dgemm_batched(s, g.nup, g.np, g.nbasis, Yu.ptr, g.nbasis, 0, An.ptr, g.np, 0, g.d_up.ptr, g.np, 0, 1));
-  RBS_TRY(g.d_up32.alloc((size_t)g.nup * g.np));
-  k_to_float<<<256, 256, 0, s>>>(g.d_up.ptr, g.d_up32.ptr, (long long)g.nup * g.np);
+  // U^T = An^T Y(upsampled)^T, stored N_p x N_up
+  {
+    DevBuf<double> YuT, AnT;
+    RBS_TRY(YuT.alloc((size_t)g.nup * g.nbasis));
+    RBS_TRY(AnT.alloc((size_t)g.np * g.nbasis));
+    k_transpose<<<cdiv((long long)g.nup * g.nbasis, 256), 256, 0, s>>>(Yu.ptr, g.nup, g.nbasis, YuT.ptr);
+    k_transpose<<<cdiv((long long)g.np * g.nbasis, 256), 256, 0, s>>>(An.ptr, g.nbasis, g.np, AnT.ptr);
+    RBS_TRY(g.d_up.alloc((size_t)g.nup * g.np));
+    RBS_TRY(dgemm_batched(s, g.np, g.nup, g.nbasis, AnT.ptr, g.nbasis, 0, YuT.ptr, g.nup, 0, g.d_up.ptr, g.nup, 0, 1));
+    RBS_TRY(g.d_up32.alloc((size_t)g.nup * g.np));
+    k_to_float<<<256, 256, 0, s>>>(g.d_up.ptr, g.d_up32.ptr, (long long)g.nup * g.np);
+    RBS_CUDA_TRY(cudaStreamSynchronize(s));
+  }
   RBS_CUDA_TRY(cudaGetLastError());
   RBS_CUDA_TRY(cudaStreamSynchronize(s));  // temporaries are released on return
   return Status::Ok();

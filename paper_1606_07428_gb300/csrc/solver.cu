@@ -6,6 +6,7 @@
 //   3. u = S[rho + mu] and the rigid velocities v (Eq. 41), omega (Eq. 42).
 // Arnoldi (two-pass classical Gram-Schmidt), Givens rotations and the least-squares solve run in
 // float64 on the GPU; the host reads one residual estimate per iteration.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <mutex>
@@ -430,7 +431,10 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
       bool conv_inner = false;
       // inner solve of A d = r with the float32 operator
       const bool start_zero = !(have_x0 && refinements == 0);  // d holds the warm start on the first pass
-      RBS_TRY(gmres(c, RBS_PREC_MIXED, r, d, start_zero, c.opt.inner_tol * rn, c.opt.max_iters - total_iters, &its, &res,
+      // each inner solve reduces its residual by inner_tol, or only as far as the final tolerance needs
+      // (half of tol ||b||), whichever is looser
+      const double inner = std::min(0.5, std::max(c.opt.inner_tol, 0.5 * tol * bnorm / rn));
+      RBS_TRY(gmres(c, RBS_PREC_MIXED, r, d, start_zero, inner * rn, c.opt.max_iters - total_iters, &its, &res,
                     &conv_inner));
       total_iters += its;
       c.stats.launches++;

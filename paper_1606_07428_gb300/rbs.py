@@ -72,6 +72,7 @@ class rbs_options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("timing", ctypes.c_int),
         ("refine_precision", ctypes.c_int),
+        ("pair_variant", ctypes.c_int),
         ("warm_start", ctypes.c_int),
     ]
 
@@ -105,6 +106,7 @@ class rbs_stats(ctypes.Structure):
         ("kernel_ms", ctypes.c_double * 8),
         ("kernel_count", ctypes.c_longlong * 8),
         ("kernel_units", ctypes.c_double * 8),
+        ("pair_variant", ctypes.c_int * 4),
     ]
 
 
@@ -367,7 +369,7 @@ def rbs_get_stats(ctx) -> dict:
     out = {}
     for name, _ in s._fields_:
         val = getattr(s, name)
-        out[name] = list(val) if name.startswith("kernel_") else val
+        out[name] = list(val) if name.startswith("kernel_") or name == "pair_variant" else val
     return out
 
 

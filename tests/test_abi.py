@@ -19,7 +19,7 @@ def declared_functions():
 def struct_fields(name):
     text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
     body = [b for b, nm in re.findall(r"typedef struct \{([^{}]*?)\}\s*(\w+);", text, flags=re.S) if nm == name][0]
-    return re.findall(r"\b([a-z_]+)\s*(?:\[[A-Z_]+\])?\s*;", body)
+    return re.findall(r"\b([a-z_]+)\s*(?:\[[A-Z_0-9]+\])?\s*;", body)
 
 
 @pytest.fixture(scope="module")

@@ -237,3 +237,18 @@ def test_device_pointer_entry_points(rbs, small):
     y = torch.zeros_like(x)
     rbs.rbs_apply_operator_device(ctx.ctx, rbs.RBS_OP_A, rbs.RBS_PREC_FP64, x, y)
     assert rel(y.cpu().numpy(), oracle_op(ref, "A", x.cpu().numpy())) < 1e-12
+
+
+@pytest.mark.parametrize("variant", [1, 2, 4])
+def test_every_pair_kernel_variant_matches_oracle(rbs, variant):
+    """The autotuner picks among 1, 2 and 4 targets per thread; each variant is held to the same bounds."""
+    s = mixed_system()
+    ref = oracle.System(s.semi_axes, s.p, s.nphi, s.centres, s.quats)
+    x = suspensions.random_density(7, s.total_nodes)
+    with rbs.Context(device=0, pair_variant=variant) as ctx:
+        ctx.set_suspension(s)
+        for name in ("K_OFF", "S_OFF"):
+            y_ref = oracle_op(ref, name, x)
+            op = getattr(rbs, "RBS_OP_" + name)
+            assert rel(rbs.rbs_apply_operator(ctx.ctx, op, rbs.RBS_PREC_MIXED, x), y_ref) < 2e-5
+            assert rel(rbs.rbs_apply_operator(ctx.ctx, op, rbs.RBS_PREC_DF, x), y_ref) < 1e-11
