@@ -46,6 +46,10 @@ FP32_LANES_PER_SM = 128
 # per pair (with the float64 reciprocal square root counted as 7): traction 27, Stokeslet 25
 FLOPS_PER_PAIR = {"traction": 30.0, "stokeslet": 28.0}
 FP64_OPS_PER_PAIR = {"traction": 27.0, "stokeslet": 25.0}
+# DRAM bytes per launch from ncu captures on the 400-ellipsoid profiling case (57,600 nodes; see
+# profiles/), scaled by node count to the benchmarked case: the pair kernels read their inputs once
+# (sources are re-read from L2), so traffic grows with N, not with the N^2 pairs
+NCU_TRAFFIC = {"pair_traction_df": (6.404864e6, 57600), "pair_traction_f32": (6.284032e6, 57600)}
 # float32-pipe operations per pair of the double-float kernels, counted from the source of
 # pair_tile_df (separation 24, r^2 28, reciprocal square root 8, r . density 28, powers 8, traction
 # tail 76 / Stokeslet tail 76)
@@ -65,6 +69,13 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain float64 solves (0 skips)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
+    ap.add_argument("--experiment", default=None, choices=[None, "warmstart"],
+                    help="warmstart: learned vs previous-step vs zero initial guesses in RK4 sedimentation "
+                         "(prints its own JSON line; the default run is the benchmark above)")
+    ap.add_argument("--train-steps", type=int, default=10)
+    ap.add_argument("--eval-steps", type=int, default=10)
+    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--dt", type=float, default=0.05)
     return ap.parse_args()
 
 
@@ -195,6 +206,37 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------------------------- our arm
+
+def kernel_rooflines(kernels, f_mhz, hbm_gbs):
+    """Achieved rate of every timed kernel class against the roofline that bounds it: float32 issue
+    (minimal instructions per pair) for float32 and double-float pair sums, the float64 FMA rate for
+    float64 pair sums, HBM bandwidth for the particle-block kernel (bytes of block entries)."""
+    f = f_mhz * 1e6
+    out = {}
+    for name, e in kernels.items():
+        if e["ms"] <= 0 or not e["launches"]:
+            continue
+        rate = e["units"] / (e["ms"] / 1e3)
+        row = {"ms_per_launch": e["ms"] / e["launches"]}
+        if name.startswith("pair_"):
+            kind = "traction" if "traction" in name else "stokeslet"
+            if name.endswith("_f32"):
+                instr = {"traction": 20.0, "stokeslet": 18.0}[kind]
+                peak = SMS * FP32_LANES_PER_SM * f / instr
+            elif name.endswith("_df"):
+                peak = SMS * FP32_LANES_PER_SM * f / DF_INSTR_PER_PAIR[kind]
+            else:
+                peak = SMS * FP64_DFMA_PER_CLK_SM * f / FP64_OPS_PER_PAIR[kind]
+            row.update({"achieved_gpair_s": rate / 1e9, "peak_gpair_s": peak / 1e9, "frac": rate / peak,
+                        "bound": "alu"})
+        elif name == "particle_blocks":
+            row.update({"achieved_gb_s": rate / 1e9, "peak_gb_s": hbm_gbs, "frac": rate / 1e9 / hbm_gbs,
+                        "bound": "hbm"})
+        else:
+            row.update({"achieved_gpair_s": rate / 1e9})
+        out[name] = row
+    return out
+
 
 def kernel_table(stats):
     from paper_1606_07428_gb300 import rbs
@@ -400,6 +442,15 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": name,
                 "peak_basis": "measured copy bandwidth" if peaks else "fallback 6.8 TB/s"}
+    try:
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
+    except Exception:
+        hbm_peak = 6800.0
+    rooflines = kernel_rooflines(kernels, f_mhz, hbm_peak)
+    if name in NCU_TRAFFIC:
+        bytes_, nodes_ = NCU_TRAFFIC[name]
+        roof["traffic"] = bytes_ * susp.total_nodes / nodes_
+        roof["traffic_basis"] = "ncu dram read+write of the 400-ellipsoid capture, scaled by node count"
     roof["ms_per_launch"] = per_launch_ms
     roof["share_of_step"] = e["ms"] / total_ms if world == 1 else None
 
@@ -429,6 +480,7 @@ def run_ours(args):
             "pair_variant": dict(zip(["traction_f32", "stokeslet_f32", "traction_df", "stokeslet_df"],
                                      stats.get("pair_variant", []))),
             "roofline": roof,
+            "kernel_rooflines": rooflines,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clocks,
@@ -442,8 +494,69 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_warmstart_experiment(args):
+    """RK4 sedimentation (Algorithm 1 without contact) of the workload: train the warm-start network on
+    the densities of the first train_steps steps (solved with the previous-stage guess), then run
+    eval_steps more steps from the same configuration with zero, previous-stage and learned initial
+    guesses, and report GMRES iterations per solve and solves/s for each."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1606_07428_gb300 import rbs
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    susp = suspensions.WORKLOADS[args.workload]()
+    tol = args.tol or 1e-8
+    prec = rbs.RBS_PREC_MIXED
+    with rbs.Context(device=0, precision=prec, warm_start=rbs.RBS_WARM_PREVIOUS, warm_record=1,
+                     stream=stream.cuda_stream) as ctx:
+        ctx.set_suspension(susp)
+        t0 = time.perf_counter()
+        its_train = rbs.rbs_advance(ctx.ctx, susp.F, susp.T, args.dt, args.train_steps, rbs.RBS_RK4, tol)
+        t_train_solves = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        loss_first = rbs.rbs_warmstart_train(ctx.ctx, 1, batch=256, lr=1e-3, seed=1)
+        loss = rbs.rbs_warmstart_train(ctx.ctx, args.epochs - 1, batch=256, lr=1e-3, seed=1)
+        t_train = time.perf_counter() - t0
+        params, scale = rbs.rbs_warmstart_weights(ctx.ctx)
+        cen, quat = rbs.rbs_get_state(ctx.ctx, susp.n)
+    out = {}
+    finals = {}
+    for mode in ("ZERO", "PREVIOUS", "LEARNED"):
+        with rbs.Context(device=0, precision=prec, warm_start=getattr(rbs, "RBS_WARM_" + mode),
+                         stream=stream.cuda_stream) as ctx:
+            ctx.set_geometry(susp.semi_axes, susp.p, susp.nphi, cen, quat)
+            if mode == "LEARNED":
+                rbs.rbs_warmstart_weights(ctx.ctx, params, scale=scale)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            its = rbs.rbs_advance(ctx.ctx, susp.F, susp.T, args.dt, args.eval_steps, rbs.RBS_RK4, tol)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            solves = 4 * args.eval_steps
+            c_end, _ = rbs.rbs_get_state(ctx.ctx, susp.n)
+            finals[mode] = c_end
+            out[mode.lower()] = {"gmres_iterations_per_solve": its / solves, "solves_per_s": solves / (ms / 1e3),
+                                 "ms": ms}
+    drift = {m: float(np.abs(finals[m] - finals["ZERO"]).max()) for m in finals}
+    line = {"experiment": "learned warm start in RK4 sedimentation", "workload": susp.name, "n_particles": susp.n,
+            "nodes": susp.total_nodes, "precision": "mixed", "tol": tol, "dt": args.dt,
+            "train_steps": args.train_steps, "train_samples": 4 * args.train_steps * susp.n,
+            "train_iterations_per_solve": its_train / (4 * args.train_steps),
+            "train_solve_seconds": t_train_solves, "epochs": args.epochs, "train_seconds": t_train,
+            "loss_first_epoch": loss_first, "loss_last_epoch": loss, "eval_steps": args.eval_steps,
+            "results": out, "max_centre_difference_vs_zero_start": drift}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.experiment == "warmstart":
+        run_warmstart_experiment(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

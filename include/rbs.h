@@ -87,6 +87,8 @@ typedef struct {
   int warm_start;      /* initial GMRES guess: RBS_WARM_ZERO (default), RBS_WARM_PREVIOUS (the last
                           solved density of this context) or RBS_WARM_LEARNED (the trained network);
                           the converged solution does not depend on it */
+  int warm_record;     /* 1: rbs_advance records a training sample (rbs_warmstart_record) after every
+                          stage solve (default 0) */
 } rbs_options;
 
 #define RBS_WARM_ZERO 0

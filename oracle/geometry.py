@@ -4,10 +4,10 @@ Eq. 18; Section 3.3, Eq. 40).
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Surfaces are ellipsoids with semi-axes (a, b, c) in the body frame, x_b = (a sin t cos f,
-b sin t sin f, c cos t).  Their coordinate functions are spherical harmonics of degree 1, so the
-spectral derivatives of Eq. 37 are the analytic ones used below.  The lab frame is
-x = c_i + R(q_i) x_b (Eq. 40 with the body frame as reference); the centroid x^c_i of Eq. 18 is the
-ellipsoid centre c_i.
+b sin t sin f, c cos t), whose coordinate functions are spherical harmonics of degree 1 (so the
+spectral derivatives of Eq. 37 are the analytic ones used below), or general coefficient surfaces
+(oracle/shapes.py).  The lab frame is x = c_i + R(q_i) x_b (Eq. 40 with the body frame as reference);
+the centroid x^c_i of Eq. 18 is the ellipsoid centre, or the area centroid of a coefficient surface.
 """
 from __future__ import annotations
 
@@ -39,8 +39,8 @@ def quat_to_rot(q: np.ndarray) -> np.ndarray:
 
 @dataclasses.dataclass
 class BodySurface:
-    """One ellipsoid on its (p + 1) x n_phi grid, in its body frame."""
-    axes: np.ndarray     # (3,)
+    """One particle surface on its (p + 1) x n_phi grid, in its body frame."""
+    axes: np.ndarray     # (3,) semi-axes of an ellipsoid; for a coefficient shape its bounding radius x3
     p: int
     nphi: int
     x: np.ndarray        # (N_p, 3) nodes
@@ -49,10 +49,21 @@ class BodySurface:
     W: np.ndarray        # (N_p,) area element of Eq. 36
     theta: np.ndarray    # (N_p,) parameter angles of the nodes
     phi: np.ndarray
+    shape: object = None  # SHShape for coefficient surfaces, None for ellipsoids
+    radius: float = 0.0   # bounding radius for the near criterion
 
     @property
     def area(self) -> float:
         return float(self.w.sum())
+
+    def point(self, s):
+        return ellipsoid_point(self.axes, s) if self.shape is None else self.shape.point(s)
+
+    def jacobian(self, s):
+        return ellipsoid_jacobian(self.axes, s) if self.shape is None else self.shape.jacobian(s)
+
+    def normal_at(self, s):
+        return ellipsoid_normal(self.axes, s) if self.shape is None else self.shape.normal(s)
 
 
 def ellipsoid_point(axes: np.ndarray, s: np.ndarray) -> np.ndarray:
@@ -91,7 +102,37 @@ def body_surface(axes, p: int, nphi: int) -> BodySurface:
     W = np.sqrt(E * G - Fm * Fm)
     normal = np.cross(x_th, x_ph) / W[:, None]
     w = 2.0 * math.pi * np.repeat(lam, nphi) * W / (nphi * st)
-    return BodySurface(axes, p, nphi, x, normal, w, W, th, ph)
+    return BodySurface(axes, p, nphi, x, normal, w, W, th, ph, None, float(np.max(axes)))
+
+
+def body_surface_sh(coef, pg: int, p: int, nphi: int, p_up: int) -> BodySurface:
+    """A coefficient surface (Eq. 31) on its grid: tangents by spectral differentiation (Eq. 37), W of
+    Eq. 36, weights of Eq. 35; the body frame is moved to the area centroid, and the bounding radius is
+    the largest centroid distance over the nodes of the order-p_up grid."""
+    from .shapes import SHShape, basis_with_derivatives
+    from .sphere_grid import grid_points
+    shape = SHShape(coef, pg)
+    theta, phi, _, lam = grid_angles(p, nphi)
+    th = np.repeat(theta, nphi)
+    ph = np.tile(phi, p + 1)
+    Y, Yt, Yp = basis_with_derivatives(pg, th, ph)
+    x = (shape.coef @ Y).T
+    x_th = (shape.coef @ Yt).T
+    x_ph = (shape.coef @ Yp).T * np.sin(th)[:, None]
+    E = np.einsum("ij,ij->i", x_th, x_th)
+    G = np.einsum("ij,ij->i", x_ph, x_ph)
+    Fm = np.einsum("ij,ij->i", x_th, x_ph)
+    W = np.sqrt(E * G - Fm * Fm)
+    normal = np.cross(x_th, x_ph) / W[:, None]
+    w = 2.0 * math.pi * np.repeat(lam, nphi) * W / (nphi * np.sin(th))
+    centroid = (w[:, None] * x).sum(0) / w.sum()
+    shape.shift = centroid
+    x = x - centroid
+    nphi_up = nphi + 2 * (p_up - p)
+    thu, phu, _ = grid_points(p_up, nphi_up)
+    su = np.stack([np.sin(thu) * np.cos(phu), np.sin(thu) * np.sin(phu), np.cos(thu)], axis=1)
+    radius = float(np.linalg.norm(shape.point(su), axis=1).max())
+    return BodySurface(np.full(3, radius), p, nphi, x, normal, w, W, th, ph, shape, radius)
 
 
 def moment_tensor(r: np.ndarray, w: np.ndarray) -> np.ndarray:
@@ -114,7 +155,7 @@ class Particle:
     area: float
     tau: np.ndarray      # (3, 3)
     suspension: int
-    radius: float        # bounding radius = largest semi-axis
+    radius: float        # bounding radius of the near criterion
     offset: int          # first global node index
 
 
@@ -125,4 +166,4 @@ def place(body: BodySurface, centre, R, index: int, suspension: int, offset: int
     x = r + centre[None, :]
     normal = body.normal @ R.T
     return Particle(index, body, centre, R, x, normal, body.w.copy(), r, float(body.w.sum()),
-                    moment_tensor(r, body.w), suspension, float(np.max(body.axes)), offset)
+                    moment_tensor(r, body.w), suspension, float(body.radius), offset)

@@ -13,7 +13,8 @@ Particles with different suspension ids do not interact.
 
 Readings of the paper used here (each a named option with this default):
 * K_ij of Eq. 22 integrates over the source surface Gamma_j (the printed Gamma_i is a typo).
-* Near pairs: particles i != j with |c_i - c_j| < R_i + R_j + delta, R the largest semi-axis,
+* Near pairs: particles i != j with |c_i - c_j| < R_i + R_j + delta, R the bounding radius (the
+  largest semi-axis of an ellipsoid, the largest node distance on the upsampled grid otherwise),
   delta = 1; sources upsampled to p_up = 2p with n_phi_up = n_phi + 2 (p_up - p).
 * Singular rule (Section 3 defers to a rule that is not reproduced in the paper): rotate the
   parameter sphere so that the target sits at the north pole, theta' = 0; integrate over the rotated
@@ -29,7 +30,6 @@ import math
 
 import numpy as np
 
-from .geometry import ellipsoid_jacobian, ellipsoid_normal, ellipsoid_point
 from .sphere_grid import angles_of, gauss_legendre, grid_points, interpolation_matrix
 
 FOUR_PI = 4.0 * math.pi
@@ -99,8 +99,8 @@ def self_rows(kind: str, body, targets, p_s: int) -> np.ndarray:
     out = np.zeros((len(targets), 3, 3, len(body.w)))
     for row, t in enumerate(targets):
         s = s0 @ pole_rotation(body.theta[t], body.phi[t]).T
-        y = ellipsoid_point(body.axes, s)
-        J = ellipsoid_jacobian(body.axes, s)
+        y = body.point(s)
+        J = body.jacobian(s)
         kern = kernel_matrix(kind, body.x[t][None, :] - y, body.normal[t][None, :])
         th, ph = angles_of(s)
         interp = interpolation_matrix(body.p, body.nphi, th, ph)
@@ -132,8 +132,8 @@ def upsampled_source(particle, p_up: int):
     nphi_up = body.nphi + 2 * (p_up - body.p)
     th, ph, q = grid_points(p_up, nphi_up)
     s = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
-    xb = ellipsoid_point(body.axes, s)
-    w = q * ellipsoid_jacobian(body.axes, s)
+    xb = body.point(s)
+    w = q * body.jacobian(s)
     U = interpolation_matrix(body.p, body.nphi, th, ph)
     return xb @ particle.R.T + particle.centre[None, :], w, U
 

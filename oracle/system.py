@@ -16,7 +16,7 @@ import dataclasses
 import numpy as np
 
 from . import operators as ops
-from .geometry import body_surface, place, quat_to_rot
+from .geometry import body_surface, body_surface_sh, place, quat_to_rot
 
 
 @dataclasses.dataclass
@@ -31,10 +31,17 @@ class System:
     """Geometry plus the pieces of the discrete operators.  Self blocks are built once per distinct
     (semi-axes, p, n_phi) in the body frame and rotated per particle (Eq. 38)."""
 
-    def __init__(self, semi_axes, p, nphi, centres, quats, suspension_id=None, options: Options | None = None):
+    def __init__(self, semi_axes, p, nphi, centres, quats, suspension_id=None, options: Options | None = None,
+                 shapes=None, shape_of=None):
+        """Ellipsoids by semi_axes (n x 3), or coefficient surfaces: shapes = list of (coef, p_g) and
+        shape_of[i] the shape of particle i (semi_axes is then ignored and may be None)."""
         self.opt = options or Options()
-        semi_axes = np.asarray(semi_axes, np.float64).reshape(-1, 3)
-        n = semi_axes.shape[0]
+        if shapes is not None:
+            n = len(shape_of)
+            semi_axes = np.zeros((n, 3))
+        else:
+            semi_axes = np.asarray(semi_axes, np.float64).reshape(-1, 3)
+            n = semi_axes.shape[0]
         p = np.broadcast_to(np.asarray(p, np.int64), (n,))
         nphi = np.broadcast_to(np.asarray(nphi, np.int64), (n,))
         centres = np.asarray(centres, np.float64).reshape(n, 3)
@@ -45,15 +52,32 @@ class System:
         self.particles = []
         offset = 0
         for i in range(n):
-            key = (tuple(semi_axes[i]), int(p[i]), int(nphi[i]))
-            if key not in self._bodies:
-                self._bodies[key] = body_surface(semi_axes[i], int(p[i]), int(nphi[i]))
+            if shapes is not None:
+                key = ("sh", int(shape_of[i]), int(p[i]), int(nphi[i]))
+                if key not in self._bodies:
+                    coef, pg = shapes[int(shape_of[i])]
+                    self._bodies[key] = body_surface_sh(coef, pg, int(p[i]), int(nphi[i]),
+                                                        self.opt.p_up_factor * int(p[i]))
+            else:
+                key = (tuple(semi_axes[i]), int(p[i]), int(nphi[i]))
+                if key not in self._bodies:
+                    self._bodies[key] = body_surface(semi_axes[i], int(p[i]), int(nphi[i]))
             body = self._bodies[key]
             self.particles.append(place(body, centres[i], quat_to_rot(quats[i]), i, int(sid[i]), offset))
             offset += len(body.w)
         self.total_nodes = offset
-        self.near = {(i, j) for i, pi in enumerate(self.particles) for j, pj in enumerate(self.particles)
-                     if ops.interacts(pi, pj) and ops.is_near(pi, pj, self.opt.delta)}
+        # near pairs: same suspension, i != j, |c_i - c_j| < R_i + R_j + delta (ops.is_near), tested
+        # for all pairs with array arithmetic in row blocks
+        cen = np.array([pt.centre for pt in self.particles])
+        rad = np.array([pt.radius for pt in self.particles])
+        self.near = set()
+        for i0 in range(0, n, 1024):
+            i1 = min(n, i0 + 1024)
+            dist = np.linalg.norm(cen[i0:i1, None, :] - cen[None, :, :], axis=2)
+            hit = (dist < rad[i0:i1, None] + rad[None, :] + self.opt.delta) & (sid[i0:i1, None] == sid[None, :])
+            for a, b in zip(*np.nonzero(hit)):
+                if i0 + a != b:
+                    self.near.add((int(i0 + a), int(b)))
 
     # -- helpers -------------------------------------------------------------------------------
     def sl(self, i: int) -> slice:
@@ -62,7 +86,7 @@ class System:
 
     def body_key(self, i: int):
         b = self.particles[i].body
-        return (tuple(b.axes), b.p, b.nphi)
+        return (id(b), b.p, b.nphi)
 
     def self_block_body(self, kind: str, i: int) -> np.ndarray:
         key = (kind,) + self.body_key(i)

@@ -99,6 +99,7 @@ void rbs_default_options(rbs_options* o) {
   o->refine_precision = RBS_PREC_DF;
   o->warm_start = RBS_WARM_ZERO;
   o->pair_variant = 0;
+  o->warm_record = 0;
 }
 
 int rbs_create(const rbs_options* opt, rbs_ctx** out) {

@@ -24,12 +24,21 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 __device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
+// Hardware reciprocal square root (PTX rsqrt.approx.ftz.f32, relative error below 2^-22): one
+// instruction, where rsqrtf without flush-to-zero adds a denormal guard.  The pair separations are
+// at least the particle gap, far from the float32 denormal range; r^2 = 0 (the excluded self pair)
+// gives +inf, which the callers replace by 0.
+__device__ __forceinline__ float rsqrt_hw(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double2 load2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
 __device__ __forceinline__ double2 load2(const float* p) {
   const float2 v = __ldg(reinterpret_cast<const float2*>(p));
   return make_double2((double)v.x, (double)v.y);
 }
-__device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
+__device__ __forceinline__ float rsq(float v) { return rsqrt_hw(v); }
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -244,7 +253,7 @@ __device__ __forceinline__ void pair_tile32(const float4* __restrict__ sp, const
     for (int u = 0; u < NT; ++u) {
       const float dx = xt[u][0] - ps.x, dy = xt[u][1] - ps.y, dz = xt[u][2] - ps.z;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      float inv = rsqrtf(r2);
+      float inv = rsqrt_hw(r2);
       if (MASK && __float_as_int(ps.w) == pt[u]) inv = 0.0f;
       const float rr = fmaf(dx, ds.x, fmaf(dy, ds.y, dz * ds.z));
       if (KIND == 0) {
@@ -267,7 +276,7 @@ __device__ __forceinline__ void pair_tile32(const float4* __restrict__ sp, const
 // NT targets per thread (block = 128 / NT threads over a 128-target work item): each staged source
 // feeds NT independent pair evaluations.
 template <int KIND, int NT>
-__global__ void __launch_bounds__(128 / NT, NT == 1 ? 6 : (NT == 2 ? 16 : 12)) k_pairs32(int nitems, const longlong4* __restrict__ work, const double4* __restrict__ x,
+__global__ void __launch_bounds__(128 / NT, NT == 1 ? 1 : (NT == 2 ? 16 : 12)) k_pairs32(int nitems, const longlong4* __restrict__ work, const double4* __restrict__ x,
                                                       const double4* __restrict__ nrm, const int* __restrict__ pid,
                                                       const double* __restrict__ dens, double* __restrict__ y) {
   constexpr int TS = 256, NTH = 128 / NT;
@@ -339,7 +348,7 @@ __global__ void __launch_bounds__(128 / NT, NT == 1 ? 6 : (NT == 2 ? 16 : 12)) k
 // Smooth pair sums in double-float arithmetic: each value is an unevaluated sum hi + lo of two
 // float32 numbers (Dekker's and Knuth's error-free transformations with fused multiply-add), so the
 // float32 pipes deliver about 44 bits per operation.  The reciprocal square root is one Newton step
-// from rsqrtf, with the residual 1 - r^2 y0^2 formed by fused multiply-adds.  Each 128-source tile
+// from the hardware estimate, with the residual 1 - r^2 y0^2 formed by fused multiply-adds.  Each 128-source tile
 // is summed in double-float and added into a float64 accumulator, so the sum keeps ~1e-12 relative
 // accuracy.  Coordinates are relative to the block's first target as in the float32 kernel.
 struct dflt {
@@ -411,8 +420,8 @@ __device__ __forceinline__ void pair_tile_df(const float4* __restrict__ sph, con
       const dflt s2 = df_two_sum(s1.h, p[2]);
       const float r2l = s1.l + s2.l + e[0] + e[1] + e[2];
       const float r2h = s2.h;
-      // 1 / sqrt(r^2): y0 = rsqrtf, one Newton step
-      const float y0 = rsqrtf(r2h);
+      // 1 / sqrt(r^2): hardware estimate y0, one Newton step
+      const float y0 = rsqrt_hw(r2h);
       const float q = y0 * y0;
       const float qe = fmaf(y0, y0, -q);
       float t = fmaf(r2h, q, -1.0f);

@@ -431,6 +431,7 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
       bool conv_inner = false;
       // inner solve of A d = r with the float32 operator
       const bool start_zero = !(have_x0 && refinements == 0);  // d holds the warm start on the first pass
+      const bool warm_first_pass = !start_zero;
       // each inner solve reduces its residual by inner_tol, or only as far as the final tolerance needs
       // (half of tol ||b||), whichever is looser
       const double inner = std::min(0.5, std::max(c.opt.inner_tol, 0.5 * tol * bnorm / rn));
@@ -453,7 +454,9 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
         converged = true;
         break;
       }
-      if (its == 0) break;
+      // stagnation: an inner solve that could not move (a warm start may already meet the inner
+      // tolerance on the first pass, which is progress, not stagnation)
+      if (its == 0 && !warm_first_pass) break;
     }
     rel = rn / bnorm;
   }

@@ -101,6 +101,18 @@ Status advance(Context& c, const double* F, const double* T, double dt, int step
       int its = 0;
       RBS_TRY(mobility_solve(c, F, T, tol, vtmp.data(), otmp.data(), nullptr, &its, false));
       total += its;
+      if (c.opt.warm_record) {
+        std::vector<double> ft(6 * (size_t)n);
+        for (int i = 0; i < n; ++i)
+          for (int q = 0; q < 3; ++q) {
+            ft[6 * i + q] = F[3 * i + q];
+            ft[6 * i + 3 + q] = T[3 * i + q];
+          }
+        DevBuf<double> dft;
+        RBS_TRY(dft.alloc(ft.size()));
+        RBS_CUDA_TRY(cudaMemcpyAsync(dft.ptr, ft.data(), sizeof(double) * ft.size(), cudaMemcpyHostToDevice, s));
+        RBS_TRY(warm_record(c, dft.ptr, c.d_prev.ptr));
+      }
       c.stats.launches += 1;
       k_rk_rates<<<nb, 128, 0, s>>>(n, c.d_vo.ptr, stage.ptr, ks.ptr + (size_t)st * 7 * n);
       RBS_CUDA_TRY(cudaGetLastError());

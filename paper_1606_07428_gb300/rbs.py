@@ -74,6 +74,7 @@ class rbs_options(ctypes.Structure):
         ("refine_precision", ctypes.c_int),
         ("pair_variant", ctypes.c_int),
         ("warm_start", ctypes.c_int),
+        ("warm_record", ctypes.c_int),
     ]
 
 

@@ -215,6 +215,16 @@ def profile_ellipsoids() -> Suspension:
     return random_ellipsoids(400, 8, 16, 0.10, 0.2, seed=1, name="profile_400_ellipsoids_p8")
 
 
+def c5_small() -> Suspension:
+    """The sedimenting-ellipsoid workload at 256 particles (same distributions as the 2,048-particle
+    one: p = 10 on an 11 x 22 grid, ~10% volume fraction, gap 0.2, F = (0, 0, -1), T = 0; seed 4),
+    small enough to time tens of RK4 steps."""
+    s = random_ellipsoids(256, 10, 22, 0.10, 0.2, seed=4, name="c5_256_ellipsoids_p10")
+    s.F = np.tile([0.0, 0.0, -1.0], (s.n, 1))
+    s.T = np.zeros((s.n, 3))
+    return s
+
+
 WORKLOADS = {
     "c1": c1_spheres,
     "profile": profile_ellipsoids,
@@ -222,4 +232,5 @@ WORKLOADS = {
     "c3": c3_ellipsoids,
     "c4": c4_batched,
     "c5": c5_sedimenting,
+    "c5_small": c5_small,
 }

@@ -1,0 +1,88 @@
+"""Parity at the full sizes of the workloads, in the launch configuration bench.py times (persistent
+grids, autotuned kernel variants): the GPU applies each operator to a seeded density over all
+312,000 (or 495,616) nodes and the oracle recomputes sampled rows one at a time, each over every
+source particle (smooth, upsampled-near and singular-rule parts).  Tolerances as in
+test_gpu_parity.py: float64 1e-12, double-float 1e-11, float32 2e-5 (relative to the largest sampled
+row); the mixed solve is checked through its residual at sampled rows and its constraints."""
+import numpy as np
+import pytest
+
+import oracle
+import suspensions
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def rbs():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1606_07428_gb300 import rbs as m
+    return m
+
+
+def sample_nodes(s, count, seed):
+    """Seeded nodes spread over the particle list, first and last node of the system included."""
+    rng = np.random.default_rng(seed)
+    pick = list(rng.choice(s.total_nodes, size=count - 2, replace=False))
+    return np.array(sorted(set(pick + [0, s.total_nodes - 1])))
+
+
+@pytest.fixture(scope="module")
+def c2(rbs):
+    s = suspensions.c2_ellipsoids()
+    ref = oracle.System(s.semi_axes, s.p, s.nphi, s.centres, s.quats)
+    ctx = rbs.Context(device=0, precision=rbs.RBS_PREC_MIXED)
+    ctx.set_suspension(s)
+    yield s, ref, ctx
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("DF", 1e-11), ("MIXED", 2e-5)])
+@pytest.mark.parametrize("op,kind,half,with_L", [("A", "K", 0.5, True), ("S", "S", 0.0, False)])
+def test_c2_operators_at_sampled_rows(rbs, c2, prec, tol, op, kind, half, with_L):
+    s, ref, ctx = c2
+    x = suspensions.random_density(21, s.total_nodes)
+    y = rbs.rbs_apply_operator(ctx.ctx, getattr(rbs, "RBS_OP_" + op), getattr(rbs, "RBS_PREC_" + prec), x)
+    rows = sample_nodes(s, 6, 5)
+    yr = ref.apply_rows(kind, x, rows, half=half, with_L=with_L)
+    assert np.abs(y[rows] - yr).max() < tol * np.abs(yr).max()
+
+
+def test_c2_float64_operator_at_sampled_rows(rbs, c2):
+    s, ref, ctx = c2
+    x = suspensions.random_density(22, s.total_nodes)
+    y = rbs.rbs_apply_operator(ctx.ctx, rbs.RBS_OP_HALF_K, rbs.RBS_PREC_FP64, x)
+    rows = sample_nodes(s, 4, 6)
+    yr = ref.apply_rows("K", x, rows, half=0.5)
+    assert np.abs(y[rows] - yr).max() < 1e-12 * np.abs(yr).max()
+
+
+def test_c2_mixed_solve_residual_rows_and_constraints(rbs, c2):
+    s, ref, ctx = c2
+    v, om, mu, its = rbs.rbs_mobility_solve(ctx.ctx, s.F, s.T, 1e-10, want_density=True)
+    rows = sample_nodes(s, 6, 7)
+    rho = ref.incident_density(s.F, s.T)
+    b_rows = -ref.apply_rows("K", rho, rows, half=0.5)
+    r_rows = b_rows - ref.apply_rows("K", mu, rows, half=0.5, with_L=True)
+    assert np.abs(r_rows).max() < 1e-8 * np.abs(b_rows).max()
+    # Eq. 20 for the solution, particle by particle
+    x, nrm, w = rbs.rbs_get_surface(ctx.ctx)
+    for i in (0, 499, 999):
+        sl = ref.sl(i)
+        pt = ref.particles[i]
+        assert np.abs((w[sl, None] * mu[sl]).sum(0)).max() < 1e-6 * np.abs(w[sl, None] * mu[sl]).sum()
+        assert np.abs((w[sl, None] * np.cross(pt.r, mu[sl])).sum(0)).max() < 1e-5 * np.abs(mu[sl]).sum() * pt.area
+
+
+def test_c5_operator_at_sampled_rows(rbs):
+    """The 2,048-ellipsoid sedimentation workload at full size (495,616 nodes), double-float."""
+    s = suspensions.c5_sedimenting()
+    ref = oracle.System(s.semi_axes, s.p, s.nphi, s.centres, s.quats)
+    x = suspensions.random_density(23, s.total_nodes)
+    with rbs.Context(device=0) as ctx:
+        ctx.set_suspension(s)
+        y = rbs.rbs_apply_operator(ctx.ctx, rbs.RBS_OP_A, rbs.RBS_PREC_DF, x)
+    rows = sample_nodes(s, 4, 8)
+    yr = ref.apply_rows("K", x, rows, half=0.5, with_L=True)
+    assert np.abs(y[rows] - yr).max() < 1e-11 * np.abs(yr).max()
