@@ -70,7 +70,9 @@ typedef struct {
   int preconditioner;  /* 1 (default): right block-diagonal preconditioner, the inverse of each
                           particle's own 1/2 I + K_ii + L_i (Section 3.2); 0: none */
   double near_delta;   /* particles i, j are near when |c_i - c_j| < R_i + R_j + near_delta, R the
-                          largest semi-axis (default 1.0); near sources use an upsampled grid */
+                          bounding radius: the largest semi-axis of an ellipsoid, see
+                          rbs_set_geometry_sh for a coefficient surface (default 1.0); near
+                          sources use an upsampled grid */
   int p_up_factor;     /* near sources are upsampled to order p_up_factor * p (default 2) */
   int p_self_factor;   /* singular self rule of order p_self_factor * p (default 2) */
   double viscosity;    /* fluid viscosity (default 1.0) */
@@ -114,7 +116,7 @@ typedef struct {
   double solve_ms;       /* wall time of the last rbs_mobility_solve */
   long long total_nodes;
   int n_particles;
-  int n_shapes;          /* distinct (semi-axes, p, n_phi) body shapes */
+  int n_shapes;          /* distinct body shapes: (semi-axes or input surface, p, n_phi) */
   long long near_pairs;  /* ordered (target, source) particle pairs treated as near */
   long long far_pairs;   /* (target node, source node) pairs of the smooth pair sum per apply */
   long long launches;    /* kernels launched by the context since creation or rbs_reset_stats */
@@ -151,6 +153,32 @@ void rbs_destroy(rbs_ctx* ctx);
  */
 int rbs_set_geometry(rbs_ctx* ctx, int n, const double* semi_axes, const int* p, const int* nphi,
                      const double* centres, const double* quats, const int* suspension_id);
+
+/* Largest degree of a coefficient surface accepted by rbs_set_geometry_sh. */
+#define RBS_MAX_SHAPE_DEGREE 24
+
+/*
+ * Define a suspension of general genus-0 particles whose surfaces are given by spherical-harmonic
+ * coefficients (Section 3, Eq. 31; tangents by spectral differentiation, Eq. 37; area element Eq. 36).
+ *  nshape       number of distinct input surfaces, >= 1
+ *  shape_pg     nshape, degree p_g of each surface, 1 <= p_g <= RBS_MAX_SHAPE_DEGREE
+ *  shape_coef   the surfaces' coefficients, one after another: surface k holds 3 x (p_g + 1)^2
+ *               doubles, the x row, then the y row, then the z row; each row in the library's basis
+ *               order of real orthonormal harmonics without the Condon-Shortley sign: m = 0..p_g,
+ *               n = m..p_g, the cos(m phi) term then, for m > 0, the sin(m phi) term
+ *  shape_of     n, the input surface of each particle, 0 <= shape_of[i] < nshape
+ *  p, nphi, centres, quats, suspension_id   as for rbs_set_geometry
+ * Each surface's body frame is centred at its area centroid on the particle's grid (the centroid of
+ * Eq. 18), so centres give that centroid's lab position.  The bounding radius R of the near criterion
+ * is the largest centroid distance over the nodes of the upsampled grid, and the overlap test uses the
+ * smallest such distance.  Returns RBS_EINVAL for a surface whose area element vanishes on a grid or
+ * whose parametrisation is inward (negative enclosed volume).  The learned warm start's features
+ * take (R, R, R) as the semi-axes of such a particle.  All arrays are host memory, read during the call
+ * and not retained.
+ */
+int rbs_set_geometry_sh(rbs_ctx* ctx, int n, int nshape, const int* shape_pg, const double* shape_coef,
+                        const int* shape_of, const int* p, const int* nphi, const double* centres,
+                        const double* quats, const int* suspension_id);
 
 /* Number of surface nodes of the current geometry (3 * that many unknowns). */
 long long rbs_total_nodes(const rbs_ctx* ctx);

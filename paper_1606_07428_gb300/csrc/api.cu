@@ -144,35 +144,34 @@ void rbs_destroy(rbs_ctx* h) {
   delete h;
 }
 
-int rbs_set_geometry(rbs_ctx* h, int n, const double* semi_axes, const int* p, const int* nphi, const double* centres,
-                     const double* quats, const int* suspension_id) {
-  if (!h) return RBS_EINVAL;
-  Context& c = h->c;
-  if (n < 1 || !semi_axes || !p || !centres || !quats)
-    return finish(c, Status::Err(RBS_EINVAL, "set_geometry: null array or n < 1"));
-  if (!finite_all(semi_axes, 3LL * n) || !finite_all(centres, 3LL * n) || !finite_all(quats, 4LL * n))
-    return finish(c, Status::Err(RBS_EINVAL, "set_geometry: non-finite input"));
+namespace {
+
+// Checks shared by both geometry entry points: grids, orientations and suspension ids.
+Status check_particles(int n, const int* p, const int* nphi, const double* centres, const double* quats,
+                       const int* suspension_id) {
+  if (!finite_all(centres, 3LL * n) || !finite_all(quats, 4LL * n))
+    return Status::Err(RBS_EINVAL, "set_geometry: non-finite input");
   for (int i = 0; i < n; ++i) {
-    if (!(semi_axes[3 * i] > 0 && semi_axes[3 * i + 1] > 0 && semi_axes[3 * i + 2] > 0))
-      return finish(c, Status::Err(RBS_EINVAL, "set_geometry: semi-axes must be positive"));
-    if (p[i] < 2 || p[i] > 32) return finish(c, Status::Err(RBS_EINVAL, "set_geometry: p must be in [2, 32]"));
+    if (p[i] < 2 || p[i] > 32) return Status::Err(RBS_EINVAL, "set_geometry: p must be in [2, 32]");
     int nf = nphi ? nphi[i] : 2 * p[i];
     if (nf < 2 * p[i] || nf % 2 != 0 || nf > 4 * p[i] + 4)
-      return finish(c, Status::Err(RBS_EINVAL, "set_geometry: nphi must be even and in [2p, 4p + 4]"));
+      return Status::Err(RBS_EINVAL, "set_geometry: nphi must be even and in [2p, 4p + 4]");
     const double* q = quats + 4 * i;
     double qn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-    if (!(qn > 1e-12)) return finish(c, Status::Err(RBS_EINVAL, "set_geometry: zero quaternion"));
+    if (!(qn > 1e-12)) return Status::Err(RBS_EINVAL, "set_geometry: zero quaternion");
     if (suspension_id && i > 0 && suspension_id[i] != suspension_id[i - 1]) {
       for (int k = 0; k < i - 1; ++k)
         if (suspension_id[k] == suspension_id[i])
-          return finish(c, Status::Err(RBS_EINVAL, "set_geometry: particles of one suspension must be contiguous"));
+          return Status::Err(RBS_EINVAL, "set_geometry: particles of one suspension must be contiguous");
     }
   }
-  Status s = enter(c);
-  if (!s.ok()) return finish(c, s);
+  return Status::Ok();
+}
+
+void store_particles(Context& c, int n, const int* p, const int* nphi, const double* centres, const double* quats,
+                     const int* suspension_id) {
   c.have_geometry = false;
   c.n = n;
-  c.axes.assign(semi_axes, semi_axes + 3LL * n);
   c.centres.assign(centres, centres + 3LL * n);
   c.quats.assign(quats, quats + 4LL * n);
   c.p.assign(p, p + n);
@@ -180,6 +179,63 @@ int rbs_set_geometry(rbs_ctx* h, int n, const double* semi_axes, const int* p, c
   for (int i = 0; i < n; ++i) c.nphi[i] = nphi ? nphi[i] : 2 * p[i];
   c.sid.assign(n, 0);
   if (suspension_id) c.sid.assign(suspension_id, suspension_id + n);
+}
+
+}  // namespace
+
+int rbs_set_geometry(rbs_ctx* h, int n, const double* semi_axes, const int* p, const int* nphi, const double* centres,
+                     const double* quats, const int* suspension_id) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (n < 1 || !semi_axes || !p || !centres || !quats)
+    return finish(c, Status::Err(RBS_EINVAL, "set_geometry: null array or n < 1"));
+  if (!finite_all(semi_axes, 3LL * n)) return finish(c, Status::Err(RBS_EINVAL, "set_geometry: non-finite input"));
+  for (int i = 0; i < n; ++i)
+    if (!(semi_axes[3 * i] > 0 && semi_axes[3 * i + 1] > 0 && semi_axes[3 * i + 2] > 0))
+      return finish(c, Status::Err(RBS_EINVAL, "set_geometry: semi-axes must be positive"));
+  Status s = check_particles(n, p, nphi, centres, quats, suspension_id);
+  if (!s.ok()) return finish(c, s);
+  s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  store_particles(c, n, p, nphi, centres, quats, suspension_id);
+  c.axes.assign(semi_axes, semi_axes + 3LL * n);
+  c.cs_of.clear();
+  c.cs_pg.clear();
+  c.cs_off.clear();
+  c.cs_coef.clear();
+  return finish(c, rbs::build_geometry(c));
+}
+
+int rbs_set_geometry_sh(rbs_ctx* h, int n, int nshape, const int* shape_pg, const double* shape_coef,
+                        const int* shape_of, const int* p, const int* nphi, const double* centres, const double* quats,
+                        const int* suspension_id) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (n < 1 || nshape < 1 || !shape_pg || !shape_coef || !shape_of || !p || !centres || !quats)
+    return finish(c, Status::Err(RBS_EINVAL, "set_geometry_sh: null array, n < 1 or nshape < 1"));
+  std::vector<long long> off(nshape);
+  long long total = 0;
+  for (int k = 0; k < nshape; ++k) {
+    if (shape_pg[k] < 1 || shape_pg[k] > RBS_MAX_SHAPE_DEGREE)
+      return finish(c, Status::Err(RBS_EINVAL, "set_geometry_sh: shape degree must be in [1, RBS_MAX_SHAPE_DEGREE]"));
+    off[k] = total;
+    total += 3LL * (shape_pg[k] + 1) * (shape_pg[k] + 1);
+  }
+  if (!finite_all(shape_coef, total))
+    return finish(c, Status::Err(RBS_EINVAL, "set_geometry_sh: non-finite coefficient"));
+  for (int i = 0; i < n; ++i)
+    if (shape_of[i] < 0 || shape_of[i] >= nshape)
+      return finish(c, Status::Err(RBS_EINVAL, "set_geometry_sh: shape_of out of range"));
+  Status s = check_particles(n, p, nphi, centres, quats, suspension_id);
+  if (!s.ok()) return finish(c, s);
+  s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  store_particles(c, n, p, nphi, centres, quats, suspension_id);
+  c.axes.assign(3LL * n, 0.0);
+  c.cs_of.assign(shape_of, shape_of + n);
+  c.cs_pg.assign(shape_pg, shape_pg + nshape);
+  c.cs_off = off;
+  c.cs_coef.assign(shape_coef, shape_coef + total);
   return finish(c, rbs::build_geometry(c));
 }
 

@@ -87,9 +87,13 @@ struct Grid {
   DevBuf<float> d_up32;
 };
 
-// One distinct body shape (semi-axes, p, n_phi).
+// One distinct body shape: an ellipsoid (semi-axes) or an input coefficient surface, on one
+// (p, n_phi) grid.
 struct Shape {
+  int kind = 0;  // 0 ellipsoid, 1 coefficient surface
   double a = 0, b = 0, c = 0;
+  int cs = -1;   // coefficient surface: index among the inputs
+  double radius = 0, rmin = 0;  // largest / smallest centroid distance (near criterion, overlap test)
   int grid = 0;
   int np = 0;
   size_t block_off = 0;  // offset (in elements) of its 3np x 3np blocks in the block arrays
@@ -127,9 +131,16 @@ struct Context {
   DevBuf<double4> d_x;  // lab position, w = quadrature weight
   DevBuf<double4> d_nrm;  // lab normal, w = unused
   DevBuf<int> d_pid;
-  // shape-level device data
-  DevBuf<double> d_shape_axes;  // nshape x 3
-  DevBuf<int> d_shape_grid_np;  // nshape x 2 (np, grid index)
+  // coefficient surfaces of rbs_set_geometry_sh (empty: every particle is an ellipsoid): per
+  // particle its input surface, per input surface its degree and first coefficient
+  std::vector<int> cs_of, cs_pg;
+  std::vector<long long> cs_off;
+  std::vector<double> cs_coef;
+  // shape-level device data (per distinct shape): kind, semi-axes, degree, coefficient offset
+  // (into d_sh_coef, -1 for none) and the centroid shift of a coefficient surface
+  DevBuf<int> d_sh_kind, d_sh_pg;
+  DevBuf<double> d_sh_axes, d_sh_coef, d_sh_shift;
+  DevBuf<long long> d_sh_coef_off;
   DevBuf<double> d_blockK, d_blockS, d_precond;  // body-frame 3np x 3np per shape, float64
   DevBuf<float> d_blockK32, d_precond32;
   DevBuf<long long> d_block_off;  // nshape
@@ -150,6 +161,7 @@ struct Context {
   std::vector<int4> bwork;
   DevBuf<int4> d_bwork;
   int max_np = 0;
+  int max_np_shape = 0;
   // per upsampled-source particle: interpolation matrix of its grid (float64 and float32)
   DevBuf<const double*> d_upU;
   DevBuf<const float*> d_upU32;

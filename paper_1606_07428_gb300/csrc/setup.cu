@@ -128,42 +128,282 @@ __global__ void k_analysis(int np, int nbasis, const double* Yg, const double4* 
   An[i] = Yg[(long long)node * nbasis + b] * gp[node].w;
 }
 
-// Surface nodes of all particles (lab frame): x = c + R D s, n = R normalise(D^{-1} s),
-// weight = (2 pi / nphi) lambda_j |cof(D) s| (Eq. 35 with W / sin(theta) = |cof(D) s|).
-__global__ void k_nodes(int n, const long long* offset, const int* pvec, const int* nphivec, const double* axes,
-                        const double* centre, const double* rot, const long long* gtab_off, const double* gtab,
-                        double4* x, double4* nrm, int* pid) {
+// ------------------------------------------------------------------------------------------
+// Particle surfaces.  An ellipsoid x = D s (D = diag(a, b, c)): J = |cof(D) s| is the area per unit
+// solid angle (W / sin(theta) of Eq. 36) and the normal is D^{-1} s normalised.  A coefficient
+// surface x = sum c_nm Y_nm (Eq. 31) in the library's basis order (m = 0..p_g, n = m..p_g, cos then
+// sin, orthonormal, no Condon-Shortley sign): tangents by spectral differentiation (Eq. 37) with the
+// regular forms dPbar_n^m/dtheta = (sqrt((n+m)(n-m+1)) Pbar_n^{m-1} - sqrt((n+m+1)(n-m)) Pbar_n^{m+1})/2,
+// dPbar_n^0/dtheta = -sqrt(n(n+1)) Pbar_n^1 and Pbar_n^m / sin(theta) from the n-recurrence started at
+// sin^(m-1)(theta), so J = |x_theta x (x_phi / sin(theta))| holds at the poles too.  The body frame of a
+// coefficient surface is centred at its area centroid (shift).
+constexpr int kMaxShapeDegree = RBS_MAX_SHAPE_DEGREE;
+
+struct ShapeRef {
+  int kind;  // 0 ellipsoid, 1 coefficient surface
+  double a, b, c;
+  const double* coef;
+  int pg;
+  double ox, oy, oz;  // centroid shift
+};
+
+__device__ ShapeRef shape_ref(int s, const int* kind, const double* axes, const int* pg, const long long* coef_off,
+                              const double* coef, const double* shift) {
+  ShapeRef r;
+  r.kind = kind[s];
+  r.a = axes[3 * s];
+  r.b = axes[3 * s + 1];
+  r.c = axes[3 * s + 2];
+  r.pg = pg[s];
+  r.coef = coef + (coef_off[s] >= 0 ? coef_off[s] : 0);
+  r.ox = shift[3 * s];
+  r.oy = shift[3 * s + 1];
+  r.oz = shift[3 * s + 2];
+  return r;
+}
+
+// One column m of normalised associated Legendre values Pbar_n^m(t), n = m..pg (index n), and of
+// Pbar_n^m / sin(theta) (m >= 1); pmm_prev is Pbar_{m-1}^{m-1} on entry, Pbar_m^m on exit.
+__device__ void legendre_column(int m, int pg, double t, double st, double& pmm, double* P, double* Q) {
+  double qmm = 0.0;
+  if (m > 0) {
+    qmm = sqrt((2.0 * m + 1.0) / (2.0 * m)) * pmm;  // Pbar_m^m / sin
+    pmm = qmm * st;
+  }
+  for (int n = 0; n <= pg; ++n) P[n] = Q[n] = 0.0;
+  P[m] = pmm;
+  Q[m] = qmm;
+  if (m + 1 <= pg) {
+    P[m + 1] = sqrt(2.0 * m + 3.0) * t * pmm;
+    Q[m + 1] = sqrt(2.0 * m + 3.0) * t * qmm;
+  }
+  for (int n = m + 2; n <= pg; ++n) {
+    const double a = sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+    const double b = sqrt(((n - 1.0) * (n - 1.0) - (double)m * m) / (4.0 * (n - 1.0) * (n - 1.0) - 1.0));
+    P[n] = a * (t * P[n - 1] - b * P[n - 2]);
+    Q[n] = a * (t * Q[n - 1] - b * Q[n - 2]);
+  }
+}
+
+__device__ void eval_surface(const ShapeRef& S, double sx, double sy, double sz, double* x, double* J, double* nrm) {
+  if (S.kind == 0) {
+    x[0] = S.a * sx;
+    x[1] = S.b * sy;
+    x[2] = S.c * sz;
+    const double cx = S.b * S.c * sx, cy = S.a * S.c * sy, cz = S.a * S.b * sz;
+    *J = sqrt(cx * cx + cy * cy + cz * cz);
+    double gx = sx / S.a, gy = sy / S.b, gz = sz / S.c;
+    const double gn = rsqrt(gx * gx + gy * gy + gz * gz);
+    nrm[0] = gx * gn;
+    nrm[1] = gy * gn;
+    nrm[2] = gz * gn;
+    return;
+  }
+  const double t = fmin(1.0, fmax(-1.0, sz)), st = sqrt(fmax(0.0, sx * sx + sy * sy));
+  const double phi = atan2(sy, sx);
+  const int pg = S.pg;
+  const int nc = (pg + 1) * (pg + 1);
+  double P0[kMaxShapeDegree + 1], P1[kMaxShapeDegree + 1], P2[kMaxShapeDegree + 1];
+  double Q0[kMaxShapeDegree + 1], Q1[kMaxShapeDegree + 1], Q2[kMaxShapeDegree + 1];
+  double* Pm = P0;  // column m - 1
+  double* Pc = P1;  // column m
+  double* Pp = P2;  // column m + 1
+  double* Qm = Q0;
+  double* Qc = Q1;
+  double* Qp = Q2;
+  double pmm = 0.28209479177387814;  // Pbar_0^0 = 1 / sqrt(4 pi)
+  legendre_column(0, pg, t, st, pmm, Pc, Qc);
+  double pmm_next = pmm;
+  if (pg >= 1) legendre_column(1, pg, t, st, pmm_next, Pp, Qp);
+  double xv[3] = {0, 0, 0}, xt[3] = {0, 0, 0}, xp[3] = {0, 0, 0};
+  const double r2 = 1.4142135623730951;
+  int b = 0;
+  for (int m = 0; m <= pg; ++m) {
+    double cm = 1.0, sm = 0.0;
+    if (m > 0) sincos(m * phi, &sm, &cm);
+    for (int n = m; n <= pg; ++n) {
+      double dP;
+      if (m == 0) {
+        dP = (n >= 1) ? -sqrt(n * (n + 1.0)) * Pp[n] : 0.0;
+      } else {
+        const double up = (m + 1 <= n) ? sqrt((n + m + 1.0) * (n - m)) * Pp[n] : 0.0;
+        dP = 0.5 * (sqrt((n + m) * (n - m + 1.0)) * Pm[n] - up);
+      }
+      if (m == 0) {
+        for (int q = 0; q < 3; ++q) {
+          const double cf = S.coef[q * nc + b];
+          xv[q] += cf * Pc[n];
+          xt[q] += cf * dP;
+        }
+        ++b;
+      } else {
+        for (int q = 0; q < 3; ++q) {
+          const double cc = S.coef[q * nc + b], cs = S.coef[q * nc + b + 1];
+          xv[q] += r2 * Pc[n] * (cc * cm + cs * sm);
+          xt[q] += r2 * dP * (cc * cm + cs * sm);
+          xp[q] += r2 * m * Qc[n] * (-cc * sm + cs * cm);
+        }
+        b += 2;
+      }
+    }
+    // roll the columns: m -> m + 1
+    double* tp = Pm;
+    Pm = Pc;
+    Pc = Pp;
+    Pp = tp;
+    tp = Qm;
+    Qm = Qc;
+    Qc = Qp;
+    Qp = tp;
+    if (m + 2 <= pg) legendre_column(m + 2, pg, t, st, pmm_next, Pp, Qp);
+  }
+  x[0] = xv[0] - S.ox;
+  x[1] = xv[1] - S.oy;
+  x[2] = xv[2] - S.oz;
+  const double c0 = xt[1] * xp[2] - xt[2] * xp[1], c1 = xt[2] * xp[0] - xt[0] * xp[2], c2 = xt[0] * xp[1] - xt[1] * xp[0];
+  *J = sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+  nrm[0] = c0 / *J;
+  nrm[1] = c1 / *J;
+  nrm[2] = c2 / *J;
+}
+
+#define RBS_SHAPE_ARGS const int *sh_kind, const double *sh_axes, const int *sh_pg, const long long *sh_coef_off, \
+                       const double *sh_coef, const double *sh_shift
+#define RBS_SHAPE_PASS c.d_sh_kind.ptr, c.d_sh_axes.ptr, c.d_sh_pg.ptr, c.d_sh_coef_off.ptr, c.d_sh_coef.ptr, \
+                       c.d_sh_shift.ptr
+#define RBS_SHAPE_REF(s) shape_ref((s), sh_kind, sh_axes, sh_pg, sh_coef_off, sh_coef, sh_shift)
+
+// Surface nodes of all particles (lab frame): x = c + R x_b(s), n = R n_b(s) and weight
+// (2 pi / nphi) lambda_j J(s) (Eq. 35 with W / sin(theta) = J), s the grid point of Eq. 33.
+__global__ void k_nodes(int n, const long long* offset, const int* pvec, const int* nphivec, const int* shape_of,
+                        RBS_SHAPE_ARGS, const double* centre, const double* rot, const long long* gtab_off,
+                        const double* gtab, double4* x, double4* nrm, int* pid) {
   for (int i = blockIdx.y; i < n; i += gridDim.y) {
-  long long o = offset[i];
-  int nphi = nphivec[i], p = pvec[i];
-  int np = (p + 1) * nphi;
-  const double* t = gtab + gtab_off[i];
+    const long long o = offset[i];
+    const int nphi = nphivec[i], p = pvec[i];
+    const int np = (p + 1) * nphi;
+    const double* t = gtab + gtab_off[i];
+    const double* lam = t + (p + 1);
+    const ShapeRef S = RBS_SHAPE_REF(shape_of[i]);
+    const double* R = rot + 9 * i;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < np; l += gridDim.x * blockDim.x) {
+      const int j = l / nphi, k = l % nphi;
+      const double ct = t[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+      double sp, cp;
+      sincospi(2.0 * k / nphi, &sp, &cp);
+      double xb[3], J, nb[3];
+      eval_surface(S, st * cp, st * sp, ct, xb, &J, nb);
+      const double w = 2.0 * kPi / nphi * lam[j] * J;
+      x[o + l] = make_double4(R[0] * xb[0] + R[1] * xb[1] + R[2] * xb[2] + centre[3 * i],
+                              R[3] * xb[0] + R[4] * xb[1] + R[5] * xb[2] + centre[3 * i + 1],
+                              R[6] * xb[0] + R[7] * xb[1] + R[8] * xb[2] + centre[3 * i + 2], w);
+      nrm[o + l] = make_double4(R[0] * nb[0] + R[1] * nb[1] + R[2] * nb[2], R[3] * nb[0] + R[4] * nb[1] + R[5] * nb[2],
+                                R[6] * nb[0] + R[7] * nb[1] + R[8] * nb[2], 0.0);
+      pid[o + l] = i;
+    }
+  }
+}
+
+// Coefficient surfaces: area centroid on the shape's own grid (the shift), then the largest and
+// smallest centroid distance over the nodes of its upsampled grid, the smallest J over both grids and
+// the enclosed volume sum w x.n / 3 (negative for an inward parametrisation).  One block per shape.
+struct ShapeGrid {
+  int s, p, nphi, pup;
+  long long t, t_up;  // offsets of (t, lambda) in the grid table
+};
+
+__global__ void k_shape_extent(const ShapeGrid* sg, RBS_SHAPE_ARGS, double* shift_out, const double* gtab,
+                               double* diag) {
+  __shared__ double red[5][256];
+  const ShapeGrid G = sg[blockIdx.x];
+  const int s = G.s;
+  ShapeRef S = RBS_SHAPE_REF(s);
+  S.ox = S.oy = S.oz = 0.0;
+  const int p = G.p, nphi = G.nphi;
+  const double* t = gtab + G.t;
   const double* lam = t + (p + 1);
-  double a = axes[3 * i], b = axes[3 * i + 1], cc = axes[3 * i + 2];
-  const double* R = rot + 9 * i;
-  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < np; l += gridDim.x * blockDim.x) {
-    int j = l / nphi, k = l % nphi;
-    double ct = t[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
-    double sp, cp;
-    sincospi(2.0 * k / nphi, &sp, &cp);
-    double sx = st * cp, sy = st * sp, sz = ct;
-    double bx = a * sx, by = b * sy, bz = cc * sz;
-    double gx = sx / a, gy = sy / b, gz = sz / cc;
-    double gn = rsqrt(gx * gx + gy * gy + gz * gz);
-    gx *= gn;
-    gy *= gn;
-    gz *= gn;
-    double J = sqrt((b * cc * sx) * (b * cc * sx) + (a * cc * sy) * (a * cc * sy) + (a * b * sz) * (a * b * sz));
-    double w = 2.0 * kPi / nphi * lam[j] * J;
-    double lx = R[0] * bx + R[1] * by + R[2] * bz + centre[3 * i];
-    double ly = R[3] * bx + R[4] * by + R[5] * bz + centre[3 * i + 1];
-    double lz = R[6] * bx + R[7] * by + R[8] * bz + centre[3 * i + 2];
-    x[o + l] = make_double4(lx, ly, lz, w);
-    nrm[o + l] = make_double4(R[0] * gx + R[1] * gy + R[2] * gz, R[3] * gx + R[4] * gy + R[5] * gz,
-                              R[6] * gx + R[7] * gy + R[8] * gz, 0.0);
-    pid[o + l] = i;
+  double acc[5] = {0, 0, 0, 0, 0};
+  double jmin = INFINITY;
+  for (int l = threadIdx.x; l < (p + 1) * nphi; l += blockDim.x) {
+    const int j = l / nphi, k = l % nphi;
+    const double ct = t[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double ssp, scp;
+    sincospi(2.0 * k / nphi, &ssp, &scp);
+    double xb[3], J, nb[3];
+    eval_surface(S, st * scp, st * ssp, ct, xb, &J, nb);
+    const double w = 2.0 * kPi / nphi * lam[j] * J;
+    acc[0] += w * xb[0];
+    acc[1] += w * xb[1];
+    acc[2] += w * xb[2];
+    acc[3] += w;
+    acc[4] += w * (xb[0] * nb[0] + xb[1] * nb[1] + xb[2] * nb[2]) / 3.0;
+    jmin = fmin(jmin, J);
   }
+  for (int q = 0; q < 5; ++q) red[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
+    __syncthreads();
   }
+  S.ox = red[0][0] / red[3][0];
+  S.oy = red[1][0] / red[3][0];
+  S.oz = red[2][0] / red[3][0];
+  const double vol = red[4][0];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    shift_out[3 * s] = S.ox;
+    shift_out[3 * s + 1] = S.oy;
+    shift_out[3 * s + 2] = S.oz;
+  }
+  const int pup = G.pup, nphi_up = nphi + 2 * (pup - p);
+  const double* tu = gtab + G.t_up;
+  double mx = 0.0, mn = INFINITY;
+  for (int l = threadIdx.x; l < (pup + 1) * nphi_up; l += blockDim.x) {
+    const int j = l / nphi_up, k = l % nphi_up;
+    const double ct = tu[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double ssp, scp;
+    sincospi(2.0 * k / nphi_up, &ssp, &scp);
+    double xb[3], J, nb[3];
+    eval_surface(S, st * scp, st * ssp, ct, xb, &J, nb);
+    const double d = sqrt(xb[0] * xb[0] + xb[1] * xb[1] + xb[2] * xb[2]);
+    mx = fmax(mx, d);
+    mn = fmin(mn, d);
+    jmin = fmin(jmin, J);
+  }
+  red[0][threadIdx.x] = mx;
+  red[1][threadIdx.x] = mn;
+  red[2][threadIdx.x] = jmin;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      red[0][threadIdx.x] = fmax(red[0][threadIdx.x], red[0][threadIdx.x + h]);
+      red[1][threadIdx.x] = fmin(red[1][threadIdx.x], red[1][threadIdx.x + h]);
+      red[2][threadIdx.x] = fmin(red[2][threadIdx.x], red[2][threadIdx.x + h]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    diag[4 * blockIdx.x] = red[0][0];
+    diag[4 * blockIdx.x + 1] = red[1][0];
+    diag[4 * blockIdx.x + 2] = red[2][0];
+    diag[4 * blockIdx.x + 3] = vol;
+  }
+}
+
+// Body-frame nodes (x_b, weight) of one shape on its own grid.
+__global__ void k_body_nodes(int np, int nphi, const double* t, const double* lam, int shape, RBS_SHAPE_ARGS,
+                             double4* out) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= np) return;
+  const ShapeRef S = RBS_SHAPE_REF(shape);
+  const int j = l / nphi, k = l % nphi;
+  const double ct = t[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+  double sp, cp;
+  sincospi(2.0 * k / nphi, &sp, &cp);
+  double xb[3], J, nb[3];
+  eval_surface(S, st * cp, st * sp, ct, xb, &J, nb);
+  out[l] = make_double4(xb[0], xb[1], xb[2], 2.0 * kPi / nphi * lam[j] * J);
 }
 
 // Per-particle area |Gamma_i| = sum w and inverse moment tensor (Eq. 18), one block per particle.
@@ -213,41 +453,35 @@ __global__ void k_moments(int n, const long long* offset, const double4* x, cons
 // C[((kind * nphi + k) * 9 + 3 al + be) * nrot + a] = omega_a J(s_a) kernel_{al be}(x_t - x(s_a)),
 // target t = (j, k), rotated point s_a = R_z(phi_k) rotpts[j][a]; kind 0 = traction (Eqs. 13, 22),
 // kind 1 = Stokeslet (Eq. 10).
-__global__ void k_self_kernel_values(int nphi, int nrot, double tj, const double* axes, const double4* rotpts_j,
-                                     double* Cbase, size_t perC) {
+__global__ void k_self_kernel_values(int nphi, int nrot, double tj, const int* shape_ids, RBS_SHAPE_ARGS,
+                                     const double4* rotpts_j, double* Cbase, size_t perC) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   int k = blockIdx.y;
   if (a >= nrot) return;
-  double ax = axes[3 * blockIdx.z], bx = axes[3 * blockIdx.z + 1], cx = axes[3 * blockIdx.z + 2];
+  const ShapeRef S = RBS_SHAPE_REF(shape_ids[blockIdx.z]);
   double* C = Cbase + perC * blockIdx.z;
   double sp, cp;
   sincospi(2.0 * k / nphi, &sp, &cp);
-  double4 q = rotpts_j[a];
-  double sx = cp * q.x - sp * q.y, sy = sp * q.x + cp * q.y, sz = q.z;
-  double st = sqrt(fmax(0.0, 1.0 - tj * tj));
-  double tx = st * cp, ty = st * sp, tz = tj;
-  double xt0 = ax * tx, xt1 = bx * ty, xt2 = cx * tz;
-  double g0 = tx / ax, g1 = ty / bx, g2 = tz / cx;
-  double gn = rsqrt(g0 * g0 + g1 * g1 + g2 * g2);
-  g0 *= gn;
-  g1 *= gn;
-  g2 *= gn;
-  double r0 = xt0 - ax * sx, r1 = xt1 - bx * sy, r2 = xt2 - cx * sz;
-  double J = sqrt((bx * cx * sx) * (bx * cx * sx) + (ax * cx * sy) * (ax * cx * sy) + (ax * bx * sz) * (ax * bx * sz));
-  double wJ = q.w * J;
-  double d2 = r0 * r0 + r1 * r1 + r2 * r2;
-  double inv = rsqrt(d2);
-  double inv2 = inv * inv;
-  double rr[3] = {r0, r1, r2};
-  double rn = r0 * g0 + r1 * g1 + r2 * g2;
-  double ck = -3.0 / (4.0 * kPi) * rn * inv2 * inv2 * inv * wJ;
-  double cs = wJ / (8.0 * kPi);
+  const double4 q = rotpts_j[a];
+  const double st = sqrt(fmax(0.0, 1.0 - tj * tj));
+  double xt[3], Jt, g[3];
+  eval_surface(S, st * cp, st * sp, tj, xt, &Jt, g);
+  double y[3], J, ny[3];
+  eval_surface(S, cp * q.x - sp * q.y, sp * q.x + cp * q.y, q.z, y, &J, ny);
+  const double r0 = xt[0] - y[0], r1 = xt[1] - y[1], r2 = xt[2] - y[2];
+  const double wJ = q.w * J;
+  const double d2 = r0 * r0 + r1 * r1 + r2 * r2;
+  const double inv = rsqrt(d2);
+  const double inv2 = inv * inv;
+  const double rr[3] = {r0, r1, r2};
+  const double rn = r0 * g[0] + r1 * g[1] + r2 * g[2];
+  const double ck = -3.0 / (4.0 * kPi) * rn * inv2 * inv2 * inv * wJ;
+  const double cs = wJ / (8.0 * kPi);
   for (int al = 0; al < 3; ++al)
     for (int be = 0; be < 3; ++be) {
-      double rab = rr[al] * rr[be];
+      const double rab = rr[al] * rr[be];
       C[((long long)(0 * nphi + k) * 9 + 3 * al + be) * nrot + a] = ck * rab;
-      C[((long long)(1 * nphi + k) * 9 + 3 * al + be) * nrot + a] =
-          cs * ((al == be ? inv : 0.0) + rab * inv2 * inv);
+      C[((long long)(1 * nphi + k) * 9 + 3 * al + be) * nrot + a] = cs * ((al == be ? inv : 0.0) + rab * inv2 * inv);
     }
 }
 
@@ -275,32 +509,18 @@ __global__ void k_self_scatter(int nphi, int np, int j, const double* Gbase, siz
 
 // Preconditioner matrix before inversion: M = 1/2 I + K0 + L0 in the body frame, with
 // L0_ts = w_s (I - [r_t]x [r_s]x) (Eq. 26 written as a block; r the body-frame node).
-__global__ void k_precond_matrix(int np, int nphi, const double* t, const double* lam, double ax, double bx,
-                                 double cx, const double* BK, double* M) {
+__global__ void k_precond_matrix(int np, const double4* body, const double* BK, double* M) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long dim = 3LL * np;
   if (i >= dim * dim) return;
   int row = (int)(i / dim), col = (int)(i % dim);
   int tn = row / 3, al = row % 3, sn = col / 3, be = col % 3;
-  auto node = [&](int l, double* r, double* w) {
-    int j = l / nphi, k = l % nphi;
-    double ct = t[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
-    double sp, cp;
-    sincospi(2.0 * k / nphi, &sp, &cp);
-    double sx = st * cp, sy = st * sp, sz = ct;
-    r[0] = ax * sx;
-    r[1] = bx * sy;
-    r[2] = cx * sz;
-    *w = 2.0 * kPi / nphi * lam[j] *
-         sqrt((bx * cx * sx) * (bx * cx * sx) + (ax * cx * sy) * (ax * cx * sy) + (ax * bx * sz) * (ax * bx * sz));
-  };
-  double rt[3], rs[3], wt, ws;
-  node(tn, rt, &wt);
-  node(sn, rs, &ws);
+  const double4 xt = body[tn], xs = body[sn];
+  const double rt[3] = {xt.x, xt.y, xt.z}, rs[3] = {xs.x, xs.y, xs.z};
   // ([a]x [b]x)_{al be} = a_be b_al - (a . b) delta_{al be}
   double dot = rt[0] * rs[0] + rt[1] * rs[1] + rt[2] * rs[2];
   double cc = rt[be] * rs[al] - (al == be ? dot : 0.0);
-  double Lv = ws * ((al == be ? 1.0 : 0.0) - cc);
+  double Lv = xs.w * ((al == be ? 1.0 : 0.0) - cc);
   M[i] = BK[i] + Lv + (row == col ? 0.5 : 0.0);
 }
 
@@ -320,30 +540,29 @@ __global__ void k_to_float(const double* in, float* out, long long n) {
 // Upsampled source nodes of every near-source particle: lab positions and weights on its
 // (pup + 1) x nphi_up grid.
 __global__ void k_up_nodes(int nu, const int* up_particle, const long long* up_off, const int* pvec, const int* nphivec,
-                           const int* pupvec, const double* axes, const double* centre, const double* rot,
-                           const long long* gtab_up_off, const double* gtab, double4* out) {
+                           const int* pupvec, const int* shape_of, RBS_SHAPE_ARGS, const double* centre,
+                           const double* rot, const long long* gtab_up_off, const double* gtab, double4* out) {
   for (int u = blockIdx.y; u < nu; u += gridDim.y) {
-  int i = up_particle[u];
-  int pup = pupvec[i];
-  int nphi_up = nphivec[i] + 2 * (pup - pvec[i]);
-  int nup = (pup + 1) * nphi_up;
-  const double* t = gtab + gtab_up_off[i];
-  const double* lam = t + (pup + 1);
-  double a = axes[3 * i], b = axes[3 * i + 1], cc = axes[3 * i + 2];
-  const double* R = rot + 9 * i;
-  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nup; l += gridDim.x * blockDim.x) {
-    int j = l / nphi_up, k = l % nphi_up;
-    double ct = t[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
-    double sp, cp;
-    sincospi(2.0 * k / nphi_up, &sp, &cp);
-    double sx = st * cp, sy = st * sp, sz = ct;
-    double bx = a * sx, by = b * sy, bz = cc * sz;
-    double J = sqrt((b * cc * sx) * (b * cc * sx) + (a * cc * sy) * (a * cc * sy) + (a * b * sz) * (a * b * sz));
-    out[up_off[u] + l] = make_double4(R[0] * bx + R[1] * by + R[2] * bz + centre[3 * i],
-                                      R[3] * bx + R[4] * by + R[5] * bz + centre[3 * i + 1],
-                                      R[6] * bx + R[7] * by + R[8] * bz + centre[3 * i + 2],
-                                      2.0 * kPi / nphi_up * lam[j] * J);
-  }
+    const int i = up_particle[u];
+    const int pup = pupvec[i];
+    const int nphi_up = nphivec[i] + 2 * (pup - pvec[i]);
+    const int nup = (pup + 1) * nphi_up;
+    const double* t = gtab + gtab_up_off[i];
+    const double* lam = t + (pup + 1);
+    const ShapeRef S = RBS_SHAPE_REF(shape_of[i]);
+    const double* R = rot + 9 * i;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nup; l += gridDim.x * blockDim.x) {
+      const int j = l / nphi_up, k = l % nphi_up;
+      const double ct = t[j], st = sqrt(fmax(0.0, 1.0 - ct * ct));
+      double sp, cp;
+      sincospi(2.0 * k / nphi_up, &sp, &cp);
+      double xb[3], J, nb[3];
+      eval_surface(S, st * cp, st * sp, ct, xb, &J, nb);
+      out[up_off[u] + l] = make_double4(R[0] * xb[0] + R[1] * xb[1] + R[2] * xb[2] + centre[3 * i],
+                                        R[3] * xb[0] + R[4] * xb[1] + R[5] * xb[2] + centre[3 * i + 1],
+                                        R[6] * xb[0] + R[7] * xb[1] + R[8] * xb[2] + centre[3 * i + 2],
+                                        2.0 * kPi / nphi_up * lam[j] * J);
+    }
   }
 }
 
@@ -486,24 +705,17 @@ static Status build_self_blocks(Context& c, int gi, const std::vector<int>& shap
   DevBuf<double> C, G;
   RBS_TRY(C.alloc(perC * chunk));
   RBS_TRY(G.alloc(perG * chunk));
-  std::vector<double> ax(3 * (size_t)nsh);
   std::vector<long long> off(nsh);
-  for (int k = 0; k < nsh; ++k) {
-    const Shape& sh = c.shapes[shape_ids[k]];
-    ax[3 * k] = sh.a;
-    ax[3 * k + 1] = sh.b;
-    ax[3 * k + 2] = sh.c;
-    off[k] = (long long)sh.block_off;
-  }
-  DevBuf<double> d_ax;
+  for (int k = 0; k < nsh; ++k) off[k] = (long long)c.shapes[shape_ids[k]].block_off;
+  DevBuf<int> d_ids;
   DevBuf<long long> d_off;
-  RBS_TRY(upload(d_ax, ax, s));
+  RBS_TRY(upload(d_ids, shape_ids, s));
   RBS_TRY(upload(d_off, off, s));
   for (int start = 0; start < nsh; start += chunk) {
     int cnt = std::min(chunk, nsh - start);
     for (int j = 0; j <= g.p; ++j) {
       dim3 grd(cdiv(g.nrot, 128), g.nphi, cnt);
-      k_self_kernel_values<<<grd, 128, 0, s>>>(g.nphi, g.nrot, g.t[j], d_ax.ptr + 3 * (size_t)start,
+      k_self_kernel_values<<<grd, 128, 0, s>>>(g.nphi, g.nrot, g.t[j], d_ids.ptr + start, RBS_SHAPE_PASS,
                                                (const double4*)g.d_rotpts.ptr + (size_t)j * g.nrot, C.ptr, perC);
       RBS_CUDA_TRY(cudaGetLastError());
       RBS_TRY(dgemm_batched(s, (int)rowsC, g.np, g.nrot, C.ptr, g.nrot, (long long)perC,
@@ -536,8 +748,8 @@ Status place_particles(Context& c) {
   int maxnp = 0;
   for (int i = 0; i < n; ++i) maxnp = std::max(maxnp, (int)(c.offset[i + 1] - c.offset[i]));
   dim3 grd(cdiv(maxnp, 128), std::min(n, 65535));
-  k_nodes<<<grd, 128, 0, s>>>(n, c.d_offset.ptr, c.d_p.ptr, c.d_nphi.ptr, c.d_axes.ptr, c.d_centre.ptr, c.d_rot.ptr,
-                              c.d_gtab_off.ptr, c.d_gtab.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr);
+  k_nodes<<<grd, 128, 0, s>>>(n, c.d_offset.ptr, c.d_p.ptr, c.d_nphi.ptr, c.d_shape.ptr, RBS_SHAPE_PASS,
+                              c.d_centre.ptr, c.d_rot.ptr, c.d_gtab_off.ptr, c.d_gtab.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr);
   k_moments<<<n, 256, 0, s>>>(n, c.d_offset.ptr, c.d_x.ptr, c.d_centre.ptr, c.d_area.ptr, c.d_tauinv.ptr);
   RBS_CUDA_TRY(cudaGetLastError());
   return Status::Ok();
@@ -553,7 +765,7 @@ Status build_near(Context& c) {
     std::vector<double> R(n);
     double rmax = 0.0;
     for (int i = 0; i < n; ++i) {
-      R[i] = std::max(c.axes[3 * i], std::max(c.axes[3 * i + 1], c.axes[3 * i + 2]));
+      R[i] = c.shapes[c.shape_of[i]].radius;
       rmax = std::max(rmax, R[i]);
     }
     double cell = 2.0 * rmax + c.opt.near_delta;
@@ -580,9 +792,7 @@ Status build_near(Context& c) {
         double dx = c.centres[3 * i] - c.centres[3 * j], dy = c.centres[3 * i + 1] - c.centres[3 * j + 1],
                dz = c.centres[3 * i + 2] - c.centres[3 * j + 2];
         double d = std::sqrt(dx * dx + dy * dy + dz * dz);
-        double rmin_i = std::min(c.axes[3 * i], std::min(c.axes[3 * i + 1], c.axes[3 * i + 2]));
-        double rmin_j = std::min(c.axes[3 * j], std::min(c.axes[3 * j + 1], c.axes[3 * j + 2]));
-        if (d < rmin_i + rmin_j)
+        if (d < c.shapes[c.shape_of[i]].rmin + c.shapes[c.shape_of[j]].rmin)
           return Status::Err(RBS_EOVERLAP, "particles " + std::to_string(i) + " and " + std::to_string(j) +
                                                " overlap (inscribed spheres intersect)");
         if (d < R[i] + R[j] + c.opt.near_delta) c.near_pairs.push_back(make_int2(i, j));
@@ -625,8 +835,8 @@ Status build_near(Context& c) {
     for (Grid* g : c.grids) maxnup = std::max(maxnup, g->nup);
     dim3 grd(cdiv(maxnup, 128), (unsigned)std::min<size_t>(c.up_particle.size(), 65535));
     k_up_nodes<<<grd, 128, 0, s>>>((int)c.up_particle.size(), c.d_up_particle.ptr, c.d_up_off.ptr, c.d_p.ptr, c.d_nphi.ptr,
-                                   c.d_pup.ptr, c.d_axes.ptr, c.d_centre.ptr, c.d_rot.ptr, c.d_gtab_up_off.ptr, c.d_gtab.ptr,
-                                   c.d_up_x.ptr);
+                                   c.d_pup.ptr, c.d_shape.ptr, RBS_SHAPE_PASS, c.d_centre.ptr, c.d_rot.ptr,
+                                   c.d_gtab_up_off.ptr, c.d_gtab.ptr, c.d_up_x.ptr);
     RBS_CUDA_TRY(cudaGetLastError());
   }
 
@@ -644,6 +854,73 @@ Status update_configuration(Context& c, const double* centres, const double* qua
   for (int i = 0; i < c.n; ++i) quat_to_rot_host(&c.quats[4 * i], &c.rot[9 * i]);
   RBS_TRY(place_particles(c));
   return build_near(c);
+}
+
+// Device tables of the distinct shapes; for coefficient surfaces, their centroid shift, bounding
+// radius and checks (a positive area element everywhere, an outward parametrisation).  Particles on a
+// coefficient surface report (R, R, R) as their semi-axes, R the bounding radius.
+static Status build_shape_tables(Context& c, const std::vector<long long>& grid_tab_off,
+                                 const std::vector<long long>& grid_tab_up_off) {
+  cudaStream_t s = c.stream;
+  const int ns = (int)c.shapes.size();
+  std::vector<int> kind(ns), pg(ns, 0);
+  std::vector<double> axes(3 * (size_t)ns, 0.0), shift(3 * (size_t)ns, 0.0);
+  std::vector<long long> coef_off(ns, -1);
+  std::vector<ShapeGrid> sg;
+  c.max_np_shape = 0;
+  for (int k = 0; k < ns; ++k) {
+    const Shape& sh = c.shapes[k];
+    c.max_np_shape = std::max(c.max_np_shape, sh.np);
+    kind[k] = sh.kind;
+    axes[3 * k] = sh.a;
+    axes[3 * k + 1] = sh.b;
+    axes[3 * k + 2] = sh.c;
+    if (sh.kind == 1) {
+      pg[k] = c.cs_pg[sh.cs];
+      coef_off[k] = c.cs_off[sh.cs];
+      const Grid& g = *c.grids[sh.grid];
+      sg.push_back(ShapeGrid{k, g.p, g.nphi, g.pup, grid_tab_off[sh.grid], grid_tab_up_off[sh.grid]});
+    }
+  }
+  std::vector<double> coef = c.cs_coef;
+  if (coef.empty()) coef.push_back(0.0);
+  RBS_TRY(upload(c.d_sh_kind, kind, s));
+  RBS_TRY(upload(c.d_sh_pg, pg, s));
+  RBS_TRY(upload(c.d_sh_axes, axes, s));
+  RBS_TRY(upload(c.d_sh_shift, shift, s));
+  RBS_TRY(upload(c.d_sh_coef_off, coef_off, s));
+  RBS_TRY(upload(c.d_sh_coef, coef, s));
+  if (sg.empty()) return Status::Ok();
+  DevBuf<ShapeGrid> d_sg;
+  DevBuf<double> d_diag;
+  RBS_TRY(upload(d_sg, sg, s));
+  RBS_TRY(d_diag.alloc(4 * sg.size()));
+  for (size_t b0 = 0; b0 < sg.size(); b0 += 65535) {
+    const int cnt = (int)std::min<size_t>(65535, sg.size() - b0);
+    k_shape_extent<<<cnt, 256, 0, s>>>(d_sg.ptr + b0, RBS_SHAPE_PASS, c.d_sh_shift.ptr, c.d_gtab.ptr,
+                                      d_diag.ptr + 4 * b0);
+  }
+  RBS_CUDA_TRY(cudaGetLastError());
+  std::vector<double> diag(4 * sg.size());
+  RBS_CUDA_TRY(cudaMemcpyAsync(diag.data(), d_diag.ptr, sizeof(double) * diag.size(), cudaMemcpyDeviceToHost, s));
+  RBS_CUDA_TRY(cudaStreamSynchronize(s));
+  for (size_t q = 0; q < sg.size(); ++q) {
+    Shape& sh = c.shapes[sg[q].s];
+    const double jmin = diag[4 * q + 2], vol = diag[4 * q + 3];
+    if (!(jmin > 0.0) || !std::isfinite(diag[4 * q]))
+      return Status::Err(RBS_EINVAL, "coefficient surface " + std::to_string(sh.cs) +
+                                         " is singular (area element vanishes on the grid)");
+    if (!(vol > 0.0))
+      return Status::Err(RBS_EINVAL, "coefficient surface " + std::to_string(sh.cs) +
+                                         " is inward-oriented (negative enclosed volume)");
+    sh.radius = diag[4 * q];
+    sh.rmin = diag[4 * q + 1];
+  }
+  for (int i = 0; i < c.n; ++i) {
+    const Shape& sh = c.shapes[c.shape_of[i]];
+    if (sh.kind == 1) c.axes[3 * i] = c.axes[3 * i + 1] = c.axes[3 * i + 2] = sh.radius;
+  }
+  return Status::Ok();
 }
 
 Status build_geometry(Context& c) {
@@ -677,19 +954,28 @@ Status build_geometry(Context& c) {
   }
   for (Grid* g : c.grids) RBS_TRY(build_grid(c, *g));
 
-  // shapes
+  // shapes: an ellipsoid is keyed by its semi-axes, a coefficient surface by its input index
   c.shapes.clear();
   c.shape_of.assign(n, 0);
-  std::map<std::tuple<double, double, double, int, int>, int> shape_id;
+  const bool coef_surfaces = !c.cs_of.empty();
+  std::map<std::tuple<int, double, double, double, int, int>, int> shape_id;
   c.block_elems = 0;
   for (int i = 0; i < n; ++i) {
-    auto key = std::make_tuple(c.axes[3 * i], c.axes[3 * i + 1], c.axes[3 * i + 2], c.p[i], c.nphi[i]);
+    const int cs = coef_surfaces ? c.cs_of[i] : -1;
+    auto key = cs >= 0 ? std::make_tuple(cs, 0.0, 0.0, 0.0, c.p[i], c.nphi[i])
+                       : std::make_tuple(-1, c.axes[3 * i], c.axes[3 * i + 1], c.axes[3 * i + 2], c.p[i], c.nphi[i]);
     auto it = shape_id.find(key);
     if (it == shape_id.end()) {
       Shape sh;
-      sh.a = c.axes[3 * i];
-      sh.b = c.axes[3 * i + 1];
-      sh.c = c.axes[3 * i + 2];
+      sh.kind = cs >= 0 ? 1 : 0;
+      sh.cs = cs;
+      if (cs < 0) {
+        sh.a = c.axes[3 * i];
+        sh.b = c.axes[3 * i + 1];
+        sh.c = c.axes[3 * i + 2];
+        sh.radius = std::max(sh.a, std::max(sh.b, sh.c));
+        sh.rmin = std::min(sh.a, std::min(sh.b, sh.c));
+      }
       sh.grid = grid_of[i];
       sh.np = c.grids[sh.grid]->np;
       sh.block_off = c.block_elems;
@@ -723,6 +1009,7 @@ Status build_geometry(Context& c) {
   RBS_TRY(upload(c.d_gtab_off, gtab_off, s));
   RBS_TRY(upload(c.d_gtab_up_off, gtab_up_off, s));
   RBS_TRY(upload(c.d_gtab, gtab, s));
+  RBS_TRY(build_shape_tables(c, grid_tab_off, grid_tab_up_off));
   RBS_TRY(upload(c.d_axes, c.axes, s));
   RBS_TRY(upload(c.d_p, c.p, s));
   RBS_TRY(upload(c.d_nphi, c.nphi, s));
@@ -755,13 +1042,17 @@ Status build_geometry(Context& c) {
   // block-diagonal preconditioner P0 = (1/2 I + K0 + L0)^{-1} per shape (Section 3.2)
   if (c.opt.preconditioner) {
     RBS_TRY(c.d_precond.alloc(c.block_elems));
+    DevBuf<double4> body;
+    RBS_TRY(body.alloc(c.max_np_shape));
     std::map<int, std::vector<int>> by_np;
     for (size_t k = 0; k < c.shapes.size(); ++k) {
       const Shape& sh = c.shapes[k];
       Grid& g = *c.grids[sh.grid];
       long long dim2 = 9LL * sh.np * sh.np;
-      k_precond_matrix<<<cdiv(dim2, 256), 256, 0, s>>>(sh.np, g.nphi, g.d_t.ptr, g.d_lam.ptr, sh.a, sh.b, sh.c,
-                                                       c.d_blockK.ptr + sh.block_off, c.d_precond.ptr + sh.block_off);
+      k_body_nodes<<<cdiv(sh.np, 128), 128, 0, s>>>(sh.np, g.nphi, g.d_t.ptr, g.d_lam.ptr, (int)k, RBS_SHAPE_PASS,
+                                                    body.ptr);
+      k_precond_matrix<<<cdiv(dim2, 256), 256, 0, s>>>(sh.np, body.ptr, c.d_blockK.ptr + sh.block_off,
+                                                       c.d_precond.ptr + sh.block_off);
       by_np[sh.np].push_back((int)k);
     }
     RBS_CUDA_TRY(cudaGetLastError());

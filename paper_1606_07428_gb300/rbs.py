@@ -44,8 +44,10 @@ EXPORTS = [
     "rbs_rigid_velocities", "rbs_apply_operator", "rbs_apply_operator_device", "rbs_get_stats",
     "rbs_reset_stats", "rbs_last_error", "rbs_rigid_velocities_noalloc", "rbs_advance", "rbs_get_state",
     "rbs_warmstart_record", "rbs_warmstart_train", "rbs_warmstart_weights", "rbs_warmstart_features",
-    "rbs_warmstart_targets", "rbs_warmstart_mlp",
+    "rbs_warmstart_targets", "rbs_warmstart_mlp", "rbs_set_geometry_sh",
 ]
+
+RBS_MAX_SHAPE_DEGREE = 24
 
 RBS_WARM_ZERO = 0
 RBS_WARM_PREVIOUS = 1
@@ -136,6 +138,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rbs_create": (I, [ctypes.POINTER(rbs_options), ctypes.POINTER(P)]),
         "rbs_destroy": (None, [P]),
         "rbs_set_geometry": (I, [P, I, P, P, P, P, P, P]),
+        "rbs_set_geometry_sh": (I, [P, I, I, P, P, P, P, P, P, P, P]),
         "rbs_total_nodes": (ctypes.c_longlong, [P]),
         "rbs_get_surface": (I, [P, P, P, P]),
         "rbs_mobility_solve": (I, [P, P, P, D, P, P, P, P]),
@@ -224,6 +227,22 @@ def rbs_set_geometry(ctx, semi_axes, p, nphi, centres, quats, suspension_id=None
     sid = None if suspension_id is None else _i32(suspension_id)
     _check(ctx, load().rbs_set_geometry(ctx, n, _ptr(semi_axes), _ptr(p), _ptr(nphi), _ptr(centres), _ptr(quats),
                                         _ptr(sid)))
+
+
+def rbs_set_geometry_sh(ctx, shapes, shape_of, p, nphi, centres, quats, suspension_id=None) -> None:
+    """shapes: list of (coef (3, (pg + 1)^2) in the library's basis order, pg); shape_of: n indices."""
+    shape_of = _i32(shape_of)
+    n = shape_of.shape[0]
+    pg = _i32([int(g) for _, g in shapes])
+    coef = _f64(np.concatenate([np.asarray(c, dtype=np.float64).reshape(3, (int(g) + 1) ** 2).ravel()
+                                for c, g in shapes]), (-1,))
+    p = _i32(np.broadcast_to(p, (n,)))
+    nphi = None if nphi is None else _i32(np.broadcast_to(nphi, (n,)))
+    centres = _f64(centres, (n, 3))
+    quats = _f64(quats, (n, 4))
+    sid = None if suspension_id is None else _i32(suspension_id)
+    _check(ctx, load().rbs_set_geometry_sh(ctx, n, len(shapes), _ptr(pg), _ptr(coef), _ptr(shape_of), _ptr(p),
+                                           _ptr(nphi), _ptr(centres), _ptr(quats), _ptr(sid)))
 
 
 def rbs_total_nodes(ctx) -> int:
@@ -392,6 +411,11 @@ class Context:
     def set_geometry(self, semi_axes, p, nphi, centres, quats, suspension_id=None):
         rbs_set_geometry(self.ctx, semi_axes, p, nphi, centres, quats, suspension_id)
         self.n = int(np.asarray(semi_axes).reshape(-1, 3).shape[0])
+        return self
+
+    def set_shapes(self, shapes, shape_of, p, nphi, centres, quats, suspension_id=None):
+        rbs_set_geometry_sh(self.ctx, shapes, shape_of, p, nphi, centres, quats, suspension_id)
+        self.n = int(np.asarray(shape_of).reshape(-1).shape[0])
         return self
 
     def set_suspension(self, s):

@@ -2,8 +2,6 @@
 by its degree-1 coefficients reproduces the analytic ellipsoid path, a non-ellipsoidal shape obeys the
 identities of the formulation (divergence theorem, Eq. 14, Eq. 17, Eq. 20, reciprocity, rigid-motion
 covariance), and its mobility converges spectrally in p."""
-import math
-
 import numpy as np
 import pytest
 
@@ -11,31 +9,11 @@ import oracle
 from oracle import shapes as shp
 from oracle.geometry import body_surface_sh
 from oracle.timestep import quat_mul
-
-
-def peanut(pg=4, seed=0):
-    """A smooth star-shaped genus-0 surface: the ellipsoid (1.2, 0.8, 0.7) scaled radially by
-    1 + 0.08 (Y_20 + random degree-2/3 terms); x = r(s) D s has degree <= pg = 4 and its coefficients
-    are taken by an exact Gauss-Legendre x trapezoid projection."""
-    rng = np.random.default_rng(seed)
-    amp = 0.08 * rng.normal(size=shp.n_coef(3))
-    amp[:4] = 0.0
-    nth, nph = pg + 1, 2 * pg + 2
-    t, lam = np.polynomial.legendre.leggauss(nth)
-    th = np.repeat(np.arccos(t), nph)
-    ph = np.tile(2 * math.pi * np.arange(nph) / nph, nth)
-    q = np.repeat(lam, nph) * 2 * math.pi / nph
-    s = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
-    Y3, _, _ = shp.basis_with_derivatives(3, th, ph)
-    r = 1.0 + amp @ Y3
-    x = r[:, None] * s * np.array([1.2, 0.8, 0.7])[None, :]
-    Y, _, _ = shp.basis_with_derivatives(pg, th, ph)
-    return (Y * q[None, :]) @ x, pg  # (n_coef, 3) -> transpose below
+from shape_inputs import star_shape
 
 
 def _peanut(pg=4, seed=0):
-    c, pg = peanut(pg, seed)
-    return c.T.copy(), pg
+    return star_shape(seed, pg)
 
 
 def test_coefficient_ellipsoid_reproduces_the_analytic_one():
