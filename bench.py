@@ -53,7 +53,7 @@ NCU_TRAFFIC = {"pair_traction_df": (6.404864e6, 57600), "pair_traction_f32": (6.
 # float32-pipe operations per pair of the double-float kernels, counted from the source of
 # pair_tile_df (separation 24, r^2 28, reciprocal square root 8, r . density 28, powers 8, traction
 # tail 76 / Stokeslet tail 76)
-DF_INSTR_PER_PAIR = {"traction": 172.0, "stokeslet": 172.0}
+DF_INSTR_PER_PAIR = {"traction": 172.0, "stokeslet": 172.0, "both": 250.0}
 
 
 def parse_args():
@@ -219,7 +219,7 @@ def kernel_rooflines(kernels, f_mhz, hbm_gbs):
         rate = e["units"] / (e["ms"] / 1e3)
         row = {"ms_per_launch": e["ms"] / e["launches"]}
         if name.startswith("pair_"):
-            kind = "traction" if "traction" in name else "stokeslet"
+            kind = "traction" if "traction" in name else ("both" if "both" in name else "stokeslet")
             if name.endswith("_f32"):
                 instr = {"traction": 20.0, "stokeslet": 18.0}[kind]
                 peak = SMS * FP32_LANES_PER_SM * f / instr
@@ -402,6 +402,7 @@ def run_ours(args):
               "stokeslet_df": rate(srates, "pair_stokeslet_df"),
               "traction_f32": rate(kernels, "pair_traction_f32"),
               "traction_df": rate(kernels, "pair_traction_df"),
+              "traction_and_stokeslet_df": rate(kernels, "pair_both_df"),
               "traction_f64": rate(kernels, "pair_traction_f64")}
     if plain:
         gpairs["stokeslet_f64_plain"] = rate(plain["kernels"], "pair_stokeslet_f64")
@@ -411,7 +412,7 @@ def run_ours(args):
     per_launch_ms = e["ms"] / e["launches"]
     units_per_launch = e["units"] / e["launches"]
     if name.startswith("pair_"):
-        kind = "traction" if "traction" in name else "stokeslet"
+        kind = "traction" if "traction" in name else ("both" if "both" in name else "stokeslet")
         if name.endswith("_df"):
             # double-float: reported as the float64-equivalent pair rate against the float32 issue rate
             # at the kernel's own instruction count per pair (DF_INSTR_PER_PAIR)
@@ -477,7 +478,8 @@ def run_ours(args):
             "speedup_vs_plain_fp64": (value / world) / plain["solves_per_s"] if plain else None,
             "gpair_per_s": gpairs,
             "kernels": kernels,
-            "pair_variant": dict(zip(["traction_f32", "stokeslet_f32", "traction_df", "stokeslet_df"],
+            "pair_variant": dict(zip(["traction_f32", "stokeslet_f32", "traction_df", "stokeslet_df",
+                                      "traction_and_stokeslet_df"],
                                      stats.get("pair_variant", []))),
             "roofline": roof,
             "kernel_rooflines": rooflines,

@@ -106,7 +106,8 @@ typedef struct {
 #define RBS_KC_NEAR 5     /* near correction (upsampling and upsampled pair sums) */
 #define RBS_KC_PAIR_KDF 6 /* smooth traction pair sum, double-float */
 #define RBS_KC_PAIR_SDF 7 /* smooth Stokeslet pair sum, double-float */
-#define RBS_KC_COUNT 8
+#define RBS_KC_PAIR_KSDF 8 /* smooth traction and Stokeslet sums of one density in one pass, double-float */
+#define RBS_KC_COUNT 9
 
 typedef struct {
   int iterations;        /* total GMRES iterations of the last solve (inner iterations for mixed) */
@@ -124,8 +125,9 @@ typedef struct {
   long long kernel_count[RBS_KC_COUNT];  /* launches per class */
   double kernel_units[RBS_KC_COUNT];     /* work per class: node pairs (pair sums, near), bytes of
                                             block entries read (particle blocks) */
-  int pair_variant[4];   /* targets per thread in use: float32 traction, float32 Stokeslet,
-                            double-float traction, double-float Stokeslet (0 = not yet chosen) */
+  int pair_variant[5];   /* targets per thread in use: float32 traction, float32 Stokeslet,
+                            double-float traction, double-float Stokeslet, fused double-float
+                            traction and Stokeslet (0 = not yet chosen) */
 } rbs_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -470,7 +470,7 @@ int rbs_get_stats(rbs_ctx* h, rbs_stats* out) {
   if (s.ok()) s = c.harvest();
   if (!s.ok()) return finish(c, s);
   *out = c.stats;
-  for (int k = 0; k < 4; ++k) out->pair_variant[k] = c.tuned[k];
+  for (int k = 0; k < 5; ++k) out->pair_variant[k] = c.tuned[k];
   return RBS_OK;
 }
 

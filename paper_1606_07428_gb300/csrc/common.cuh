@@ -167,15 +167,16 @@ struct Context {
   DevBuf<const float*> d_upU32;
 
   std::map<const void*, int> resident;  // kernel -> resident blocks per SM
-  int tuned[4] = {0, 0, 0, 0};          // chosen targets per thread: (float32, double-float) x (K, S)
-  float tune_ms[4] = {0, 0, 0, 0};
+  // chosen targets per thread: (float32, double-float) x (K, S), then the fused double-float K + S
+  int tuned[5] = {0, 0, 0, 0, 0};
+  float tune_ms[5] = {0, 0, 0, 0, 0};
 
   // smooth pair-sum work list: (target begin, target end, source begin, source end)
   std::vector<longlong4> work;
   DevBuf<longlong4> d_work;
 
   // scratch vectors (3N doubles each) and GMRES workspace
-  DevBuf<double> d_vec[8];
+  DevBuf<double> d_vec[10];
   DevBuf<double> d_V, d_H, d_givens, d_partials;
   DevBuf<double> d_FT;  // forces and torques, n x 6
   DevBuf<double> d_vo;  // velocities, n x 6
@@ -229,6 +230,8 @@ enum BlockMode {
 };
 Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, double* aux, double scale);
 Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y);  // y += off-diagonal kind (0 K, 1 S)
+// yK += off-diagonal K x and yS += off-diagonal S x in one pass over the pairs (double-float)
+Status apply_pairs_both(Context& c, int prec, const double* x, double* yK, double* yS);
 Status apply_operator(Context& c, int op, int prec, const double* x, double* y);
 
 // ---- solver (solver.cu)

@@ -391,11 +391,13 @@ __device__ __forceinline__ void df_acc(dflt& acc, dflt v) {
   acc.l += s.l + v.l;
 }
 
+// KIND 0: traction into acc; 1: Stokeslet into acc; 2: both for the same density, traction into acc
+// and Stokeslet into acc2, sharing the separation, its inverse powers and r . w rho.
 template <int KIND, bool MASK, int NT>
 __device__ __forceinline__ void pair_tile_df(const float4* __restrict__ sph, const float4* __restrict__ spl,
                                              const float4* __restrict__ sdh, const float4* __restrict__ sdl, int cnt,
                                              const dflt (&xt)[NT][3], const dflt (&nt)[NT][3], const int (&pt)[NT],
-                                             dflt (&acc)[NT][3]) {
+                                             dflt (&acc)[NT][3], dflt (&acc2)[NT][3]) {
   for (int l = 0; l < cnt; ++l) {
     const float4 yh = sph[l], yl = spl[l], dh = sdh[l], dl = sdl[l];
     const dflt den[3] = {{dh.x, dl.x}, {dh.y, dl.y}, {dh.z, dl.z}};
@@ -438,6 +440,17 @@ __device__ __forceinline__ void pair_tile_df(const float4* __restrict__ sph, con
         const dflt cc = df_mul(df_mul(rn, rr), inv5);
 #pragma unroll
         for (int c = 0; c < 3; ++c) df_acc(acc[u][c], df_mul(cc, d[c]));
+      } else if (KIND == 2) {
+        const dflt inv5 = df_mul(inv3, inv2);
+        const dflt rn = df_dot3(d[0], nt[u][0], d[1], nt[u][1], d[2], nt[u][2]);
+        const dflt ck = df_mul(df_mul(rn, rr), inv5);
+        const dflt cs = df_mul(rr, inv3);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          df_acc(acc[u][c], df_mul(ck, d[c]));
+          df_acc(acc2[u][c], df_mul(den[c], inv));
+          df_acc(acc2[u][c], df_mul(cs, d[c]));
+        }
       } else {
         const dflt cc = df_mul(rr, inv3);
 #pragma unroll
@@ -450,10 +463,12 @@ __device__ __forceinline__ void pair_tile_df(const float4* __restrict__ sph, con
   }
 }
 
+// y += traction sum (KIND 0, 2) or Stokeslet sum (KIND 1); KIND 2 also y2 += Stokeslet sum.
 template <int KIND, int NT>
 __global__ void __launch_bounds__(128 / NT, 8) k_pairs_df(int nitems, const longlong4* __restrict__ work, const double4* __restrict__ x,
                                                        const double4* __restrict__ nrm, const int* __restrict__ pid,
-                                                       const double* __restrict__ dens, double* __restrict__ y) {
+                                                       const double* __restrict__ dens, double* __restrict__ y,
+                                                       double* __restrict__ y2) {
   constexpr int TS = 128, NTH = 128 / NT;
   __shared__ float4 sph[TS], spl[TS], sdh[TS], sdl[TS];
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -481,9 +496,9 @@ __global__ void __launch_bounds__(128 / NT, 8) k_pairs_df(int nitems, const long
     nt[u][2] = df_split(nn.z);
   }
   const int pid_lo = pid[w.x], pid_hi = pid[w.y - 1];
-  double a[NT][3];
+  double a[NT][3], a2[NT][3];
 #pragma unroll
-  for (int u = 0; u < NT; ++u) a[u][0] = a[u][1] = a[u][2] = 0.0;
+  for (int u = 0; u < NT; ++u) a[u][0] = a[u][1] = a[u][2] = a2[u][0] = a2[u][1] = a2[u][2] = 0.0;
   for (long long s0 = w.z; s0 < w.w; s0 += TS) {
     const int cnt = (int)min((long long)TS, w.w - s0);
     __syncthreads();
@@ -500,25 +515,33 @@ __global__ void __launch_bounds__(128 / NT, 8) k_pairs_df(int nitems, const long
     }
     __syncthreads();
     const int tlo = pid[s0], thi = pid[s0 + cnt - 1];
-    dflt acc[NT][3];
-#pragma unroll
-    for (int u = 0; u < NT; ++u) acc[u][0] = acc[u][1] = acc[u][2] = dflt{0.0f, 0.0f};
-    if (thi < pid_lo || tlo > pid_hi)
-      pair_tile_df<KIND, false, NT>(sph, spl, sdh, sdl, cnt, xt, nt, pt, acc);
-    else
-      pair_tile_df<KIND, true, NT>(sph, spl, sdh, sdl, cnt, xt, nt, pt, acc);
+    dflt acc[NT][3], acc2[NT][3];
 #pragma unroll
     for (int u = 0; u < NT; ++u)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) a[u][c] += (double)acc[u][c].h + (double)acc[u][c].l;
+      for (int c = 0; c < 3; ++c) acc[u][c] = acc2[u][c] = dflt{0.0f, 0.0f};
+    if (thi < pid_lo || tlo > pid_hi)
+      pair_tile_df<KIND, false, NT>(sph, spl, sdh, sdl, cnt, xt, nt, pt, acc, acc2);
+    else
+      pair_tile_df<KIND, true, NT>(sph, spl, sdh, sdl, cnt, xt, nt, pt, acc, acc2);
+#pragma unroll
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        a[u][c] += (double)acc[u][c].h + (double)acc[u][c].l;
+        if (KIND == 2) a2[u][c] += (double)acc2[u][c].h + (double)acc2[u][c].l;
+      }
   }
-  const double sc = KIND == 0 ? kTractionScale : kStokesletScale;
+  const double sc = KIND == 1 ? kStokesletScale : kTractionScale;
 #pragma unroll
   for (int u = 0; u < NT; ++u) {
     if (!valid[u]) continue;
     const long long t = w.x + threadIdx.x + NTH * u;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) atomicAdd(y + 3 * t + c, sc * a[u][c]);
+    for (int c = 0; c < 3; ++c) {
+      atomicAdd(y + 3 * t + c, sc * a[u][c]);
+      if (KIND == 2) atomicAdd(y2 + 3 * t + c, kStokesletScale * a2[u][c]);
+    }
   }
   }
 }
@@ -722,7 +745,7 @@ __global__ void __launch_bounds__(512) k_near_tiled(const int2* __restrict__ nea
         const dflt nd[1][3] = {{df_split(nt.x), df_split(nt.y), df_split(nt.z)}};
         const int none[1] = {-1};
         dflt acc[1][3] = {{{0, 0}, {0, 0}, {0, 0}}};
-        pair_tile_df<KIND, false, 1>(s0, s1, s2, s3, cnt, xd, nd, none, acc);
+        pair_tile_df<KIND, false, 1>(s0, s1, s2, s3, cnt, xd, nd, none, acc, acc);
         a0 += (double)acc[0][0].h + (double)acc[0][0].l;
         a1 += (double)acc[0][1].h + (double)acc[0][1].l;
         a2 += (double)acc[0][2].h + (double)acc[0][2].l;
@@ -765,18 +788,21 @@ static int resident_grid(Context& c, const void* kernel, int threads, int items)
 }
 
 // Launch of the smooth pair sum over the first `items` work items with NT targets per thread.
+// KIND 2 (traction into y and Stokeslet into y2 in one pass) exists in double-float only.
 template <int KIND>
-static void launch_pairs_kind(Context& c, int prec, int nt, int items, const double* x, double* y) {
+static void launch_pairs_kind(Context& c, int prec, int nt, int items, const double* x, double* y, double* y2) {
 #define RBS_PAIR_ARGS items, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y
-  if (prec == RBS_PREC_FP64) {
-    k_pairs64<KIND><<<resident_grid(c, (const void*)k_pairs64<KIND>, 128, items), 128, 0, c.stream>>>(RBS_PAIR_ARGS);
-  } else if (prec == RBS_PREC_DF) {
+  if (prec == RBS_PREC_DF) {
     if (nt == 1)
-      k_pairs_df<KIND, 1><<<resident_grid(c, (const void*)k_pairs_df<KIND, 1>, 128, items), 128, 0, c.stream>>>(RBS_PAIR_ARGS);
+      k_pairs_df<KIND, 1><<<resident_grid(c, (const void*)k_pairs_df<KIND, 1>, 128, items), 128, 0, c.stream>>>(RBS_PAIR_ARGS, y2);
     else if (nt == 2)
-      k_pairs_df<KIND, 2><<<resident_grid(c, (const void*)k_pairs_df<KIND, 2>, 64, items), 64, 0, c.stream>>>(RBS_PAIR_ARGS);
+      k_pairs_df<KIND, 2><<<resident_grid(c, (const void*)k_pairs_df<KIND, 2>, 64, items), 64, 0, c.stream>>>(RBS_PAIR_ARGS, y2);
     else
-      k_pairs_df<KIND, 4><<<resident_grid(c, (const void*)k_pairs_df<KIND, 4>, 32, items), 32, 0, c.stream>>>(RBS_PAIR_ARGS);
+      k_pairs_df<KIND, 4><<<resident_grid(c, (const void*)k_pairs_df<KIND, 4>, 32, items), 32, 0, c.stream>>>(RBS_PAIR_ARGS, y2);
+  } else if constexpr (KIND == 2) {
+    return;
+  } else if (prec == RBS_PREC_FP64) {
+    k_pairs64<KIND><<<resident_grid(c, (const void*)k_pairs64<KIND>, 128, items), 128, 0, c.stream>>>(RBS_PAIR_ARGS);
   } else {
     if (nt == 1)
       k_pairs32<KIND, 1><<<resident_grid(c, (const void*)k_pairs32<KIND, 1>, 128, items), 128, 0, c.stream>>>(RBS_PAIR_ARGS);
@@ -788,11 +814,14 @@ static void launch_pairs_kind(Context& c, int prec, int nt, int items, const dou
 #undef RBS_PAIR_ARGS
 }
 
-static Status launch_pairs(Context& c, int kind, int prec, int nt, int items, const double* x, double* y) {
+static Status launch_pairs(Context& c, int kind, int prec, int nt, int items, const double* x, double* y,
+                           double* y2 = nullptr) {
   if (kind == 0)
-    launch_pairs_kind<0>(c, prec, nt, items, x, y);
+    launch_pairs_kind<0>(c, prec, nt, items, x, y, y2);
+  else if (kind == 1)
+    launch_pairs_kind<1>(c, prec, nt, items, x, y, y2);
   else
-    launch_pairs_kind<1>(c, prec, nt, items, x, y);
+    launch_pairs_kind<2>(c, prec, nt, items, x, y, y2);
   RBS_CUDA_TRY(cudaGetLastError());
   return Status::Ok();
 }
@@ -802,19 +831,19 @@ static Status launch_pairs(Context& c, int kind, int prec, int nt, int items, co
 // list (the same items for every variant, into a scratch output).
 static int pair_variant(Context& c, int kind, int prec, const double* x) {
   if (c.opt.pair_variant == 1 || c.opt.pair_variant == 2 || c.opt.pair_variant == 4) return c.opt.pair_variant;
-  const int key = 2 * (prec == RBS_PREC_DF ? 1 : 0) + kind;
+  const int key = kind == 2 ? 4 : 2 * (prec == RBS_PREC_DF ? 1 : 0) + kind;
   if (c.tuned[key]) return c.tuned[key];
   int best = 2;
   const int items = std::min<int>((int)c.work.size(), 2 * 32 * std::max(1, c.sm_count));
   double* scratch = nullptr;
   cudaEvent_t a = nullptr, b = nullptr;
-  if (cudaMalloc(&scratch, sizeof(double) * 3 * c.N) == cudaSuccess && cudaEventCreate(&a) == cudaSuccess &&
+  if (cudaMalloc(&scratch, sizeof(double) * 6 * c.N) == cudaSuccess && cudaEventCreate(&a) == cudaSuccess &&
       cudaEventCreate(&b) == cudaSuccess) {
     float best_ms = 1e30f;
     for (int nt : {1, 2, 4}) {
-      launch_pairs(c, kind, prec, nt, items, x, scratch);  // warm (first launch of this variant)
+      launch_pairs(c, kind, prec, nt, items, x, scratch, scratch + 3 * c.N);  // warm (first launch of this variant)
       cudaEventRecord(a, c.stream);
-      launch_pairs(c, kind, prec, nt, items, x, scratch);
+      launch_pairs(c, kind, prec, nt, items, x, scratch, scratch + 3 * c.N);
       cudaEventRecord(b, c.stream);
       float ms = 0.0f;
       if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
@@ -867,6 +896,56 @@ Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, 
   return Status::Ok();
 }
 
+// Near correction, step 1: upsampled densities of the near-source particles (float32 interpolation
+// for the inner solve, float64 otherwise).
+static Status near_upsample(Context& c, bool f32, const double* x) {
+  size_t smem = sizeof(double) * 3 * (size_t)c.max_np;
+  if (smem > 48 * 1024) {
+    RBS_CUDA_TRY(cudaFuncSetAttribute(k_upsample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RBS_CUDA_TRY(cudaFuncSetAttribute(k_upsample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  int maxup = 0;
+  for (Grid* g : c.grids) maxup = std::max(maxup, g->nup);
+  const int nup_p = (int)c.up_particle.size();
+  dim3 gu(cdiv(maxup, 128), (unsigned)std::min(nup_p, 65535));
+  if (f32)
+    k_upsample<float><<<gu, 128, smem, c.stream>>>(nup_p, c.d_up_particle.ptr, c.d_up_off.ptr, c.d_offset.ptr, c.d_nodes.ptr,
+                                                   c.d_upU32.ptr, x, c.d_up_mu.ptr);
+  else
+    k_upsample<double><<<gu, 128, smem, c.stream>>>(nup_p, c.d_up_particle.ptr, c.d_up_off.ptr, c.d_offset.ptr,
+                                                    c.d_nodes.ptr, c.d_upU.ptr, x, c.d_up_mu.ptr);
+  RBS_CUDA_TRY(cudaGetLastError());
+  return Status::Ok();
+}
+
+// Near correction, step 2: for every near pair, the base-grid term is replaced by the upsampled one.
+static Status near_sums(Context& c, int kind, int prec, const double* x, double* y) {
+  const int nn = (int)c.near_pairs.size();
+#define RBS_NEAR_ARGS                                                                                            \
+  c.d_near.ptr, c.d_offset.ptr, c.d_nodes.ptr, c.d_centre.ptr, c.d_up_index.ptr, c.d_up_off.ptr, c.d_x.ptr, \
+      c.d_nrm.ptr, x, c.d_up_x.ptr, c.d_up_mu.ptr, y
+  const int nthr = std::min(512, std::max(64, (c.max_np + 31) / 32 * 32));
+  if (prec == RBS_PREC_DF) {
+    if (kind == 0)
+      k_near_tiled<0, true><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
+    else
+      k_near_tiled<1, true><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
+  } else if (prec == RBS_PREC_MIXED) {
+    if (kind == 0)
+      k_near_tiled<0, false><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
+    else
+      k_near_tiled<1, false><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
+  } else {
+    if (kind == 0)
+      k_near<0, double><<<nn, 256, 0, c.stream>>>(RBS_NEAR_ARGS);
+    else
+      k_near<1, double><<<nn, 256, 0, c.stream>>>(RBS_NEAR_ARGS);
+  }
+#undef RBS_NEAR_ARGS
+  RBS_CUDA_TRY(cudaGetLastError());
+  return Status::Ok();
+}
+
 Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y) {
   const int nw = (int)c.work.size();
   const bool f32 = (prec == RBS_PREC_MIXED);
@@ -879,48 +958,44 @@ Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y) {
     RBS_CUDA_TRY(cudaGetLastError());
     timer.done((double)c.stats.far_pairs);
   }
-  const int nn = (int)c.near_pairs.size();
-  if (nn > 0) {
+  if (!c.near_pairs.empty()) {
     KernelTimer timer(c, RBS_KC_NEAR);
-    size_t smem = sizeof(double) * 3 * (size_t)c.max_np;
-    if (smem > 48 * 1024) {
-      RBS_CUDA_TRY(cudaFuncSetAttribute(k_upsample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      RBS_CUDA_TRY(cudaFuncSetAttribute(k_upsample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    }
-    int maxup = 0;
-    for (Grid* g : c.grids) maxup = std::max(maxup, g->nup);
-    const int nup_p = (int)c.up_particle.size();
-    dim3 gu(cdiv(maxup, 128), (unsigned)std::min(nup_p, 65535));
-    if (f32)
-      k_upsample<float><<<gu, 128, smem, c.stream>>>(nup_p, c.d_up_particle.ptr, c.d_up_off.ptr, c.d_offset.ptr, c.d_nodes.ptr,
-                                                     c.d_upU32.ptr, x, c.d_up_mu.ptr);
-    else
-      k_upsample<double><<<gu, 128, smem, c.stream>>>(nup_p, c.d_up_particle.ptr, c.d_up_off.ptr, c.d_offset.ptr,
-                                                      c.d_nodes.ptr, c.d_upU.ptr, x, c.d_up_mu.ptr);
-    RBS_CUDA_TRY(cudaGetLastError());
-#define RBS_NEAR_ARGS                                                                                            \
-  c.d_near.ptr, c.d_offset.ptr, c.d_nodes.ptr, c.d_centre.ptr, c.d_up_index.ptr, c.d_up_off.ptr, c.d_x.ptr, \
-      c.d_nrm.ptr, x, c.d_up_x.ptr, c.d_up_mu.ptr, y
-    const int nthr = std::min(512, std::max(64, (c.max_np + 31) / 32 * 32));
-    if (prec == RBS_PREC_DF) {
-      if (kind == 0)
-        k_near_tiled<0, true><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
-      else
-        k_near_tiled<1, true><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
-    } else if (f32) {
-      if (kind == 0)
-        k_near_tiled<0, false><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
-      else
-        k_near_tiled<1, false><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
-    } else {
-      if (kind == 0)
-        k_near<0, double><<<nn, 256, 0, c.stream>>>(RBS_NEAR_ARGS);
-      else
-        k_near<1, double><<<nn, 256, 0, c.stream>>>(RBS_NEAR_ARGS);
-    }
-#undef RBS_NEAR_ARGS
-    RBS_CUDA_TRY(cudaGetLastError());
+    RBS_TRY(near_upsample(c, f32, x));
+    RBS_TRY(near_sums(c, kind, prec, x, y));
     timer.done((double)c.near_pair_nodes, 2);
+  }
+  return Status::Ok();
+}
+
+Status apply_pairs_both(Context& c, int prec, const double* x, double* yK, double* yS) {
+  if (prec == RBS_PREC_MIXED) {
+    RBS_TRY(apply_pairs(c, 0, prec, x, yK));
+    return apply_pairs(c, 1, prec, x, yS);
+  }
+  const int nw = (int)c.work.size();
+  if (nw > 0) {
+    if (prec == RBS_PREC_DF) {
+      const int nt = pair_variant(c, 2, prec, x);
+      KernelTimer timer(c, RBS_KC_PAIR_KSDF);
+      RBS_TRY(launch_pairs(c, 2, prec, nt, nw, x, yK, yS));
+      timer.done((double)c.stats.far_pairs);
+    } else {
+      {
+        KernelTimer timer(c, RBS_KC_PAIR_K64);
+        RBS_TRY(launch_pairs(c, 0, prec, 1, nw, x, yK));
+        timer.done((double)c.stats.far_pairs);
+      }
+      KernelTimer timer(c, RBS_KC_PAIR_S64);
+      RBS_TRY(launch_pairs(c, 1, prec, 1, nw, x, yS));
+      timer.done((double)c.stats.far_pairs);
+    }
+  }
+  if (!c.near_pairs.empty()) {
+    KernelTimer timer(c, RBS_KC_NEAR);
+    RBS_TRY(near_upsample(c, false, x));
+    RBS_TRY(near_sums(c, 0, prec, x, yK));
+    RBS_TRY(near_sums(c, 1, prec, x, yS));
+    timer.done(2.0 * c.near_pair_nodes, 3);
   }
   return Status::Ok();
 }

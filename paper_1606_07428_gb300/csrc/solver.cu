@@ -364,6 +364,29 @@ __global__ void k_unpack_vo(int n, const double* vo, double* v, double* om) {
   }
 }
 
+// Relative error of a float32 operator application (float32 pair sums with per-tile compensation,
+// float32 blocks and interpolation), a bound on the measured relative L2 error (a few 1e-7 on the
+// 1,000-ellipsoid p = 12 suspension); it decides when a refinement residual may be updated in float32.
+constexpr double kF32OperatorError = 1e-5;
+
+// Float64-class residual and surface velocity of one iterate x, sharing one pass over the pairs:
+// with sigma = rho + x,  r = b - A x = -(1/2 I + K) sigma - L x = L rho - A sigma  (Eq. 25, A the
+// operator 1/2 I + K + L) and  u = S sigma  (the velocity of Section 2.3).
+static Status residual_and_velocity(Context& c, int prec, const double* rho, const double* lrho, const double* x,
+                                    double* sigma, double* r, double* u) {
+  const long long n3 = 3 * c.N;
+  const int nbk = vec_blocks(c, n3);
+  c.stats.launches++;
+  k_add<<<nbk, 256, 0, c.stream>>>(sigma, rho, x, n3);
+  RBS_TRY(apply_blocks(c, kModeSelfK, prec, sigma, r, nullptr, 1.0));
+  RBS_TRY(apply_blocks(c, kModeSelfS, prec, sigma, u, nullptr, 1.0));
+  RBS_TRY(apply_pairs_both(c, prec, sigma, r, u));
+  c.stats.launches++;
+  k_axpby<<<nbk, 256, 0, c.stream>>>(r, 1.0, lrho, -1.0, n3);
+  RBS_CUDA_TRY(cudaGetLastError());
+  return Status::Ok();
+}
+
 Status mobility_solve(Context& c, const double* F, const double* T, double tol, double* v, double* om, double* density,
                       int* iters_out, bool device_io) {
   auto t0 = std::chrono::steady_clock::now();
@@ -387,22 +410,26 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
     k_pack_ft<<<cdiv(n, 128), 128, 0, c.stream>>>(n, c.d_vo.ptr, c.d_vo.ptr + 3 * n, c.d_FT.ptr);
   }
   RBS_CUDA_TRY(cudaGetLastError());
-  // 1. incident density; right-hand side b = -(1/2 I + K) rho in float64
+  // 1. incident density; right-hand side b = -(1/2 I + K) rho (Eq. 25): float64 for the float64 path;
+  //    float32 for the mixed path, where b only seeds the first inner solve (every refinement residual
+  //    below is formed from rho in float64-class arithmetic, so b's float32 error does not persist)
   RBS_TRY(incident_density(c, c.d_FT.ptr, rho));
-  const int hi = (c.opt.precision == RBS_PREC_MIXED) ? c.opt.refine_precision : RBS_PREC_FP64;
-  RBS_TRY(apply_operator(c, RBS_OP_HALF_K, hi, rho, b));
+  const bool mixed = (c.opt.precision == RBS_PREC_MIXED);
+  const int hi = mixed ? c.opt.refine_precision : RBS_PREC_FP64;
+  RBS_TRY(apply_operator(c, RBS_OP_HALF_K, mixed ? RBS_PREC_MIXED : RBS_PREC_FP64, rho, b));
   c.stats.launches++;
   k_axpby<<<nbk, 256, 0, c.stream>>>(b, 0.0, b, -1.0, n3);
-  RBS_TRY(norm2_dev(c, b, n3, c.d_partials.ptr + (size_t)(c.opt.restart + 1) * 1024 + 8));
+  double* sc = c.d_partials.ptr + (size_t)(c.opt.restart + 1) * 1024 + 8;
+  RBS_TRY(norm2_dev(c, b, n3, sc));
   double bn2;
-  RBS_TRY(read_scalar(c, c.d_partials.ptr + (size_t)(c.opt.restart + 1) * 1024 + 8, &bn2));
+  RBS_TRY(read_scalar(c, sc, &bn2));
   const double bnorm = std::sqrt(bn2);
   int total_iters = 0, refinements = 0;
   double rel = 0.0;
   bool converged = true;
   // initial guess: zero, the previous solution, or the learned warm start
   bool have_x0 = false;
-  double* x0 = d;  // the first GMRES call starts from here
+  double* x0 = d;
   if (bnorm > 0.0 && c.opt.warm_start == RBS_WARM_PREVIOUS && c.have_prev && c.d_prev.n == (size_t)n3) {
     RBS_CUDA_TRY(cudaMemcpyAsync(x0, c.d_prev.ptr, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
     have_x0 = true;
@@ -410,10 +437,14 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
     RBS_TRY(warm_guess(c, c.d_FT.ptr, x0));
     have_x0 = true;
   }
+  double* sigma = c.d_vec[9].ptr;
+  double* u = c.d_vec[1].ptr;  // b's storage once b has been used
+  double* w = c.d_vec[4].ptr;
+  bool u_done = false;
   // 2. the scattered density
   if (bnorm == 0.0) {
     RBS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n3, c.stream));
-  } else if (c.opt.precision == RBS_PREC_FP64) {
+  } else if (!mixed) {
     int its = 0;
     double res = 0.0;
     if (have_x0) RBS_CUDA_TRY(cudaMemcpyAsync(x, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
@@ -421,55 +452,82 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
     total_iters = its;
     rel = res / bnorm;
   } else {
-    RBS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n3, c.stream));
-    RBS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+    // Iterative refinement around float32 inner solves.  A float64-class pass gives the true
+    // residual r = b - A x and, from the same pair sums, u = S[rho + x].  After a pass, a small
+    // correction d may instead update r -= A d and u += S d in float32: the float32 operator's error
+    // on d is kF32OperatorError ||A d||, and these updates are taken only while that error, summed
+    // since the last pass, stays below a tenth of the tolerance.
+    double* lrho = c.d_vec[8].ptr;  // L rho (Eq. 26), float64
+    RBS_TRY(apply_blocks(c, kModeL, RBS_PREC_FP64, rho, lrho, nullptr, 1.0));
     double rn = bnorm;
-    converged = false;
-    while (refinements < c.opt.max_refinements && total_iters < c.opt.max_iters) {
-      int its = 0;
-      double res = 0.0;
-      bool conv_inner = false;
-      // inner solve of A d = r with the float32 operator
-      const bool start_zero = !(have_x0 && refinements == 0);  // d holds the warm start on the first pass
-      const bool warm_first_pass = !start_zero;
-      // each inner solve reduces its residual by inner_tol, or only as far as the final tolerance needs
-      // (half of tol ||b||), whichever is looser
-      const double inner = std::min(0.5, std::max(c.opt.inner_tol, 0.5 * tol * bnorm / rn));
-      RBS_TRY(gmres(c, RBS_PREC_MIXED, r, d, start_zero, inner * rn, c.opt.max_iters - total_iters, &its, &res,
-                    &conv_inner));
-      total_iters += its;
-      c.stats.launches++;
-      k_axpby<<<nbk, 256, 0, c.stream>>>(x, 1.0, d, 1.0, n3);
-      // float64 residual r = b - A x
-      RBS_TRY(apply_operator(c, RBS_OP_A, hi, x, r));
-      c.stats.launches++;
-      k_axpby<<<nbk, 256, 0, c.stream>>>(r, 1.0, b, -1.0, n3);
-      double* sc = c.d_partials.ptr + (size_t)(c.opt.restart + 1) * 1024 + 8;
+    if (have_x0) {
+      RBS_CUDA_TRY(cudaMemcpyAsync(x, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+      RBS_TRY(residual_and_velocity(c, hi, rho, lrho, x, sigma, r, u));
+      u_done = true;
       RBS_TRY(norm2_dev(c, r, n3, sc));
       double rn2;
       RBS_TRY(read_scalar(c, sc, &rn2));
       rn = std::sqrt(rn2);
+    } else {
+      RBS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n3, c.stream));
+      RBS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+    }
+    // sigma accumulates the corrections applied in float32 since the last float64-class pass
+    if (u_done) RBS_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(double) * n3, c.stream));
+    double pending = 0.0;
+    converged = u_done && rn <= tol * bnorm;
+    while (!converged && refinements < c.opt.max_refinements && total_iters < c.opt.max_iters) {
+      int its = 0;
+      double res = 0.0;
+      bool conv_inner = false;
+      // each inner solve reduces its residual by inner_tol, or only as far as the final tolerance needs
+      // (half of tol ||b||), whichever is looser
+      const double inner = std::min(0.5, std::max(c.opt.inner_tol, 0.5 * tol * bnorm / rn));
+      RBS_TRY(gmres(c, RBS_PREC_MIXED, r, d, true, inner * rn, c.opt.max_iters - total_iters, &its, &res,
+                    &conv_inner));
+      total_iters += its;
       ++refinements;
+      c.stats.launches++;
+      k_axpby<<<nbk, 256, 0, c.stream>>>(x, 1.0, d, 1.0, n3);
+      if (u_done && kF32OperatorError * (pending + rn) <= 0.1 * tol * bnorm) {
+        RBS_TRY(apply_operator(c, RBS_OP_A, RBS_PREC_MIXED, d, w));
+        c.stats.launches += 2;
+        k_axpby<<<nbk, 256, 0, c.stream>>>(r, -1.0, w, 1.0, n3);
+        k_axpby<<<nbk, 256, 0, c.stream>>>(sigma, 1.0, d, 1.0, n3);
+        pending += rn;
+      } else {
+        RBS_TRY(residual_and_velocity(c, hi, rho, lrho, x, sigma, r, u));
+        u_done = true;
+        RBS_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(double) * n3, c.stream));
+        pending = 0.0;
+      }
+      RBS_TRY(norm2_dev(c, r, n3, sc));
+      double rn2;
+      RBS_TRY(read_scalar(c, sc, &rn2));
+      rn = std::sqrt(rn2);
       if (rn <= tol * bnorm) {
         converged = true;
         break;
       }
-      // stagnation: an inner solve that could not move (a warm start may already meet the inner
-      // tolerance on the first pass, which is progress, not stagnation)
-      if (its == 0 && !warm_first_pass) break;
+      if (its == 0) break;  // the inner solve could not move
     }
     rel = rn / bnorm;
+    if (u_done && pending > 0.0) {
+      RBS_TRY(apply_operator(c, RBS_OP_S, RBS_PREC_MIXED, sigma, w));
+      c.stats.launches++;
+      k_axpby<<<nbk, 256, 0, c.stream>>>(u, 1.0, w, 1.0, n3);
+    }
   }
   // keep the density for a previous-solution warm start and for recording training samples
   if (c.d_prev.n != (size_t)n3) RBS_TRY(c.d_prev.alloc(n3));
   RBS_CUDA_TRY(cudaMemcpyAsync(c.d_prev.ptr, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
   c.have_prev = true;
-  // 3. u = S[rho + mu] and the rigid velocities
-  double* sigma = c.d_vec[6].ptr;
-  double* u = c.d_vec[4].ptr;
-  c.stats.launches++;
-  k_add<<<nbk, 256, 0, c.stream>>>(sigma, rho, x, n3);
-  RBS_TRY(apply_operator(c, RBS_OP_S, hi, sigma, u));
+  // 3. u = S[rho + mu] (already formed by the mixed path's float64-class passes) and the rigid velocities
+  if (!u_done) {
+    c.stats.launches++;
+    k_add<<<nbk, 256, 0, c.stream>>>(sigma, rho, x, n3);
+    RBS_TRY(apply_operator(c, RBS_OP_S, hi, sigma, u));
+  }
   RBS_TRY(rigid_velocities(c, u, c.d_vo.ptr));
   if (device_io) {
     c.stats.launches++;

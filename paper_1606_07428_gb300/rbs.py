@@ -88,9 +88,10 @@ RBS_KC_BLOCKS = 4
 RBS_KC_NEAR = 5
 RBS_KC_PAIR_KDF = 6
 RBS_KC_PAIR_SDF = 7
-RBS_KC_COUNT = 8
+RBS_KC_PAIR_KSDF = 8
+RBS_KC_COUNT = 9
 KERNEL_CLASSES = ["pair_traction_f32", "pair_stokeslet_f32", "pair_traction_f64", "pair_stokeslet_f64",
-                  "particle_blocks", "near_correction", "pair_traction_df", "pair_stokeslet_df"]
+                  "particle_blocks", "near_correction", "pair_traction_df", "pair_stokeslet_df", "pair_both_df"]
 
 
 class rbs_stats(ctypes.Structure):
@@ -106,10 +107,10 @@ class rbs_stats(ctypes.Structure):
         ("near_pairs", ctypes.c_longlong),
         ("far_pairs", ctypes.c_longlong),
         ("launches", ctypes.c_longlong),
-        ("kernel_ms", ctypes.c_double * 8),
-        ("kernel_count", ctypes.c_longlong * 8),
-        ("kernel_units", ctypes.c_double * 8),
-        ("pair_variant", ctypes.c_int * 4),
+        ("kernel_ms", ctypes.c_double * RBS_KC_COUNT),
+        ("kernel_count", ctypes.c_longlong * RBS_KC_COUNT),
+        ("kernel_units", ctypes.c_double * RBS_KC_COUNT),
+        ("pair_variant", ctypes.c_int * 5),
     ]
 
 

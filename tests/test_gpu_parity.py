@@ -161,6 +161,22 @@ def test_mixed_solve_matches_oracle(rbs, small, refine):
     assert st["refinements"] >= 1 and st["residual"] <= 1e-10
 
 
+def test_mixed_solve_at_tight_tolerance(rbs, small):
+    """At tol 1e-12 the refinement takes float64-class passes (fused traction + Stokeslet) until the
+    residual is small enough for float32 updates; the answer meets the oracle's LU at the double-float
+    level, and a previous-solution warm start reaches the same answer."""
+    s, ref, _ = small
+    vr, omr, *_ = ref.solve(s.F, s.T)
+    with rbs.Context(device=0, precision=rbs.RBS_PREC_MIXED, warm_start=rbs.RBS_WARM_PREVIOUS) as ctx:
+        ctx.set_suspension(s)
+        v, om, _, _ = rbs.rbs_mobility_solve(ctx.ctx, s.F, s.T, 1e-12)
+        st = rbs.rbs_get_stats(ctx.ctx)
+        assert st["residual"] <= 1e-12 and st["kernel_count"][rbs.RBS_KC_PAIR_KSDF] >= 1
+        assert rel(np.concatenate([v, om]), np.concatenate([vr, omr])) < 1e-10
+        v2, om2, _, its2 = rbs.rbs_mobility_solve(ctx.ctx, s.F, s.T, 1e-12)
+    assert rel(np.concatenate([v2, om2]), np.concatenate([vr, omr])) < 1e-10
+
+
 def test_unpreconditioned_solve_agrees(rbs, small):
     s, ref, _ = small
     with rbs.Context(device=0, preconditioner=0) as ctx:
