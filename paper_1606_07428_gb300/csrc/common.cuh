@@ -85,6 +85,23 @@ struct Grid {
   DevBuf<double> d_an;      // nbasis x np: analysis (grid values -> coefficients)
   DevBuf<double> d_yg;      // np x nbasis: basis values at the grid nodes
   DevBuf<float> d_up32;
+
+  // Reflection symmetry of the grid (reflections x -> -x, y -> -y, z -> -z map nodes to nodes, since
+  // the Gauss-Legendre nodes are symmetric and n_phi is even).  Representative nodes are
+  // (j, k) with j <= p / 2 and k <= n_phi / 4: nrep = nj * nk of them, one per orbit.
+  int nj = 0, nk = 0, nrep = 0;
+  std::vector<int> rep_of, g_of;        // per node: its orbit's representative and a reflection taking the representative to it
+  std::vector<int> orbit, stab;         // per representative: orbit size, bit mask of the reflections fixing it
+  std::vector<int> orb_node, orb_g;     // per representative: its orbit's nodes and the reflection reaching each (8 slots)
+  std::vector<int> irrep_pos;           // 8 x 3 nrep: position of (representative, component) in each irrep's basis, or -1
+  int irrep_dim[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int dmax = 0;                         // largest irrep dimension
+  DevBuf<int> d_sym;                    // device copy of the tables above and each irrep's basis list (see sym_tables)
+};
+
+// Offsets of the grid's symmetry tables inside Grid::d_sym.
+struct SymTables {
+  const int *rep_of, *g_of, *orbit, *orb_node, *orb_g, *irrep_pos, *irrep_list;
 };
 
 // One distinct body shape: an ellipsoid (semi-axes) or an input coefficient surface, on one
@@ -96,7 +113,9 @@ struct Shape {
   double radius = 0, rmin = 0;  // largest / smallest centroid distance (near criterion, overlap test)
   int grid = 0;
   int np = 0;
-  size_t block_off = 0;  // offset (in elements) of its 3np x 3np blocks in the block arrays
+  bool sym = false;      // an ellipsoid: blocks stored as the rows of the representative nodes only
+  int rows = 0;          // stored rows: 3 nrep (sym) or 3 np
+  size_t block_off = 0;  // offset (in elements) of its rows x 3np blocks in the block arrays
 };
 
 struct Context {
@@ -157,9 +176,13 @@ struct Context {
   DevBuf<int> d_up_particle, d_up_index;
   DevBuf<double> d_up_mu;          // upsampled densities, n_up_nodes x 3
 
-  // particle-block work list: (particle, first node, end node, 0), 24 nodes per block
+  // particle-block work lists: particles whose shape stores every row, as (particle, first node,
+  // end node, 0) items of 24 nodes; particles whose shape stores representative rows, one per block
   std::vector<int4> bwork;
   DevBuf<int4> d_bwork;
+  std::vector<int> sym_list;
+  DevBuf<int> d_sym_list;
+  int max_np_sym = 0;
   int max_np = 0;
   int max_np_shape = 0;
   // per upsampled-source particle: interpolation matrix of its grid (float64 and float32)

@@ -159,6 +159,161 @@ __global__ void __launch_bounds__(256) k_blocks(int mode, const int4* __restrict
 }
 
 // ------------------------------------------------------------------------------------------
+// Particle-block kernel for shapes stored by the rows of their representative nodes (ellipsoids).
+// The blocks commute with the grid's eight reflections g (node map g(.), sign matrix D_g):
+// A_{g(t), g(s)} = D_g A_{t,s} D_g, so y_{g(t)} = D_g sum_s A_{t,s} (D_g z_{g(s)}) for each stored
+// row t.  One block per particle, 256 threads: the eight reflected copies of z = R_i^T x_i are staged
+// in shared memory (in the block type), each warp takes one representative at a time and reads its
+// three rows once for all eight reflections (one fused multiply-add per reflection and entry, in
+// the block type), and lane g writes node g(t) when no smaller reflection reaches it.  1/2 x, L x and
+// the preconditioner's copy of x are added as in k_blocks.
+__device__ __forceinline__ int reflect_node_dev(int g, int t, int p, int nphi) {
+  int j = t / nphi, k = t - (t / nphi) * nphi;
+  if (g & 4) j = p - j;
+  if (g & 2) k = k == 0 ? 0 : nphi - k;
+  if (g & 1) k = (nphi / 2 - k + nphi) % nphi;
+  return j * nphi + k;
+}
+
+template <typename TB>
+__device__ __forceinline__ TB warp_sum_t(TB v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename TB>
+__global__ void __launch_bounds__(256) k_blocks_sym(int mode, const int* __restrict__ sym_list,
+                                                    const long long* __restrict__ offset, const int* __restrict__ pvec,
+                                                    const int* __restrict__ nphivec, const double* __restrict__ rot,
+                                                    const double* __restrict__ centre, const int* __restrict__ shape_of,
+                                                    const long long* __restrict__ block_off, const TB* __restrict__ blocks,
+                                                    const double4* __restrict__ x, const double* __restrict__ in,
+                                                    double* __restrict__ out, double* __restrict__ aux, double scale) {
+  extern __shared__ __align__(16) unsigned char zraw[];
+  TB* zg = reinterpret_cast<TB*>(zraw);  // 8 x 3 N_p
+  __shared__ double red[8][6];
+  __shared__ double mom[6];
+  const int i = sym_list[blockIdx.x];
+  const int p = pvec[i], nphi = nphivec[i], np = (p + 1) * nphi, dim = 3 * np;
+  const int nk = nphi / 4 + 1, nrep = (p / 2 + 1) * nk;
+  const long long o = offset[i];
+  const double* R = rot + 9 * i;
+  const double R0 = R[0], R1 = R[1], R2 = R[2], R3 = R[3], R4 = R[4], R5 = R[5], R6 = R[6], R7 = R[7], R8 = R[8];
+  const double cx = centre[3 * i], cy = centre[3 * i + 1], cz = centre[3 * i + 2];
+  const bool has_block = (mode != kModeL);
+  const bool has_L = (mode == kModeSelfK || mode == kModeL);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double m[6] = {0, 0, 0, 0, 0, 0};
+  for (int sp = threadIdx.x; sp < np; sp += blockDim.x) {
+    const double* xs = in + 3 * (o + sp);
+    const double a = xs[0], b = xs[1], cc = xs[2];
+    if (has_block) {
+      const double z0 = R0 * a + R3 * b + R6 * cc;
+      const double z1 = R1 * a + R4 * b + R7 * cc;
+      const double z2 = R2 * a + R5 * b + R8 * cc;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        const int sn = reflect_node_dev(g, sp, p, nphi);  // g is an involution: z_{g(sn)} = z_{sp}
+        TB* zz = zg + g * dim + 3 * sn;
+        zz[0] = (TB)((g & 1) ? -z0 : z0);
+        zz[1] = (TB)((g & 2) ? -z1 : z1);
+        zz[2] = (TB)((g & 4) ? -z2 : z2);
+      }
+    }
+    if (has_L) {
+      const double4 q = x[o + sp];
+      const double rx = q.x - cx, ry = q.y - cy, rz = q.z - cz, w = q.w;
+      m[0] += w * a;
+      m[1] += w * b;
+      m[2] += w * cc;
+      m[3] += w * (ry * cc - rz * b);
+      m[4] += w * (rz * a - rx * cc);
+      m[5] += w * (rx * b - ry * a);
+    }
+  }
+  if (has_L) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) m[q] = warp_sum(m[q]);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) red[warp][q] = m[q];
+  }
+  __syncthreads();
+  if (has_L && threadIdx.x < 6) {
+    double acc = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][threadIdx.x];
+    mom[threadIdx.x] = acc;
+  }
+  __syncthreads();
+  // finish one node t of the particle from its body-frame block product (l0, l1, l2)
+  auto finish = [&](int t, double l0b, double l1b, double l2b) {
+    const long long gi = o + t;
+    double l0 = R0 * l0b + R1 * l1b + R2 * l2b;
+    double l1 = R3 * l0b + R4 * l1b + R5 * l2b;
+    double l2 = R6 * l0b + R7 * l1b + R8 * l2b;
+    const double* xt = in + 3 * gi;
+    if (mode == kModeSelfK || mode == kModeSelfKNoL) {
+      l0 += 0.5 * xt[0];
+      l1 += 0.5 * xt[1];
+      l2 += 0.5 * xt[2];
+    }
+    if (has_L) {
+      const double4 q = x[gi];
+      const double rx = q.x - cx, ry = q.y - cy, rz = q.z - cz;
+      l0 += mom[0] + (mom[4] * rz - mom[5] * ry);
+      l1 += mom[1] + (mom[5] * rx - mom[3] * rz);
+      l2 += mom[2] + (mom[3] * ry - mom[4] * rx);
+    }
+    if (mode == kModePrecond) {
+      aux[3 * gi + 0] = xt[0];
+      aux[3 * gi + 1] = xt[1];
+      aux[3 * gi + 2] = xt[2];
+    }
+    out[3 * gi + 0] = scale * l0;
+    out[3 * gi + 1] = scale * l1;
+    out[3 * gi + 2] = scale * l2;
+  };
+  if (!has_block) {
+    for (int t = threadIdx.x; t < np; t += blockDim.x) finish(t, 0.0, 0.0, 0.0);
+    return;
+  }
+  const TB* A = blocks + block_off[shape_of[i]];
+  for (int r = warp; r < nrep; r += (int)(blockDim.x >> 5)) {
+    TB y[8][3];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) y[g][0] = y[g][1] = y[g][2] = (TB)0;
+    const TB* row = A + (long long)(3 * r) * dim;
+    for (int col = lane; col < dim; col += 32) {
+      const TB a0 = __ldg(row + col), a1 = __ldg(row + dim + col), a2 = __ldg(row + 2 * dim + col);
+#pragma unroll
+      for (int g = 0; g < 8; ++g) {
+        const TB zv = zg[g * dim + col];
+        y[g][0] = fma(a0, zv, y[g][0]);
+        y[g][1] = fma(a1, zv, y[g][1]);
+        y[g][2] = fma(a2, zv, y[g][2]);
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) y[g][q] = warp_sum_t(y[g][q]);
+    const int t0 = (r / nk) * nphi + r % nk;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      if (lane != g) continue;
+      const int t = reflect_node_dev(g, t0, p, nphi);
+      bool first = true;
+      for (int h = 0; h < g; ++h)
+        if (reflect_node_dev(h, t0, p, nphi) == t) first = false;
+      if (!first) continue;
+      const double b0 = (double)y[g][0], b1 = (double)y[g][1], b2 = (double)y[g][2];
+      finish(t, (g & 1) ? -b0 : b0, (g & 2) ? -b1 : b1, (g & 4) ? -b2 : b2);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Smooth pair sums in float64.  One block per work item (128 targets x a source range); each
 // thread owns one target; sources are staged 128 at a time in shared memory with their weighted
 // density w_s mu_s.  Pairs on the same particle are excluded (their contribution is the singular
@@ -872,10 +1027,34 @@ Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, 
   }
   size_t smem = sizeof(double) * 3 * (size_t)c.max_np;
   const int nb = (int)c.bwork.size();
+  const int ns = (int)c.sym_list.size();
   bool use32 = (prec == RBS_PREC_MIXED) && (mode == kModeSelfK || mode == kModeSelfKNoL || mode == kModeKOnlySelf ||
                                              mode == kModePrecond);
   const double bytes = (mode == kModeL) ? 0.0 : (double)c.particle_block_entries * (use32 ? 4.0 : 8.0);
   KernelTimer timer(c, RBS_KC_BLOCKS);
+  if (ns > 0) {
+    const size_t zs = (use32 ? sizeof(float) : sizeof(double)) * 8 * 3 * (size_t)c.max_np_sym;
+#define RBS_SYM_ARGS                                                                                              \
+  mode, c.d_sym_list.ptr, c.d_offset.ptr, c.d_p.ptr, c.d_nphi.ptr, c.d_rot.ptr, c.d_centre.ptr, c.d_shape.ptr, \
+      c.d_block_off.ptr, B, c.d_x.ptr, x, y, aux, scale
+    if (use32) {
+      const float* B = (mode == kModePrecond) ? c.d_precond32.ptr : c.d_blockK32.ptr;
+      if (zs > 48 * 1024)
+        RBS_CUDA_TRY(cudaFuncSetAttribute(k_blocks_sym<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs));
+      k_blocks_sym<float><<<ns, 256, zs, c.stream>>>(RBS_SYM_ARGS);
+    } else {
+      const double* B = (mode == kModePrecond) ? c.d_precond.ptr : (mode == kModeSelfS ? c.d_blockS.ptr : c.d_blockK.ptr);
+      if (zs > 48 * 1024)
+        RBS_CUDA_TRY(cudaFuncSetAttribute(k_blocks_sym<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs));
+      k_blocks_sym<double><<<ns, 256, zs, c.stream>>>(RBS_SYM_ARGS);
+    }
+#undef RBS_SYM_ARGS
+    RBS_CUDA_TRY(cudaGetLastError());
+  }
+  if (nb == 0) {
+    timer.done(bytes);
+    return Status::Ok();
+  }
   if (use32) {
     const float* B = (mode == kModePrecond) ? c.d_precond32.ptr : c.d_blockK32.ptr;
     if (smem > 48 * 1024)

@@ -449,11 +449,11 @@ __global__ void k_moments(int n, const long long* offset, const double4* x, cons
   }
 }
 
-// Kernel-value matrix of the singular rule for one shape and polar index j, all azimuthal k:
-// C[((kind * nphi + k) * 9 + 3 al + be) * nrot + a] = omega_a J(s_a) kernel_{al be}(x_t - x(s_a)),
+// Kernel-value matrix of the singular rule for one shape and polar index j, azimuthal k < nkc:
+// C[((kind * nkc + k) * 9 + 3 al + be) * nrot + a] = omega_a J(s_a) kernel_{al be}(x_t - x(s_a)),
 // target t = (j, k), rotated point s_a = R_z(phi_k) rotpts[j][a]; kind 0 = traction (Eqs. 13, 22),
 // kind 1 = Stokeslet (Eq. 10).
-__global__ void k_self_kernel_values(int nphi, int nrot, double tj, const int* shape_ids, RBS_SHAPE_ARGS,
+__global__ void k_self_kernel_values(int nphi, int nkc, int nrot, double tj, const int* shape_ids, RBS_SHAPE_ARGS,
                                      const double4* rotpts_j, double* Cbase, size_t perC) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   int k = blockIdx.y;
@@ -480,48 +480,107 @@ __global__ void k_self_kernel_values(int nphi, int nrot, double tj, const int* s
   for (int al = 0; al < 3; ++al)
     for (int be = 0; be < 3; ++be) {
       const double rab = rr[al] * rr[be];
-      C[((long long)(0 * nphi + k) * 9 + 3 * al + be) * nrot + a] = ck * rab;
-      C[((long long)(1 * nphi + k) * 9 + 3 * al + be) * nrot + a] = cs * ((al == be ? inv : 0.0) + rab * inv2 * inv);
+      C[((long long)(0 * nkc + k) * 9 + 3 * al + be) * nrot + a] = ck * rab;
+      C[((long long)(1 * nkc + k) * 9 + 3 * al + be) * nrot + a] = cs * ((al == be ? inv : 0.0) + rab * inv2 * inv);
     }
 }
 
-// Scatter G[((kind * nphi + k) * 9 + 3 al + be) * np + (j' nphi + k')] into the body blocks:
-// row 3 t + al, t = j nphi + k; column 3 s + be, s = j' nphi + (k' + k) mod nphi.
-__global__ void k_self_scatter(int nphi, int np, int j, const double* Gbase, size_t perG, const long long* block_off,
-                               double* BKbase, double* BSbase) {
+// Scatter G[((kind * nkc + k) * 9 + 3 al + be) * np + (j' nphi + k')] into the body blocks:
+// stored row 3 r + al, r = j nkc + k (the node (j, k) itself when nkc = nphi, its representative
+// index when nkc = nk); column 3 s + be, s = j' nphi + (k' + k) mod nphi.
+__global__ void k_self_scatter(int nphi, int nkc, int np, int j, const double* Gbase, size_t perG,
+                               const long long* block_off, double* BKbase, double* BSbase) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const double* G = Gbase + perG * blockIdx.y;
   double* BK = BKbase + block_off[blockIdx.y];
   double* BS = BSbase + block_off[blockIdx.y];
-  long long total = 2LL * nphi * 9 * np;
+  long long total = 2LL * nkc * 9 * np;
   if (i >= total) return;
   int col = (int)(i % np);
   long long row = i / np;
   int ab = (int)(row % 9);
   long long kk = row / 9;
-  int k = (int)(kk % nphi), kind = (int)(kk / nphi);
+  int k = (int)(kk % nkc), kind = (int)(kk / nkc);
   int al = ab / 3, be = ab % 3;
   int jp = col / nphi, kp = col % nphi;
-  int t = j * nphi + k, s = jp * nphi + (kp + k) % nphi;
+  int r = j * nkc + k, s = jp * nphi + (kp + k) % nphi;
   double* B = kind == 0 ? BK : BS;
-  B[(long long)(3 * t + al) * (3 * np) + 3 * s + be] = G[i];
+  B[(long long)(3 * r + al) * (3 * np) + 3 * s + be] = G[i];
 }
 
 // Preconditioner matrix before inversion: M = 1/2 I + K0 + L0 in the body frame, with
 // L0_ts = w_s (I - [r_t]x [r_s]x) (Eq. 26 written as a block; r the body-frame node).
-__global__ void k_precond_matrix(int np, const double4* body, const double* BK, double* M) {
+// Stored row 3 r + al belongs to node (r / nk) nphi + r % nk (the node r itself when nk = nphi).
+__global__ void k_precond_matrix(int np, int nphi, int nk, int rows, const double4* body, const double* BK, double* M) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long dim = 3LL * np;
-  if (i >= dim * dim) return;
+  if (i >= (long long)rows * dim) return;
   int row = (int)(i / dim), col = (int)(i % dim);
-  int tn = row / 3, al = row % 3, sn = col / 3, be = col % 3;
+  int r = row / 3, al = row % 3, sn = col / 3, be = col % 3;
+  int tn = (r / nk) * nphi + r % nk;
   const double4 xt = body[tn], xs = body[sn];
   const double rt[3] = {xt.x, xt.y, xt.z}, rs[3] = {xs.x, xs.y, xs.z};
   // ([a]x [b]x)_{al be} = a_be b_al - (a . b) delta_{al be}
   double dot = rt[0] * rs[0] + rt[1] * rs[1] + rt[2] * rs[2];
   double cc = rt[be] * rs[al] - (al == be ? dot : 0.0);
   double Lv = xs.w * ((al == be ? 1.0 : 0.0) - cc);
-  M[i] = BK[i] + Lv + (row == col ? 0.5 : 0.0);
+  M[i] = BK[i] + Lv + (3 * tn + al == col ? 0.5 : 0.0);
+}
+
+// The preconditioner of an ellipsoid by symmetry: M = 1/2 I + K0 + L0 commutes with the eight
+// reflections of the grid, so in the basis of the irreducible representations it splits into eight
+// diagonal blocks.  Block c, entry (a, b), a = (orbit O, beta), b = (orbit O', beta'):
+//   sqrt(|O| / |O'|) sum over nodes z of O' of chi_c(g_z) sign_{g_z}(beta') M[3 rep(O) + beta][3 z + beta'],
+// g_z the reflection taking rep(O') to z; only representative rows of M are read.  Blocks are padded
+// to dmax with the identity.  Grid: (dmax^2 / 256, 8, shapes).
+__global__ void k_irrep_blocks(int np, int nrep, int dmax, int d0, int d1, int d2, int d3, int d4, int d5, int d6,
+                               int d7, SymTables T, const long long* block_off, const double* Mrows, double* out) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= (long long)dmax * dmax) return;
+  const int cc = blockIdx.y;
+  const int dims[8] = {d0, d1, d2, d3, d4, d5, d6, d7};
+  const int d = dims[cc];
+  const int a = (int)(e / dmax), b = (int)(e % dmax);
+  double* B = out + ((long long)blockIdx.z * 8 + cc) * dmax * dmax;
+  if (a >= d || b >= d) {
+    B[e] = (a == b) ? 1.0 : 0.0;
+    return;
+  }
+  const int qa = T.irrep_list[cc * 3 * nrep + a], qb = T.irrep_list[cc * 3 * nrep + b];
+  const int ra = qa / 3, bea = qa % 3, rb = qb / 3, beb = qb % 3;
+  const double* row = Mrows + block_off[blockIdx.z] + (long long)(3 * ra + bea) * (3 * np);
+  double acc = 0.0;
+  for (int q = 0; q < T.orbit[rb]; ++q) {
+    const int z = T.orb_node[8 * rb + q], g = T.orb_g[8 * rb + q];
+    const double chi = (__popc(cc & g) & 1) ? -1.0 : 1.0;
+    const double sg = ((g >> beb) & 1) ? -1.0 : 1.0;
+    acc += chi * sg * row[3 * z + beb];
+  }
+  B[e] = sqrt((double)T.orbit[ra] / (double)T.orbit[rb]) * acc;
+}
+
+// Representative rows of M^{-1} from the inverted irrep blocks: entry (3 r + al, 3 s + be) =
+// sum over irreps c holding both (r, al) and (rep(s), be) of
+//   Binv_c[(r, al), (rep(s), be)] chi_c(g_s) sign_{g_s}(be) / sqrt(|O_r| |O_rep(s)|).
+// Grid: (rows * 3 np / 256, shapes).
+__global__ void k_irrep_assemble(int np, int nrep, int dmax, SymTables T, const double* binv,
+                                 const long long* block_off, double* Mrows) {
+  const long long dim = 3LL * np;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= 3LL * nrep * dim) return;
+  const int row = (int)(e / dim), col = (int)(e % dim);
+  const int r = row / 3, al = row % 3, sn = col / 3, be = col % 3;
+  const int rs = T.rep_of[sn], gs = T.g_of[sn];
+  const double sg = ((gs >> be) & 1) ? -1.0 : 1.0;
+  const double norm = rsqrt((double)T.orbit[r] * (double)T.orbit[rs]);
+  double acc = 0.0;
+  for (int cc = 0; cc < 8; ++cc) {
+    const int pa = T.irrep_pos[cc * 3 * nrep + 3 * r + al], pb = T.irrep_pos[cc * 3 * nrep + 3 * rs + be];
+    if (pa < 0 || pb < 0) continue;
+    const double chi = (__popc(cc & gs) & 1) ? -1.0 : 1.0;
+    acc += binv[((long long)blockIdx.y * 8 + cc) * dmax * dmax + (long long)pa * dmax + pb] * chi;
+  }
+  Mrows[block_off[blockIdx.y] + e] = acc * sg * norm;
 }
 
 // out (cols x rows) = in (rows x cols)^T
@@ -600,6 +659,79 @@ static int count_basis(int p, int mmax) {
   return nb;
 }
 
+// Node (j, k) under the reflection g (bit 0: x -> -x, i.e. phi -> pi - phi; bit 1: y -> -y, phi -> -phi;
+// bit 2: z -> -z, theta -> pi - theta).
+static int reflect_node(int g, int t, int p, int nphi) {
+  int j = t / nphi, k = t % nphi;
+  if (g & 4) j = p - j;
+  if (g & 2) k = (nphi - k) % nphi;
+  if (g & 1) k = (nphi / 2 - k + nphi) % nphi;
+  return j * nphi + k;
+}
+
+// Orbits of the grid's nodes under the eight reflections, and the bases of the eight irreducible
+// representations of the reflection group on surface fields: the basis vector of (orbit O, component
+// beta) in irrep c exists when every reflection h fixing O's representative has chi_c(h) sign_h(beta) = 1,
+// chi_c(h) = (-1)^popcount(c & h), sign_h(beta) = -1 when h reflects component beta.
+static void build_symmetry(Grid& g) {
+  g.nj = g.p / 2 + 1;
+  g.nk = g.nphi / 4 + 1;
+  g.nrep = g.nj * g.nk;
+  g.rep_of.assign(g.np, -1);
+  g.g_of.assign(g.np, -1);
+  g.orbit.assign(g.nrep, 0);
+  g.stab.assign(g.nrep, 0);
+  g.orb_node.assign(8 * g.nrep, -1);
+  g.orb_g.assign(8 * g.nrep, -1);
+  for (int r = 0; r < g.nrep; ++r) {
+    const int t0 = (r / g.nk) * g.nphi + r % g.nk;
+    for (int h = 0; h < 8; ++h) {
+      const int t = reflect_node(h, t0, g.p, g.nphi);
+      if (t == t0) g.stab[r] |= 1 << h;
+      if (g.rep_of[t] < 0) {
+        g.rep_of[t] = r;
+        g.g_of[t] = h;
+        g.orb_node[8 * r + g.orbit[r]] = t;
+        g.orb_g[8 * r + g.orbit[r]] = h;
+        ++g.orbit[r];
+      }
+    }
+  }
+  g.irrep_pos.assign(8 * 3 * g.nrep, -1);
+  g.dmax = 0;
+  for (int cc = 0; cc < 8; ++cc) {
+    int d = 0;
+    for (int r = 0; r < g.nrep; ++r)
+      for (int be = 0; be < 3; ++be) {
+        bool ok = true;
+        for (int h = 0; h < 8; ++h)
+          if ((g.stab[r] >> h) & 1) {
+            const int chi = (__builtin_popcount(cc & h) & 1) ? -1 : 1;
+            const int sg = ((h >> be) & 1) ? -1 : 1;
+            if (chi * sg != 1) ok = false;
+          }
+        if (ok) g.irrep_pos[cc * 3 * g.nrep + 3 * r + be] = d++;
+      }
+    g.irrep_dim[cc] = d;
+    g.dmax = std::max(g.dmax, d);
+  }
+}
+
+// Device layout of the symmetry tables: rep_of, g_of (np each), orbit (nrep), orb_node, orb_g
+// (8 nrep each), irrep_pos (24 nrep), irrep_list (24 nrep: per irrep, 3 r + beta of each basis vector).
+static SymTables sym_tables(const Grid& g) {
+  const int* b = g.d_sym.ptr;
+  SymTables t;
+  t.rep_of = b;
+  t.g_of = b + g.np;
+  t.orbit = t.g_of + g.np;
+  t.orb_node = t.orbit + g.nrep;
+  t.orb_g = t.orb_node + 8 * g.nrep;
+  t.irrep_pos = t.orb_g + 8 * g.nrep;
+  t.irrep_list = t.irrep_pos + 24 * g.nrep;
+  return t;
+}
+
 // Build one grid's tables.
 static Status build_grid(Context& c, Grid& g) {
   cudaStream_t s = c.stream;
@@ -616,6 +748,24 @@ static Status build_grid(Context& c, Grid& g) {
   gauss_legendre_newton(g.pup + 1, g.t_up, g.lam_up);
   RBS_TRY(upload(g.d_t, g.t, s));
   RBS_TRY(upload(g.d_lam, g.lam, s));
+  build_symmetry(g);
+  {
+    std::vector<int> tab;
+    tab.insert(tab.end(), g.rep_of.begin(), g.rep_of.end());
+    tab.insert(tab.end(), g.g_of.begin(), g.g_of.end());
+    tab.insert(tab.end(), g.orbit.begin(), g.orbit.end());
+    tab.insert(tab.end(), g.orb_node.begin(), g.orb_node.end());
+    tab.insert(tab.end(), g.orb_g.begin(), g.orb_g.end());
+    tab.insert(tab.end(), g.irrep_pos.begin(), g.irrep_pos.end());
+    std::vector<int> list(24 * g.nrep, -1);
+    for (int cc = 0; cc < 8; ++cc)
+      for (int q = 0; q < 3 * g.nrep; ++q) {
+        const int pos = g.irrep_pos[cc * 3 * g.nrep + q];
+        if (pos >= 0) list[cc * 3 * g.nrep + pos] = q;
+      }
+    tab.insert(tab.end(), list.begin(), list.end());
+    RBS_TRY(upload(g.d_sym, tab, s));
+  }
   RBS_TRY(upload(g.d_t_up, g.t_up, s));
   RBS_TRY(upload(g.d_lam_up, g.lam_up, s));
 
@@ -691,12 +841,15 @@ static Status build_grid(Context& c, Grid& g) {
 }
 
 // Self blocks of every shape of one grid, in chunks of shapes.  For each chunk and polar index j:
-// kernel values C (18 nphi x nrot per shape), one batched GEMM G = C x Interp_j, and the scatter
-// into the body-frame blocks with the azimuthal shift.
-static Status build_self_blocks(Context& c, int gi, const std::vector<int>& shape_ids) {
+// kernel values C (18 nkc x nrot per shape), one batched GEMM G = C x Interp_j, and the scatter
+// into the body-frame blocks with the azimuthal shift.  Shapes stored by representative rows (sym)
+// need the targets j <= p / 2, k <= nphi / 4 only.
+static Status build_self_blocks(Context& c, int gi, const std::vector<int>& shape_ids, bool sym) {
   cudaStream_t s = c.stream;
   Grid& g = *c.grids[gi];
-  long long rowsC = 18LL * g.nphi;
+  const int nkc = sym ? g.nk : g.nphi;
+  const int jmax = sym ? g.nj - 1 : g.p;
+  long long rowsC = 18LL * nkc;
   size_t perC = (size_t)rowsC * g.nrot, perG = (size_t)rowsC * g.np;
   size_t budget = (size_t)1 << 27;  // doubles, 1 GB
   int per_chunk = (int)std::max<size_t>(1, budget / (perC + perG));
@@ -713,16 +866,16 @@ static Status build_self_blocks(Context& c, int gi, const std::vector<int>& shap
   RBS_TRY(upload(d_off, off, s));
   for (int start = 0; start < nsh; start += chunk) {
     int cnt = std::min(chunk, nsh - start);
-    for (int j = 0; j <= g.p; ++j) {
-      dim3 grd(cdiv(g.nrot, 128), g.nphi, cnt);
-      k_self_kernel_values<<<grd, 128, 0, s>>>(g.nphi, g.nrot, g.t[j], d_ids.ptr + start, RBS_SHAPE_PASS,
+    for (int j = 0; j <= jmax; ++j) {
+      dim3 grd(cdiv(g.nrot, 128), nkc, cnt);
+      k_self_kernel_values<<<grd, 128, 0, s>>>(g.nphi, nkc, g.nrot, g.t[j], d_ids.ptr + start, RBS_SHAPE_PASS,
                                                (const double4*)g.d_rotpts.ptr + (size_t)j * g.nrot, C.ptr, perC);
       RBS_CUDA_TRY(cudaGetLastError());
       RBS_TRY(dgemm_batched(s, (int)rowsC, g.np, g.nrot, C.ptr, g.nrot, (long long)perC,
                             g.d_interp.ptr + (size_t)j * g.nrot * g.np, g.np, 0, G.ptr, g.np, (long long)perG, cnt));
-      long long tot = 2LL * g.nphi * 9 * g.np;
+      long long tot = 2LL * nkc * 9 * g.np;
       dim3 grs(cdiv(tot, 256), cnt);
-      k_self_scatter<<<grs, 256, 0, s>>>(g.nphi, g.np, j, G.ptr, perG, d_off.ptr + start, c.d_blockK.ptr,
+      k_self_scatter<<<grs, 256, 0, s>>>(g.nphi, nkc, g.np, j, G.ptr, perG, d_off.ptr + start, c.d_blockK.ptr,
                                          c.d_blockS.ptr);
       RBS_CUDA_TRY(cudaGetLastError());
     }
@@ -978,8 +1131,12 @@ Status build_geometry(Context& c) {
       }
       sh.grid = grid_of[i];
       sh.np = c.grids[sh.grid]->np;
+      // ellipsoids store representative rows when the eight reflected copies of a float64 surface
+      // field fit in shared memory (N_p <= 1066, e.g. p = 16 on a 17 x 32 grid)
+      sh.sym = (sh.kind == 0) && 24LL * sh.np * (long long)sizeof(double) <= 200 * 1024;
+      sh.rows = sh.sym ? 3 * c.grids[sh.grid]->nrep : 3 * sh.np;
       sh.block_off = c.block_elems;
-      c.block_elems += (size_t)9 * sh.np * sh.np;
+      c.block_elems += (size_t)sh.rows * 3 * sh.np;
       it = shape_id.emplace(key, (int)c.shapes.size()).first;
       c.shapes.push_back(sh);
     }
@@ -1030,10 +1187,11 @@ Status build_geometry(Context& c) {
   RBS_TRY(c.d_blockK.alloc(c.block_elems));
   RBS_TRY(c.d_blockS.alloc(c.block_elems));
   {
-    std::vector<std::vector<int>> by_grid(c.grids.size());
-    for (size_t k = 0; k < c.shapes.size(); ++k) by_grid[c.shapes[k].grid].push_back((int)k);
-    for (size_t gi = 0; gi < c.grids.size(); ++gi)
-      if (!by_grid[gi].empty()) RBS_TRY(build_self_blocks(c, (int)gi, by_grid[gi]));
+    std::vector<std::vector<int>> by_grid(2 * c.grids.size());
+    for (size_t k = 0; k < c.shapes.size(); ++k)
+      by_grid[2 * c.shapes[k].grid + (c.shapes[k].sym ? 1 : 0)].push_back((int)k);
+    for (size_t q = 0; q < by_grid.size(); ++q)
+      if (!by_grid[q].empty()) RBS_TRY(build_self_blocks(c, (int)(q / 2), by_grid[q], q % 2 == 1));
   }
   std::vector<long long> boff(c.shapes.size());
   for (size_t k = 0; k < c.shapes.size(); ++k) boff[k] = (long long)c.shapes[k].block_off;
@@ -1044,29 +1202,65 @@ Status build_geometry(Context& c) {
     RBS_TRY(c.d_precond.alloc(c.block_elems));
     DevBuf<double4> body;
     RBS_TRY(body.alloc(c.max_np_shape));
-    std::map<int, std::vector<int>> by_np;
     for (size_t k = 0; k < c.shapes.size(); ++k) {
       const Shape& sh = c.shapes[k];
       Grid& g = *c.grids[sh.grid];
-      long long dim2 = 9LL * sh.np * sh.np;
+      long long elems = (long long)sh.rows * 3 * sh.np;
       k_body_nodes<<<cdiv(sh.np, 128), 128, 0, s>>>(sh.np, g.nphi, g.d_t.ptr, g.d_lam.ptr, (int)k, RBS_SHAPE_PASS,
                                                     body.ptr);
-      k_precond_matrix<<<cdiv(dim2, 256), 256, 0, s>>>(sh.np, body.ptr, c.d_blockK.ptr + sh.block_off,
-                                                       c.d_precond.ptr + sh.block_off);
-      by_np[sh.np].push_back((int)k);
+      k_precond_matrix<<<cdiv(elems, 256), 256, 0, s>>>(sh.np, g.nphi, sh.sym ? g.nk : g.nphi, sh.rows, body.ptr,
+                                                        c.d_blockK.ptr + sh.block_off, c.d_precond.ptr + sh.block_off);
     }
     RBS_CUDA_TRY(cudaGetLastError());
-    // shapes of equal size are contiguous in the block arrays only if allocated in order; invert
-    // runs of contiguous equal-size shapes together.
+    // shapes storing every row: invert runs of consecutive (hence contiguous) shapes of one size
     size_t k = 0;
     while (k < c.shapes.size()) {
+      if (c.shapes[k].sym) {
+        ++k;
+        continue;
+      }
       size_t e = k + 1;
-      while (e < c.shapes.size() && c.shapes[e].np == c.shapes[k].np) ++e;
+      while (e < c.shapes.size() && !c.shapes[e].sym && c.shapes[e].np == c.shapes[k].np) ++e;
       RBS_TRY(invert_batched(c, c.d_precond.ptr + c.shapes[k].block_off, 3 * c.shapes[k].np, (int)(e - k)));
       k = e;
     }
-    RBS_TRY(c.d_precond32.alloc(c.block_elems));
-    k_to_float<<<1024, 256, 0, s>>>(c.d_precond.ptr, c.d_precond32.ptr, (long long)c.block_elems);
+    // ellipsoids: by irreducible representation, per grid, in chunks of shapes
+    for (size_t gi = 0; gi < c.grids.size(); ++gi) {
+      std::vector<long long> offs;
+      for (const Shape& sh : c.shapes)
+        if (sh.sym && sh.grid == (int)gi) offs.push_back((long long)sh.block_off);
+      if (offs.empty()) continue;
+      const Grid& g = *c.grids[gi];
+      const SymTables T = sym_tables(g);
+      const long long per = 8LL * g.dmax * g.dmax;
+      const int chunk = (int)std::max<long long>(1, std::min<long long>((long long)offs.size(), (1LL << 28) / per));
+      DevBuf<double> blocks;
+      DevBuf<long long> d_offs;
+      RBS_TRY(blocks.alloc((size_t)per * chunk));
+      RBS_TRY(upload(d_offs, offs, s));
+      for (size_t b0 = 0; b0 < offs.size(); b0 += chunk) {
+        const int cnt = (int)std::min<size_t>(chunk, offs.size() - b0);
+        dim3 gb(cdiv((long long)g.dmax * g.dmax, 256), 8, cnt);
+        k_irrep_blocks<<<gb, 256, 0, s>>>(g.np, g.nrep, g.dmax, g.irrep_dim[0], g.irrep_dim[1], g.irrep_dim[2],
+                                          g.irrep_dim[3], g.irrep_dim[4], g.irrep_dim[5], g.irrep_dim[6],
+                                          g.irrep_dim[7], T, d_offs.ptr + b0, c.d_precond.ptr, blocks.ptr);
+        RBS_CUDA_TRY(cudaGetLastError());
+        RBS_TRY(invert_batched(c, blocks.ptr, g.dmax, 8 * cnt));
+        dim3 ga(cdiv(9LL * g.nrep * g.np, 256), cnt);
+        k_irrep_assemble<<<ga, 256, 0, s>>>(g.np, g.nrep, g.dmax, T, blocks.ptr, d_offs.ptr + b0, c.d_precond.ptr);
+        RBS_CUDA_TRY(cudaGetLastError());
+      }
+      RBS_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    // the float32 copy serves the inner solves of the mixed path, the float64 one the float64 path
+    if (c.opt.precision == RBS_PREC_MIXED) {
+      RBS_TRY(c.d_precond32.alloc(c.block_elems));
+      k_to_float<<<1024, 256, 0, s>>>(c.d_precond.ptr, c.d_precond32.ptr, (long long)c.block_elems);
+      RBS_CUDA_TRY(cudaStreamSynchronize(s));
+      c.d_precond.release();
+    } else {
+      c.d_precond32.release();
+    }
   }
   RBS_TRY(c.d_blockK32.alloc(c.block_elems));
   k_to_float<<<1024, 256, 0, s>>>(c.d_blockK.ptr, c.d_blockK32.ptr, (long long)c.block_elems);
@@ -1112,12 +1306,20 @@ Status build_geometry(Context& c) {
 
   // particle-block work list
   c.bwork.clear();
+  c.sym_list.clear();
   c.max_np = 0;
+  c.max_np_sym = 0;
   for (int i = 0; i < n; ++i) {
     c.max_np = std::max(c.max_np, nodes[i]);
+    if (c.shapes[c.shape_of[i]].sym) {
+      c.sym_list.push_back(i);
+      c.max_np_sym = std::max(c.max_np_sym, nodes[i]);
+      continue;
+    }
     for (int b = 0; b < nodes[i]; b += 24) c.bwork.push_back(make_int4(i, b, std::min(b + 24, nodes[i]), 0));
   }
   RBS_TRY(upload(c.d_bwork, c.bwork, s));
+  RBS_TRY(upload(c.d_sym_list, c.sym_list, s));
 
   // workspace
   for (auto& v : c.d_vec) RBS_TRY(v.alloc(3 * c.N));
@@ -1148,7 +1350,7 @@ Status build_geometry(Context& c) {
   }
   c.stats.far_pairs = fp;
   c.particle_block_entries = 0;
-  for (int k = 0; k < n; ++k) c.particle_block_entries += 9.0 * nodes[k] * nodes[k];
+  for (int k = 0; k < n; ++k) c.particle_block_entries += (double)c.shapes[c.shape_of[k]].rows * 3.0 * nodes[k];
 
   c.stats.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   c.have_geometry = true;
