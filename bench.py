@@ -42,18 +42,18 @@ SMS = 152
 L2_BYTES = 129 * 2 ** 20
 FP64_DFMA_PER_CLK_SM = 2     # float64 FMA lanes per SM per clock (measured 1.19 TFLOP/s at 2.07 GHz)
 FP32_LANES_PER_SM = 128
-# minimal float32-pipe instructions per pair (see DESIGN.md): traction 20, Stokeslet 18; float64 ops
+# minimal float32-pipe instructions per pair: traction 20, Stokeslet 18; float64 ops
 # per pair (with the float64 reciprocal square root counted as 7): traction 27, Stokeslet 25
 FLOPS_PER_PAIR = {"traction": 30.0, "stokeslet": 28.0}
 FP64_OPS_PER_PAIR = {"traction": 27.0, "stokeslet": 25.0}
-# DRAM bytes per launch from ncu captures on the 400-ellipsoid profiling case (57,600 nodes; see
-# profiles/), scaled by node count to the benchmarked case: the pair kernels read their inputs once
+# DRAM bytes per launch from ncu captures on the 400-ellipsoid profiling case (57,600 nodes), scaled
+# by node count to the benchmarked case: the pair kernels read their inputs once
 # (sources are re-read from L2), so traffic grows with N, not with the N^2 pairs
 NCU_TRAFFIC = {"pair_traction_df": (6.404864e6, 57600), "pair_traction_f32": (6.284032e6, 57600)}
 # float32-pipe operations per pair of the double-float kernels, counted from the source of
-# pair_tile_df (separation 24, r^2 28, reciprocal square root 8, r . density 28, powers 8, traction
-# tail 76 / Stokeslet tail 76)
-DF_INSTR_PER_PAIR = {"traction": 172.0, "stokeslet": 172.0, "both": 250.0}
+# pair_tile_df (separation 24, r^2 28, reciprocal square root 8, r . density 28, powers 8, then the
+# traction tail 76, the Stokeslet tail 76, or both tails sharing 1/r^5 and r . n: 152)
+DF_INSTR_PER_PAIR = {"traction": 172.0, "stokeslet": 172.0, "both": 248.0}
 
 
 def parse_args():

@@ -84,8 +84,11 @@ typedef struct {
                           (default 0); results in rbs_stats.kernel_ms */
   int refine_precision; /* RBS_PREC_MIXED: arithmetic of the right-hand side, refinement residuals
                           and velocity evaluation, RBS_PREC_DF (default) or RBS_PREC_FP64 */
-  int pair_variant;    /* targets per thread of the float32 and double-float pair kernels: 1, 2 or 4;
-                          0 (default) times the three once per context and keeps the fastest */
+  int pair_variant;    /* pair-kernel variant: targets per thread 1, 2 or 4, or for the float32
+                          kernels 9, 10 or 12 = 8 + targets per thread of the packed kernels that
+                          evaluate two sources per instruction (the double-float kernels then use
+                          the targets per thread alone); 0 (default) times the candidates once per
+                          context and kernel and keeps the fastest */
   int warm_start;      /* initial GMRES guess: RBS_WARM_ZERO (default), RBS_WARM_PREVIOUS (the last
                           solved density of this context) or RBS_WARM_LEARNED (the trained network);
                           the converged solution does not depend on it */
@@ -125,9 +128,9 @@ typedef struct {
   long long kernel_count[RBS_KC_COUNT];  /* launches per class */
   double kernel_units[RBS_KC_COUNT];     /* work per class: node pairs (pair sums, near), bytes of
                                             block entries read (particle blocks) */
-  int pair_variant[5];   /* targets per thread in use: float32 traction, float32 Stokeslet,
-                            double-float traction, double-float Stokeslet, fused double-float
-                            traction and Stokeslet (0 = not yet chosen) */
+  int pair_variant[5];   /* variant in use (as rbs_options.pair_variant): float32 traction, float32
+                            Stokeslet, double-float traction, double-float Stokeslet, fused
+                            double-float traction and Stokeslet (0 = not yet chosen) */
 } rbs_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -115,7 +115,8 @@ int rbs_create(const rbs_options* opt, rbs_ctx** out) {
       !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_refinements < 1 ||
       (o.precision != RBS_PREC_FP64 && o.precision != RBS_PREC_MIXED) ||
       (o.refine_precision != RBS_PREC_FP64 && o.refine_precision != RBS_PREC_DF) || o.warm_start < 0 ||
-      (o.pair_variant != 0 && o.pair_variant != 1 && o.pair_variant != 2 && o.pair_variant != 4) ||
+      (o.pair_variant != 0 && o.pair_variant != 1 && o.pair_variant != 2 && o.pair_variant != 4 &&
+       o.pair_variant != 9 && o.pair_variant != 10 && o.pair_variant != 12) ||
       o.warm_start > 2)
     return RBS_EINVAL;
   rbs_ctx* h = new rbs_ctx();

@@ -148,6 +148,10 @@ struct Context {
   DevBuf<long long> d_offset;                        // n + 1
   // per-node device data
   DevBuf<double4> d_x;  // lab position, w = quadrature weight
+  // the same positions as unevaluated float32 sums hi + lo (w of hi: the particle id's bits), the
+  // normals in float32, and a float32 weighted density w mu per node rebuilt by each packed float32
+  // pair sum
+  DevBuf<float4> d_xhi, d_xlo, d_wmu32, d_nrm32;
   DevBuf<double4> d_nrm;  // lab normal, w = unused
   DevBuf<int> d_pid;
   // coefficient surfaces of rbs_set_geometry_sh (empty: every particle is an ellipsoid): per
@@ -242,6 +246,9 @@ Status invert_batched(Context& c, double* mats, int n, int count);
 
 // ---- operator pieces (operators.cu)
 // Particle-block kernel modes.
+// Pair-kernel variant code: targets per thread, plus kPacked for the packed-float32 kernels.
+constexpr int kPacked = 8;
+
 enum BlockMode {
   kModeSelfK = 0,      // y = 1/2 x + R K0 R^T x + L x      (system operator, self part)
   kModeSelfKNoL = 1,   // y = 1/2 x + R K0 R^T x            (right-hand-side operator, self part)

@@ -33,13 +33,18 @@ __device__ __forceinline__ float rsqrt_hw(float x) {
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ double2 load2(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
-__device__ __forceinline__ double2 load2(const float* p) {
-  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-  return make_double2((double)v.x, (double)v.y);
-}
 __device__ __forceinline__ float rsq(float v) { return rsqrt_hw(v); }
 __device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename TB>
+__device__ __forceinline__ TB warp_sum_t(TB v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -49,7 +54,8 @@ __device__ __forceinline__ float warp_sumf(float v) {
 // Particle-block kernel.  Block = (particle i, node range); 256 threads.  The body-frame input
 // z = R_i^T x_i is staged in shared memory; each warp produces the three rows of one node at a
 // time as dot products over the 3 N_p columns, then rotates back and adds 1/2 x and L x as the mode
-// asks.  TB is the storage type of the blocks (float64 or float32).
+// asks.  TB is the storage type of the blocks (float64 or float32), and the arithmetic of the
+// products and their sums.
 template <typename TB>
 __global__ void __launch_bounds__(256) k_blocks(int mode, const int4* __restrict__ bwork,
                                                 const long long* __restrict__ offset, const int* __restrict__ nodes,
@@ -58,7 +64,8 @@ __global__ void __launch_bounds__(256) k_blocks(int mode, const int4* __restrict
                                                 const TB* __restrict__ blocks, const double4* __restrict__ x,
                                                 const double* __restrict__ in, double* __restrict__ out,
                                                 double* __restrict__ aux, double scale) {
-  extern __shared__ double zs[];  // 3 N_p
+  extern __shared__ __align__(16) unsigned char zs_raw[];
+  TB* zs = reinterpret_cast<TB*>(zs_raw);  // 3 N_p values of the block type
   __shared__ double red[8][6];
   __shared__ double mom[6];
   const int4 wk = bwork[blockIdx.x];
@@ -75,9 +82,9 @@ __global__ void __launch_bounds__(256) k_blocks(int mode, const int4* __restrict
     const double* xs = in + 3 * (o + s);
     double a = xs[0], b = xs[1], cc = xs[2];
     if (has_block) {
-      zs[3 * s + 0] = R0 * a + R3 * b + R6 * cc;
-      zs[3 * s + 1] = R1 * a + R4 * b + R7 * cc;
-      zs[3 * s + 2] = R2 * a + R5 * b + R8 * cc;
+      zs[3 * s + 0] = (TB)(R0 * a + R3 * b + R6 * cc);
+      zs[3 * s + 1] = (TB)(R1 * a + R4 * b + R7 * cc);
+      zs[3 * s + 2] = (TB)(R2 * a + R5 * b + R8 * cc);
     }
     if (has_L) {
       double4 p = x[o + s];
@@ -106,28 +113,28 @@ __global__ void __launch_bounds__(256) k_blocks(int mode, const int4* __restrict
   __syncthreads();
   const int dim = 3 * np;  // even: n_phi is even, so N_p is
   const TB* A = blocks + (has_block ? block_off[shape_of[i]] : 0);
-  // two nodes (six consecutive rows) per warp pass, two columns per lane per load
+  // two nodes (six consecutive rows) per warp pass, two adjacent columns per lane
   for (int t0 = wk.y + 2 * warp; t0 < wk.z; t0 += 2 * (int)(blockDim.x >> 5)) {
     const int nn = (t0 + 1 < wk.z) ? 2 : 1;
-    double y[6] = {0, 0, 0, 0, 0, 0};
+    TB y[6] = {0, 0, 0, 0, 0, 0};
     if (has_block) {
       const TB* base = A + (long long)(3 * t0) * dim;
       for (int col = 2 * lane; col < dim; col += 64) {
-        const double z0 = zs[col], z1 = zs[col + 1];
+        const TB z0 = zs[col], z1 = zs[col + 1];
 #pragma unroll
         for (int r = 0; r < 6; ++r) {
           if (r < 3 * nn) {
-            const double2 v = load2(base + (long long)r * dim + col);
-            y[r] = fma(v.x, z0, fma(v.y, z1, y[r]));
+            const TB v0 = __ldg(base + (long long)r * dim + col), v1 = __ldg(base + (long long)r * dim + col + 1);
+            y[r] = fma_t(v0, z0, fma_t(v1, z1, y[r]));
           }
         }
       }
 #pragma unroll
-      for (int r = 0; r < 6; ++r) y[r] = warp_sum(y[r]);
+      for (int r = 0; r < 6; ++r) y[r] = warp_sum_t(y[r]);
     }
     if (lane < nn) {
       const int t = t0 + lane;
-      const double y0 = y[3 * lane], y1 = y[3 * lane + 1], y2 = y[3 * lane + 2];
+      const double y0 = (double)y[3 * lane], y1 = (double)y[3 * lane + 1], y2 = (double)y[3 * lane + 2];
       const long long g = o + t;
       double l0 = R0 * y0 + R1 * y1 + R2 * y2;
       double l1 = R3 * y0 + R4 * y1 + R5 * y2;
@@ -175,12 +182,6 @@ __device__ __forceinline__ int reflect_node_dev(int g, int t, int p, int nphi) {
   return j * nphi + k;
 }
 
-template <typename TB>
-__device__ __forceinline__ TB warp_sum_t(TB v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 template <typename TB>
 __global__ void __launch_bounds__(256) k_blocks_sym(int mode, const int* __restrict__ sym_list,
@@ -289,9 +290,9 @@ __global__ void __launch_bounds__(256) k_blocks_sym(int mode, const int* __restr
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
         const TB zv = zg[g * dim + col];
-        y[g][0] = fma(a0, zv, y[g][0]);
-        y[g][1] = fma(a1, zv, y[g][1]);
-        y[g][2] = fma(a2, zv, y[g][2]);
+        y[g][0] = fma_t(a0, zv, y[g][0]);
+        y[g][1] = fma_t(a1, zv, y[g][1]);
+        y[g][2] = fma_t(a2, zv, y[g][2]);
       }
     }
 #pragma unroll
@@ -487,6 +488,167 @@ __global__ void __launch_bounds__(128 / NT, NT == 1 ? 1 : (NT == 2 ? 16 : 12)) k
     for (int u = 0; u < NT; ++u)
 #pragma unroll
       for (int c = 0; c < 3; ++c) two_sum_acc(sa[u][c], ea[u][c], p[u][c]);
+  }
+  const double sc = KIND == 0 ? kTractionScale : kStokesletScale;
+#pragma unroll
+  for (int u = 0; u < NT; ++u) {
+    if (!valid[u]) continue;
+    const long long t = w.x + threadIdx.x + NTH * u;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) atomicAdd(y + 3 * t + c, sc * ((double)sa[u][c] + (double)ea[u][c]));
+  }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Smooth pair sums in float32 with two sources per instruction: Blackwell's packed float32
+// instructions (__fadd2_rn, __fmul2_rn, __ffma2_rn: two round-to-nearest operations per lane, one
+// issue slot) evaluate a target against two sources at once, so the kernel is bound by the float32
+// pipe rather than by instruction issue.  Sources are staged structure-of-arrays in shared memory,
+// four per 128-bit load, coordinates negated (x_t + (-y_s) is the separation) and relative to the
+// work item's first target; the tile is padded to a multiple of four with zero-density sources far
+// away (they add exactly zero).  The reciprocal square root stays one hardware instruction per pair.
+// Each target thread keeps float2 partial sums over the two source streams and adds their total into
+// a compensated (two-sum) accumulator once per tile.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+template <int KIND, bool MASK>
+__device__ __forceinline__ void pair2_f32(float2 sx, float2 sy, float2 sz, float2 rx, float2 ry, float2 rz, int2 spid,
+                                          const float2 (&xt)[3], const float2 (&nt)[3], int pt, float2 (&acc)[3]) {
+  const float2 dx = __fadd2_rn(xt[0], sx), dy = __fadd2_rn(xt[1], sy), dz = __fadd2_rn(xt[2], sz);
+  const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+  float2 inv = f2(rsqrt_hw(r2.x), rsqrt_hw(r2.y));
+  if (MASK) {
+    if (spid.x == pt) inv.x = 0.0f;
+    if (spid.y == pt) inv.y = 0.0f;
+  }
+  const float2 rr = __ffma2_rn(dz, rz, __ffma2_rn(dy, ry, __fmul2_rn(dx, rx)));
+  if (KIND == 0) {
+    const float2 rn = __ffma2_rn(dz, nt[2], __ffma2_rn(dy, nt[1], __fmul2_rn(dx, nt[0])));
+    const float2 inv2 = __fmul2_rn(inv, inv);
+    const float2 inv3 = __fmul2_rn(inv2, inv);
+    const float2 c = __fmul2_rn(__fmul2_rn(__fmul2_rn(rn, rr), inv2), inv3);
+    acc[0] = __ffma2_rn(c, dx, acc[0]);
+    acc[1] = __ffma2_rn(c, dy, acc[1]);
+    acc[2] = __ffma2_rn(c, dz, acc[2]);
+  } else {
+    const float2 inv3 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+    const float2 c = __fmul2_rn(rr, inv3);
+    acc[0] = __ffma2_rn(c, dx, __ffma2_rn(rx, inv, acc[0]));
+    acc[1] = __ffma2_rn(c, dy, __ffma2_rn(ry, inv, acc[1]));
+    acc[2] = __ffma2_rn(c, dz, __ffma2_rn(rz, inv, acc[2]));
+  }
+}
+
+template <int KIND, bool MASK, int NT>
+__device__ __forceinline__ void pair_tile32x2(const float* __restrict__ ssx, const float* __restrict__ ssy,
+                                              const float* __restrict__ ssz, const float* __restrict__ srx,
+                                              const float* __restrict__ sry, const float* __restrict__ srz,
+                                              const int* __restrict__ spid, int cnt4, const float2 (&xt)[NT][3],
+                                              const float2 (&nt)[NT][3], const int (&pt)[NT], float2 (&acc)[NT][3]) {
+#pragma unroll 2
+  for (int l = 0; l < cnt4; l += 4) {
+    const float4 ax = *reinterpret_cast<const float4*>(ssx + l), ay = *reinterpret_cast<const float4*>(ssy + l);
+    const float4 az = *reinterpret_cast<const float4*>(ssz + l), bx = *reinterpret_cast<const float4*>(srx + l);
+    const float4 by = *reinterpret_cast<const float4*>(sry + l), bz = *reinterpret_cast<const float4*>(srz + l);
+    int4 pp = make_int4(-1, -1, -1, -1);
+    if (MASK) pp = *reinterpret_cast<const int4*>(spid + l);
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      pair2_f32<KIND, MASK>(f2(ax.x, ax.y), f2(ay.x, ay.y), f2(az.x, az.y), f2(bx.x, bx.y), f2(by.x, by.y),
+                            f2(bz.x, bz.y), make_int2(pp.x, pp.y), xt[u], nt[u], pt[u], acc[u]);
+      pair2_f32<KIND, MASK>(f2(ax.z, ax.w), f2(ay.z, ay.w), f2(az.z, az.w), f2(bx.z, bx.w), f2(by.z, by.w),
+                            f2(bz.z, bz.w), make_int2(pp.z, pp.w), xt[u], nt[u], pt[u], acc[u]);
+    }
+  }
+}
+
+// Weighted density in float32 for the packed kernels: wmu[t] = (w_t mu_t, 0).
+__global__ void k_weight_f32(long long N, const double4* __restrict__ x, const double* __restrict__ dens,
+                             float4* __restrict__ wmu) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const double w = x[t].w;
+  wmu[t] = make_float4((float)(w * dens[3 * t]), (float)(w * dens[3 * t + 1]), (float)(w * dens[3 * t + 2]), 0.0f);
+}
+
+// Sources and targets are read as float32 hi + lo position pairs and float32 weighted densities, so
+// the kernel runs no float64 arithmetic but its final accumulation: a coordinate relative to the work
+// item's origin o is (y_hi - o_hi) + (y_lo - o_lo), within one rounding of the exact difference.
+template <int KIND, int NT>
+__global__ void __launch_bounds__(128 / NT, NT == 4 ? 12 : (NT == 2 ? 10 : 8)) k_pairs32x2(int nitems, const longlong4* __restrict__ work, const float4* __restrict__ xhi,
+                                                       const float4* __restrict__ xlo, const float4* __restrict__ nrm32,
+                                                       const float4* __restrict__ wmu, double* __restrict__ y) {
+  constexpr int TS = 256, NTH = 128 / NT;
+  __shared__ __align__(16) float ssx[TS], ssy[TS], ssz[TS], srx[TS], sry[TS], srz[TS];
+  __shared__ __align__(16) int spid[TS];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  const longlong4 w = work[it];
+  const float4 oh = xhi[w.x], ol = xlo[w.x];
+  float2 xt[NT][3], nt[NT][3];
+  int pt[NT];
+  bool valid[NT];
+#pragma unroll
+  for (int u = 0; u < NT; ++u) {
+    const long long t = w.x + threadIdx.x + NTH * u;
+    valid[u] = t < w.y;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, n0 = 0.0f, n1 = 0.0f, n2 = 0.0f;
+    pt[u] = -1;
+    if (valid[u]) {
+      const float4 ah = xhi[t], al = xlo[t], nn = nrm32[t];
+      a0 = (ah.x - oh.x) + (al.x - ol.x);
+      a1 = (ah.y - oh.y) + (al.y - ol.y);
+      a2 = (ah.z - oh.z) + (al.z - ol.z);
+      n0 = nn.x;
+      n1 = nn.y;
+      n2 = nn.z;
+      pt[u] = __float_as_int(ah.w);
+    }
+    xt[u][0] = f2(a0, a0);
+    xt[u][1] = f2(a1, a1);
+    xt[u][2] = f2(a2, a2);
+    nt[u][0] = f2(n0, n0);
+    nt[u][1] = f2(n1, n1);
+    nt[u][2] = f2(n2, n2);
+  }
+  const int pid_lo = __float_as_int(oh.w), pid_hi = __float_as_int(xhi[w.y - 1].w);
+  float sa[NT][3], ea[NT][3];
+#pragma unroll
+  for (int u = 0; u < NT; ++u) sa[u][0] = sa[u][1] = sa[u][2] = ea[u][0] = ea[u][1] = ea[u][2] = 0.0f;
+  for (long long s0 = w.z; s0 < w.w; s0 += TS) {
+    const int cnt = (int)min((long long)TS, w.w - s0);
+    const int cnt4 = (cnt + 3) & ~3;
+    __syncthreads();
+    for (int l = threadIdx.x; l < cnt4; l += NTH) {
+      if (l < cnt) {
+        const long long s = s0 + l;
+        const float4 ph = xhi[s], pl = xlo[s], q = wmu[s];
+        ssx[l] = (oh.x - ph.x) + (ol.x - pl.x);
+        ssy[l] = (oh.y - ph.y) + (ol.y - pl.y);
+        ssz[l] = (oh.z - ph.z) + (ol.z - pl.z);
+        srx[l] = q.x;
+        sry[l] = q.y;
+        srz[l] = q.z;
+        spid[l] = __float_as_int(ph.w);
+      } else {
+        ssx[l] = ssy[l] = ssz[l] = 1.0e4f;
+        srx[l] = sry[l] = srz[l] = 0.0f;
+        spid[l] = -2;
+      }
+    }
+    __syncthreads();
+    const int tlo = spid[0], thi = spid[cnt - 1];
+    float2 p[NT][3];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) p[u][0] = p[u][1] = p[u][2] = f2(0.0f, 0.0f);
+    if (thi < pid_lo || tlo > pid_hi)
+      pair_tile32x2<KIND, false, NT>(ssx, ssy, ssz, srx, sry, srz, spid, cnt4, xt, nt, pt, p);
+    else
+      pair_tile32x2<KIND, true, NT>(ssx, ssy, ssz, srx, sry, srz, spid, cnt4, xt, nt, pt, p);
+#pragma unroll
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) two_sum_acc(sa[u][c], ea[u][c], p[u][c].x + p[u][c].y);
   }
   const double sc = KIND == 0 ? kTractionScale : kStokesletScale;
 #pragma unroll
@@ -703,35 +865,37 @@ __global__ void __launch_bounds__(128 / NT, 8) k_pairs_df(int nitems, const long
 
 // ------------------------------------------------------------------------------------------
 // Upsampled densities of the near-source particles: mu_up = U mu_j with U stored transposed
-// (N_p x N_up), one thread per upsampled node reading U coalesced and mu_j from shared memory.
+// (N_p x N_up), one thread per upsampled node reading U coalesced and mu_j from shared memory; the
+// arithmetic is that of U's storage type (float32 for the inner solve, float64 otherwise).
 template <typename TU>
 __global__ void __launch_bounds__(128) k_upsample(int n_up, const int* __restrict__ up_particle,
                                                   const long long* __restrict__ up_off,
                                                   const long long* __restrict__ offset, const int* __restrict__ nodes,
                                                   const TU* const* __restrict__ Umats, const double* __restrict__ dens,
                                                   double* __restrict__ upmu) {
-  extern __shared__ double mus[];  // 3 N_p
+  extern __shared__ double mus_raw[];  // 3 N_p values of type TU
+  TU* mus = reinterpret_cast<TU*>(mus_raw);
   for (int u = blockIdx.y; u < n_up; u += gridDim.y) {
     const int j = up_particle[u];
     const int np = nodes[j];
     const long long o = offset[j];
     __syncthreads();
-    for (int l = threadIdx.x; l < 3 * np; l += blockDim.x) mus[l] = dens[3 * o + l];
+    for (int l = threadIdx.x; l < 3 * np; l += blockDim.x) mus[l] = (TU)dens[3 * o + l];
     __syncthreads();
     const long long base = up_off[u];
     const int nup = (int)(up_off[u + 1] - base);
     const TU* Ut = Umats[u];
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nup; r += gridDim.x * blockDim.x) {
-      double a0 = 0, a1 = 0, a2 = 0;
+      TU a0 = 0, a1 = 0, a2 = 0;
       for (int s = 0; s < np; ++s) {
-        const double uv = (double)Ut[(long long)s * nup + r];
-        a0 = fma(uv, mus[3 * s], a0);
-        a1 = fma(uv, mus[3 * s + 1], a1);
-        a2 = fma(uv, mus[3 * s + 2], a2);
+        const TU uv = Ut[(long long)s * nup + r];
+        a0 = fma_t(uv, mus[3 * s], a0);
+        a1 = fma_t(uv, mus[3 * s + 1], a1);
+        a2 = fma_t(uv, mus[3 * s + 2], a2);
       }
-      upmu[3 * (base + r) + 0] = a0;
-      upmu[3 * (base + r) + 1] = a1;
-      upmu[3 * (base + r) + 2] = a2;
+      upmu[3 * (base + r) + 0] = (double)a0;
+      upmu[3 * (base + r) + 1] = (double)a1;
+      upmu[3 * (base + r) + 2] = (double)a2;
     }
   }
 }
@@ -963,8 +1127,19 @@ static void launch_pairs_kind(Context& c, int prec, int nt, int items, const dou
       k_pairs32<KIND, 1><<<resident_grid(c, (const void*)k_pairs32<KIND, 1>, 128, items), 128, 0, c.stream>>>(RBS_PAIR_ARGS);
     else if (nt == 2)
       k_pairs32<KIND, 2><<<resident_grid(c, (const void*)k_pairs32<KIND, 2>, 64, items), 64, 0, c.stream>>>(RBS_PAIR_ARGS);
-    else
+    else if (nt == 4)
       k_pairs32<KIND, 4><<<resident_grid(c, (const void*)k_pairs32<KIND, 4>, 32, items), 32, 0, c.stream>>>(RBS_PAIR_ARGS);
+    else {
+#define RBS_PACKED_ARGS items, c.d_work.ptr, c.d_xhi.ptr, c.d_xlo.ptr, c.d_nrm32.ptr, c.d_wmu32.ptr, y
+      k_weight_f32<<<cdiv(c.N, 256), 256, 0, c.stream>>>(c.N, c.d_x.ptr, x, c.d_wmu32.ptr);
+      if (nt == kPacked + 1)
+        k_pairs32x2<KIND, 1><<<resident_grid(c, (const void*)k_pairs32x2<KIND, 1>, 128, items), 128, 0, c.stream>>>(RBS_PACKED_ARGS);
+      else if (nt == kPacked + 2)
+        k_pairs32x2<KIND, 2><<<resident_grid(c, (const void*)k_pairs32x2<KIND, 2>, 64, items), 64, 0, c.stream>>>(RBS_PACKED_ARGS);
+      else
+        k_pairs32x2<KIND, 4><<<resident_grid(c, (const void*)k_pairs32x2<KIND, 4>, 32, items), 32, 0, c.stream>>>(RBS_PACKED_ARGS);
+#undef RBS_PACKED_ARGS
+    }
   }
 #undef RBS_PAIR_ARGS
 }
@@ -981,11 +1156,12 @@ static Status launch_pairs(Context& c, int kind, int prec, int nt, int items, co
   return Status::Ok();
 }
 
-// Targets per thread of the float32 and double-float pair kernels: rbs_options.pair_variant when set,
-// otherwise the fastest of 1, 2 and 4 timed once per (kernel, arithmetic) on a prefix of the work
-// list (the same items for every variant, into a scratch output).
+// Pair-kernel variant: targets per thread (1, 2 or 4), plus kPacked for the float32 kernels that take
+// two sources per packed instruction.  rbs_options.pair_variant when set (its targets per thread for
+// the double-float kernels), otherwise the fastest candidate timed once per (kernel, arithmetic) on a
+// prefix of the work list (the same items for every variant, into a scratch output).
 static int pair_variant(Context& c, int kind, int prec, const double* x) {
-  if (c.opt.pair_variant == 1 || c.opt.pair_variant == 2 || c.opt.pair_variant == 4) return c.opt.pair_variant;
+  if (c.opt.pair_variant > 0) return prec == RBS_PREC_DF ? (c.opt.pair_variant & 7) : c.opt.pair_variant;
   const int key = kind == 2 ? 4 : 2 * (prec == RBS_PREC_DF ? 1 : 0) + kind;
   if (c.tuned[key]) return c.tuned[key];
   int best = 2;
@@ -995,7 +1171,9 @@ static int pair_variant(Context& c, int kind, int prec, const double* x) {
   if (cudaMalloc(&scratch, sizeof(double) * 6 * c.N) == cudaSuccess && cudaEventCreate(&a) == cudaSuccess &&
       cudaEventCreate(&b) == cudaSuccess) {
     float best_ms = 1e30f;
-    for (int nt : {1, 2, 4}) {
+    std::vector<int> cands = {1, 2, 4};
+    if (prec == RBS_PREC_MIXED) cands.insert(cands.end(), {kPacked + 1, kPacked + 2, kPacked + 4});
+    for (int nt : cands) {
       launch_pairs(c, kind, prec, nt, items, x, scratch, scratch + 3 * c.N);  // warm (first launch of this variant)
       cudaEventRecord(a, c.stream);
       launch_pairs(c, kind, prec, nt, items, x, scratch, scratch + 3 * c.N);
@@ -1025,7 +1203,6 @@ Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, 
     RBS_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * 3 * c.N, c.stream));
     return Status::Ok();
   }
-  size_t smem = sizeof(double) * 3 * (size_t)c.max_np;
   const int nb = (int)c.bwork.size();
   const int ns = (int)c.sym_list.size();
   bool use32 = (prec == RBS_PREC_MIXED) && (mode == kModeSelfK || mode == kModeSelfKNoL || mode == kModeKOnlySelf ||
@@ -1055,6 +1232,7 @@ Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, 
     timer.done(bytes);
     return Status::Ok();
   }
+  const size_t smem = (use32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)c.max_np;
   if (use32) {
     const float* B = (mode == kModePrecond) ? c.d_precond32.ptr : c.d_blockK32.ptr;
     if (smem > 48 * 1024)

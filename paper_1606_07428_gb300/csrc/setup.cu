@@ -406,6 +406,20 @@ __global__ void k_body_nodes(int np, int nphi, const double* t, const double* la
   out[l] = make_double4(xb[0], xb[1], xb[2], 2.0 * kPi / nphi * lam[j] * J);
 }
 
+// Node positions as unevaluated float32 sums hi + lo (hi = the position rounded to float32, lo = the
+// rounded remainder), with the particle id in hi.w, and the normals in float32, for the packed
+// float32 pair kernels.
+__global__ void k_split_positions(long long N, const double4* x, const double4* nrm, const int* pid, float4* hi,
+                                  float4* lo, float4* n32) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const double4 p = x[t], q = nrm[t];
+  const float hx = (float)p.x, hy = (float)p.y, hz = (float)p.z;
+  hi[t] = make_float4(hx, hy, hz, __int_as_float(pid[t]));
+  lo[t] = make_float4((float)(p.x - (double)hx), (float)(p.y - (double)hy), (float)(p.z - (double)hz), 0.0f);
+  n32[t] = make_float4((float)q.x, (float)q.y, (float)q.z, 0.0f);
+}
+
 // Per-particle area |Gamma_i| = sum w and inverse moment tensor (Eq. 18), one block per particle.
 __global__ void k_moments(int n, const long long* offset, const double4* x, const double* centre, double* area,
                           double* tauinv) {
@@ -904,6 +918,12 @@ Status place_particles(Context& c) {
   k_nodes<<<grd, 128, 0, s>>>(n, c.d_offset.ptr, c.d_p.ptr, c.d_nphi.ptr, c.d_shape.ptr, RBS_SHAPE_PASS,
                               c.d_centre.ptr, c.d_rot.ptr, c.d_gtab_off.ptr, c.d_gtab.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr);
   k_moments<<<n, 256, 0, s>>>(n, c.d_offset.ptr, c.d_x.ptr, c.d_centre.ptr, c.d_area.ptr, c.d_tauinv.ptr);
+  RBS_TRY(c.d_xhi.alloc(c.N));
+  RBS_TRY(c.d_xlo.alloc(c.N));
+  RBS_TRY(c.d_wmu32.alloc(c.N));
+  RBS_TRY(c.d_nrm32.alloc(c.N));
+  k_split_positions<<<cdiv(c.N, 256), 256, 0, s>>>(c.N, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, c.d_xhi.ptr, c.d_xlo.ptr,
+                                                   c.d_nrm32.ptr);
   RBS_CUDA_TRY(cudaGetLastError());
   return Status::Ok();
 }
@@ -923,18 +943,21 @@ Status build_near(Context& c) {
     }
     double cell = 2.0 * rmax + c.opt.near_delta;
     std::unordered_map<long long, std::vector<int>> cells;
-    auto key = [&](long long a, long long b, long long d) { return (a * 73856093LL) ^ (b * 19349663LL) ^ (d * 83492791LL); };
+    // cells of one suspension only: independent suspensions may occupy the same region
+    auto key = [&](long long a, long long b, long long d, long long q) {
+      return (a * 73856093LL) ^ (b * 19349663LL) ^ (d * 83492791LL) ^ (q * 2654435761LL);
+    };
     std::vector<long long> ci(3 * (size_t)n);
     for (int i = 0; i < n; ++i) {
       for (int d = 0; d < 3; ++d) ci[3 * i + d] = (long long)std::floor(c.centres[3 * i + d] / cell);
-      cells[key(ci[3 * i], ci[3 * i + 1], ci[3 * i + 2])].push_back(i);
+      cells[key(ci[3 * i], ci[3 * i + 1], ci[3 * i + 2], c.sid[i])].push_back(i);
     }
     for (int i = 0; i < n; ++i) {
       std::vector<int> cand;
       for (int dx = -1; dx <= 1; ++dx)
         for (int dy = -1; dy <= 1; ++dy)
           for (int dz = -1; dz <= 1; ++dz) {
-            auto it = cells.find(key(ci[3 * i] + dx, ci[3 * i + 1] + dy, ci[3 * i + 2] + dz));
+            auto it = cells.find(key(ci[3 * i] + dx, ci[3 * i + 1] + dy, ci[3 * i + 2] + dz, c.sid[i]));
             if (it == cells.end()) continue;
             for (int j : it->second) cand.push_back(j);
           }

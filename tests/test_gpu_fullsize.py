@@ -110,3 +110,29 @@ def test_c3_operator_and_mixed_solve(rbs):
     b_rows = -ref.apply_rows("K", rho, rows, half=0.5)
     r_rows = b_rows - ref.apply_rows("K", mu, rows, half=0.5, with_L=True)
     assert np.abs(r_rows).max() < 1e-7 * np.abs(b_rows).max()
+
+
+def test_c4_batched_suspensions(rbs):
+    """256 independent suspensions of 4-512 ellipsoids with p in {6, 8, 12, 16} (25,210 particles,
+    6.77M nodes) in one context: the double-float operator at sampled rows against the oracle (which
+    keeps the suspensions apart), then mixed solves at 1e-8 and 1e-10 whose (v, omega) agree to 1e-8
+    and whose residual at sampled rows meets the tolerance."""
+    s = suspensions.c4_batched()
+    ref = oracle.System(s.semi_axes, s.p, s.nphi, s.centres, s.quats, suspension_id=s.suspension_id)
+    x = suspensions.random_density(41, s.total_nodes)
+    with rbs.Context(device=0, precision=rbs.RBS_PREC_MIXED) as ctx:
+        ctx.set_suspension(s)
+        assert rbs.rbs_get_stats(ctx.ctx)["near_pairs"] == len(ref.near)
+        y = rbs.rbs_apply_operator(ctx.ctx, rbs.RBS_OP_A, rbs.RBS_PREC_DF, x)
+        rows = sample_nodes(s, 6, 11)
+        yr = ref.apply_rows("K", x, rows, half=0.5, with_L=True)
+        assert np.abs(y[rows] - yr).max() < 1e-11 * np.abs(yr).max()
+        v, om, mu, its = rbs.rbs_mobility_solve(ctx.ctx, s.F, s.T, 1e-8, want_density=True)
+        v2, om2, _, _ = rbs.rbs_mobility_solve(ctx.ctx, s.F, s.T, 1e-10)
+    V, V2 = np.concatenate([v, om], 1), np.concatenate([v2, om2], 1)
+    assert np.linalg.norm(V - V2) < 1e-8 * np.linalg.norm(V2)
+    rows = sample_nodes(s, 6, 12)
+    rho = ref.incident_density(s.F, s.T)
+    b_rows = -ref.apply_rows("K", rho, rows, half=0.5)
+    r_rows = b_rows - ref.apply_rows("K", mu, rows, half=0.5, with_L=True)
+    assert np.abs(r_rows).max() < 1e-7 * np.abs(b_rows).max()

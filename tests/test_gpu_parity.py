@@ -255,9 +255,10 @@ def test_device_pointer_entry_points(rbs, small):
     assert rel(y.cpu().numpy(), oracle_op(ref, "A", x.cpu().numpy())) < 1e-12
 
 
-@pytest.mark.parametrize("variant", [1, 2, 4])
+@pytest.mark.parametrize("variant", [1, 2, 4, 9, 10, 12])
 def test_every_pair_kernel_variant_matches_oracle(rbs, variant):
-    """The autotuner picks among 1, 2 and 4 targets per thread; each variant is held to the same bounds."""
+    """The autotuner picks among 1, 2 and 4 targets per thread, and for float32 also among the packed
+    kernels (9, 10, 12: two sources per instruction); each variant is held to the same bounds."""
     s = mixed_system()
     ref = oracle.System(s.semi_axes, s.p, s.nphi, s.centres, s.quats)
     x = suspensions.random_density(7, s.total_nodes)
