@@ -49,7 +49,8 @@ FP64_OPS_PER_PAIR = {"traction": 27.0, "stokeslet": 25.0}
 # DRAM bytes per launch from ncu captures on the 400-ellipsoid profiling case (57,600 nodes), scaled
 # by node count to the benchmarked case: the pair kernels read their inputs once
 # (sources are re-read from L2), so traffic grows with N, not with the N^2 pairs
-NCU_TRAFFIC = {"pair_traction_df": (6.404864e6, 57600), "pair_traction_f32": (6.284032e6, 57600)}
+NCU_TRAFFIC = {"pair_traction_df": (6.404864e6, 57600), "pair_traction_f32": (4.872192e6, 57600),
+               "pair_both_df": (7.357184e6, 57600)}
 # float32-pipe operations per pair of the double-float kernels, counted from the source of
 # pair_tile_df (separation 24, r^2 28, reciprocal square root 8, r . density 28, powers 8, then the
 # traction tail 76, the Stokeslet tail 76, or both tails sharing 1/r^5 and r . n: 152)
