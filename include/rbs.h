@@ -94,6 +94,13 @@ typedef struct {
                           the converged solution does not depend on it */
   int warm_record;     /* 1: rbs_advance records a training sample (rbs_warmstart_record) after every
                           stage solve (default 0) */
+  double contact_gap;  /* 0 (default): no contact handling; > 0: the contact algorithm of Section
+                          3.4 after every mobility solve (and so in every rbs_advance stage): two
+                          particles of one suspension are in contact when the smallest distance
+                          between the nodes of their upsampled grids is below contact_gap, at the
+                          midpoint of that closest node pair; contact forces that make the two
+                          rigid velocities agree there are found from 3 n_c extra solves, and the
+                          velocities and density returned include them */
 } rbs_options;
 
 #define RBS_WARM_ZERO 0
@@ -128,6 +135,7 @@ typedef struct {
   long long kernel_count[RBS_KC_COUNT];  /* launches per class */
   double kernel_units[RBS_KC_COUNT];     /* work per class: node pairs (pair sums, near), bytes of
                                             block entries read (particle blocks) */
+  int n_contacts;        /* contacts found by the last mobility solve (rbs_options.contact_gap > 0) */
   int pair_variant[5];   /* variant in use (as rbs_options.pair_variant): float32 traction, float32
                             Stokeslet, double-float traction, double-float Stokeslet, fused
                             double-float traction and Stokeslet (0 = not yet chosen) */
@@ -185,6 +193,15 @@ int rbs_set_geometry_sh(rbs_ctx* ctx, int n, int nshape, const int* shape_pg, co
                         const int* shape_of, const int* p, const int* nphi, const double* centres,
                         const double* quats, const int* suspension_id);
 
+/*
+ * The contacts of the last mobility solve (Section 3.4; rbs_options.contact_gap > 0), in ascending
+ * (first, second) particle order: pairs (max x 2 ints: first < second particle), points (max x 3:
+ * the contact point x*) and forces (max x 3: the contact force on the first particle; the second
+ * receives its negative).  Any output may be NULL.  Returns the number of contacts (which may exceed
+ * max; only the first max are written) or a negative status.
+ */
+int rbs_get_contacts(rbs_ctx* ctx, int max, int* pairs, double* points, double* forces);
+
 /* Number of surface nodes of the current geometry (3 * that many unknowns). */
 long long rbs_total_nodes(const rbs_ctx* ctx);
 
@@ -217,13 +234,14 @@ int rbs_mobility_solve_device(rbs_ctx* ctx, const double* F_dev, const double* T
 #define RBS_RK4 4
 
 /*
- * Rigid-body time stepping (Section 3.3, Eqs. 40 and 43; Algorithm 1 without contact): `steps`
- * explicit Runge-Kutta steps of size dt (scheme RBS_RK_EULER, RBS_RK_TRAPEZOID or RBS_RK4) of
- * dc_i/dt = v_i, dq_i/dt = 1/2 (0, omega_i) q_i, with the forces F and torques T (n x 3 each, host)
- * held fixed.  Every stage is one mobility solve to relative tolerance tol at the stage
- * configuration (the body-frame self blocks and preconditioner are reused, Eq. 38); quaternions are
- * renormalised after each step.  The context's configuration is updated in place; iterations (may be
- * NULL) receives the total GMRES iterations.  Returns RBS_EOVERLAP if particles come into contact.
+ * Rigid-body time stepping (Section 3.3, Eqs. 40 and 43; Algorithm 1): `steps` explicit
+ * Runge-Kutta steps of size dt (scheme RBS_RK_EULER, RBS_RK_TRAPEZOID or RBS_RK4) of dc_i/dt = v_i,
+ * dq_i/dt = 1/2 (0, omega_i) q_i, with the forces F and torques T (n x 3 each, host) held fixed.
+ * Every stage is one mobility solve to relative tolerance tol at the stage configuration (the
+ * body-frame self blocks and preconditioner are reused, Eq. 38), with the contact correction of
+ * Section 3.4 when rbs_options.contact_gap > 0; quaternions are renormalised after each step.  The
+ * context's configuration is updated in place; iterations (may be NULL) receives the total GMRES
+ * iterations.  Returns RBS_EOVERLAP if the inscribed spheres of two particles intersect.
  */
 int rbs_advance(rbs_ctx* ctx, const double* F, const double* T, double dt, int steps, int scheme, double tol,
                 int* iterations);

@@ -15,6 +15,9 @@ Modules:
 * system: incident density (Eq. 19), the augmented system (Eq. 25), its dense and matrix-free
   solution, velocity extraction (Eqs. 41-42), the mobility matrix (Eq. 1).
 * timestep: rigid-body time stepping (Section 3.3, Eqs. 40, 43) with quaternions and RK4.
+* shapes: general surfaces given by spherical-harmonic coefficients (Eqs. 31, 36, 37).
+* warmstart: features, network and training of the learned initial guess.
+* contact: the contact force algorithm (Section 3.4).
 """
 from .geometry import body_surface, quat_to_rot  # noqa: F401
 from .system import Options, System, gmres  # noqa: F401

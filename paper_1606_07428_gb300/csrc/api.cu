@@ -1,4 +1,5 @@
 // The C ABI of include/rbs.h: argument checks, host <-> device copies and dispatch.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -100,6 +101,7 @@ void rbs_default_options(rbs_options* o) {
   o->warm_start = RBS_WARM_ZERO;
   o->pair_variant = 0;
   o->warm_record = 0;
+  o->contact_gap = 0.0;
 }
 
 int rbs_create(const rbs_options* opt, rbs_ctx** out) {
@@ -117,7 +119,7 @@ int rbs_create(const rbs_options* opt, rbs_ctx** out) {
       (o.refine_precision != RBS_PREC_FP64 && o.refine_precision != RBS_PREC_DF) || o.warm_start < 0 ||
       (o.pair_variant != 0 && o.pair_variant != 1 && o.pair_variant != 2 && o.pair_variant != 4 &&
        o.pair_variant != 9 && o.pair_variant != 10 && o.pair_variant != 12) ||
-      o.warm_start > 2)
+      o.warm_start > 2 || !(o.contact_gap >= 0.0))
     return RBS_EINVAL;
   rbs_ctx* h = new rbs_ctx();
   Context& c = h->c;
@@ -488,6 +490,24 @@ int rbs_reset_stats(rbs_ctx* h) {
     c.stats.kernel_units[k] = 0.0;
   }
   return RBS_OK;
+}
+
+int rbs_get_contacts(rbs_ctx* h, int max, int* pairs, double* points, double* forces) {
+  if (!h || max < 0) return RBS_EINVAL;
+  const Context& c = h->c;
+  const int nc = (int)c.contacts.size();
+  for (int k = 0; k < std::min(nc, max); ++k) {
+    const Context::Contact& ct = c.contacts[k];
+    if (pairs) {
+      pairs[2 * k] = ct.i;
+      pairs[2 * k + 1] = ct.j;
+    }
+    for (int q = 0; q < 3; ++q) {
+      if (points) points[3 * k + q] = ct.x[q];
+      if (forces) forces[3 * k + q] = ct.f[q];
+    }
+  }
+  return nc;
 }
 
 const char* rbs_last_error(const rbs_ctx* h) {

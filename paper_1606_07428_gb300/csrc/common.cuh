@@ -152,6 +152,9 @@ struct Context {
   // normals in float32, and a float32 weighted density w mu per node rebuilt by each packed float32
   // pair sum
   DevBuf<float4> d_xhi, d_xlo, d_wmu32, d_nrm32;
+  // for the double-float kernels: positions as exact sums of three float32 numbers (hi has the
+  // particle id's bits in w), normals and the per-pass weighted density as hi + lo float32 pairs
+  DevBuf<float4> d_x3h, d_x3m, d_x3l, d_nrmh, d_nrml, d_wmuh, d_wmul;
   DevBuf<double4> d_nrm;  // lab normal, w = unused
   DevBuf<int> d_pid;
   // coefficient surfaces of rbs_set_geometry_sh (empty: every particle is an ellipsoid): per
@@ -208,6 +211,13 @@ struct Context {
   DevBuf<double> d_FT;  // forces and torques, n x 6
   DevBuf<double> d_vo;  // velocities, n x 6
   double* h_pinned = nullptr;
+
+  // contacts of the last mobility solve (Section 3.4): particles i < j, point x*, force f on i
+  struct Contact {
+    int i, j;
+    double x[3], f[3];
+  };
+  std::vector<Contact> contacts;
 
   rbs_stats stats{};
   WarmState* warm = nullptr;       // learned warm start (warmstart.cu)

@@ -780,17 +780,57 @@ __device__ __forceinline__ void pair_tile_df(const float4* __restrict__ sph, con
   }
 }
 
-// y += traction sum (KIND 0, 2) or Stokeslet sum (KIND 1); KIND 2 also y2 += Stokeslet sum.
+// Weighted density as double-float pairs for the double-float kernels: (w mu) rounded to float32 and
+// the rounded remainder.
+__global__ void k_weight_df(long long N, const double4* __restrict__ x, const double* __restrict__ dens,
+                            float4* __restrict__ wh, float4* __restrict__ wl) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const double w = x[t].w;
+  const dflt a = df_split(w * dens[3 * t]), b = df_split(w * dens[3 * t + 1]), c = df_split(w * dens[3 * t + 2]);
+  wh[t] = make_float4(a.h, b.h, c.h, 0.0f);
+  wl[t] = make_float4(a.l, b.l, c.l, 0.0f);
+}
+
+// y - o for y = yh + ym + yl and o = oh + om + ol (exact three-float splits), as a double-float pair:
+// the three part differences are formed exactly by two-sums, the leading pair is added exactly, and
+// the remaining small terms (at most 2^-48 |y| in size) are summed in float32 before renormalising.
+__device__ __forceinline__ dflt df_diff3(float yh, float ym, float yl, float oh, float om, float ol) {
+  const dflt s = df_two_sum(yh, -oh), t = df_two_sum(ym, -om), u = df_two_sum(yl, -ol);
+  const dflt h = df_two_sum(s.h, t.h);
+  const float l = ((s.l + t.l) + (u.h + u.l)) + h.l;
+  const float hi = h.h + l;
+  return {hi, l - (hi - h.h)};
+}
+
+// a + b for double-float pairs, both parts added with two-sums and the result renormalised twice.
+__device__ __forceinline__ dflt df_add_accurate(dflt a, dflt b) {
+  dflt s = df_two_sum(a.h, b.h);
+  const dflt t = df_two_sum(a.l, b.l);
+  s.l += t.h;
+  float h = s.h + s.l;
+  float l = s.l - (h - s.h);
+  l += t.l;
+  const float h2 = h + l;
+  return {h2, l - (h2 - h)};
+}
+
+// y += traction sum (KIND 0, 2) or Stokeslet sum (KIND 1); KIND 2 also y2 += Stokeslet sum.  No float64
+// arithmetic runs per pair or per staged source: positions come as exact three-float splits, the
+// weighted density and normals as double-float pairs, and tile sums are accumulated in double-float;
+// the total is converted to float64 once per target.
 template <int KIND, int NT>
-__global__ void __launch_bounds__(128 / NT, 8) k_pairs_df(int nitems, const longlong4* __restrict__ work, const double4* __restrict__ x,
-                                                       const double4* __restrict__ nrm, const int* __restrict__ pid,
-                                                       const double* __restrict__ dens, double* __restrict__ y,
+__global__ void __launch_bounds__(128 / NT, 8) k_pairs_df(int nitems, const longlong4* __restrict__ work,
+                                                       const float4* __restrict__ x3h, const float4* __restrict__ x3m,
+                                                       const float4* __restrict__ x3l, const float4* __restrict__ nh,
+                                                       const float4* __restrict__ nl, const float4* __restrict__ wh,
+                                                       const float4* __restrict__ wl, double* __restrict__ y,
                                                        double* __restrict__ y2) {
   constexpr int TS = 128, NTH = 128 / NT;
   __shared__ float4 sph[TS], spl[TS], sdh[TS], sdl[TS];
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
   const longlong4 w = work[it];
-  const double4 org = x[w.x];
+  const float4 oh = x3h[w.x], om = x3m[w.x], ol = x3l[w.x];
   dflt xt[NT][3], nt[NT][3];
   int pt[NT];
   bool valid[NT];
@@ -798,40 +838,45 @@ __global__ void __launch_bounds__(128 / NT, 8) k_pairs_df(int nitems, const long
   for (int u = 0; u < NT; ++u) {
     const long long t = w.x + threadIdx.x + NTH * u;
     valid[u] = t < w.y;
-    double4 a = make_double4(org.x, org.y, org.z, 0.0), nn = make_double4(0, 0, 0, 0);
+    float4 ah = oh, am = om, al = ol, bh = make_float4(0, 0, 0, 0), bl = make_float4(0, 0, 0, 0);
     pt[u] = -1;
     if (valid[u]) {
-      a = x[t];
-      nn = nrm[t];
-      pt[u] = pid[t];
+      ah = x3h[t];
+      am = x3m[t];
+      al = x3l[t];
+      bh = nh[t];
+      bl = nl[t];
+      pt[u] = __float_as_int(ah.w);
     }
-    xt[u][0] = df_split(a.x - org.x);
-    xt[u][1] = df_split(a.y - org.y);
-    xt[u][2] = df_split(a.z - org.z);
-    nt[u][0] = df_split(nn.x);
-    nt[u][1] = df_split(nn.y);
-    nt[u][2] = df_split(nn.z);
+    xt[u][0] = df_diff3(ah.x, am.x, al.x, oh.x, om.x, ol.x);
+    xt[u][1] = df_diff3(ah.y, am.y, al.y, oh.y, om.y, ol.y);
+    xt[u][2] = df_diff3(ah.z, am.z, al.z, oh.z, om.z, ol.z);
+    nt[u][0] = {bh.x, bl.x};
+    nt[u][1] = {bh.y, bl.y};
+    nt[u][2] = {bh.z, bl.z};
   }
-  const int pid_lo = pid[w.x], pid_hi = pid[w.y - 1];
-  double a[NT][3], a2[NT][3];
+  const int pid_lo = __float_as_int(oh.w), pid_hi = __float_as_int(x3h[w.y - 1].w);
+  dflt a[NT][3], a2[NT][3];
 #pragma unroll
-  for (int u = 0; u < NT; ++u) a[u][0] = a[u][1] = a[u][2] = a2[u][0] = a2[u][1] = a2[u][2] = 0.0;
+  for (int u = 0; u < NT; ++u)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a[u][c] = a2[u][c] = dflt{0.0f, 0.0f};
   for (long long s0 = w.z; s0 < w.w; s0 += TS) {
     const int cnt = (int)min((long long)TS, w.w - s0);
     __syncthreads();
     for (int l = threadIdx.x; l < cnt; l += NTH) {
       const long long s = s0 + l;
-      const double4 ps = x[s];
-      const double* dd = dens + 3 * s;
-      const dflt px = df_split(ps.x - org.x), py = df_split(ps.y - org.y), pz = df_split(ps.z - org.z);
-      const dflt d0 = df_split(ps.w * dd[0]), d1 = df_split(ps.w * dd[1]), d2 = df_split(ps.w * dd[2]);
-      sph[l] = make_float4(px.h, py.h, pz.h, __int_as_float(pid[s]));
+      const float4 ph = x3h[s], pm = x3m[s], pl = x3l[s];
+      const dflt px = df_diff3(ph.x, pm.x, pl.x, oh.x, om.x, ol.x);
+      const dflt py = df_diff3(ph.y, pm.y, pl.y, oh.y, om.y, ol.y);
+      const dflt pz = df_diff3(ph.z, pm.z, pl.z, oh.z, om.z, ol.z);
+      sph[l] = make_float4(px.h, py.h, pz.h, ph.w);
       spl[l] = make_float4(px.l, py.l, pz.l, 0.0f);
-      sdh[l] = make_float4(d0.h, d1.h, d2.h, 0.0f);
-      sdl[l] = make_float4(d0.l, d1.l, d2.l, 0.0f);
+      sdh[l] = wh[s];
+      sdl[l] = wl[s];
     }
     __syncthreads();
-    const int tlo = pid[s0], thi = pid[s0 + cnt - 1];
+    const int tlo = __float_as_int(sph[0].w), thi = __float_as_int(sph[cnt - 1].w);
     dflt acc[NT][3], acc2[NT][3];
 #pragma unroll
     for (int u = 0; u < NT; ++u)
@@ -845,8 +890,8 @@ __global__ void __launch_bounds__(128 / NT, 8) k_pairs_df(int nitems, const long
     for (int u = 0; u < NT; ++u)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        a[u][c] += (double)acc[u][c].h + (double)acc[u][c].l;
-        if (KIND == 2) a2[u][c] += (double)acc2[u][c].h + (double)acc2[u][c].l;
+        a[u][c] = df_add_accurate(a[u][c], acc[u][c]);
+        if (KIND == 2) a2[u][c] = df_add_accurate(a2[u][c], acc2[u][c]);
       }
   }
   const double sc = KIND == 1 ? kStokesletScale : kTractionScale;
@@ -856,8 +901,224 @@ __global__ void __launch_bounds__(128 / NT, 8) k_pairs_df(int nitems, const long
     const long long t = w.x + threadIdx.x + NTH * u;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      atomicAdd(y + 3 * t + c, sc * a[u][c]);
-      if (KIND == 2) atomicAdd(y2 + 3 * t + c, kStokesletScale * a2[u][c]);
+      atomicAdd(y + 3 * t + c, sc * ((double)a[u][c].h + (double)a[u][c].l));
+      if (KIND == 2) atomicAdd(y2 + 3 * t + c, kStokesletScale * ((double)a2[u][c].h + (double)a2[u][c].l));
+    }
+  }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Double-float pair sums with two sources per instruction: the operations of pair_tile_df on float2
+// pairs (__fadd2_rn, __fmul2_rn, __ffma2_rn, each two round-to-nearest float32 operations, so the
+// error-free transformations stay exact per source), sources staged structure-of-arrays and padded
+// to an even count with zero-density sources far away (they add exactly zero).
+struct df2 {
+  float2 h, l;
+};
+__device__ __forceinline__ float2 ng2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ df2 two_sum2(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  const float2 bb = __fadd2_rn(s, ng2(a));
+  const float2 e = __fadd2_rn(__fadd2_rn(a, ng2(__fadd2_rn(s, ng2(bb)))), __fadd2_rn(b, ng2(bb)));
+  return {s, e};
+}
+__device__ __forceinline__ df2 mul2(df2 a, df2 b) {
+  const float2 p = __fmul2_rn(a.h, b.h);
+  float2 e = __ffma2_rn(a.h, b.h, ng2(p));
+  e = __ffma2_rn(a.h, b.l, e);
+  e = __ffma2_rn(a.l, b.h, e);
+  return {p, e};
+}
+__device__ __forceinline__ df2 dot3_2(df2 a0, df2 b0, df2 a1, df2 b1, df2 a2, df2 b2) {
+  const df2 p0 = mul2(a0, b0), p1 = mul2(a1, b1), p2 = mul2(a2, b2);
+  const df2 s1 = two_sum2(p0.h, p1.h);
+  const df2 s2 = two_sum2(s1.h, p2.h);
+  return {s2.h, __fadd2_rn(__fadd2_rn(__fadd2_rn(s1.l, s2.l), __fadd2_rn(p0.l, p1.l)), p2.l)};
+}
+__device__ __forceinline__ void acc2_add(df2& acc, df2 v) {
+  const df2 s = two_sum2(acc.h, v.h);
+  acc.h = s.h;
+  acc.l = __fadd2_rn(acc.l, __fadd2_rn(s.l, v.l));
+}
+// the two lanes' double-float values added into one (unnormalised) pair
+__device__ __forceinline__ dflt fold2(const df2& a) {
+  const dflt s = df_two_sum(a.h.x, a.h.y);
+  return {s.h, s.l + (a.l.x + a.l.y)};
+}
+
+template <int KIND, bool MASK>
+__device__ __forceinline__ void pair2_df(const df2 (&y)[3], const df2 (&den)[3], int2 spid, const df2 (&xt)[3],
+                                         const df2 (&nt)[3], int pt, df2 (&acc)[3], df2 (&acc2)[3]) {
+  df2 d[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    d[c] = two_sum2(xt[c].h, ng2(y[c].h));
+    d[c].l = __fadd2_rn(d[c].l, __fadd2_rn(xt[c].l, ng2(y[c].l)));
+  }
+  float2 p[3], e[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    p[c] = __fmul2_rn(d[c].h, d[c].h);
+    e[c] = __ffma2_rn(d[c].h, d[c].h, ng2(p[c]));
+    e[c] = __ffma2_rn(__fadd2_rn(d[c].h, d[c].h), d[c].l, e[c]);
+  }
+  const df2 s1 = two_sum2(p[0], p[1]);
+  const df2 s2 = two_sum2(s1.h, p[2]);
+  const float2 r2l = __fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(s1.l, s2.l), e[0]), e[1]), e[2]);
+  const float2 r2h = s2.h;
+  const float2 y0 = make_float2(rsqrt_hw(r2h.x), rsqrt_hw(r2h.y));
+  const float2 q = __fmul2_rn(y0, y0);
+  const float2 qe = __ffma2_rn(y0, y0, ng2(q));
+  float2 t = __ffma2_rn(r2h, q, dup2(-1.0f));
+  t = __ffma2_rn(r2h, qe, t);
+  t = __ffma2_rn(r2l, q, t);
+  df2 inv = {y0, __fmul2_rn(__fmul2_rn(dup2(-0.5f), t), y0)};
+  if (MASK) {
+    if (spid.x == pt) inv.h.x = inv.l.x = 0.0f;
+    if (spid.y == pt) inv.h.y = inv.l.y = 0.0f;
+  }
+  const df2 rr = dot3_2(d[0], den[0], d[1], den[1], d[2], den[2]);
+  const df2 inv2 = mul2(inv, inv);
+  const df2 inv3 = mul2(inv2, inv);
+  if (KIND == 0 || KIND == 2) {
+    const df2 inv5 = mul2(inv3, inv2);
+    const df2 rn = dot3_2(d[0], nt[0], d[1], nt[1], d[2], nt[2]);
+    const df2 ck = mul2(mul2(rn, rr), inv5);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc2_add(acc[c], mul2(ck, d[c]));
+  }
+  if (KIND == 1 || KIND == 2) {
+    const df2 cs = mul2(rr, inv3);
+    df2(&as)[3] = KIND == 2 ? acc2 : acc;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc2_add(as[c], mul2(den[c], inv));
+      acc2_add(as[c], mul2(cs, d[c]));
+    }
+  }
+}
+
+template <int KIND, int NT>
+__global__ void __launch_bounds__(128 / NT, NT == 1 ? 5 : 6) k_pairs_df2(int nitems, const longlong4* __restrict__ work,
+                                                        const float4* __restrict__ x3h, const float4* __restrict__ x3m,
+                                                        const float4* __restrict__ x3l, const float4* __restrict__ nh,
+                                                        const float4* __restrict__ nl, const float4* __restrict__ wh,
+                                                        const float4* __restrict__ wl, double* __restrict__ y,
+                                                        double* __restrict__ y2) {
+  constexpr int TS = 128, NTH = 128 / NT;
+  // structure of arrays: separation parts x, y, z (hi, lo), weighted density (hi, lo), particle id
+  __shared__ __align__(16) float sa[12][TS];
+  __shared__ __align__(16) int spid[TS];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  const longlong4 w = work[it];
+  const float4 oh = x3h[w.x], om = x3m[w.x], ol = x3l[w.x];
+  df2 xt[NT][3], nt[NT][3];
+  int pt[NT];
+  bool valid[NT];
+#pragma unroll
+  for (int u = 0; u < NT; ++u) {
+    const long long t = w.x + threadIdx.x + NTH * u;
+    valid[u] = t < w.y;
+    float4 ah = oh, am = om, al = ol, bh = make_float4(0, 0, 0, 0), bl = make_float4(0, 0, 0, 0);
+    pt[u] = -1;
+    if (valid[u]) {
+      ah = x3h[t];
+      am = x3m[t];
+      al = x3l[t];
+      bh = nh[t];
+      bl = nl[t];
+      pt[u] = __float_as_int(ah.w);
+    }
+    const dflt dx = df_diff3(ah.x, am.x, al.x, oh.x, om.x, ol.x), dy = df_diff3(ah.y, am.y, al.y, oh.y, om.y, ol.y),
+               dz = df_diff3(ah.z, am.z, al.z, oh.z, om.z, ol.z);
+    xt[u][0] = {dup2(dx.h), dup2(dx.l)};
+    xt[u][1] = {dup2(dy.h), dup2(dy.l)};
+    xt[u][2] = {dup2(dz.h), dup2(dz.l)};
+    nt[u][0] = {dup2(bh.x), dup2(bl.x)};
+    nt[u][1] = {dup2(bh.y), dup2(bl.y)};
+    nt[u][2] = {dup2(bh.z), dup2(bl.z)};
+  }
+  const int pid_lo = __float_as_int(oh.w), pid_hi = __float_as_int(x3h[w.y - 1].w);
+  dflt a[NT][3], a2[NT][3];
+#pragma unroll
+  for (int u = 0; u < NT; ++u)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a[u][c] = a2[u][c] = dflt{0.0f, 0.0f};
+  for (long long s0 = w.z; s0 < w.w; s0 += TS) {
+    const int cnt = (int)min((long long)TS, w.w - s0);
+    const int cnt2 = (cnt + 1) & ~1;
+    __syncthreads();
+    for (int l = threadIdx.x; l < cnt2; l += NTH) {
+      if (l < cnt) {
+        const long long s = s0 + l;
+        const float4 ph = x3h[s], pm = x3m[s], pl = x3l[s], qh = wh[s], ql = wl[s];
+        const dflt px = df_diff3(ph.x, pm.x, pl.x, oh.x, om.x, ol.x);
+        const dflt py = df_diff3(ph.y, pm.y, pl.y, oh.y, om.y, ol.y);
+        const dflt pz = df_diff3(ph.z, pm.z, pl.z, oh.z, om.z, ol.z);
+        sa[0][l] = px.h;
+        sa[1][l] = px.l;
+        sa[2][l] = py.h;
+        sa[3][l] = py.l;
+        sa[4][l] = pz.h;
+        sa[5][l] = pz.l;
+        sa[6][l] = qh.x;
+        sa[7][l] = ql.x;
+        sa[8][l] = qh.y;
+        sa[9][l] = ql.y;
+        sa[10][l] = qh.z;
+        sa[11][l] = ql.z;
+        spid[l] = __float_as_int(ph.w);
+      } else {
+        sa[0][l] = sa[2][l] = sa[4][l] = 1.0e4f;
+        sa[1][l] = sa[3][l] = sa[5][l] = 0.0f;
+        for (int q = 6; q < 12; ++q) sa[q][l] = 0.0f;
+        spid[l] = -2;
+      }
+    }
+    __syncthreads();
+    const int tlo = spid[0], thi = spid[cnt - 1];
+    const bool masked = !(thi < pid_lo || tlo > pid_hi);
+    df2 acc[NT][3], acc2[NT][3];
+#pragma unroll
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[u][c] = acc2[u][c] = df2{dup2(0.0f), dup2(0.0f)};
+    for (int l = 0; l < cnt2; l += 2) {
+      df2 ys[3], den[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        ys[c] = {*reinterpret_cast<const float2*>(&sa[2 * c][l]), *reinterpret_cast<const float2*>(&sa[2 * c + 1][l])};
+        den[c] = {*reinterpret_cast<const float2*>(&sa[6 + 2 * c][l]),
+                  *reinterpret_cast<const float2*>(&sa[7 + 2 * c][l])};
+      }
+      const int2 pp = *reinterpret_cast<const int2*>(&spid[l]);
+#pragma unroll
+      for (int u = 0; u < NT; ++u) {
+        if (masked)
+          pair2_df<KIND, true>(ys, den, pp, xt[u], nt[u], pt[u], acc[u], acc2[u]);
+        else
+          pair2_df<KIND, false>(ys, den, pp, xt[u], nt[u], pt[u], acc[u], acc2[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        a[u][c] = df_add_accurate(a[u][c], fold2(acc[u][c]));
+        if (KIND == 2) a2[u][c] = df_add_accurate(a2[u][c], fold2(acc2[u][c]));
+      }
+  }
+  const double sc = KIND == 1 ? kStokesletScale : kTractionScale;
+#pragma unroll
+  for (int u = 0; u < NT; ++u) {
+    if (!valid[u]) continue;
+    const long long t = w.x + threadIdx.x + NTH * u;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      atomicAdd(y + 3 * t + c, sc * ((double)a[u][c].h + (double)a[u][c].l));
+      if (KIND == 2) atomicAdd(y2 + 3 * t + c, kStokesletScale * ((double)a2[u][c].h + (double)a2[u][c].l));
     }
   }
   }
@@ -1112,12 +1373,20 @@ template <int KIND>
 static void launch_pairs_kind(Context& c, int prec, int nt, int items, const double* x, double* y, double* y2) {
 #define RBS_PAIR_ARGS items, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, x, y
   if (prec == RBS_PREC_DF) {
+#define RBS_DF_ARGS items, c.d_work.ptr, c.d_x3h.ptr, c.d_x3m.ptr, c.d_x3l.ptr, c.d_nrmh.ptr, c.d_nrml.ptr, \
+                    c.d_wmuh.ptr, c.d_wmul.ptr, y, y2
+    k_weight_df<<<cdiv(c.N, 256), 256, 0, c.stream>>>(c.N, c.d_x.ptr, x, c.d_wmuh.ptr, c.d_wmul.ptr);
     if (nt == 1)
-      k_pairs_df<KIND, 1><<<resident_grid(c, (const void*)k_pairs_df<KIND, 1>, 128, items), 128, 0, c.stream>>>(RBS_PAIR_ARGS, y2);
+      k_pairs_df<KIND, 1><<<resident_grid(c, (const void*)k_pairs_df<KIND, 1>, 128, items), 128, 0, c.stream>>>(RBS_DF_ARGS);
     else if (nt == 2)
-      k_pairs_df<KIND, 2><<<resident_grid(c, (const void*)k_pairs_df<KIND, 2>, 64, items), 64, 0, c.stream>>>(RBS_PAIR_ARGS, y2);
+      k_pairs_df<KIND, 2><<<resident_grid(c, (const void*)k_pairs_df<KIND, 2>, 64, items), 64, 0, c.stream>>>(RBS_DF_ARGS);
+    else if (nt == 4)
+      k_pairs_df<KIND, 4><<<resident_grid(c, (const void*)k_pairs_df<KIND, 4>, 32, items), 32, 0, c.stream>>>(RBS_DF_ARGS);
+    else if (nt == kPacked + 1)
+      k_pairs_df2<KIND, 1><<<resident_grid(c, (const void*)k_pairs_df2<KIND, 1>, 128, items), 128, 0, c.stream>>>(RBS_DF_ARGS);
     else
-      k_pairs_df<KIND, 4><<<resident_grid(c, (const void*)k_pairs_df<KIND, 4>, 32, items), 32, 0, c.stream>>>(RBS_PAIR_ARGS, y2);
+      k_pairs_df2<KIND, 2><<<resident_grid(c, (const void*)k_pairs_df2<KIND, 2>, 64, items), 64, 0, c.stream>>>(RBS_DF_ARGS);
+#undef RBS_DF_ARGS
   } else if constexpr (KIND == 2) {
     return;
   } else if (prec == RBS_PREC_FP64) {
@@ -1161,7 +1430,8 @@ static Status launch_pairs(Context& c, int kind, int prec, int nt, int items, co
 // the double-float kernels), otherwise the fastest candidate timed once per (kernel, arithmetic) on a
 // prefix of the work list (the same items for every variant, into a scratch output).
 static int pair_variant(Context& c, int kind, int prec, const double* x) {
-  if (c.opt.pair_variant > 0) return prec == RBS_PREC_DF ? (c.opt.pair_variant & 7) : c.opt.pair_variant;
+  if (c.opt.pair_variant > 0)
+    return (prec == RBS_PREC_DF && c.opt.pair_variant == kPacked + 4) ? 4 : c.opt.pair_variant;
   const int key = kind == 2 ? 4 : 2 * (prec == RBS_PREC_DF ? 1 : 0) + kind;
   if (c.tuned[key]) return c.tuned[key];
   int best = 2;
@@ -1173,6 +1443,7 @@ static int pair_variant(Context& c, int kind, int prec, const double* x) {
     float best_ms = 1e30f;
     std::vector<int> cands = {1, 2, 4};
     if (prec == RBS_PREC_MIXED) cands.insert(cands.end(), {kPacked + 1, kPacked + 2, kPacked + 4});
+    if (prec == RBS_PREC_DF) cands.insert(cands.end(), {kPacked + 1, kPacked + 2});
     for (int nt : cands) {
       launch_pairs(c, kind, prec, nt, items, x, scratch, scratch + 3 * c.N);  // warm (first launch of this variant)
       cudaEventRecord(a, c.stream);

@@ -409,15 +409,28 @@ __global__ void k_body_nodes(int np, int nphi, const double* t, const double* la
 // Node positions as unevaluated float32 sums hi + lo (hi = the position rounded to float32, lo = the
 // rounded remainder), with the particle id in hi.w, and the normals in float32, for the packed
 // float32 pair kernels.
+// For the double-float pair kernels: positions split exactly into three float32 parts
+// (v = hi + mid + lo: each part is the float32 rounding of what the previous ones leave, and 72 bits
+// hold the 53 of a float64), and normals as hi + lo pairs.
 __global__ void k_split_positions(long long N, const double4* x, const double4* nrm, const int* pid, float4* hi,
-                                  float4* lo, float4* n32) {
+                                  float4* lo, float4* n32, float4* x3h, float4* x3m, float4* x3l, float4* nh,
+                                  float4* nl) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= N) return;
   const double4 p = x[t], q = nrm[t];
   const float hx = (float)p.x, hy = (float)p.y, hz = (float)p.z;
-  hi[t] = make_float4(hx, hy, hz, __int_as_float(pid[t]));
+  const float pw = __int_as_float(pid[t]);
+  hi[t] = make_float4(hx, hy, hz, pw);
   lo[t] = make_float4((float)(p.x - (double)hx), (float)(p.y - (double)hy), (float)(p.z - (double)hz), 0.0f);
   n32[t] = make_float4((float)q.x, (float)q.y, (float)q.z, 0.0f);
+  const double rx = p.x - (double)hx, ry = p.y - (double)hy, rz = p.z - (double)hz;
+  const float mx = (float)rx, my = (float)ry, mz = (float)rz;
+  x3h[t] = make_float4(hx, hy, hz, pw);
+  x3m[t] = make_float4(mx, my, mz, 0.0f);
+  x3l[t] = make_float4((float)(rx - (double)mx), (float)(ry - (double)my), (float)(rz - (double)mz), 0.0f);
+  const float ax = (float)q.x, ay = (float)q.y, az = (float)q.z;
+  nh[t] = make_float4(ax, ay, az, 0.0f);
+  nl[t] = make_float4((float)(q.x - (double)ax), (float)(q.y - (double)ay), (float)(q.z - (double)az), 0.0f);
 }
 
 // Per-particle area |Gamma_i| = sum w and inverse moment tensor (Eq. 18), one block per particle.
@@ -922,8 +935,11 @@ Status place_particles(Context& c) {
   RBS_TRY(c.d_xlo.alloc(c.N));
   RBS_TRY(c.d_wmu32.alloc(c.N));
   RBS_TRY(c.d_nrm32.alloc(c.N));
+  for (DevBuf<float4>* b : {&c.d_x3h, &c.d_x3m, &c.d_x3l, &c.d_nrmh, &c.d_nrml, &c.d_wmuh, &c.d_wmul})
+    RBS_TRY(b->alloc(c.N));
   k_split_positions<<<cdiv(c.N, 256), 256, 0, s>>>(c.N, c.d_x.ptr, c.d_nrm.ptr, c.d_pid.ptr, c.d_xhi.ptr, c.d_xlo.ptr,
-                                                   c.d_nrm32.ptr);
+                                                   c.d_nrm32.ptr, c.d_x3h.ptr, c.d_x3m.ptr, c.d_x3l.ptr, c.d_nrmh.ptr,
+                                                   c.d_nrml.ptr);
   RBS_CUDA_TRY(cudaGetLastError());
   return Status::Ok();
 }

@@ -8,6 +8,7 @@
 // float64 on the GPU; the host reads one residual estimate per iteration.
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <mutex>
 
@@ -387,29 +388,18 @@ static Status residual_and_velocity(Context& c, int prec, const double* rho, con
   return Status::Ok();
 }
 
-Status mobility_solve(Context& c, const double* F, const double* T, double tol, double* v, double* om, double* density,
-                      int* iters_out, bool device_io) {
-  auto t0 = std::chrono::steady_clock::now();
+// One mobility solve of the forces and torques in c.d_FT (n x 6, device) in the context's arithmetic:
+// the scattered density in d_vec[2] and the rigid velocities in c.d_vo (n x 6).  `warm` allows the
+// configured warm start.
+static Status solve_core(Context& c, double tol, bool warm, int* iters_out, int* refinements_out, double* rel_out,
+                         bool* converged_out) {
   const long long n3 = 3 * c.N;
-  const int n = c.n;
   const int nbk = vec_blocks(c, n3);
   double* rho = c.d_vec[0].ptr;
   double* b = c.d_vec[1].ptr;
   double* x = c.d_vec[2].ptr;
   double* r = c.d_vec[3].ptr;
   double* d = c.d_vec[7].ptr;
-  // forces and torques to the device (n x 6)
-  if (device_io) {
-    c.stats.launches++;
-    k_pack_ft<<<cdiv(n, 128), 128, 0, c.stream>>>(n, F, T, c.d_FT.ptr);
-  } else {
-    // staged through the velocity buffer: F then T, then packed
-    RBS_CUDA_TRY(cudaMemcpyAsync(c.d_vo.ptr, F, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c.stream));
-    RBS_CUDA_TRY(cudaMemcpyAsync(c.d_vo.ptr + 3 * n, T, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c.stream));
-    c.stats.launches++;
-    k_pack_ft<<<cdiv(n, 128), 128, 0, c.stream>>>(n, c.d_vo.ptr, c.d_vo.ptr + 3 * n, c.d_FT.ptr);
-  }
-  RBS_CUDA_TRY(cudaGetLastError());
   // 1. incident density; right-hand side b = -(1/2 I + K) rho (Eq. 25): float64 for the float64 path;
   //    float32 for the mixed path, where b only seeds the first inner solve (every refinement residual
   //    below is formed from rho in float64-class arithmetic, so b's float32 error does not persist)
@@ -430,10 +420,10 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
   // initial guess: zero, the previous solution, or the learned warm start
   bool have_x0 = false;
   double* x0 = d;
-  if (bnorm > 0.0 && c.opt.warm_start == RBS_WARM_PREVIOUS && c.have_prev && c.d_prev.n == (size_t)n3) {
+  if (warm && bnorm > 0.0 && c.opt.warm_start == RBS_WARM_PREVIOUS && c.have_prev && c.d_prev.n == (size_t)n3) {
     RBS_CUDA_TRY(cudaMemcpyAsync(x0, c.d_prev.ptr, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
     have_x0 = true;
-  } else if (bnorm > 0.0 && c.opt.warm_start == RBS_WARM_LEARNED) {
+  } else if (warm && bnorm > 0.0 && c.opt.warm_start == RBS_WARM_LEARNED) {
     RBS_TRY(warm_guess(c, c.d_FT.ptr, x0));
     have_x0 = true;
   }
@@ -461,9 +451,13 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
     RBS_TRY(apply_blocks(c, kModeL, RBS_PREC_FP64, rho, lrho, nullptr, 1.0));
     double rn = bnorm;
     if (have_x0) {
+      // the first inner solve starts from the warm start's residual in float32 arithmetic, like a
+      // zero start from b; the float64-class pass follows it
       RBS_CUDA_TRY(cudaMemcpyAsync(x, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
-      RBS_TRY(residual_and_velocity(c, hi, rho, lrho, x, sigma, r, u));
-      u_done = true;
+      RBS_TRY(apply_operator(c, RBS_OP_A, RBS_PREC_MIXED, x, w));
+      RBS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+      c.stats.launches++;
+      k_axpby<<<nbk, 256, 0, c.stream>>>(r, -1.0, w, 1.0, n3);
       RBS_TRY(norm2_dev(c, r, n3, sc));
       double rn2;
       RBS_TRY(read_scalar(c, sc, &rn2));
@@ -518,10 +512,6 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
       k_axpby<<<nbk, 256, 0, c.stream>>>(u, 1.0, w, 1.0, n3);
     }
   }
-  // keep the density for a previous-solution warm start and for recording training samples
-  if (c.d_prev.n != (size_t)n3) RBS_TRY(c.d_prev.alloc(n3));
-  RBS_CUDA_TRY(cudaMemcpyAsync(c.d_prev.ptr, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
-  c.have_prev = true;
   // 3. u = S[rho + mu] (already formed by the mixed path's float64-class passes) and the rigid velocities
   if (!u_done) {
     c.stats.launches++;
@@ -529,6 +519,253 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
     RBS_TRY(apply_operator(c, RBS_OP_S, hi, sigma, u));
   }
   RBS_TRY(rigid_velocities(c, u, c.d_vo.ptr));
+  RBS_CUDA_TRY(cudaGetLastError());
+  *iters_out = total_iters;
+  *refinements_out = refinements;
+  *rel_out = rel;
+  *converged_out = converged;
+  return Status::Ok();
+}
+
+// ------------------------------------------------------------------------------------------
+// Contact force algorithm (Section 3.4).  Candidates are near pairs i < j of one suspension whose
+// bounding spheres come within the gap; for each, the closest pair of upsampled nodes decides.
+
+// Closest pair of upsampled nodes of two particles, one block (256 threads) per candidate pair.
+// Squared distances are formed with every product and sum rounded once (no fused multiply-add), and
+// ties go to the first pair in node order (a * n_b + b smallest).
+__global__ void __launch_bounds__(256) k_closest_nodes(const int2* __restrict__ pairs,
+                                                       const long long* __restrict__ up_off,
+                                                       const int* __restrict__ up_index,
+                                                       const double4* __restrict__ up_x, double* __restrict__ d2_out,
+                                                       long long* __restrict__ arg_out) {
+  __shared__ double sd[256];
+  __shared__ long long sk[256];
+  const int2 pr = pairs[blockIdx.x];
+  const int ua = up_index[pr.x], ub = up_index[pr.y];
+  const long long oa = up_off[ua], ob = up_off[ub];
+  const long long na = up_off[ua + 1] - oa, nb = up_off[ub + 1] - ob;
+  double best = INFINITY;
+  long long bk = LLONG_MAX;
+  for (long long k = threadIdx.x; k < na * nb; k += blockDim.x) {
+    const long long a = k / nb, b = k - (k / nb) * nb;
+    const double4 p = up_x[oa + a], q = up_x[ob + b];
+    const double dx = __dsub_rn(p.x, q.x), dy = __dsub_rn(p.y, q.y), dz = __dsub_rn(p.z, q.z);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    if (d2 < best || (d2 == best && k < bk)) {
+      best = d2;
+      bk = k;
+    }
+  }
+  sd[threadIdx.x] = best;
+  sk[threadIdx.x] = bk;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      const double o = sd[threadIdx.x + h];
+      const long long ok = sk[threadIdx.x + h];
+      if (o < sd[threadIdx.x] || (o == sd[threadIdx.x] && ok < sk[threadIdx.x])) {
+        sd[threadIdx.x] = o;
+        sk[threadIdx.x] = ok;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    d2_out[blockIdx.x] = sd[0];
+    arg_out[blockIdx.x] = sk[0];
+  }
+}
+
+// Contacts of the current configuration into c.contacts (ascending (i, j)).
+static Status find_contacts(Context& c) {
+  c.contacts.clear();
+  std::vector<int2> cand;
+  for (const int2& pr : c.near_pairs) {
+    if (pr.x >= pr.y) continue;
+    const double dx = c.centres[3 * pr.x] - c.centres[3 * pr.y], dy = c.centres[3 * pr.x + 1] - c.centres[3 * pr.y + 1],
+                 dz = c.centres[3 * pr.x + 2] - c.centres[3 * pr.y + 2];
+    const double R = c.shapes[c.shape_of[pr.x]].radius + c.shapes[c.shape_of[pr.y]].radius;
+    if (std::sqrt(dx * dx + dy * dy + dz * dz) < R + c.opt.contact_gap) cand.push_back(pr);
+  }
+  if (cand.empty()) return Status::Ok();
+  std::sort(cand.begin(), cand.end(), [](int2 a, int2 b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });
+  DevBuf<int2> d_cand;
+  DevBuf<double> d_d2;
+  DevBuf<long long> d_arg;
+  RBS_TRY(d_cand.alloc(cand.size()));
+  RBS_TRY(d_d2.alloc(cand.size()));
+  RBS_TRY(d_arg.alloc(cand.size()));
+  RBS_CUDA_TRY(cudaMemcpyAsync(d_cand.ptr, cand.data(), sizeof(int2) * cand.size(), cudaMemcpyHostToDevice, c.stream));
+  c.stats.launches++;
+  k_closest_nodes<<<(unsigned)cand.size(), 256, 0, c.stream>>>(d_cand.ptr, c.d_up_off.ptr, c.d_up_index.ptr,
+                                                              c.d_up_x.ptr, d_d2.ptr, d_arg.ptr);
+  RBS_CUDA_TRY(cudaGetLastError());
+  std::vector<double> d2(cand.size());
+  std::vector<long long> arg(cand.size());
+  RBS_CUDA_TRY(cudaMemcpyAsync(d2.data(), d_d2.ptr, sizeof(double) * d2.size(), cudaMemcpyDeviceToHost, c.stream));
+  RBS_CUDA_TRY(cudaMemcpyAsync(arg.data(), d_arg.ptr, sizeof(long long) * arg.size(), cudaMemcpyDeviceToHost, c.stream));
+  RBS_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  for (size_t q = 0; q < cand.size(); ++q) {
+    if (!(std::sqrt(d2[q]) < c.opt.contact_gap)) continue;
+    const int ua = c.up_index[cand[q].x], ub = c.up_index[cand[q].y];
+    const long long nb = c.up_offset[ub + 1] - c.up_offset[ub];
+    const long long a = arg[q] / nb, b = arg[q] % nb;
+    double4 pa, pb;
+    RBS_CUDA_TRY(cudaMemcpy(&pa, c.d_up_x.ptr + c.up_offset[ua] + a, sizeof(double4), cudaMemcpyDeviceToHost));
+    RBS_CUDA_TRY(cudaMemcpy(&pb, c.d_up_x.ptr + c.up_offset[ub] + b, sizeof(double4), cudaMemcpyDeviceToHost));
+    Context::Contact ct;
+    ct.i = cand[q].x;
+    ct.j = cand[q].y;
+    ct.x[0] = 0.5 * (pa.x + pb.x);
+    ct.x[1] = 0.5 * (pa.y + pb.y);
+    ct.x[2] = 0.5 * (pa.z + pb.z);
+    ct.f[0] = ct.f[1] = ct.f[2] = 0.0;
+    c.contacts.push_back(ct);
+  }
+  return Status::Ok();
+}
+
+// Column 3 k + a of C (n x 6 forces and torques of a unit force along axis a at contact k) added,
+// times s, into FT.
+static void add_contact_column(const Context& c, int k, int a, double s, std::vector<double>& FT) {
+  const Context::Contact& ct = c.contacts[k];
+  double f[3] = {0.0, 0.0, 0.0};
+  f[a] = s;
+  for (int side = 0; side < 2; ++side) {
+    const int p = side == 0 ? ct.i : ct.j;
+    const double sg = side == 0 ? 1.0 : -1.0;
+    const double r[3] = {ct.x[0] - c.centres[3 * p], ct.x[1] - c.centres[3 * p + 1], ct.x[2] - c.centres[3 * p + 2]};
+    FT[6 * p + 0] += sg * f[0];
+    FT[6 * p + 1] += sg * f[1];
+    FT[6 * p + 2] += sg * f[2];
+    FT[6 * p + 3] += sg * (r[1] * f[2] - r[2] * f[1]);
+    FT[6 * p + 4] += sg * (r[2] * f[0] - r[0] * f[2]);
+    FT[6 * p + 5] += sg * (r[0] * f[1] - r[1] * f[0]);
+  }
+}
+
+// Velocity difference at contact k from the rigid velocities V (n x 6): v_i + w_i x r_i - v_j - w_j x r_j.
+static void contact_slip(const Context& c, int k, const std::vector<double>& V, double out[3]) {
+  const Context::Contact& ct = c.contacts[k];
+  for (int q = 0; q < 3; ++q) out[q] = 0.0;
+  for (int side = 0; side < 2; ++side) {
+    const int p = side == 0 ? ct.i : ct.j;
+    const double sg = side == 0 ? 1.0 : -1.0;
+    const double r[3] = {ct.x[0] - c.centres[3 * p], ct.x[1] - c.centres[3 * p + 1], ct.x[2] - c.centres[3 * p + 2]};
+    const double* v = &V[6 * p];
+    out[0] += sg * (v[0] + v[4] * r[2] - v[5] * r[1]);
+    out[1] += sg * (v[1] + v[5] * r[0] - v[3] * r[2]);
+    out[2] += sg * (v[2] + v[3] * r[1] - v[4] * r[0]);
+  }
+}
+
+// Dense solve of A x = y (m x m, row-major) by Gaussian elimination with partial pivoting.
+static Status dense_solve(std::vector<double> A, std::vector<double>& y, int m) {
+  for (int k = 0; k < m; ++k) {
+    int piv = k;
+    for (int r = k + 1; r < m; ++r)
+      if (std::fabs(A[(size_t)r * m + k]) > std::fabs(A[(size_t)piv * m + k])) piv = r;
+    if (!(std::fabs(A[(size_t)piv * m + k]) > 0.0)) return Status::Err(RBS_ENOTCONV, "contact system is singular");
+    if (piv != k) {
+      for (int q = 0; q < m; ++q) std::swap(A[(size_t)k * m + q], A[(size_t)piv * m + q]);
+      std::swap(y[k], y[piv]);
+    }
+    for (int r = k + 1; r < m; ++r) {
+      const double f = A[(size_t)r * m + k] / A[(size_t)k * m + k];
+      for (int q = k; q < m; ++q) A[(size_t)r * m + q] -= f * A[(size_t)k * m + q];
+      y[r] -= f * y[k];
+    }
+  }
+  for (int k = m - 1; k >= 0; --k) {
+    double acc = y[k];
+    for (int q = k + 1; q < m; ++q) acc -= A[(size_t)k * m + q] * y[q];
+    y[k] = acc / A[(size_t)k * m + k];
+  }
+  return Status::Ok();
+}
+
+// Contact correction of the solve just made (its forces in c.d_FT, velocities in c.d_vo): the
+// columns M C from 3 n_c solves, the contact forces from (D M C) F_c = -D V_0, and a final solve with
+// the forces and torques F + C F_c, which gives the corrected velocities and density together.
+static Status contact_correction(Context& c, double tol, int* iters) {
+  RBS_TRY(find_contacts(c));
+  c.stats.n_contacts = (int)c.contacts.size();
+  const int nc = (int)c.contacts.size();
+  if (nc == 0) return Status::Ok();
+  const int n = c.n, m = 3 * nc;
+  std::vector<double> V0(6 * (size_t)n), FT0(6 * (size_t)n);
+  RBS_CUDA_TRY(cudaMemcpyAsync(V0.data(), c.d_vo.ptr, sizeof(double) * V0.size(), cudaMemcpyDeviceToHost, c.stream));
+  RBS_CUDA_TRY(cudaMemcpyAsync(FT0.data(), c.d_FT.ptr, sizeof(double) * FT0.size(), cudaMemcpyDeviceToHost, c.stream));
+  RBS_CUDA_TRY(cudaStreamSynchronize(c.stream));
+  std::vector<double> DMC((size_t)m * m), rhs(m), Vk(6 * (size_t)n), FT(6 * (size_t)n);
+  for (int col = 0; col < m; ++col) {
+    std::fill(FT.begin(), FT.end(), 0.0);
+    add_contact_column(c, col / 3, col % 3, 1.0, FT);
+    RBS_CUDA_TRY(cudaMemcpyAsync(c.d_FT.ptr, FT.data(), sizeof(double) * FT.size(), cudaMemcpyHostToDevice, c.stream));
+    int its = 0, refs = 0;
+    double rel = 0.0;
+    bool conv = false;
+    RBS_TRY(solve_core(c, tol, false, &its, &refs, &rel, &conv));
+    if (!conv) return Status::Err(RBS_ENOTCONV, "a contact column solve did not converge");
+    *iters += its;
+    RBS_CUDA_TRY(cudaMemcpyAsync(Vk.data(), c.d_vo.ptr, sizeof(double) * Vk.size(), cudaMemcpyDeviceToHost, c.stream));
+    RBS_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    for (int k = 0; k < nc; ++k) {
+      double s[3];
+      contact_slip(c, k, Vk, s);
+      for (int q = 0; q < 3; ++q) DMC[(size_t)(3 * k + q) * m + col] = s[q];
+    }
+  }
+  for (int k = 0; k < nc; ++k) {
+    double s[3];
+    contact_slip(c, k, V0, s);
+    for (int q = 0; q < 3; ++q) rhs[3 * k + q] = -s[q];
+  }
+  RBS_TRY(dense_solve(DMC, rhs, m));
+  FT = FT0;
+  for (int col = 0; col < m; ++col) add_contact_column(c, col / 3, col % 3, rhs[col], FT);
+  for (int k = 0; k < nc; ++k)
+    for (int q = 0; q < 3; ++q) c.contacts[k].f[q] = rhs[3 * k + q];
+  RBS_CUDA_TRY(cudaMemcpyAsync(c.d_FT.ptr, FT.data(), sizeof(double) * FT.size(), cudaMemcpyHostToDevice, c.stream));
+  int its = 0, refs = 0;
+  double rel = 0.0;
+  bool conv = false;
+  RBS_TRY(solve_core(c, tol, false, &its, &refs, &rel, &conv));
+  if (!conv) return Status::Err(RBS_ENOTCONV, "the contact-corrected solve did not converge");
+  *iters += its;
+  return Status::Ok();
+}
+
+Status mobility_solve(Context& c, const double* F, const double* T, double tol, double* v, double* om, double* density,
+                      int* iters_out, bool device_io) {
+  auto t0 = std::chrono::steady_clock::now();
+  const long long n3 = 3 * c.N;
+  const int n = c.n;
+  double* x = c.d_vec[2].ptr;
+  // forces and torques to the device (n x 6)
+  if (device_io) {
+    c.stats.launches++;
+    k_pack_ft<<<cdiv(n, 128), 128, 0, c.stream>>>(n, F, T, c.d_FT.ptr);
+  } else {
+    // staged through the velocity buffer: F then T, then packed
+    RBS_CUDA_TRY(cudaMemcpyAsync(c.d_vo.ptr, F, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c.stream));
+    RBS_CUDA_TRY(cudaMemcpyAsync(c.d_vo.ptr + 3 * n, T, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c.stream));
+    c.stats.launches++;
+    k_pack_ft<<<cdiv(n, 128), 128, 0, c.stream>>>(n, c.d_vo.ptr, c.d_vo.ptr + 3 * n, c.d_FT.ptr);
+  }
+  RBS_CUDA_TRY(cudaGetLastError());
+  int total_iters = 0, refinements = 0;
+  double rel = 0.0;
+  bool converged = false;
+  RBS_TRY(solve_core(c, tol, true, &total_iters, &refinements, &rel, &converged));
+  c.stats.n_contacts = 0;
+  c.contacts.clear();
+  if (converged && c.opt.contact_gap > 0.0) RBS_TRY(contact_correction(c, tol, &total_iters));
+  // keep the density for a previous-solution warm start and for recording training samples
+  if (c.d_prev.n != (size_t)n3) RBS_TRY(c.d_prev.alloc(n3));
+  RBS_CUDA_TRY(cudaMemcpyAsync(c.d_prev.ptr, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+  c.have_prev = true;
   if (device_io) {
     c.stats.launches++;
     k_unpack_vo<<<cdiv(n, 128), 128, 0, c.stream>>>(n, c.d_vo.ptr, v, om);

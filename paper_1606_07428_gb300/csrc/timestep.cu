@@ -1,8 +1,8 @@
-// Rigid-body time stepping (Section 3.3, Eqs. 40 and 43; Algorithm 1 without contact): explicit
-// Runge-Kutta steps of dc_i/dt = v_i and dq_i/dt = 1/2 (0, omega_i) q_i (Hamilton product) with the
-// forces and torques held fixed; each stage is one mobility solve at the stage configuration, whose
-// self blocks are the body-frame blocks rotated by R(q) (Eq. 38).  Quaternions are renormalised
-// after each step.
+// Rigid-body time stepping (Section 3.3, Eqs. 40 and 43; Algorithm 1): explicit Runge-Kutta steps of
+// dc_i/dt = v_i and dq_i/dt = 1/2 (0, omega_i) q_i (Hamilton product) with the forces and torques held
+// fixed; each stage is one mobility solve at the stage configuration, whose self blocks are the
+// body-frame blocks rotated by R(q) (Eq. 38), followed by the contact correction of Section 3.4 when
+// rbs_options.contact_gap > 0.  Quaternions are renormalised after each step.
 #include <vector>
 
 #include "common.cuh"

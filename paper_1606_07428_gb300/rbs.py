@@ -44,7 +44,7 @@ EXPORTS = [
     "rbs_rigid_velocities", "rbs_apply_operator", "rbs_apply_operator_device", "rbs_get_stats",
     "rbs_reset_stats", "rbs_last_error", "rbs_rigid_velocities_noalloc", "rbs_advance", "rbs_get_state",
     "rbs_warmstart_record", "rbs_warmstart_train", "rbs_warmstart_weights", "rbs_warmstart_features",
-    "rbs_warmstart_targets", "rbs_warmstart_mlp", "rbs_set_geometry_sh",
+    "rbs_warmstart_targets", "rbs_warmstart_mlp", "rbs_set_geometry_sh", "rbs_get_contacts",
 ]
 
 RBS_MAX_SHAPE_DEGREE = 24
@@ -77,6 +77,7 @@ class rbs_options(ctypes.Structure):
         ("pair_variant", ctypes.c_int),
         ("warm_start", ctypes.c_int),
         ("warm_record", ctypes.c_int),
+        ("contact_gap", ctypes.c_double),
     ]
 
 
@@ -110,6 +111,7 @@ class rbs_stats(ctypes.Structure):
         ("kernel_ms", ctypes.c_double * RBS_KC_COUNT),
         ("kernel_count", ctypes.c_longlong * RBS_KC_COUNT),
         ("kernel_units", ctypes.c_double * RBS_KC_COUNT),
+        ("n_contacts", ctypes.c_int),
         ("pair_variant", ctypes.c_int * 5),
     ]
 
@@ -140,6 +142,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rbs_destroy": (None, [P]),
         "rbs_set_geometry": (I, [P, I, P, P, P, P, P, P]),
         "rbs_set_geometry_sh": (I, [P, I, I, P, P, P, P, P, P, P, P]),
+        "rbs_get_contacts": (I, [P, I, P, P, P]),
         "rbs_total_nodes": (ctypes.c_longlong, [P]),
         "rbs_get_surface": (I, [P, P, P, P]),
         "rbs_mobility_solve": (I, [P, P, P, D, P, P, P, P]),
@@ -244,6 +247,18 @@ def rbs_set_geometry_sh(ctx, shapes, shape_of, p, nphi, centres, quats, suspensi
     sid = None if suspension_id is None else _i32(suspension_id)
     _check(ctx, load().rbs_set_geometry_sh(ctx, n, len(shapes), _ptr(pg), _ptr(coef), _ptr(shape_of), _ptr(p),
                                            _ptr(nphi), _ptr(centres), _ptr(quats), _ptr(sid)))
+
+
+def rbs_get_contacts(ctx):
+    """The last solve's contacts: (pairs (n_c, 2) int32, points (n_c, 3), forces on the first particle
+    (n_c, 3))."""
+    n = _check(ctx, load().rbs_get_contacts(ctx, 0, None, None, None), allow=range(0, 1 << 30))
+    pairs = np.zeros((n, 2), np.int32)
+    points = np.zeros((n, 3))
+    forces = np.zeros((n, 3))
+    if n:
+        _check(ctx, load().rbs_get_contacts(ctx, n, _ptr(pairs), _ptr(points), _ptr(forces)), allow=range(0, 1 << 30))
+    return pairs, points, forces
 
 
 def rbs_total_nodes(ctx) -> int:
