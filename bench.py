@@ -50,7 +50,7 @@ FP64_OPS_PER_PAIR = {"traction": 27.0, "stokeslet": 25.0}
 # by node count to the benchmarked case: the pair kernels read their inputs once
 # (sources are re-read from L2), so traffic grows with N, not with the N^2 pairs
 NCU_TRAFFIC = {"pair_traction_df": (6.404864e6, 57600), "pair_traction_f32": (4.872192e6, 57600),
-               "pair_both_df": (7.357184e6, 57600)}
+               "pair_both_df": (8.511744e6, 57600)}
 # float32-pipe operations per pair of the double-float kernels, counted from the source of
 # pair_tile_df (separation 24, r^2 28, reciprocal square root 8, r . density 28, powers 8, then the
 # traction tail 76, the Stokeslet tail 76, or both tails sharing 1/r^5 and r . n: 152)
