@@ -101,6 +101,10 @@ typedef struct {
                           midpoint of that closest node pair; contact forces that make the two
                           rigid velocities agree there are found from 3 n_c extra solves, and the
                           velocities and density returned include them */
+  double magnetic_field[3]; /* uniform applied field H0 for rbs_advance (default 0) */
+  double mu_ratio;     /* permeability of the particles over that of the fluid, mu / mu0 (default 1);
+                          with mu_ratio != 1 and a non-zero field, every rbs_advance stage adds the
+                          magnetic forces and torques of rbs_magnetic_forces to F and T */
 } rbs_options;
 
 #define RBS_WARM_ZERO 0
@@ -201,6 +205,24 @@ int rbs_set_geometry_sh(rbs_ctx* ctx, int n, int nshape, const int* shape_pg, co
  * max; only the first max are written) or a negative status.
  */
 int rbs_get_contacts(rbs_ctx* ctx, int max, int* pairs, double* points, double* forces);
+
+/*
+ * Magnetostatic coupling (Section 4.1.3): the net magnetic force and torque on every particle of the
+ * current geometry in the uniform field H0 (3 doubles) for particles of permeability mu_ratio times
+ * the fluid's.  The potential is phi = -H0 . x + S^L[q] with (1/2 I + eta K^L) q = eta H0 . n,
+ * eta = (mu_ratio - 1) / (mu_ratio + 1), solved by float64 GMRES to relative tolerance tol with the
+ * library's smooth, near and singular rules (scalar kernels); the fluid-side field
+ * H = -grad_s phi + (H0 . n + q/2 - K^L[q]) n gives the Maxwell traction (H . n) H - |H|^2 n / 2 (the
+ * fluid's permeability mu0 taken as 1), integrated over each surface.  F and T: n x 3 host outputs;
+ * q: total_nodes host output or NULL; iterations may be NULL.  The scalar self blocks (every row, per
+ * distinct shape) are built on the first call for a geometry.
+ */
+int rbs_magnetic_forces(rbs_ctx* ctx, const double* H0, double mu_ratio, double tol, double* F, double* T,
+                        double* q, int* iterations);
+
+/* The Laplace operators of the magnetostatic coupling on scalar node fields (host arrays of
+ * total_nodes): kind 0 gives y = K^L x, kind 1 gives y = S^L x (Section 4.1.3). */
+int rbs_apply_laplace(rbs_ctx* ctx, int kind, const double* x, double* y);
 
 /* Number of surface nodes of the current geometry (3 * that many unknowns). */
 long long rbs_total_nodes(const rbs_ctx* ctx);

@@ -102,6 +102,8 @@ void rbs_default_options(rbs_options* o) {
   o->pair_variant = 0;
   o->warm_record = 0;
   o->contact_gap = 0.0;
+  o->magnetic_field[0] = o->magnetic_field[1] = o->magnetic_field[2] = 0.0;
+  o->mu_ratio = 1.0;
 }
 
 int rbs_create(const rbs_options* opt, rbs_ctx** out) {
@@ -119,7 +121,8 @@ int rbs_create(const rbs_options* opt, rbs_ctx** out) {
       (o.refine_precision != RBS_PREC_FP64 && o.refine_precision != RBS_PREC_DF) || o.warm_start < 0 ||
       (o.pair_variant != 0 && o.pair_variant != 1 && o.pair_variant != 2 && o.pair_variant != 4 &&
        o.pair_variant != 9 && o.pair_variant != 10 && o.pair_variant != 12) ||
-      o.warm_start > 2 || !(o.contact_gap >= 0.0))
+      o.warm_start > 2 || !(o.contact_gap >= 0.0) || !(o.mu_ratio > 0.0) ||
+      !std::isfinite(o.magnetic_field[0]) || !std::isfinite(o.magnetic_field[1]) || !std::isfinite(o.magnetic_field[2]))
     return RBS_EINVAL;
   rbs_ctx* h = new rbs_ctx();
   Context& c = h->c;
@@ -490,6 +493,54 @@ int rbs_reset_stats(rbs_ctx* h) {
     c.stats.kernel_units[k] = 0.0;
   }
   return RBS_OK;
+}
+
+int rbs_magnetic_forces(rbs_ctx* h, const double* H0, double mu_ratio, double tol, double* F, double* T, double* q,
+                        int* iterations) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!H0 || !F || !T) return finish(c, Status::Err(RBS_EINVAL, "magnetic_forces: null array"));
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  if (!finite_all(H0, 3) || !(mu_ratio > 0.0) || !(tol > 0.0 && tol < 1.0))
+    return finish(c, Status::Err(RBS_EINVAL, "magnetic_forces: bad field, permeability ratio or tolerance"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  s = c.mag.d_FT.alloc(6 * (size_t)c.n);
+  int its = 0;
+  if (s.ok()) s = rbs::magnetic_forces(c, H0, mu_ratio, tol, c.mag.d_FT.ptr, q, &its);
+  if (s.ok()) {
+    std::vector<double> ft(6 * (size_t)c.n);
+    cudaError_t e = cudaMemcpyAsync(ft.data(), c.mag.d_FT.ptr, sizeof(double) * ft.size(), cudaMemcpyDeviceToHost,
+                                    c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) s = Status::Err(RBS_ECUDA, std::string("magnetic_forces: ") + cudaGetErrorString(e));
+    for (int i = 0; s.ok() && i < c.n; ++i)
+      for (int k = 0; k < 3; ++k) {
+        F[3 * i + k] = ft[6 * i + k];
+        T[3 * i + k] = ft[6 * i + 3 + k];
+      }
+  }
+  if (iterations) *iterations = its;
+  return finish(c, s);
+}
+
+int rbs_apply_laplace(rbs_ctx* h, int kind, const double* x, double* y) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!x || !y || (kind != 0 && kind != 1)) return finish(c, Status::Err(RBS_EINVAL, "apply_laplace: bad arguments"));
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  Status s = enter(c);
+  if (!s.ok()) return finish(c, s);
+  rbs::DevBuf<double> dx, dy;
+  s = dx.alloc(c.N);
+  if (s.ok()) s = dy.alloc(c.N);
+  cudaError_t e = cudaSuccess;
+  if (s.ok()) e = cudaMemcpyAsync(dx.ptr, x, sizeof(double) * c.N, cudaMemcpyHostToDevice, c.stream);
+  if (s.ok() && e == cudaSuccess) s = rbs::laplace_operator(c, kind, dx.ptr, dy.ptr);
+  if (s.ok() && e == cudaSuccess) e = cudaMemcpyAsync(y, dy.ptr, sizeof(double) * c.N, cudaMemcpyDeviceToHost, c.stream);
+  if (s.ok() && e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (s.ok() && e != cudaSuccess) s = Status::Err(RBS_ECUDA, std::string("apply_laplace: ") + cudaGetErrorString(e));
+  return finish(c, s);
 }
 
 int rbs_get_contacts(rbs_ctx* h, int max, int* pairs, double* points, double* forces) {

@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <cstdio>
 #include <string>
@@ -118,6 +119,25 @@ struct Shape {
   size_t block_off = 0;  // offset (in elements) of its rows x 3np blocks in the block arrays
 };
 
+// Magnetostatic coupling state (magnetic.cu): scalar self blocks, the preconditioner for the last
+// eta, differentiation matrices per grid, and work vectors; built on first use per geometry.
+struct MagState {
+  bool built = false;
+  double eta = 0.0;
+  std::vector<long long> block_off;
+  DevBuf<long long> d_block_off;
+  DevBuf<double> d_blockK, d_blockS, d_precond;
+  std::vector<DevBuf<double>*> d_Dt, d_Dp;
+  DevBuf<const double*> d_Dt_ptr, d_Dp_ptr, d_upU;
+  DevBuf<int> d_grid_of;
+  DevBuf<double> d_q, d_b, d_phi, d_hn, d_f, d_qup, d_FT;
+  void release();
+  MagState() = default;
+  ~MagState();
+  MagState(const MagState&) = delete;
+  MagState& operator=(const MagState&) = delete;
+};
+
 struct Context {
   rbs_options opt{};
   cudaStream_t stream = nullptr;
@@ -219,6 +239,8 @@ struct Context {
   };
   std::vector<Contact> contacts;
 
+  MagState mag;  // magnetostatic coupling (magnetic.cu)
+
   rbs_stats stats{};
   WarmState* warm = nullptr;       // learned warm start (warmstart.cu)
   DevBuf<double> d_prev;           // last solved density (previous-solution warm start)
@@ -240,6 +262,25 @@ struct Context {
   Context(const Context&) = delete;
   Context& operator=(const Context&) = delete;
 };
+
+// A linear operator for gmres_op on device vectors of length n: w = A P v (z = P v), y = A x, and the
+// right preconditioner z = P v (empty: none; aux is scratch of length n).
+struct LinOp {
+  long long n = 0;
+  std::function<Status(const double* v, double* w, double* z)> apply_AP;
+  std::function<Status(const double* x, double* y)> apply_A;
+  std::function<Status(const double* v, double* z, double* aux)> apply_P;
+};
+Status gmres_op(Context& c, const LinOp& op, const double* b, double* x, bool x_zero, double tol_abs, int max_iters,
+                int* iters, double* res_out, bool* converged);
+
+// ---- magnetostatic coupling (magnetic.cu)
+// Net magnetic force and torque (n x 6 interleaved, device) of the current geometry in the uniform
+// field H0 with permeability ratio mu / mu0; q_out (host, total_nodes, may be NULL) receives q.
+Status magnetic_forces(Context& c, const double H0[3], double mu_ratio, double tol, double* FT_dev, double* q_out,
+                       int* iters);
+// y = K^L x (kind 0) or S^L x (kind 1), scalar fields on the nodes (device).
+Status laplace_operator(Context& c, int kind, const double* x, double* y);
 
 // ---- setup (setup.cu)
 Status build_geometry(Context& c);

@@ -238,11 +238,12 @@ static Status gmres_operator(Context& c, int prec, const double* v, double* w, d
   return apply_operator(c, RBS_OP_A, prec, v, w);
 }
 
-// Restarted, right-preconditioned GMRES for A x = b (A in arithmetic `prec`).  x is the initial guess
-// (x_zero: treat it as zero without reading it).  Stops when the residual estimate is <= tol_abs.
-static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zero, double tol_abs, int max_iters,
-                    int* iters, double* res_out, bool* converged) {
-  const long long n3 = 3 * c.N;
+// Restarted, right-preconditioned GMRES for A x = b with the operator `op` (vectors of length op.n).
+// x is the initial guess (x_zero: treat it as zero without reading it).  Stops when the residual
+// estimate is <= tol_abs.
+Status gmres_op(Context& c, const LinOp& op, const double* b, double* x, bool x_zero, double tol_abs, int max_iters,
+                int* iters, double* res_out, bool* converged) {
+  const long long n3 = op.n;
   const int m = c.opt.restart;
   const int ld = m + 1;
   double* H = c.d_H.ptr;
@@ -267,7 +268,7 @@ static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zer
     if (first && x_zero) {
       RBS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
     } else {
-      RBS_TRY(apply_operator(c, RBS_OP_A, prec, x, r));
+      RBS_TRY(op.apply_A(x, r));
       c.stats.launches++;
       k_axpby<<<nbk, 256, 0, c.stream>>>(r, 1.0, b, -1.0, n3);
     }
@@ -289,7 +290,7 @@ static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zer
     int kdone = 0;
     for (int k = 0; k < m && *iters < max_iters; ++k) {
       double* vk = V + (size_t)k * n3;
-      RBS_TRY(gmres_operator(c, prec, vk, w, z));
+      RBS_TRY(op.apply_AP(vk, w, z));
       double* hcol = H + (size_t)k * ld;
       for (int pass = 0; pass < 2; ++pass) {
         RBS_TRY(multidot(c, V, n3, k + 1, w, n3, hvec, hcol));
@@ -310,10 +311,10 @@ static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zer
     // x += P (V y)
     c.stats.launches++;
     k_trisolve<<<1, 1, 0, c.stream>>>(H, ld, kdone, g, y);
-    if (c.opt.preconditioner) {
+    if (op.apply_P) {
       c.stats.launches++;
       k_combine<<<nbk, 256, 0, c.stream>>>(w, 0.0, V, n3, kdone, y, 1.0, n3);
-      RBS_TRY(apply_blocks(c, kModePrecond, prec, w, z, r, 1.0));
+      RBS_TRY(op.apply_P(w, z, r));
       c.stats.launches++;
       k_axpby<<<nbk, 256, 0, c.stream>>>(x, 1.0, z, 1.0, n3);
     } else {
@@ -329,6 +330,21 @@ static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zer
   }
   *res_out = res;
   return Status::Ok();
+}
+
+// The mobility system's operator for gmres_op: A = 1/2 I + K + L on 3N-vectors in arithmetic prec,
+// right-preconditioned by the block-diagonal inverse when the context has one.
+static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zero, double tol_abs, int max_iters,
+                    int* iters, double* res_out, bool* converged) {
+  LinOp op;
+  op.n = 3 * c.N;
+  op.apply_AP = [&c, prec](const double* v, double* w, double* z) { return gmres_operator(c, prec, v, w, z); };
+  op.apply_A = [&c, prec](const double* xx, double* y) { return apply_operator(c, RBS_OP_A, prec, xx, y); };
+  if (c.opt.preconditioner)
+    op.apply_P = [&c, prec](const double* v, double* z, double* aux) {
+      return apply_blocks(c, kModePrecond, prec, v, z, aux, 1.0);
+    };
+  return gmres_op(c, op, b, x, x_zero, tol_abs, max_iters, iters, res_out, converged);
 }
 
 Status incident_density(Context& c, const double* FT_dev, double* rho) {

@@ -2,7 +2,9 @@
 // dc_i/dt = v_i and dq_i/dt = 1/2 (0, omega_i) q_i (Hamilton product) with the forces and torques held
 // fixed; each stage is one mobility solve at the stage configuration, whose self blocks are the
 // body-frame blocks rotated by R(q) (Eq. 38), followed by the contact correction of Section 3.4 when
-// rbs_options.contact_gap > 0.  Quaternions are renormalised after each step.
+// rbs_options.contact_gap > 0; with a magnetic field and mu_ratio != 1 in the options, each stage first
+// adds the particles' magnetic forces and torques (Section 4.1.3).  Quaternions are renormalised after
+// each step.
 #include <vector>
 
 #include "common.cuh"
@@ -82,6 +84,9 @@ Status advance(Context& c, const double* F, const double* T, double dt, int step
   }
   RBS_CUDA_TRY(cudaMemcpyAsync(state0.ptr, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s));
   std::vector<double> vtmp(3 * (size_t)n), otmp(3 * (size_t)n), cen(3 * (size_t)n), qu(4 * (size_t)n);
+  const bool magnetic = c.opt.mu_ratio != 1.0 && (c.opt.magnetic_field[0] != 0.0 || c.opt.magnetic_field[1] != 0.0 ||
+                                                  c.opt.magnetic_field[2] != 0.0);
+  std::vector<double> Fm(magnetic ? 3 * (size_t)n : 0), Tm(magnetic ? 3 * (size_t)n : 0);
   int total = 0;
   const int nb = cdiv(n, 128);
   for (int step = 0; step < steps; ++step) {
@@ -99,14 +104,32 @@ Status advance(Context& c, const double* F, const double* T, double dt, int step
       }
       RBS_TRY(update_configuration(c, cen.data(), qu.data()));
       int its = 0;
-      RBS_TRY(mobility_solve(c, F, T, tol, vtmp.data(), otmp.data(), nullptr, &its, false));
+      const double* Fs = F;
+      const double* Ts = T;
+      if (magnetic) {
+        // the magnetic force and torque of the stage configuration (Section 4.1.3) join the applied ones
+        int mits = 0;
+        RBS_TRY(c.mag.d_FT.alloc(6 * (size_t)n));
+        RBS_TRY(magnetic_forces(c, c.opt.magnetic_field, c.opt.mu_ratio, tol, c.mag.d_FT.ptr, nullptr, &mits));
+        std::vector<double> ftm(6 * (size_t)n);
+        RBS_CUDA_TRY(cudaMemcpyAsync(ftm.data(), c.mag.d_FT.ptr, sizeof(double) * ftm.size(), cudaMemcpyDeviceToHost, s));
+        RBS_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int i = 0; i < n; ++i)
+          for (int q = 0; q < 3; ++q) {
+            Fm[3 * i + q] = F[3 * i + q] + ftm[6 * i + q];
+            Tm[3 * i + q] = T[3 * i + q] + ftm[6 * i + 3 + q];
+          }
+        Fs = Fm.data();
+        Ts = Tm.data();
+      }
+      RBS_TRY(mobility_solve(c, Fs, Ts, tol, vtmp.data(), otmp.data(), nullptr, &its, false));
       total += its;
       if (c.opt.warm_record) {
         std::vector<double> ft(6 * (size_t)n);
         for (int i = 0; i < n; ++i)
           for (int q = 0; q < 3; ++q) {
-            ft[6 * i + q] = F[3 * i + q];
-            ft[6 * i + 3 + q] = T[3 * i + q];
+            ft[6 * i + q] = Fs[3 * i + q];
+            ft[6 * i + 3 + q] = Ts[3 * i + q];
           }
         DevBuf<double> dft;
         RBS_TRY(dft.alloc(ft.size()));

@@ -45,6 +45,7 @@ EXPORTS = [
     "rbs_reset_stats", "rbs_last_error", "rbs_rigid_velocities_noalloc", "rbs_advance", "rbs_get_state",
     "rbs_warmstart_record", "rbs_warmstart_train", "rbs_warmstart_weights", "rbs_warmstart_features",
     "rbs_warmstart_targets", "rbs_warmstart_mlp", "rbs_set_geometry_sh", "rbs_get_contacts",
+    "rbs_magnetic_forces", "rbs_apply_laplace",
 ]
 
 RBS_MAX_SHAPE_DEGREE = 24
@@ -78,6 +79,8 @@ class rbs_options(ctypes.Structure):
         ("warm_start", ctypes.c_int),
         ("warm_record", ctypes.c_int),
         ("contact_gap", ctypes.c_double),
+        ("magnetic_field", ctypes.c_double * 3),
+        ("mu_ratio", ctypes.c_double),
     ]
 
 
@@ -143,6 +146,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rbs_set_geometry": (I, [P, I, P, P, P, P, P, P]),
         "rbs_set_geometry_sh": (I, [P, I, I, P, P, P, P, P, P, P, P]),
         "rbs_get_contacts": (I, [P, I, P, P, P]),
+        "rbs_magnetic_forces": (I, [P, P, D, D, P, P, P, P]),
+        "rbs_apply_laplace": (I, [P, I, P, P]),
         "rbs_total_nodes": (ctypes.c_longlong, [P]),
         "rbs_get_surface": (I, [P, P, P, P]),
         "rbs_mobility_solve": (I, [P, P, P, D, P, P, P, P]),
@@ -259,6 +264,26 @@ def rbs_get_contacts(ctx):
     if n:
         _check(ctx, load().rbs_get_contacts(ctx, n, _ptr(pairs), _ptr(points), _ptr(forces)), allow=range(0, 1 << 30))
     return pairs, points, forces
+
+
+def rbs_magnetic_forces(ctx, H0, mu_ratio, tol, n, total_nodes=None):
+    """Magnetic force and torque (n x 3 each) per particle in the uniform field H0; with total_nodes
+    also the single-layer density q."""
+    H0 = _f64(H0, (3,))
+    F = np.zeros((n, 3))
+    T = np.zeros((n, 3))
+    q = None if total_nodes is None else np.zeros(total_nodes)
+    its = ctypes.c_int(0)
+    _check(ctx, load().rbs_magnetic_forces(ctx, _ptr(H0), float(mu_ratio), float(tol), _ptr(F), _ptr(T), _ptr(q),
+                                           ctypes.byref(its)))
+    return F, T, q, its.value
+
+
+def rbs_apply_laplace(ctx, kind, x):
+    x = _f64(x, (-1,))
+    y = np.zeros_like(x)
+    _check(ctx, load().rbs_apply_laplace(ctx, int(kind), _ptr(x), _ptr(y)))
+    return y
 
 
 def rbs_total_nodes(ctx) -> int:
