@@ -131,6 +131,7 @@ struct MagState {
   DevBuf<const double*> d_Dt_ptr, d_Dp_ptr, d_upU;
   DevBuf<int> d_grid_of;
   DevBuf<double> d_q, d_b, d_phi, d_hn, d_f, d_qup, d_FT;
+  DevBuf<float2> d_wq;
   void release();
   MagState() = default;
   ~MagState();

@@ -6,8 +6,9 @@
 // S^L (kernel -(r . n_x) / (4 pi |r|^3), r = x - y).  It is discretised like the mobility operators:
 // the smooth rule over distinct particles, upsampled sources for near pairs, and the rotated-pole
 // singular rule on each particle's own surface (scalar blocks, invariant under the particle's rotation,
-// stored per shape with every row).  The solve is float64 GMRES, right-preconditioned by the inverse
-// of each particle's own 1/2 I + eta K^L block.
+// stored per shape with every row).  The smooth pair sums run in double-float arithmetic (about 1e-12),
+// the near corrections and blocks in float64; the solve is float64 GMRES, right-preconditioned by the
+// inverse of each particle's own 1/2 I + eta K^L block.
 //
 // On the fluid side of each surface the field is H = -grad_s phi + H_n n, the tangential gradient by
 // spectral differentiation of phi on the particle's grid (Eq. 37) and H_n = H0 . n + q / 2 - K^L[q];
@@ -17,6 +18,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "surface.cuh"
 
 namespace rbs {
@@ -134,51 +136,102 @@ __global__ void k_basis_derivs(int p, int mmax, int nphi, int nb, const double* 
   }
 }
 
-// Smooth scalar pair sums in float64 over the work list (128 targets x a source range per item):
-// y_t += scale * sum_s k(x_t - y_s) w_s q_s, same-particle pairs excluded; KIND 0 = K^L, 1 = S^L.
+// Weighted scalar density w q as a double-float pair per node.
+__global__ void k_weight_df1(long long N, const double4* __restrict__ x, const double* __restrict__ q,
+                             float2* __restrict__ wq) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const dflt a = df_split(x[t].w * q[t]);
+  wq[t] = make_float2(a.h, a.l);
+}
+
+// The smooth scalar pair sums in double-float arithmetic (about 1e-12 relative, like float64 here, on
+// the float32 pipes): positions staged from exact three-float splits relative to the item's first
+// target, the weighted density as double-float pairs, tiles accumulated in double-float.
 template <int KIND>
-__global__ void __launch_bounds__(128) k_lap64(int nitems, const longlong4* __restrict__ work, const double4* __restrict__ x,
-                                               const double4* __restrict__ nrm, const int* __restrict__ pid,
-                                               const double* __restrict__ q, double scale, double* __restrict__ y) {
+__global__ void __launch_bounds__(128, 8) k_lap_df(int nitems, const longlong4* __restrict__ work,
+                                                   const float4* __restrict__ x3h, const float4* __restrict__ x3m,
+                                                   const float4* __restrict__ x3l, const float4* __restrict__ nh,
+                                                   const float4* __restrict__ nl, const float2* __restrict__ wq,
+                                                   double scale, double* __restrict__ y) {
   constexpr int TS = 128;
-  __shared__ double4 sp[TS];
-  __shared__ int spid[TS];
+  __shared__ float4 sph[TS], spl[TS];
+  __shared__ float2 sq[TS];
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const longlong4 w = work[it];
+    const float4 oh = x3h[w.x], om = x3m[w.x], ol = x3l[w.x];
     const long long t = w.x + threadIdx.x;
     const bool valid = t < w.y;
-    double4 xt = make_double4(0, 0, 0, 0), nt = make_double4(0, 0, 0, 0);
+    float4 ah = oh, am = om, al = ol, bh = make_float4(0, 0, 0, 0), bl = make_float4(0, 0, 0, 0);
     int pt = -1;
     if (valid) {
-      xt = x[t];
-      nt = nrm[t];
-      pt = pid[t];
+      ah = x3h[t];
+      am = x3m[t];
+      al = x3l[t];
+      bh = nh[t];
+      bl = nl[t];
+      pt = __float_as_int(ah.w);
     }
-    double acc = 0.0;
+    const dflt xt[3] = {df_diff3(ah.x, am.x, al.x, oh.x, om.x, ol.x), df_diff3(ah.y, am.y, al.y, oh.y, om.y, ol.y),
+                        df_diff3(ah.z, am.z, al.z, oh.z, om.z, ol.z)};
+    const dflt nt[3] = {{bh.x, bl.x}, {bh.y, bl.y}, {bh.z, bl.z}};
+    dflt a = {0.0f, 0.0f};
     for (long long s0 = w.z; s0 < w.w; s0 += TS) {
       const int cnt = (int)min((long long)TS, w.w - s0);
       __syncthreads();
       if ((int)threadIdx.x < cnt) {
         const long long s = s0 + threadIdx.x;
-        double4 ps = x[s];
-        ps.w *= q[s];
-        sp[threadIdx.x] = ps;
-        spid[threadIdx.x] = pid[s];
+        const float4 ph = x3h[s], pm = x3m[s], pl = x3l[s];
+        const dflt px = df_diff3(ph.x, pm.x, pl.x, oh.x, om.x, ol.x);
+        const dflt py = df_diff3(ph.y, pm.y, pl.y, oh.y, om.y, ol.y);
+        const dflt pz = df_diff3(ph.z, pm.z, pl.z, oh.z, om.z, ol.z);
+        sph[threadIdx.x] = make_float4(px.h, py.h, pz.h, ph.w);
+        spl[threadIdx.x] = make_float4(px.l, py.l, pz.l, 0.0f);
+        sq[threadIdx.x] = wq[s];
       }
       __syncthreads();
-#pragma unroll 4
+      dflt acc = {0.0f, 0.0f};
       for (int l = 0; l < cnt; ++l) {
-        const double4 ps = sp[l];
-        const double dx = xt.x - ps.x, dy = xt.y - ps.y, dz = xt.z - ps.z;
-        double inv = rsqrt(dx * dx + dy * dy + dz * dz);
-        if (spid[l] == pt) inv = 0.0;
-        if (KIND == 0)
-          acc = fma(-(dx * nt.x + dy * nt.y + dz * nt.z) * inv * inv * inv, ps.w, acc);
-        else
-          acc = fma(inv, ps.w, acc);
+        const float4 yh = sph[l], yl = spl[l];
+        const float2 qq = sq[l];
+        dflt d[3];
+        d[0] = df_two_sum(xt[0].h, -yh.x);
+        d[0].l += xt[0].l - yl.x;
+        d[1] = df_two_sum(xt[1].h, -yh.y);
+        d[1].l += xt[1].l - yl.y;
+        d[2] = df_two_sum(xt[2].h, -yh.z);
+        d[2].l += xt[2].l - yl.z;
+        float p[3], e[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          p[c] = d[c].h * d[c].h;
+          e[c] = fmaf(d[c].h, d[c].h, -p[c]);
+          e[c] = fmaf(d[c].h + d[c].h, d[c].l, e[c]);
+        }
+        const dflt s1 = df_two_sum(p[0], p[1]);
+        const dflt s2 = df_two_sum(s1.h, p[2]);
+        const float r2l = s1.l + s2.l + e[0] + e[1] + e[2];
+        const float r2h = s2.h;
+        const float y0 = rsqrt_hw(r2h);
+        const float q0 = y0 * y0;
+        const float qe = fmaf(y0, y0, -q0);
+        float tt = fmaf(r2h, q0, -1.0f);
+        tt = fmaf(r2h, qe, tt);
+        tt = fmaf(r2l, q0, tt);
+        dflt inv = {y0, -0.5f * tt * y0};
+        if (__float_as_int(yh.w) == pt) inv = {0.0f, 0.0f};
+        const dflt wqv = {qq.x, qq.y};
+        if (KIND == 0) {
+          const dflt rn = df_dot3(d[0], nt[0], d[1], nt[1], d[2], nt[2]);
+          const dflt inv3 = df_mul(df_mul(inv, inv), inv);
+          df_acc(acc, df_mul(df_mul(rn, inv3), wqv));
+        } else {
+          df_acc(acc, df_mul(inv, wqv));
+        }
       }
+      a = df_add_accurate(a, acc);
     }
-    if (valid) atomicAdd(y + t, scale * kInv4Pi * acc);
+    if (valid) atomicAdd(y + t, (KIND == 0 ? -scale : scale) * kInv4Pi * ((double)a.h + (double)a.l));
   }
 }
 
@@ -510,13 +563,16 @@ static Status apply_laplace(Context& c, int kind, double half, double scale, con
   k_lap_blocks<<<c.n, 256, 0, s>>>(c.d_offset.ptr, c.d_nodes.ptr, c.d_shape.ptr, M.d_block_off.ptr, B, x, scale, half, y);
   const int nw = (int)c.work.size();
   if (nw > 0) {
-    c.stats.launches++;
+    RBS_TRY(M.d_wq.alloc(c.N));
+    c.stats.launches += 2;
+    k_weight_df1<<<cdiv(c.N, 256), 256, 0, s>>>(c.N, c.d_x.ptr, x, M.d_wq.ptr);
+    const int grid = std::min(nw, 8 * std::max(1, c.sm_count));
+#define RBS_LAP_ARGS nw, c.d_work.ptr, c.d_x3h.ptr, c.d_x3m.ptr, c.d_x3l.ptr, c.d_nrmh.ptr, c.d_nrml.ptr, M.d_wq.ptr, scale, y
     if (kind == 0)
-      k_lap64<0><<<std::min(nw, 16 * std::max(1, c.sm_count)), 128, 0, s>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr,
-                                                                           c.d_pid.ptr, x, scale, y);
+      k_lap_df<0><<<grid, 128, 0, s>>>(RBS_LAP_ARGS);
     else
-      k_lap64<1><<<std::min(nw, 16 * std::max(1, c.sm_count)), 128, 0, s>>>(nw, c.d_work.ptr, c.d_x.ptr, c.d_nrm.ptr,
-                                                                           c.d_pid.ptr, x, scale, y);
+      k_lap_df<1><<<grid, 128, 0, s>>>(RBS_LAP_ARGS);
+#undef RBS_LAP_ARGS
   }
   const int nn = (int)c.near_pairs.size();
   if (nn > 0) {

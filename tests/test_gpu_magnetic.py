@@ -1,8 +1,9 @@
 """Parity of the magnetostatic coupling (Section 4.1.3) with the oracle: the Laplace operators K^L and
 S^L on scalar node fields (smooth, near and singular rules), the single-layer density q, and the net
 magnetic forces and torques; the sphere's closed form and the ellipsoid's demagnetisation torque on the
-GPU; and one Euler step of two paramagnetic spheres against the oracle.  Tolerances: operators 1e-12
-(relative L2), q and the forces 1e-10 (GMRES to 1e-13)."""
+GPU; and one Euler step of two paramagnetic spheres against the oracle.  Tolerances: operators 1e-11
+(relative L2; the smooth sums run in double-float arithmetic), q and the forces 1e-10 (GMRES to
+1e-13)."""
 import math
 
 import numpy as np
@@ -41,7 +42,7 @@ def test_laplace_operators_match_oracle(rbs, trio, kind):
     s, m, ctx = trio
     x = np.random.default_rng(3).normal(size=s.total_nodes)
     y = rbs.rbs_apply_laplace(ctx.ctx, kind, x)
-    assert rel(y, m.assemble("KS"[kind]) @ x) < 1e-12
+    assert rel(y, m.assemble("KS"[kind]) @ x) < 1e-11
 
 
 def test_magnetic_forces_match_oracle(rbs, trio):
