@@ -291,6 +291,41 @@ __global__ void k_gather_rows(int rows, int cols, const int* __restrict__ idx, c
   }
 }
 
+// The same for minibatch number *step of a device permutation: rows perm[*step * rows + r].
+template <typename T>
+__global__ void k_gather_step(int rows, int cols, const int* __restrict__ perm, const int* __restrict__ step,
+                              const T* __restrict__ src, T* __restrict__ dst) {
+  const int* idx = perm + (long long)(*step) * rows;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)rows * cols;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / cols, cc = i % cols;
+    dst[i] = src[(size_t)idx[r] * cols + cc];
+  }
+}
+
+// Adam with the step count t + 1 read from the device (bias corrections 1 - b^(t+1)).
+__global__ void k_adam_dev(long long n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                           float* __restrict__ v, float lr, float b1, float b2, float eps, const long long* __restrict__ t,
+                           __nv_bfloat16* __restrict__ wb) {
+  const float tt = (float)(*t + 1);
+  const float c1 = 1.0f - powf(b1, tt), c2 = 1.0f - powf(b2, tt);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16(wi);
+  }
+}
+
+__global__ void k_next_step(int* step, long long* t) {
+  *step += 1;
+  *t += 1;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
@@ -319,6 +354,21 @@ struct WarmState {
   DevBuf<float> t;
   DevBuf<double> loss;
   size_t off[6] = {0, 0, 0, 0, 0, 0};
+  // the training step as a CUDA graph (fixed batch size), launched on its own stream
+  cudaGraphExec_t step_exec = nullptr;
+  int step_batch = 0;
+  int step_kernels = 0;
+  std::vector<const void*> step_sig;
+  cudaStream_t gs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  DevBuf<int> perm, step;
+  DevBuf<long long> t_dev;
+  ~WarmState() {
+    if (step_exec) cudaGraphExecDestroy(step_exec);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (gs) cudaStreamDestroy(gs);
+  }
 };
 
 static size_t param_count(int D) {
@@ -428,7 +478,8 @@ static Status mlp_backward(Context& c, int rows, double* loss_out) {
   const __nv_bfloat16* wb = W.wb.ptr;
   float* g = W.g.ptr;
   const long long tot = (long long)rows * W.D;
-  RBS_CUDA_TRY(cudaMemsetAsync(W.loss.ptr, 0, sizeof(double), s));
+  // with loss_out the loss of this batch is returned; without, the squared errors accumulate in W.loss
+  if (loss_out) RBS_CUDA_TRY(cudaMemsetAsync(W.loss.ptr, 0, sizeof(double), s));
   c.stats.launches += 1;
   k_mse_grad<<<std::min(1024, cdiv(tot, 256)), 256, 0, s>>>(tot, W.y.ptr, W.t.ptr, 1.0f / W.out_scale,
                                                              1.0f / (float)tot, W.dyb.ptr, W.dy.ptr, W.loss.ptr);
@@ -563,10 +614,53 @@ Status warm_train(Context& c, int epochs, int batch, double lr, unsigned seed, d
     k_to_bf16<<<1024, 256, 0, s>>>(W.w.ptr, W.wb.ptr, W.nparam);
     W.have_weights = true;
   }
-  // shuffled minibatches (host permutation, seeded)
+  // Shuffled minibatches (host permutation, seeded, one upload per epoch).  One training step (gather,
+  // forward, backward, Adam, step counters) is captured once as a CUDA graph on a private stream and
+  // replayed for every minibatch; the loss is summed on the device and read once per epoch.
+  const int steps = (int)(W.count / batch);
   std::vector<int> perm(W.count);
-  DevBuf<int> d_idx;
-  RBS_TRY(d_idx.alloc(batch));
+  RBS_TRY(W.perm.alloc(W.count));
+  RBS_TRY(W.step.alloc(1));
+  RBS_TRY(W.t_dev.alloc(1));
+  if (!W.gs) {
+    RBS_CUDA_TRY(cudaStreamCreateWithFlags(&W.gs, cudaStreamNonBlocking));
+    RBS_CUDA_TRY(cudaEventCreateWithFlags(&W.ev_in, cudaEventDisableTiming));
+    RBS_CUDA_TRY(cudaEventCreateWithFlags(&W.ev_out, cudaEventDisableTiming));
+  }
+  // the captured graph holds raw pointers: recapture when the batch size or any buffer it touches changed
+  const std::vector<const void*> sig = {W.Xs.ptr, W.Ys.ptr, W.perm.ptr, W.step.ptr, W.t_dev.ptr, W.w.ptr, W.g.ptr,
+                                        W.m.ptr,  W.v.ptr,  W.wb.ptr,   W.xb.ptr,   W.t.ptr,     W.z1.ptr, W.h1.ptr,
+                                        W.z2.ptr, W.h2.ptr, W.y.ptr,    W.dy.ptr,   W.dyb.ptr,   W.dh.ptr, W.dz.ptr,
+                                        W.dzb.ptr, W.loss.ptr};
+  if (W.step_exec && (W.step_batch != batch || W.step_sig != sig)) {
+    RBS_CUDA_TRY(cudaGraphExecDestroy(W.step_exec));
+    W.step_exec = nullptr;
+  }
+  if (!W.step_exec && steps > 0) {
+    const cudaStream_t user = c.stream;
+    const long long launches0 = c.stats.launches;
+    c.stream = W.gs;
+    cudaGraph_t graph = nullptr;
+    RBS_CUDA_TRY(cudaStreamBeginCapture(W.gs, cudaStreamCaptureModeThreadLocal));
+    k_gather_step<__nv_bfloat16><<<256, 256, 0, W.gs>>>(batch, kFeat, W.perm.ptr, W.step.ptr, W.Xs.ptr, W.xb.ptr);
+    k_gather_step<float><<<256, 256, 0, W.gs>>>(batch, W.D, W.perm.ptr, W.step.ptr, W.Ys.ptr, W.t.ptr);
+    Status st1 = mlp_forward(c, batch);
+    Status st2 = st1.ok() ? mlp_backward(c, batch, nullptr) : st1;
+    k_adam_dev<<<1024, 256, 0, W.gs>>>(W.nparam, W.w.ptr, W.g.ptr, W.m.ptr, W.v.ptr, (float)lr, 0.9f, 0.999f, 1e-8f,
+                                       W.t_dev.ptr, W.wb.ptr);
+    k_next_step<<<1, 1, 0, W.gs>>>(W.step.ptr, W.t_dev.ptr);
+    cudaError_t ce = cudaStreamEndCapture(W.gs, &graph);
+    c.stream = user;
+    W.step_kernels = (int)(c.stats.launches - launches0) + 4;
+    c.stats.launches = launches0;
+    RBS_TRY(st2);
+    RBS_CUDA_TRY(ce);
+    ce = cudaGraphInstantiate(&W.step_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    RBS_CUDA_TRY(ce);
+    W.step_batch = batch;
+    W.step_sig = sig;
+  }
   unsigned long long st = 0xD1B54A32D192ED03ULL ^ (seed * 2654435761ULL);
   double last = 0.0;
   for (int e = 0; e < epochs; ++e) {
@@ -576,26 +670,22 @@ Status warm_train(Context& c, int epochs, int batch, double lr, unsigned seed, d
       long long j = (long long)((st >> 33) % (unsigned long long)(k + 1));
       std::swap(perm[k], perm[j]);
     }
-    double esum = 0.0;
-    int nbt = 0;
-    for (long long b0 = 0; b0 + batch <= W.count; b0 += batch) {
-      RBS_CUDA_TRY(cudaMemcpyAsync(d_idx.ptr, perm.data() + b0, sizeof(int) * batch, cudaMemcpyHostToDevice, s));
-      c.stats.launches += 2;
-      k_gather_rows<__nv_bfloat16><<<256, 256, 0, s>>>(batch, kFeat, d_idx.ptr, W.Xs.ptr, W.xb.ptr);
-      k_gather_rows<float><<<256, 256, 0, s>>>(batch, W.D, d_idx.ptr, W.Ys.ptr, W.t.ptr);
-      RBS_TRY(mlp_forward(c, batch));
-      double l = 0.0;
-      RBS_TRY(mlp_backward(c, batch, &l));
-      esum += l;
-      ++nbt;
-      ++W.adam_t;
-      const float b1 = 0.9f, b2 = 0.999f;
-      c.stats.launches += 1;
-      k_adam<<<1024, 256, 0, s>>>(W.nparam, W.w.ptr, W.g.ptr, W.m.ptr, W.v.ptr, (float)lr, b1, b2, 1e-8f,
-                                  1.0f - std::pow(b1, (float)W.adam_t), 1.0f - std::pow(b2, (float)W.adam_t), W.wb.ptr);
-      RBS_CUDA_TRY(cudaGetLastError());
-    }
-    last = nbt ? esum / nbt : 0.0;
+    if (steps == 0) continue;
+    RBS_CUDA_TRY(cudaMemcpyAsync(W.perm.ptr, perm.data(), sizeof(int) * W.count, cudaMemcpyHostToDevice, s));
+    RBS_CUDA_TRY(cudaMemsetAsync(W.step.ptr, 0, sizeof(int), s));
+    RBS_CUDA_TRY(cudaMemcpyAsync(W.t_dev.ptr, &W.adam_t, sizeof(long long), cudaMemcpyHostToDevice, s));
+    RBS_CUDA_TRY(cudaMemsetAsync(W.loss.ptr, 0, sizeof(double), s));
+    RBS_CUDA_TRY(cudaEventRecord(W.ev_in, s));
+    RBS_CUDA_TRY(cudaStreamWaitEvent(W.gs, W.ev_in, 0));
+    for (int b = 0; b < steps; ++b) RBS_CUDA_TRY(cudaGraphLaunch(W.step_exec, W.gs));
+    RBS_CUDA_TRY(cudaEventRecord(W.ev_out, W.gs));
+    RBS_CUDA_TRY(cudaStreamWaitEvent(s, W.ev_out, 0));
+    c.stats.launches += (long long)steps * W.step_kernels;
+    W.adam_t += steps;
+    double l = 0.0;
+    RBS_CUDA_TRY(cudaMemcpyAsync(&l, W.loss.ptr, sizeof(double), cudaMemcpyDeviceToHost, s));
+    RBS_CUDA_TRY(cudaStreamSynchronize(s));
+    last = l / ((double)steps * batch * W.D);
   }
   RBS_CUDA_TRY(cudaStreamSynchronize(s));
   if (final_loss) *final_loss = last;
