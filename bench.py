@@ -70,6 +70,8 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain float64 solves (0 skips)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
+    ap.add_argument("--pair-variant", type=int, default=0,
+                    help="pair-kernel variant (rbs_options.pair_variant); 0 lets the library's autotuner choose")
     ap.add_argument("--experiment", default=None, choices=[None, "warmstart", "magnetic"],
                     help="warmstart: learned vs previous-step vs zero initial guesses in RK4 sedimentation; "
                          "magnetic: time steps of paramagnetic spheres in a uniform field (each prints its own "
@@ -275,7 +277,8 @@ def run_ours(args):
     susp = suspensions.WORKLOADS[args.workload]()
     n = susp.n
     stream = torch.cuda.current_stream()
-    ctx = rbs.Context(device=local, precision=rbs.RBS_PREC_MIXED, timing=1, stream=stream.cuda_stream)
+    ctx = rbs.Context(device=local, precision=rbs.RBS_PREC_MIXED, timing=1, stream=stream.cuda_stream,
+                      pair_variant=args.pair_variant)
     ctx.set_suspension(susp)
     setup_ms = rbs.rbs_get_stats(ctx.ctx)["setup_ms"]
 

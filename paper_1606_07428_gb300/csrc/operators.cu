@@ -571,7 +571,7 @@ template <int KIND, int NT>
 __global__ void __launch_bounds__(128 / NT, NT == 4 ? 12 : (NT == 2 ? 10 : 8)) k_pairs32x2(int nitems, const longlong4* __restrict__ work, const float4* __restrict__ xhi,
                                                        const float4* __restrict__ xlo, const float4* __restrict__ nrm32,
                                                        const float4* __restrict__ wmu, double* __restrict__ y) {
-  constexpr int TS = 256, NTH = 128 / NT;
+  constexpr int TS = 512, NTH = 128 / NT;  // 512 sources per tile: the staging latency is amortised over more pairs
   __shared__ __align__(16) float ssx[TS], ssy[TS], ssz[TS], srx[TS], sry[TS], srz[TS];
   __shared__ __align__(16) int spid[TS];
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
