@@ -72,6 +72,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
     ap.add_argument("--pair-variant", type=int, default=0,
                     help="pair-kernel variant (rbs_options.pair_variant); 0 lets the library's autotuner choose")
+    ap.add_argument("--far-field", default="direct", choices=["direct", "tree"],
+                    help="float32 inner applies: direct sums over all node pairs, or the treecode "
+                         "(rbs_options.far_field; double-float passes stay direct either way)")
     ap.add_argument("--experiment", default=None, choices=[None, "warmstart", "magnetic"],
                     help="warmstart: learned vs previous-step vs zero initial guesses in RK4 sedimentation; "
                          "magnetic: time steps of paramagnetic spheres in a uniform field (each prints its own "
@@ -277,10 +280,19 @@ def run_ours(args):
     susp = suspensions.WORKLOADS[args.workload]()
     n = susp.n
     stream = torch.cuda.current_stream()
+    far = rbs.RBS_FAR_TREECODE if args.far_field == "tree" else rbs.RBS_FAR_DIRECT
     ctx = rbs.Context(device=local, precision=rbs.RBS_PREC_MIXED, timing=1, stream=stream.cuda_stream,
-                      pair_variant=args.pair_variant)
+                      pair_variant=args.pair_variant, far_field=far)
     ctx.set_suspension(susp)
-    setup_ms = rbs.rbs_get_stats(ctx.ctx)["setup_ms"]
+    st0 = rbs.rbs_get_stats(ctx.ctx)
+    setup_ms = st0["setup_ms"]
+    tree_info = None
+    if far == rbs.RBS_FAR_TREECODE:
+        opts = rbs.rbs_default_options()
+        tree_info = {"theta": opts.tree_theta, "degree": opts.tree_degree, "cells": st0["tree_cells"],
+                     "pairs_per_apply": st0["tree_pairs"], "proxy_pairs_per_apply": st0["tree_proxy_pairs"],
+                     "direct_pairs_per_apply": st0["far_pairs"],
+                     "reduction": st0["far_pairs"] / max(1, st0["tree_pairs"])}
 
     draws = [suspensions.forces(100 + rank, n, k) for k in range(args.warmup + args.steps)]
     F_dev = torch.tensor(np.stack([d[0] for d in draws]), device="cuda")
@@ -473,6 +485,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": susp.name, "n_particles": n, "p": int(susp.p[0]), "nodes": susp.total_nodes,
                        "unknowns": 3 * susp.total_nodes, "tol": args.tol, "precision": "mixed",
+                       "far_field": ("treecode for the float32 inner applies, direct double-float passes"
+                                     if tree_info else "direct sums"),
                        "preconditioner": "block-diagonal", "gmres_iterations": iters,
                        "refinements_last": refinements, "setup_ms": setup_ms,
                        "l2": "flushed before every timed solve (258 MB write); working set > L2",
@@ -486,6 +500,7 @@ def run_ours(args):
             "pair_variant": dict(zip(["traction_f32", "stokeslet_f32", "traction_df", "stokeslet_df",
                                       "traction_and_stokeslet_df"],
                                      stats.get("pair_variant", []))),
+            "treecode": tree_info,
             "roofline": roof,
             "kernel_rooflines": rooflines,
             "e2e": e2e,

@@ -105,7 +105,22 @@ typedef struct {
   double mu_ratio;     /* permeability of the particles over that of the fluid, mu / mu0 (default 1);
                           with mu_ratio != 1 and a non-zero field, every rbs_advance stage adds the
                           magnetic forces and torques of rbs_magnetic_forces to F and T */
+  int far_field;       /* RBS_FAR_DIRECT (default): every smooth pair sum runs over all node pairs.
+                          RBS_FAR_TREECODE: the float32 applies of the mixed solve (inner GMRES and
+                          float32 corrections) approximate the smooth sums over well-separated
+                          clusters of particles with a barycentric Lagrange treecode, the
+                          hierarchical far field in place of Section 3.1's fast multipole method;
+                          the double-float and float64 passes, and so the converged result, stay
+                          direct.  Only with precision RBS_PREC_MIXED */
+  double tree_theta;   /* treecode opening criterion: a cluster of radius r_C is approximated for a
+                          target particle of radius r_B at centre distance d when r_B + r_C <
+                          tree_theta d (default 0.5; 0 < tree_theta < 1) */
+  int tree_degree;     /* treecode interpolation degree n per axis: (n + 1)^3 Chebyshev proxy points
+                          per cluster (default 7; 2 <= n <= 10) */
 } rbs_options;
+
+#define RBS_FAR_DIRECT 0
+#define RBS_FAR_TREECODE 1
 
 #define RBS_WARM_ZERO 0
 #define RBS_WARM_PREVIOUS 1
@@ -121,7 +136,9 @@ typedef struct {
 #define RBS_KC_PAIR_KDF 6 /* smooth traction pair sum, double-float */
 #define RBS_KC_PAIR_SDF 7 /* smooth Stokeslet pair sum, double-float */
 #define RBS_KC_PAIR_KSDF 8 /* smooth traction and Stokeslet sums of one density in one pass, double-float */
-#define RBS_KC_COUNT 9
+#define RBS_KC_TREE 9     /* treecode cluster charges (RBS_FAR_TREECODE); the treecode's pair sums count
+                             under RBS_KC_PAIR_K32 / RBS_KC_PAIR_S32 with their evaluated pairs as units */
+#define RBS_KC_COUNT 10
 
 typedef struct {
   int iterations;        /* total GMRES iterations of the last solve (inner iterations for mixed) */
@@ -143,6 +160,11 @@ typedef struct {
   int pair_variant[5];   /* variant in use (as rbs_options.pair_variant): float32 traction, float32
                             Stokeslet, double-float traction, double-float Stokeslet, fused
                             double-float traction and Stokeslet (0 = not yet chosen) */
+  long long tree_pairs;  /* RBS_FAR_TREECODE: (target node, source) pairs one treecode apply evaluates,
+                            direct node pairs (the target's own particle included, masked) plus
+                            proxy pairs; 0 without a treecode */
+  long long tree_proxy_pairs; /* of these, the (target node, cluster proxy point) pairs */
+  int tree_cells;        /* clusters that carry proxy points */
 } rbs_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -104,6 +104,9 @@ void rbs_default_options(rbs_options* o) {
   o->contact_gap = 0.0;
   o->magnetic_field[0] = o->magnetic_field[1] = o->magnetic_field[2] = 0.0;
   o->mu_ratio = 1.0;
+  o->far_field = RBS_FAR_DIRECT;
+  o->tree_theta = 0.5;
+  o->tree_degree = 7;
 }
 
 int rbs_create(const rbs_options* opt, rbs_ctx** out) {
@@ -122,7 +125,9 @@ int rbs_create(const rbs_options* opt, rbs_ctx** out) {
       (o.pair_variant != 0 && o.pair_variant != 1 && o.pair_variant != 2 && o.pair_variant != 4 &&
        o.pair_variant != 9 && o.pair_variant != 10 && o.pair_variant != 12) ||
       o.warm_start > 2 || !(o.contact_gap >= 0.0) || !(o.mu_ratio > 0.0) ||
-      !std::isfinite(o.magnetic_field[0]) || !std::isfinite(o.magnetic_field[1]) || !std::isfinite(o.magnetic_field[2]))
+      !std::isfinite(o.magnetic_field[0]) || !std::isfinite(o.magnetic_field[1]) || !std::isfinite(o.magnetic_field[2]) ||
+      (o.far_field != RBS_FAR_DIRECT && o.far_field != RBS_FAR_TREECODE) ||
+      !(o.tree_theta > 0.0 && o.tree_theta < 1.0) || o.tree_degree < 2 || o.tree_degree > 10)
     return RBS_EINVAL;
   rbs_ctx* h = new rbs_ctx();
   Context& c = h->c;

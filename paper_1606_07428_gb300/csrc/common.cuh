@@ -139,6 +139,37 @@ struct MagState {
   MagState& operator=(const MagState&) = delete;
 };
 
+// Barycentric Lagrange treecode for the float32 smooth pair sums (treecode.cu), rebuilt with the
+// geometry when rbs_options.far_field is RBS_FAR_TREECODE.
+struct TreeItem {  // one work item of the treecode pair sum
+  int t0, t1;      // target nodes [t0, t1), all on one particle
+  int s0, s1;      // source segments [s0, s1) of that particle's list
+  int nmask;       // leading sources of the item that may lie on the target's own particle
+  int pad0, pad1, pad2;
+};
+struct TreeState {
+  bool active = false;
+  int degree = 0, npx = 0;   // interpolation degree and (degree + 1)^3 proxy points per cluster
+  int n_cells = 0;           // clusters with proxy points
+  double theta = 0.0;
+  long long n_src = 0;       // sources: N nodes, then n_cells * npx proxy points
+  std::vector<TreeItem> items;
+  std::vector<int2> segs;    // (first source, count): contiguous runs of the source arrays
+  std::vector<int4> charge_items;  // (cluster, first, end) over d_order: the particles of one charge block
+  DevBuf<TreeItem> d_items;
+  DevBuf<int2> d_segs;
+  DevBuf<int4> d_charge_items;
+  DevBuf<int> d_order;       // particles in tree order
+  DevBuf<double> d_box;      // per cluster with proxies: box midpoint (3), 1 / half-width (3)
+  DevBuf<float> d_cheb;      // Chebyshev points, then barycentric weights (degree + 1 each)
+  DevBuf<double> d_pbox;     // per particle: node bounding box lo (3), hi (3)
+  // sources for the pair kernel: positions as float32 hi + lo (w of hi: particle id bits, -3 for a
+  // proxy point) and float32 weighted density (nodes) or cluster charge (proxy points)
+  DevBuf<float4> d_hi, d_lo, d_q;
+  long long direct_pairs = 0, proxy_pairs = 0, charge_work = 0;
+  void release();
+};
+
 struct Context {
   rbs_options opt{};
   cudaStream_t stream = nullptr;
@@ -241,6 +272,7 @@ struct Context {
   std::vector<Contact> contacts;
 
   MagState mag;  // magnetostatic coupling (magnetic.cu)
+  TreeState tree;  // treecode for the float32 smooth sums (treecode.cu)
 
   rbs_stats stats{};
   WarmState* warm = nullptr;       // learned warm start (warmstart.cu)
@@ -282,6 +314,16 @@ Status magnetic_forces(Context& c, const double H0[3], double mu_ratio, double t
                        int* iters);
 // y = K^L x (kind 0) or S^L x (kind 1), scalar fields on the nodes (device).
 Status laplace_operator(Context& c, int kind, const double* x, double* y);
+
+// ---- treecode (treecode.cu)
+// Builds (or clears) the treecode of the current geometry; called after the near-pair lists.
+Status build_far_field(Context& c);
+// y += the treecode's float32 smooth pair sum of kind (0 traction, 1 Stokeslet) for density x, with
+// nt targets per thread (1, 2 or 4).
+Status apply_tree(Context& c, int kind, const double* x, double* y, int nt);
+// Relative error assumed for a float32 operator application: rounding plus, with the treecode,
+// its approximation model C(theta) rho^-n.
+double f32_operator_error(const Context& c);
 
 // ---- setup (setup.cu)
 Status build_geometry(Context& c);

@@ -895,7 +895,7 @@ Status build_near(Context& c) {
     c.near_pair_nodes += (double)(c.offset[pr.x + 1] - c.offset[pr.x]) *
                          (c.grids[c.grid_of[pr.y]]->nup + (c.offset[pr.y + 1] - c.offset[pr.y]));
   c.stats.near_pairs = (long long)c.near_pairs.size();
-  return Status::Ok();
+  return build_far_field(c);
 }
 
 Status update_configuration(Context& c, const double* centres, const double* quats) {

@@ -381,10 +381,10 @@ __global__ void k_unpack_vo(int n, const double* vo, double* v, double* om) {
   }
 }
 
-// Relative error of a float32 operator application (float32 pair sums with per-tile compensation,
-// float32 blocks and interpolation), a bound on the measured relative L2 error (a few 1e-7 on the
-// 1,000-ellipsoid p = 12 suspension); it decides when a refinement residual may be updated in float32.
-constexpr double kF32OperatorError = 1e-5;
+// The relative error of a float32 operator application (f32_operator_error: 1e-5 for float32 pair
+// sums with per-tile compensation, float32 blocks and interpolation, a bound on the measured relative
+// L2 error of a few 1e-7 on the 1,000-ellipsoid p = 12 suspension, plus the treecode's model when it
+// is on) decides when a refinement residual may be updated in float32.
 
 // Float64-class residual and surface velocity of one iterate x, sharing one pass over the pairs:
 // with sigma = rho + x,  r = b - A x = -(1/2 I + K) sigma - L x = L rho - A sigma  (Eq. 25, A the
@@ -461,7 +461,7 @@ static Status solve_core(Context& c, double tol, bool warm, int* iters_out, int*
     // Iterative refinement around float32 inner solves.  A float64-class pass gives the true
     // residual r = b - A x and, from the same pair sums, u = S[rho + x].  After a pass, a small
     // correction d may instead update r -= A d and u += S d in float32: the float32 operator's error
-    // on d is kF32OperatorError ||A d||, and these updates are taken only while that error, summed
+    // on d is f32_operator_error ||A d||, and these updates are taken only while that error, summed
     // since the last pass, stays below a tenth of the tolerance.
     double* lrho = c.d_vec[8].ptr;  // L rho (Eq. 26), float64
     RBS_TRY(apply_blocks(c, kModeL, RBS_PREC_FP64, rho, lrho, nullptr, 1.0));
@@ -499,7 +499,7 @@ static Status solve_core(Context& c, double tol, bool warm, int* iters_out, int*
       ++refinements;
       c.stats.launches++;
       k_axpby<<<nbk, 256, 0, c.stream>>>(x, 1.0, d, 1.0, n3);
-      if (u_done && kF32OperatorError * (pending + rn) <= 0.1 * tol * bnorm) {
+      if (u_done && f32_operator_error(c) * (pending + rn) <= 0.1 * tol * bnorm) {
         RBS_TRY(apply_operator(c, RBS_OP_A, RBS_PREC_MIXED, d, w));
         c.stats.launches += 2;
         k_axpby<<<nbk, 256, 0, c.stream>>>(r, -1.0, w, 1.0, n3);

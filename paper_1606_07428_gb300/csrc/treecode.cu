@@ -1,0 +1,666 @@
+// Hierarchical far field for the float32 smooth pair sums: a barycentric Lagrange treecode (Wang,
+// Krasny and Tlupova, 2020) in place of the fast multipole method of Section 3.1.
+//
+// Per suspension, an octree over the particle centres (a cell with more than one particle splits at
+// the midpoint of its centres' bounding box; children in octant order, particles ascending).  Each
+// cell has the box of its particles' nodes, the box midpoint as centre, a radius
+// r = max_j (|c_j - centre| + R_j) bounding its nodes, and a node count.  The targets of each particle
+// form one batch (its leaf cell); a depth-first traversal accepts a cell C for approximation when
+//   r_B + r_C < theta d,  d >= r_B + r_C + near_delta  and  (n + 1)^3 < nodes(C),
+// else descends, and evaluates the particles of unaccepted leaves directly.  An accepted cell
+// carries (n + 1)^3 proxy points on the tensor Chebyshev grid of its box and charges
+//   q_abc = sum_s L_a(y_s,x) L_b(y_s,y) L_c(y_s,z) w_s mu_s     (barycentric Lagrange basis L),
+// recomputed for every apply; the pair kernel then treats proxy points as ordinary sources.
+//
+// Layout: one source array holds the N nodes (float32 hi + lo positions, weighted density) followed
+// by the proxy points of every accepted cell; each target particle has a list of (first, count)
+// segments into it: its own particle first (masked by particle id), then the directly evaluated
+// particles, then its accepted cells.  Work items pair 128 targets of one particle with a run of
+// those segments.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "pairs32.cuh"
+
+namespace rbs {
+
+namespace {
+
+constexpr int kTreeMaxQ = 11;        // degree <= 10
+constexpr int kTreeTargets = 128;    // targets per work item
+constexpr int kProxyPid = -3;        // particle id carried by proxy points (never a target's)
+
+// Bounding box of each particle's nodes: lo (3) then hi (3) per particle.
+__global__ void __launch_bounds__(128) k_particle_boxes(int n, const long long* __restrict__ offset,
+                                                        const double4* __restrict__ x, double* __restrict__ out) {
+  __shared__ double red[6][4];
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (long long t = offset[i] + threadIdx.x; t < offset[i + 1]; t += blockDim.x) {
+    const double4 p = x[t];
+    lo[0] = fmin(lo[0], p.x);
+    lo[1] = fmin(lo[1], p.y);
+    lo[2] = fmin(lo[2], p.z);
+    hi[0] = fmax(hi[0], p.x);
+    hi[1] = fmax(hi[1], p.y);
+    hi[2] = fmax(hi[2], p.z);
+  }
+  for (int o = 16; o > 0; o >>= 1)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fmin(lo[d], __shfl_down_sync(0xffffffffu, lo[d], o));
+      hi[d] = fmax(hi[d], __shfl_down_sync(0xffffffffu, hi[d], o));
+    }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int d = 0; d < 3; ++d) {
+      red[d][warp] = lo[d];
+      red[3 + d][warp] = hi[d];
+    }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int d = threadIdx.x;
+    double v = red[d][0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = d < 3 ? fmin(v, red[d][w]) : fmax(v, red[d][w]);
+    out[6 * (size_t)i + d] = v;
+  }
+}
+
+// Float32 weighted density of the nodes, the sources' charges: q[t] = (w_t mu_t, 0).
+__global__ void k_tree_node_charges(long long N, const double4* __restrict__ x, const double* __restrict__ dens,
+                                    float4* __restrict__ q) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const double w = x[t].w;
+  q[t] = make_float4((float)(w * dens[3 * t]), (float)(w * dens[3 * t + 1]), (float)(w * dens[3 * t + 2]), 0.0f);
+}
+
+// Barycentric Lagrange basis of the nq Chebyshev points s (weights bw) at u in [-1, 1]; a point on a
+// node gets that node's unit vector.
+__device__ __forceinline__ void lagrange_row(float u, const float* s, const float* bw, int nq, float* L) {
+  float t[kTreeMaxQ];
+  float sum = 0.0f;
+  int hit = -1;
+#pragma unroll
+  for (int k = 0; k < kTreeMaxQ; ++k) {
+    t[k] = 0.0f;
+    if (k < nq) {
+      const float d = u - s[k];
+      if (d == 0.0f)
+        hit = k;
+      else
+        t[k] = bw[k] / d;
+      sum += t[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kTreeMaxQ; ++k)
+    if (k < nq) L[k] = hit >= 0 ? (k == hit ? 1.0f : 0.0f) : t[k] / sum;
+}
+
+// Cluster charges: one block per (cluster, run of its particles); each thread owns up to
+// kProxyPerThread proxy points and sums L_a L_b L_c q over the run's nodes, staged 256 at a time with
+// their Lagrange rows; the partial charges are added atomically (the charges are zeroed first).
+constexpr int kChargeThreads = 256;
+constexpr int kProxyPerThread = (kTreeMaxQ * kTreeMaxQ * kTreeMaxQ + kChargeThreads - 1) / kChargeThreads;
+
+__global__ void __launch_bounds__(kChargeThreads) k_tree_charges(const int4* __restrict__ items,
+                                                                 const int* __restrict__ order,
+                                                                 const long long* __restrict__ offset,
+                                                                 const double4* __restrict__ x,
+                                                                 const float4* __restrict__ qnode,
+                                                                 const double* __restrict__ box,
+                                                                 const float* __restrict__ cheb, int nq,
+                                                                 float4* __restrict__ qproxy) {
+  constexpr int TS = kChargeThreads;
+  __shared__ float sL[3][TS][kTreeMaxQ];
+  __shared__ float4 sq[TS];
+  __shared__ float s_pts[kTreeMaxQ], s_bw[kTreeMaxQ];
+  const int npx = nq * nq * nq;
+  if (threadIdx.x < nq) {
+    s_pts[threadIdx.x] = cheb[threadIdx.x];
+    s_bw[threadIdx.x] = cheb[nq + threadIdx.x];
+  }
+  const int4 it = items[blockIdx.x];
+  const int u = it.x;
+  const double m0 = box[6 * (size_t)u], m1 = box[6 * (size_t)u + 1], m2 = box[6 * (size_t)u + 2];
+  const double h0 = box[6 * (size_t)u + 3], h1 = box[6 * (size_t)u + 4], h2 = box[6 * (size_t)u + 5];
+  int ka[kProxyPerThread], kb[kProxyPerThread], kc[kProxyPerThread];
+  float acc[kProxyPerThread][3];
+#pragma unroll
+  for (int m = 0; m < kProxyPerThread; ++m) {
+    const int k = threadIdx.x + kChargeThreads * m;
+    ka[m] = k / (nq * nq);
+    kb[m] = (k / nq) % nq;
+    kc[m] = k % nq;
+    acc[m][0] = acc[m][1] = acc[m][2] = 0.0f;
+  }
+  for (int pi = it.y; pi < it.z; ++pi) {
+    const int j = order[pi];
+    const long long o = offset[j], e = offset[j + 1];
+    for (long long s0 = o; s0 < e; s0 += TS) {
+      const int cnt = (int)min((long long)TS, e - s0);
+      __syncthreads();
+      if ((int)threadIdx.x < cnt) {
+        const double4 p = x[s0 + threadIdx.x];
+        lagrange_row((float)((p.x - m0) * h0), s_pts, s_bw, nq, sL[0][threadIdx.x]);
+        lagrange_row((float)((p.y - m1) * h1), s_pts, s_bw, nq, sL[1][threadIdx.x]);
+        lagrange_row((float)((p.z - m2) * h2), s_pts, s_bw, nq, sL[2][threadIdx.x]);
+        sq[threadIdx.x] = qnode[s0 + threadIdx.x];
+      }
+      __syncthreads();
+      for (int l = 0; l < cnt; ++l) {
+        const float4 q = sq[l];
+#pragma unroll
+        for (int m = 0; m < kProxyPerThread; ++m) {
+          if (threadIdx.x + kChargeThreads * m < npx) {
+            const float f = sL[0][l][ka[m]] * sL[1][l][kb[m]] * sL[2][l][kc[m]];
+            acc[m][0] = fmaf(f, q.x, acc[m][0]);
+            acc[m][1] = fmaf(f, q.y, acc[m][1]);
+            acc[m][2] = fmaf(f, q.z, acc[m][2]);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < kProxyPerThread; ++m) {
+    const int k = threadIdx.x + kChargeThreads * m;
+    if (k < npx) {
+      float4* dst = qproxy + (size_t)u * npx + k;
+      atomicAdd(&dst->x, acc[m][0]);
+      atomicAdd(&dst->y, acc[m][1]);
+      atomicAdd(&dst->z, acc[m][2]);
+    }
+  }
+}
+
+// The treecode's pair sum: the packed float32 tile loop of the direct kernel (pairs32.cuh) over
+// source tiles filled from the item's segments.  Coordinates are relative to the item's first target;
+// tiles that may hold nodes of the targets' own particle (the first nmask sources) mask them by
+// particle id.
+template <int KIND, int NT>
+__global__ void __launch_bounds__(128 / NT, NT == 4 ? 12 : (NT == 2 ? 10 : 8))
+    k_tree32x2(int nitems, const TreeItem* __restrict__ items, const int2* __restrict__ segs,
+               const float4* __restrict__ xhi, const float4* __restrict__ xlo, const float4* __restrict__ nrm32,
+               const float4* __restrict__ shi, const float4* __restrict__ slo, const float4* __restrict__ sq,
+               double* __restrict__ y) {
+  constexpr int TS = 512, NTH = 128 / NT;
+  __shared__ __align__(16) float ssx[TS], ssy[TS], ssz[TS], srx[TS], sry[TS], srz[TS];
+  __shared__ __align__(16) int spid[TS];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const TreeItem w = items[it];
+    const float4 oh = xhi[w.t0], ol = xlo[w.t0];
+    float2 xt[NT][3], nt[NT][3];
+    int pt[NT];
+    bool valid[NT];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      const int t = w.t0 + threadIdx.x + NTH * u;
+      valid[u] = t < w.t1;
+      float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, n0 = 0.0f, n1 = 0.0f, n2 = 0.0f;
+      pt[u] = -1;
+      if (valid[u]) {
+        const float4 ah = xhi[t], al = xlo[t], nn = nrm32[t];
+        a0 = (ah.x - oh.x) + (al.x - ol.x);
+        a1 = (ah.y - oh.y) + (al.y - ol.y);
+        a2 = (ah.z - oh.z) + (al.z - ol.z);
+        n0 = nn.x;
+        n1 = nn.y;
+        n2 = nn.z;
+        pt[u] = __float_as_int(ah.w);
+      }
+      xt[u][0] = f2(a0, a0);
+      xt[u][1] = f2(a1, a1);
+      xt[u][2] = f2(a2, a2);
+      nt[u][0] = f2(n0, n0);
+      nt[u][1] = f2(n1, n1);
+      nt[u][2] = f2(n2, n2);
+    }
+    float sa[NT][3], ea[NT][3];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) sa[u][0] = sa[u][1] = sa[u][2] = ea[u][0] = ea[u][1] = ea[u][2] = 0.0f;
+    int seg = w.s0, off = 0, done = 0;
+    while (seg < w.s1) {
+      __syncthreads();
+      // fill up to TS slots from consecutive segments (the same walk in every thread)
+      int filled = 0;
+      while (filled < TS && seg < w.s1) {
+        const int2 sg = segs[seg];
+        const int take = min(sg.y - off, TS - filled);
+        for (int l = threadIdx.x; l < take; l += NTH) {
+          const int s = sg.x + off + l;
+          const float4 ph = shi[s], pl = slo[s], q = sq[s];
+          ssx[filled + l] = (oh.x - ph.x) + (ol.x - pl.x);
+          ssy[filled + l] = (oh.y - ph.y) + (ol.y - pl.y);
+          ssz[filled + l] = (oh.z - ph.z) + (ol.z - pl.z);
+          srx[filled + l] = q.x;
+          sry[filled + l] = q.y;
+          srz[filled + l] = q.z;
+          spid[filled + l] = __float_as_int(ph.w);
+        }
+        filled += take;
+        off += take;
+        if (off >= sg.y) {
+          ++seg;
+          off = 0;
+        }
+      }
+      const int cnt4 = (filled + 3) & ~3;
+      for (int l = filled + threadIdx.x; l < cnt4; l += NTH) {
+        ssx[l] = ssy[l] = ssz[l] = 1.0e4f;
+        srx[l] = sry[l] = srz[l] = 0.0f;
+        spid[l] = -2;
+      }
+      __syncthreads();
+      float2 p[NT][3];
+#pragma unroll
+      for (int u = 0; u < NT; ++u) p[u][0] = p[u][1] = p[u][2] = f2(0.0f, 0.0f);
+      if (done < w.nmask)
+        pair_tile32x2<KIND, true, NT>(ssx, ssy, ssz, srx, sry, srz, spid, cnt4, xt, nt, pt, p);
+      else
+        pair_tile32x2<KIND, false, NT>(ssx, ssy, ssz, srx, sry, srz, spid, cnt4, xt, nt, pt, p);
+      done += filled;
+#pragma unroll
+      for (int u = 0; u < NT; ++u)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) two_sum_acc(sa[u][c], ea[u][c], p[u][c].x + p[u][c].y);
+    }
+    const double sc = KIND == 0 ? kTractionScale : kStokesletScale;
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      if (!valid[u]) continue;
+      const long long t = w.t0 + threadIdx.x + NTH * u;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) atomicAdd(y + 3 * t + c, sc * ((double)sa[u][c] + (double)ea[u][c]));
+    }
+  }
+}
+
+template <typename T>
+Status upload_vec(DevBuf<T>& buf, const std::vector<T>& host, cudaStream_t s) {
+  RBS_TRY(buf.alloc(std::max<size_t>(1, host.size())));
+  if (!host.empty())
+    RBS_CUDA_TRY(cudaMemcpyAsync(buf.ptr, host.data(), sizeof(T) * host.size(), cudaMemcpyHostToDevice, s));
+  return Status::Ok();
+}
+
+// Host octree cell.
+struct HCell {
+  int pb = 0, pe = 0;          // particles order[pb, pe)
+  double lo[3], hi[3], cen[3];
+  double r = 0.0;
+  long long nodes = 0;
+  int kid[8];
+  int nkid = 0;
+  int used = -1;               // index among the cells with proxy points
+};
+
+struct TreeBuilder {
+  const Context& c;
+  const std::vector<double>& pbox;
+  std::vector<int>& order;
+  std::vector<HCell>& cells;
+  std::vector<int>& leaf_of;
+
+  int build(int pb, int pe, int depth) {
+    HCell h;
+    h.pb = pb;
+    h.pe = pe;
+    for (int d = 0; d < 3; ++d) {
+      h.lo[d] = INFINITY;
+      h.hi[d] = -INFINITY;
+    }
+    for (int q = pb; q < pe; ++q) {
+      const int j = order[q];
+      for (int d = 0; d < 3; ++d) {
+        h.lo[d] = std::min(h.lo[d], pbox[6 * (size_t)j + d]);
+        h.hi[d] = std::max(h.hi[d], pbox[6 * (size_t)j + 3 + d]);
+      }
+      h.nodes += c.offset[j + 1] - c.offset[j];
+    }
+    for (int d = 0; d < 3; ++d) h.cen[d] = 0.5 * (h.lo[d] + h.hi[d]);
+    for (int q = pb; q < pe; ++q) {
+      const int j = order[q];
+      const double dx = c.centres[3 * j] - h.cen[0], dy = c.centres[3 * j + 1] - h.cen[1],
+                   dz = c.centres[3 * j + 2] - h.cen[2];
+      h.r = std::max(h.r, std::sqrt(dx * dx + dy * dy + dz * dz) + c.shapes[c.shape_of[j]].radius);
+    }
+    const int id = (int)cells.size();
+    cells.push_back(h);
+    if (pe - pb > 1 && depth < 64) {
+      double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int q = pb; q < pe; ++q)
+        for (int d = 0; d < 3; ++d) {
+          clo[d] = std::min(clo[d], c.centres[3 * order[q] + d]);
+          chi[d] = std::max(chi[d], c.centres[3 * order[q] + d]);
+        }
+      double mid[3];
+      for (int d = 0; d < 3; ++d) mid[d] = 0.5 * (clo[d] + chi[d]);
+      // stable partition by octant (x the low bit), keeping ascending particle order in each
+      std::vector<int> oct(pe - pb);
+      int count[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int q = pb; q < pe; ++q) {
+        const int j = order[q];
+        const int o = (c.centres[3 * j] > mid[0] ? 1 : 0) + (c.centres[3 * j + 1] > mid[1] ? 2 : 0) +
+                      (c.centres[3 * j + 2] > mid[2] ? 4 : 0);
+        oct[q - pb] = o;
+        ++count[o];
+      }
+      int groups = 0;
+      for (int o = 0; o < 8; ++o) groups += count[o] > 0;
+      if (groups > 1) {
+        int start[8];
+        int acc = pb;
+        for (int o = 0; o < 8; ++o) {
+          start[o] = acc;
+          acc += count[o];
+        }
+        std::vector<int> tmp(pe - pb);
+        int pos[8];
+        for (int o = 0; o < 8; ++o) pos[o] = start[o] - pb;
+        for (int q = pb; q < pe; ++q) tmp[pos[oct[q - pb]]++] = order[q];
+        std::copy(tmp.begin(), tmp.end(), order.begin() + pb);
+        int kids[8], nk = 0;
+        for (int o = 0; o < 8; ++o)
+          if (count[o] > 0) kids[nk++] = build(start[o], start[o] + count[o], depth + 1);
+        for (int k = 0; k < nk; ++k) cells[id].kid[k] = kids[k];
+        cells[id].nkid = nk;
+        return id;
+      }
+    }
+    for (int q = pb; q < pe; ++q) leaf_of[order[q]] = id;
+    return id;
+  }
+};
+
+}  // namespace
+
+void TreeState::release() {
+  active = false;
+  n_cells = 0;
+  n_src = 0;
+  items.clear();
+  segs.clear();
+  charge_items.clear();
+  for (DevBuf<float4>* b : {&d_hi, &d_lo, &d_q}) b->release();
+  d_items.release();
+  d_segs.release();
+  d_charge_items.release();
+  d_order.release();
+  d_box.release();
+  d_cheb.release();
+  d_pbox.release();
+  direct_pairs = proxy_pairs = charge_work = 0;
+}
+
+double f32_operator_error(const Context& c) {
+  constexpr double kF32OperatorError = 1e-5;  // float32 rounding of one apply (measured: a few 1e-7)
+  if (!c.tree.active) return kF32OperatorError;
+  // empirical model of the treecode's relative error: C(theta) rho^-n with rho the Bernstein ellipse
+  // parameter 1/theta + sqrt(1/theta^2 - 1) and C = 0.25 max(1, (theta / 0.5)^2)
+  const double th = c.tree.theta, a = 1.0 / th;
+  const double C = 0.25 * std::max(1.0, (th / 0.5) * (th / 0.5));
+  return kF32OperatorError + C * std::pow(a + std::sqrt(a * a - 1.0), -c.tree.degree);
+}
+
+Status build_far_field(Context& c) {
+  TreeState& T = c.tree;
+  c.stats.tree_pairs = c.stats.tree_proxy_pairs = 0;
+  c.stats.tree_cells = 0;
+  if (c.opt.far_field != RBS_FAR_TREECODE || c.opt.precision != RBS_PREC_MIXED || c.n == 0) {
+    T.release();
+    return Status::Ok();
+  }
+  cudaStream_t s = c.stream;
+  const int n = c.n;
+  const int degree = c.opt.tree_degree, nq = degree + 1, npx = nq * nq * nq;
+  T.degree = degree;
+  T.npx = npx;
+  T.theta = c.opt.tree_theta;
+
+  // 1. node bounding boxes of the particles
+  RBS_TRY(T.d_pbox.alloc(6 * (size_t)n));
+  k_particle_boxes<<<n, 128, 0, s>>>(n, c.d_offset.ptr, c.d_x.ptr, T.d_pbox.ptr);
+  RBS_CUDA_TRY(cudaGetLastError());
+  std::vector<double> pbox(6 * (size_t)n);
+  RBS_CUDA_TRY(cudaMemcpyAsync(pbox.data(), T.d_pbox.ptr, sizeof(double) * pbox.size(), cudaMemcpyDeviceToHost, s));
+  RBS_CUDA_TRY(cudaStreamSynchronize(s));
+
+  // 2. one octree per suspension (particles of a suspension are contiguous)
+  std::vector<int> order(n), leaf_of(n, -1), root_of(n, -1);
+  std::vector<HCell> cells;
+  cells.reserve(2 * (size_t)n + 8);
+  TreeBuilder tb{c, pbox, order, cells, leaf_of};
+  for (int a = 0; a < n;) {
+    int e = a + 1;
+    while (e < n && c.sid[e] == c.sid[a]) ++e;
+    for (int q = a; q < e; ++q) order[q] = q;
+    const int root = tb.build(a, e, 0);
+    for (int q = a; q < e; ++q) root_of[q] = root;
+    a = e;
+  }
+
+  // 3. interaction lists and source segments per target particle
+  const long long N = c.N;
+  std::vector<std::vector<int2>> seg_of(n);
+  std::vector<long long> proxy_src(n, 0);
+  int n_used = 0;
+  std::vector<int> used_cells;
+  std::vector<int> stack;
+  for (int i = 0; i < n; ++i) {
+    const HCell& B = cells[leaf_of[i]];
+    std::vector<int2>& L = seg_of[i];
+    const int np_i = (int)(c.offset[i + 1] - c.offset[i]);
+    L.push_back(make_int2((int)c.offset[i], np_i));
+    std::vector<int> approx;
+    stack.clear();
+    stack.push_back(root_of[i]);
+    while (!stack.empty()) {
+      const int id = stack.back();
+      stack.pop_back();
+      const HCell& C = cells[id];
+      const double dx = B.cen[0] - C.cen[0], dy = B.cen[1] - C.cen[1], dz = B.cen[2] - C.cen[2];
+      const double d = std::sqrt(dx * dx + dy * dy + dz * dz);
+      const double rr = B.r + C.r;
+      if (rr < T.theta * d && d >= rr + c.opt.near_delta && (long long)npx < C.nodes) {
+        approx.push_back(id);
+      } else if (C.nkid > 0) {
+        for (int k = C.nkid - 1; k >= 0; --k) stack.push_back(C.kid[k]);
+      } else {
+        for (int q = C.pb; q < C.pe; ++q) {
+          const int j = order[q];
+          if (j != i) L.push_back(make_int2((int)c.offset[j], (int)(c.offset[j + 1] - c.offset[j])));
+        }
+      }
+    }
+    for (int id : approx) {
+      if (cells[id].used < 0) {
+        cells[id].used = n_used++;
+        used_cells.push_back(id);
+      }
+      const long long first = N + (long long)cells[id].used * npx;
+      if (first + npx > INT_MAX) return Status::Err(RBS_ENOMEM, "treecode: more than 2^31 sources");
+      L.push_back(make_int2((int)first, npx));
+      proxy_src[i] += npx;
+    }
+  }
+  T.n_cells = n_used;
+  T.n_src = N + (long long)n_used * npx;
+  if (T.n_src > INT_MAX) return Status::Err(RBS_ENOMEM, "treecode: more than 2^31 sources");
+
+  // 4. work items: 128-target tiles of each particle times runs of its segments, split so that the
+  // grid has about 96 items per SM
+  long long tiles = 0;
+  for (int i = 0; i < n; ++i) tiles += (c.offset[i + 1] - c.offset[i] + kTreeTargets - 1) / kTreeTargets;
+  const long long want = 96LL * std::max(1, c.sm_count);
+  const int splits = (int)std::max(1LL, (want + tiles - 1) / std::max(1LL, tiles));
+  T.items.clear();
+  T.segs.clear();
+  T.direct_pairs = T.proxy_pairs = 0;
+  for (int i = 0; i < n; ++i) {
+    const std::vector<int2>& L = seg_of[i];
+    const int base = (int)T.segs.size();
+    T.segs.insert(T.segs.end(), L.begin(), L.end());
+    long long total = 0;
+    for (const int2& g : L) total += g.y;
+    const int chunks = (int)std::min<long long>(splits, std::max(1LL, total / 2048));
+    // cut points at segment boundaries, each run about total / chunks sources
+    std::vector<int> cut = {0};
+    long long acc = 0;
+    for (int k = 0; k < (int)L.size(); ++k) {
+      acc += L[k].y;
+      const int runs = (int)cut.size();
+      if (runs < chunks && k + 1 < (int)L.size() && acc * chunks >= total * runs) cut.push_back(k + 1);
+    }
+    cut.push_back((int)L.size());
+    const int np_i = (int)(c.offset[i + 1] - c.offset[i]);
+    for (int t0 = (int)c.offset[i]; t0 < (int)c.offset[i + 1]; t0 += kTreeTargets) {
+      const int t1 = std::min(t0 + kTreeTargets, (int)c.offset[i + 1]);
+      for (size_t r = 0; r + 1 < cut.size(); ++r) {
+        TreeItem it{};
+        it.t0 = t0;
+        it.t1 = t1;
+        it.s0 = base + cut[r];
+        it.s1 = base + cut[r + 1];
+        it.nmask = r == 0 ? np_i : 0;
+        T.items.push_back(it);
+      }
+    }
+    T.direct_pairs += (long long)np_i * (total - proxy_src[i]);
+    T.proxy_pairs += (long long)np_i * proxy_src[i];
+  }
+
+  // 5. cluster boxes, proxy points and charge blocks
+  std::vector<double> box(6 * (size_t)std::max(1, n_used));
+  std::vector<float4> phi((size_t)n_used * npx), plo((size_t)n_used * npx);
+  std::vector<float> cheb(2 * (size_t)nq);
+  for (int k = 0; k < nq; ++k) {
+    cheb[k] = (float)std::cos(k * kPi / degree);
+    cheb[nq + k] = (float)(((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == degree) ? 0.5 : 1.0));
+  }
+  std::vector<int> corder;
+  T.charge_items.clear();
+  T.charge_work = 0;
+  int proxy_pid;
+  {
+    const int v = kProxyPid;
+    std::memcpy(&proxy_pid, &v, sizeof(int));
+  }
+  float proxy_w;
+  std::memcpy(&proxy_w, &proxy_pid, sizeof(float));
+  for (int u = 0; u < n_used; ++u) {
+    const HCell& C = cells[used_cells[u]];
+    double mid[3], half[3];
+    for (int d = 0; d < 3; ++d) {
+      mid[d] = 0.5 * (C.lo[d] + C.hi[d]);
+      half[d] = 0.5 * (C.hi[d] - C.lo[d]);
+      box[6 * (size_t)u + d] = mid[d];
+      box[6 * (size_t)u + 3 + d] = half[d] > 0.0 ? 1.0 / half[d] : 0.0;
+    }
+    for (int a = 0; a < nq; ++a)
+      for (int b = 0; b < nq; ++b)
+        for (int e = 0; e < nq; ++e) {
+          const double v[3] = {mid[0] + half[0] * std::cos(a * kPi / degree), mid[1] + half[1] * std::cos(b * kPi / degree),
+                               mid[2] + half[2] * std::cos(e * kPi / degree)};
+          float h[3], l[3];
+          for (int d = 0; d < 3; ++d) {
+            h[d] = (float)v[d];
+            l[d] = (float)(v[d] - (double)h[d]);
+          }
+          const size_t k = (size_t)u * npx + ((size_t)a * nq + b) * nq + e;
+          phi[k] = make_float4(h[0], h[1], h[2], proxy_w);
+          plo[k] = make_float4(l[0], l[1], l[2], 0.0f);
+        }
+    // charge blocks over the cell's particles, about 4,096 nodes each
+    int q = C.pb;
+    while (q < C.pe) {
+      const int first = (int)corder.size();
+      long long nodes = 0;
+      while (q < C.pe && (nodes == 0 || nodes + (c.offset[order[q] + 1] - c.offset[order[q]]) <= 4096)) {
+        nodes += c.offset[order[q] + 1] - c.offset[order[q]];
+        corder.push_back(order[q]);
+        ++q;
+      }
+      T.charge_items.push_back(make_int4(u, first, (int)corder.size(), 0));
+    }
+    T.charge_work += C.nodes * (long long)npx;
+  }
+
+  // 6. device copies
+  RBS_TRY(upload_vec(T.d_items, T.items, s));
+  RBS_TRY(upload_vec(T.d_segs, T.segs, s));
+  RBS_TRY(upload_vec(T.d_charge_items, T.charge_items, s));
+  RBS_TRY(upload_vec(T.d_order, corder, s));
+  RBS_TRY(upload_vec(T.d_box, box, s));
+  RBS_TRY(upload_vec(T.d_cheb, cheb, s));
+  RBS_TRY(T.d_hi.alloc(T.n_src));
+  RBS_TRY(T.d_lo.alloc(T.n_src));
+  RBS_TRY(T.d_q.alloc(T.n_src));
+  RBS_CUDA_TRY(cudaMemcpyAsync(T.d_hi.ptr, c.d_xhi.ptr, sizeof(float4) * N, cudaMemcpyDeviceToDevice, s));
+  RBS_CUDA_TRY(cudaMemcpyAsync(T.d_lo.ptr, c.d_xlo.ptr, sizeof(float4) * N, cudaMemcpyDeviceToDevice, s));
+  if (n_used > 0) {
+    RBS_CUDA_TRY(cudaMemcpyAsync(T.d_hi.ptr + N, phi.data(), sizeof(float4) * phi.size(), cudaMemcpyHostToDevice, s));
+    RBS_CUDA_TRY(cudaMemcpyAsync(T.d_lo.ptr + N, plo.data(), sizeof(float4) * plo.size(), cudaMemcpyHostToDevice, s));
+  }
+  // the host vectors above must outlive their copies
+  RBS_CUDA_TRY(cudaStreamSynchronize(s));
+  T.active = true;
+  c.stats.tree_pairs = T.direct_pairs + T.proxy_pairs;
+  c.stats.tree_proxy_pairs = T.proxy_pairs;
+  c.stats.tree_cells = n_used;
+  return Status::Ok();
+}
+
+Status apply_tree(Context& c, int kind, const double* x, double* y, int nt) {
+  TreeState& T = c.tree;
+  const long long N = c.N;
+  {
+    KernelTimer timer(c, RBS_KC_TREE);
+    k_tree_node_charges<<<cdiv(N, 256), 256, 0, c.stream>>>(N, c.d_x.ptr, x, T.d_q.ptr);
+    int launches = 1;
+    if (T.n_cells > 0) {
+      RBS_CUDA_TRY(cudaMemsetAsync(T.d_q.ptr + N, 0, sizeof(float4) * (size_t)T.n_cells * T.npx, c.stream));
+      k_tree_charges<<<(unsigned)T.charge_items.size(), kChargeThreads, 0, c.stream>>>(
+          T.d_charge_items.ptr, T.d_order.ptr, c.d_offset.ptr, c.d_x.ptr, T.d_q.ptr, T.d_box.ptr, T.d_cheb.ptr,
+          T.degree + 1, T.d_q.ptr + N);
+      launches = 2;
+    }
+    RBS_CUDA_TRY(cudaGetLastError());
+    timer.done((double)T.charge_work, launches);
+  }
+  const int items = (int)T.items.size();
+  if (items == 0) return Status::Ok();
+  KernelTimer timer(c, kind == 0 ? RBS_KC_PAIR_K32 : RBS_KC_PAIR_S32);
+#define RBS_TREE_ARGS items, T.d_items.ptr, T.d_segs.ptr, c.d_xhi.ptr, c.d_xlo.ptr, c.d_nrm32.ptr, T.d_hi.ptr, T.d_lo.ptr, \
+                      T.d_q.ptr, y
+  auto grid = [&](const void* k, int threads) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    return std::max(1, std::min(items, per_sm * std::max(1, c.sm_count)));
+  };
+  if (kind == 0) {
+    if (nt == 1)
+      k_tree32x2<0, 1><<<grid((const void*)k_tree32x2<0, 1>, 128), 128, 0, c.stream>>>(RBS_TREE_ARGS);
+    else if (nt == 4)
+      k_tree32x2<0, 4><<<grid((const void*)k_tree32x2<0, 4>, 32), 32, 0, c.stream>>>(RBS_TREE_ARGS);
+    else
+      k_tree32x2<0, 2><<<grid((const void*)k_tree32x2<0, 2>, 64), 64, 0, c.stream>>>(RBS_TREE_ARGS);
+  } else {
+    if (nt == 1)
+      k_tree32x2<1, 1><<<grid((const void*)k_tree32x2<1, 1>, 128), 128, 0, c.stream>>>(RBS_TREE_ARGS);
+    else if (nt == 4)
+      k_tree32x2<1, 4><<<grid((const void*)k_tree32x2<1, 4>, 32), 32, 0, c.stream>>>(RBS_TREE_ARGS);
+    else
+      k_tree32x2<1, 2><<<grid((const void*)k_tree32x2<1, 2>, 64), 64, 0, c.stream>>>(RBS_TREE_ARGS);
+  }
+#undef RBS_TREE_ARGS
+  RBS_CUDA_TRY(cudaGetLastError());
+  timer.done((double)(T.direct_pairs + T.proxy_pairs));
+  return Status::Ok();
+}
+
+}  // namespace rbs

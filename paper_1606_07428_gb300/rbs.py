@@ -81,7 +81,14 @@ class rbs_options(ctypes.Structure):
         ("contact_gap", ctypes.c_double),
         ("magnetic_field", ctypes.c_double * 3),
         ("mu_ratio", ctypes.c_double),
+        ("far_field", ctypes.c_int),
+        ("tree_theta", ctypes.c_double),
+        ("tree_degree", ctypes.c_int),
     ]
+
+
+RBS_FAR_DIRECT = 0
+RBS_FAR_TREECODE = 1
 
 
 RBS_KC_PAIR_K32 = 0
@@ -93,9 +100,11 @@ RBS_KC_NEAR = 5
 RBS_KC_PAIR_KDF = 6
 RBS_KC_PAIR_SDF = 7
 RBS_KC_PAIR_KSDF = 8
-RBS_KC_COUNT = 9
+RBS_KC_TREE = 9
+RBS_KC_COUNT = 10
 KERNEL_CLASSES = ["pair_traction_f32", "pair_stokeslet_f32", "pair_traction_f64", "pair_stokeslet_f64",
-                  "particle_blocks", "near_correction", "pair_traction_df", "pair_stokeslet_df", "pair_both_df"]
+                  "particle_blocks", "near_correction", "pair_traction_df", "pair_stokeslet_df", "pair_both_df",
+                  "tree_charges"]
 
 
 class rbs_stats(ctypes.Structure):
@@ -116,6 +125,9 @@ class rbs_stats(ctypes.Structure):
         ("kernel_units", ctypes.c_double * RBS_KC_COUNT),
         ("n_contacts", ctypes.c_int),
         ("pair_variant", ctypes.c_int * 5),
+        ("tree_pairs", ctypes.c_longlong),
+        ("tree_proxy_pairs", ctypes.c_longlong),
+        ("tree_cells", ctypes.c_int),
     ]
 
 

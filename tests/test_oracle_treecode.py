@@ -125,7 +125,7 @@ def test_vanishing_opening_angle_is_the_direct_sum(cloud):
 
 
 def test_error_falls_with_degree_inside_the_model(cloud):
-    """The model 0.25 rho^-n holds from degree 2 on (degree 1 exceeds it at theta >= 0.6)."""
+    """The model C(theta) rho^-n holds from degree 2 on (degree 1 exceeds it at theta >= 0.6)."""
     s = cloud
     x = suspensions.random_density(5, s.total_nodes)
     theta = 0.6
@@ -142,8 +142,9 @@ def test_error_falls_with_degree_inside_the_model(cloud):
 
 
 def test_error_bound_values():
-    """rho = 1/theta + sqrt(1/theta^2 - 1): theta = 0.5 gives 2 + sqrt(3)."""
+    """rho = 1/theta + sqrt(1/theta^2 - 1): theta = 0.5 gives 2 + sqrt(3), theta = 0.6 gives 3."""
     assert abs(tc.tree_error_bound(0.5, 7) - 0.25 * (2 + math.sqrt(3)) ** -7) < 1e-18
+    assert abs(tc.tree_error_bound(0.6, 4) - 0.36 / 81) < 1e-15
     assert tc.tree_error_bound(0.5, 8) < tc.tree_error_bound(0.5, 7) < tc.tree_error_bound(0.6, 7)
 
 
@@ -158,3 +159,16 @@ def test_offdiagonal_with_tree_matches_operator_when_exact(cloud):
     ref = s.apply_rows("K", x, nodes) - np.concatenate(
         [(s.self_block_lab("K", i) @ x[s.sl(i)].reshape(-1)).reshape(-1, 3) for i in range(len(s.particles))])[nodes]
     assert np.abs(full[nodes] - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_error_model_with_whole_particle_clusters():
+    """64 ellipsoids at p = 8 (144 nodes each): at degrees 3 and 4 single particles are approximated,
+    the hardest case for the model."""
+    s = system_of(suspensions.random_ellipsoids(64, 8, 16, 0.10, 0.2, seed=12))
+    x = suspensions.random_density(31, s.total_nodes)
+    ref = {k: tc.direct_smooth(s, k, x) for k in "KS"}
+    for theta, degree in ((0.5, 3), (0.6, 4), (0.7, 3)):
+        t = tc.Treecode(s, theta, degree)
+        for k in "KS":
+            e = np.linalg.norm(t.smooth(k, x) - ref[k]) / np.linalg.norm(ref[k])
+            assert e <= tc.tree_error_bound(theta, degree), (theta, degree, k, e)
