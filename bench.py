@@ -72,7 +72,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
     ap.add_argument("--pair-variant", type=int, default=0,
                     help="pair-kernel variant (rbs_options.pair_variant); 0 lets the library's autotuner choose")
-    ap.add_argument("--far-field", default="direct", choices=["direct", "tree"],
+    ap.add_argument("--far-field", default="tree", choices=["direct", "tree"],
                     help="float32 inner applies: direct sums over all node pairs, or the treecode "
                          "(rbs_options.far_field; double-float passes stay direct either way)")
     ap.add_argument("--experiment", default=None, choices=[None, "warmstart", "magnetic"],

@@ -151,6 +151,8 @@ struct TreeState {
   bool active = false;
   int degree = 0, npx = 0;   // interpolation degree and (degree + 1)^3 proxy points per cluster
   int n_cells = 0;           // clusters with proxy points
+  int tmax = 0;              // largest target count of a work item
+  int nt[2] = {0, 0};        // targets per thread chosen for (traction, Stokeslet), 0: not yet
   double theta = 0.0;
   long long n_src = 0;       // sources: N nodes, then n_cells * npx proxy points
   std::vector<TreeItem> items;
@@ -319,7 +321,7 @@ Status laplace_operator(Context& c, int kind, const double* x, double* y);
 // Builds (or clears) the treecode of the current geometry; called after the near-pair lists.
 Status build_far_field(Context& c);
 // y += the treecode's float32 smooth pair sum of kind (0 traction, 1 Stokeslet) for density x, with
-// nt targets per thread (1, 2 or 4).
+// nt targets per thread (1, 2 or 4; 0: the fastest, timed once per geometry).
 Status apply_tree(Context& c, int kind, const double* x, double* y, int nt);
 // Relative error assumed for a float32 operator application: rounding plus, with the treecode,
 // its approximation model C(theta) rho^-n.

@@ -1436,9 +1436,7 @@ Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y) {
   const int nw = (int)c.work.size();
   const bool f32 = (prec == RBS_PREC_MIXED);
   if (f32 && c.tree.active) {
-    // treecode in place of the direct float32 sum, with the direct kernel's targets per thread
-    const int nt = pair_variant(c, kind, prec, x);
-    RBS_TRY(apply_tree(c, kind, x, y, nt > kPacked ? nt - kPacked : 2));
+    RBS_TRY(apply_tree(c, kind, x, y, 0));  // treecode in place of the direct float32 sum
   } else if (nw > 0) {
     int cls = f32 ? (kind == 0 ? RBS_KC_PAIR_K32 : RBS_KC_PAIR_S32) : (kind == 0 ? RBS_KC_PAIR_K64 : RBS_KC_PAIR_S64);
     if (prec == RBS_PREC_DF) cls = kind == 0 ? RBS_KC_PAIR_KDF : RBS_KC_PAIR_SDF;

@@ -30,7 +30,7 @@ namespace rbs {
 namespace {
 
 constexpr int kTreeMaxQ = 11;        // degree <= 10
-constexpr int kTreeTargets = 128;    // targets per work item
+constexpr int kTreeMaxTargets = 512; // targets per work item at most
 constexpr int kProxyPid = -3;        // particle id carried by proxy points (never a target's)
 
 // Bounding box of each particle's nodes: lo (3) then hi (3) per particle.
@@ -181,14 +181,16 @@ __global__ void __launch_bounds__(kChargeThreads) k_tree_charges(const int4* __r
 // The treecode's pair sum: the packed float32 tile loop of the direct kernel (pairs32.cuh) over
 // source tiles filled from the item's segments.  Coordinates are relative to the item's first target;
 // tiles that may hold nodes of the targets' own particle (the first nmask sources) mask them by
-// particle id.
+// particle id.  The block size is chosen at launch so that blockDim.x * NT covers the largest item
+// (a whole particle where it fits), so a particle's targets share every staged tile.
 template <int KIND, int NT>
-__global__ void __launch_bounds__(128 / NT, NT == 4 ? 12 : (NT == 2 ? 10 : 8))
+__global__ void __launch_bounds__(kTreeMaxTargets / NT)
     k_tree32x2(int nitems, const TreeItem* __restrict__ items, const int2* __restrict__ segs,
                const float4* __restrict__ xhi, const float4* __restrict__ xlo, const float4* __restrict__ nrm32,
                const float4* __restrict__ shi, const float4* __restrict__ slo, const float4* __restrict__ sq,
                double* __restrict__ y) {
-  constexpr int TS = 512, NTH = 128 / NT;
+  constexpr int TS = 512;
+  const int NTH = blockDim.x;
   __shared__ __align__(16) float ssx[TS], ssy[TS], ssz[TS], srx[TS], sry[TS], srz[TS];
   __shared__ __align__(16) int spid[TS];
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -381,6 +383,8 @@ struct TreeBuilder {
 
 void TreeState::release() {
   active = false;
+  tmax = 0;
+  nt[0] = nt[1] = 0;
   n_cells = 0;
   n_src = 0;
   items.clear();
@@ -492,10 +496,46 @@ Status build_far_field(Context& c) {
   T.n_src = N + (long long)n_used * npx;
   if (T.n_src > INT_MAX) return Status::Err(RBS_ENOMEM, "treecode: more than 2^31 sources");
 
-  // 4. work items: 128-target tiles of each particle times runs of its segments, split so that the
-  // grid has about 96 items per SM
+  // 4. work items: target parts of each particle times runs of its segments, split so that the grid
+  // has about 96 items per SM.  A particle is one part where it has at most `cap` nodes, else
+  // near-equal parts; cap is the candidate (multiples of 32 up to 512, and the particle sizes up to
+  // 512) whose items waste the fewest thread slots when every block covers the largest part in
+  // steps of 32 targets (ties: the larger cap, fewer stagings per pair).
+  std::vector<int> caps;
+  for (int cap = 32; cap <= kTreeMaxTargets; cap += 32) caps.push_back(cap);
+  for (int i = 0; i < n; ++i) {
+    const int np_i = (int)(c.offset[i + 1] - c.offset[i]);
+    if (np_i <= kTreeMaxTargets) caps.push_back(np_i);
+  }
+  std::sort(caps.begin(), caps.end());
+  caps.erase(std::unique(caps.begin(), caps.end()), caps.end());
+  int cap = 128;
+  double best_eff = -1.0;
+  for (int cand : caps) {
+    long long parts = 0;
+    int tmax = 0;
+    for (int i = 0; i < n; ++i) {
+      const int np_i = (int)(c.offset[i + 1] - c.offset[i]);
+      const int k = (np_i + cand - 1) / cand;
+      parts += k;
+      tmax = std::max(tmax, (np_i + k - 1) / k);
+    }
+    const double eff = (double)N / ((double)parts * (double)((tmax + 31) / 32 * 32));
+    if (eff >= best_eff * (1.0 - 1e-12)) {
+      best_eff = eff;
+      cap = cand;
+    }
+  }
   long long tiles = 0;
-  for (int i = 0; i < n; ++i) tiles += (c.offset[i + 1] - c.offset[i] + kTreeTargets - 1) / kTreeTargets;
+  const int old_tmax = T.tmax;
+  T.tmax = 0;
+  for (int i = 0; i < n; ++i) {
+    const int np_i = (int)(c.offset[i + 1] - c.offset[i]);
+    const int k = (np_i + cap - 1) / cap;
+    tiles += k;
+    T.tmax = std::max(T.tmax, (np_i + k - 1) / k);
+  }
+  if (T.tmax != old_tmax) T.nt[0] = T.nt[1] = 0;  // the block shape changed: time the variants again
   const long long want = 96LL * std::max(1, c.sm_count);
   const int splits = (int)std::max(1LL, (want + tiles - 1) / std::max(1LL, tiles));
   T.items.clear();
@@ -518,8 +558,9 @@ Status build_far_field(Context& c) {
     }
     cut.push_back((int)L.size());
     const int np_i = (int)(c.offset[i + 1] - c.offset[i]);
-    for (int t0 = (int)c.offset[i]; t0 < (int)c.offset[i + 1]; t0 += kTreeTargets) {
-      const int t1 = std::min(t0 + kTreeTargets, (int)c.offset[i + 1]);
+    const int nparts = (np_i + cap - 1) / cap, psize = (np_i + nparts - 1) / nparts;
+    for (int t0 = (int)c.offset[i]; t0 < (int)c.offset[i + 1]; t0 += psize) {
+      const int t1 = std::min(t0 + psize, (int)c.offset[i + 1]);
       for (size_t r = 0; r + 1 < cut.size(); ++r) {
         TreeItem it{};
         it.t0 = t0;
@@ -615,6 +656,78 @@ Status build_far_field(Context& c) {
   return Status::Ok();
 }
 
+// Launch of the treecode pair sum over the first `items` work items with nt targets per thread,
+// blocks just large enough for the largest item.
+static Status launch_tree(Context& c, int kind, int nt, int items, double* y) {
+  TreeState& T = c.tree;
+  const int threads = ((T.tmax + nt - 1) / nt + 31) / 32 * 32;
+#define RBS_TREE_ARGS items, T.d_items.ptr, T.d_segs.ptr, c.d_xhi.ptr, c.d_xlo.ptr, c.d_nrm32.ptr, T.d_hi.ptr, T.d_lo.ptr, \
+                      T.d_q.ptr, y
+  auto grid = [&](const void* k) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    return std::max(1, std::min(items, per_sm * std::max(1, c.sm_count)));
+  };
+  if (kind == 0) {
+    if (nt == 1)
+      k_tree32x2<0, 1><<<grid((const void*)k_tree32x2<0, 1>), threads, 0, c.stream>>>(RBS_TREE_ARGS);
+    else if (nt == 4)
+      k_tree32x2<0, 4><<<grid((const void*)k_tree32x2<0, 4>), threads, 0, c.stream>>>(RBS_TREE_ARGS);
+    else
+      k_tree32x2<0, 2><<<grid((const void*)k_tree32x2<0, 2>), threads, 0, c.stream>>>(RBS_TREE_ARGS);
+  } else {
+    if (nt == 1)
+      k_tree32x2<1, 1><<<grid((const void*)k_tree32x2<1, 1>), threads, 0, c.stream>>>(RBS_TREE_ARGS);
+    else if (nt == 4)
+      k_tree32x2<1, 4><<<grid((const void*)k_tree32x2<1, 4>), threads, 0, c.stream>>>(RBS_TREE_ARGS);
+    else
+      k_tree32x2<1, 2><<<grid((const void*)k_tree32x2<1, 2>), threads, 0, c.stream>>>(RBS_TREE_ARGS);
+  }
+#undef RBS_TREE_ARGS
+  RBS_CUDA_TRY(cudaGetLastError());
+  return Status::Ok();
+}
+
+// Targets per thread of the treecode pair sum: rbs_options.pair_variant when set (its targets per
+// thread), otherwise the fastest of 1, 2 and 4 timed once per geometry and kind on a prefix of the
+// work items (the charges of the current apply as sources, into a scratch output).
+static int tree_variant(Context& c, int kind, const double* y_unused) {
+  (void)y_unused;
+  TreeState& T = c.tree;
+  if (c.opt.pair_variant > 0) {
+    const int v = c.opt.pair_variant > kPacked ? c.opt.pair_variant - kPacked : c.opt.pair_variant;
+    return (v == 1 || v == 4) ? v : 2;
+  }
+  if (T.nt[kind]) return T.nt[kind];
+  int best = 2;
+  const int items = std::min<int>((int)T.items.size(), 8 * std::max(1, c.sm_count));
+  double* scratch = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaMalloc(&scratch, sizeof(double) * 3 * c.N) == cudaSuccess && cudaEventCreate(&a) == cudaSuccess &&
+      cudaEventCreate(&b) == cudaSuccess) {
+    float best_ms = 1e30f;
+    for (int nt : {1, 2, 4}) {
+      if (((T.tmax + nt - 1) / nt + 31) / 32 * 32 > kTreeMaxTargets / nt) continue;  // block too large
+      if (!launch_tree(c, kind, nt, items, scratch).ok()) continue;  // warm
+      cudaEventRecord(a, c.stream);
+      if (!launch_tree(c, kind, nt, items, scratch).ok()) continue;
+      cudaEventRecord(b, c.stream);
+      float ms = 0.0f;
+      if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = nt;
+      }
+      c.stats.launches += 2;
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (scratch) cudaFree(scratch);
+  cudaGetLastError();
+  T.nt[kind] = best;
+  return best;
+}
+
 Status apply_tree(Context& c, int kind, const double* x, double* y, int nt) {
   TreeState& T = c.tree;
   const long long N = c.N;
@@ -634,30 +747,9 @@ Status apply_tree(Context& c, int kind, const double* x, double* y, int nt) {
   }
   const int items = (int)T.items.size();
   if (items == 0) return Status::Ok();
+  if (nt <= 0) nt = tree_variant(c, kind, y);
   KernelTimer timer(c, kind == 0 ? RBS_KC_PAIR_K32 : RBS_KC_PAIR_S32);
-#define RBS_TREE_ARGS items, T.d_items.ptr, T.d_segs.ptr, c.d_xhi.ptr, c.d_xlo.ptr, c.d_nrm32.ptr, T.d_hi.ptr, T.d_lo.ptr, \
-                      T.d_q.ptr, y
-  auto grid = [&](const void* k, int threads) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
-    return std::max(1, std::min(items, per_sm * std::max(1, c.sm_count)));
-  };
-  if (kind == 0) {
-    if (nt == 1)
-      k_tree32x2<0, 1><<<grid((const void*)k_tree32x2<0, 1>, 128), 128, 0, c.stream>>>(RBS_TREE_ARGS);
-    else if (nt == 4)
-      k_tree32x2<0, 4><<<grid((const void*)k_tree32x2<0, 4>, 32), 32, 0, c.stream>>>(RBS_TREE_ARGS);
-    else
-      k_tree32x2<0, 2><<<grid((const void*)k_tree32x2<0, 2>, 64), 64, 0, c.stream>>>(RBS_TREE_ARGS);
-  } else {
-    if (nt == 1)
-      k_tree32x2<1, 1><<<grid((const void*)k_tree32x2<1, 1>, 128), 128, 0, c.stream>>>(RBS_TREE_ARGS);
-    else if (nt == 4)
-      k_tree32x2<1, 4><<<grid((const void*)k_tree32x2<1, 4>, 32), 32, 0, c.stream>>>(RBS_TREE_ARGS);
-    else
-      k_tree32x2<1, 2><<<grid((const void*)k_tree32x2<1, 2>, 64), 64, 0, c.stream>>>(RBS_TREE_ARGS);
-  }
-#undef RBS_TREE_ARGS
+  RBS_TRY(launch_tree(c, kind, nt, items, y));
   RBS_CUDA_TRY(cudaGetLastError());
   timer.done((double)(T.direct_pairs + T.proxy_pairs));
   return Status::Ok();
