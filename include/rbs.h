@@ -158,8 +158,9 @@ typedef struct {
                                             block entries read (particle blocks) */
   int n_contacts;        /* contacts found by the last mobility solve (rbs_options.contact_gap > 0) */
   int pair_variant[5];   /* variant in use (as rbs_options.pair_variant): float32 traction, float32
-                            Stokeslet, double-float traction, double-float Stokeslet, fused
-                            double-float traction and Stokeslet (0 = not yet chosen) */
+                            Stokeslet (the treecode kernel's with RBS_FAR_TREECODE), double-float
+                            traction, double-float Stokeslet, fused double-float traction and
+                            Stokeslet (0 = not yet chosen) */
   long long tree_pairs;  /* RBS_FAR_TREECODE: (target node, source) pairs one treecode apply evaluates,
                             direct node pairs (the target's own particle included, masked) plus
                             proxy pairs; 0 without a treecode */

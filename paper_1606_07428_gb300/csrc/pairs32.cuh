@@ -60,7 +60,9 @@ __device__ __forceinline__ void pair2_f32(float2 sx, float2 sy, float2 sz, float
   }
 }
 
-template <int KIND, bool MASK, int NT>
+// Targets u < NU of the thread's NT (the rest of the arrays untouched): a warp whose later target
+// slots are all empty skips them.
+template <int KIND, bool MASK, int NT, int NU = NT>
 __device__ __forceinline__ void pair_tile32x2(const float* __restrict__ ssx, const float* __restrict__ ssy,
                                               const float* __restrict__ ssz, const float* __restrict__ srx,
                                               const float* __restrict__ sry, const float* __restrict__ srz,
@@ -74,7 +76,7 @@ __device__ __forceinline__ void pair_tile32x2(const float* __restrict__ ssx, con
     int4 pp = make_int4(-1, -1, -1, -1);
     if (MASK) pp = *reinterpret_cast<const int4*>(spid + l);
 #pragma unroll
-    for (int u = 0; u < NT; ++u) {
+    for (int u = 0; u < NU; ++u) {
       pair2_f32<KIND, MASK>(f2(ax.x, ax.y), f2(ay.x, ay.y), f2(az.x, az.y), f2(bx.x, bx.y), f2(by.x, by.y),
                             f2(bz.x, bz.y), make_int2(pp.x, pp.y), xt[u], nt[u], pt[u], acc[u]);
       pair2_f32<KIND, MASK>(f2(ax.z, ax.w), f2(ay.z, ay.w), f2(az.z, az.w), f2(bx.z, bx.w), f2(by.z, by.w),

@@ -225,6 +225,9 @@ __global__ void __launch_bounds__(kTreeMaxTargets / NT)
     float sa[NT][3], ea[NT][3];
 #pragma unroll
     for (int u = 0; u < NT; ++u) sa[u][0] = sa[u][1] = sa[u][2] = ea[u][0] = ea[u][1] = ea[u][2] = 0.0f;
+    // target slots of this warp that hold a target: u < nu for lane 0 (the warp's last slot may be
+    // partly empty; later slots are skipped, so a ragged particle costs whole warps only where it fills them)
+    const int nu = min(NT, max(0, (w.t1 - w.t0 - (int)(threadIdx.x & ~31u) + NTH - 1) / NTH));
     int seg = w.s0, off = 0, done = 0;
     while (seg < w.s1) {
       __syncthreads();
@@ -261,10 +264,23 @@ __global__ void __launch_bounds__(kTreeMaxTargets / NT)
       float2 p[NT][3];
 #pragma unroll
       for (int u = 0; u < NT; ++u) p[u][0] = p[u][1] = p[u][2] = f2(0.0f, 0.0f);
-      if (done < w.nmask)
-        pair_tile32x2<KIND, true, NT>(ssx, ssy, ssz, srx, sry, srz, spid, cnt4, xt, nt, pt, p);
-      else
-        pair_tile32x2<KIND, false, NT>(ssx, ssy, ssz, srx, sry, srz, spid, cnt4, xt, nt, pt, p);
+#define RBS_TILE(NUV)                                                                              \
+  do {                                                                                             \
+    if (done < w.nmask)                                                                            \
+      pair_tile32x2<KIND, true, NT, NUV>(ssx, ssy, ssz, srx, sry, srz, spid, cnt4, xt, nt, pt, p);  \
+    else                                                                                           \
+      pair_tile32x2<KIND, false, NT, NUV>(ssx, ssy, ssz, srx, sry, srz, spid, cnt4, xt, nt, pt, p); \
+  } while (0)
+      if (nu == NT) {
+        RBS_TILE(NT);
+      } else if constexpr (NT > 1) {
+        if (nu == 1) RBS_TILE(1);
+        if constexpr (NT > 2) {
+          if (nu == 2) RBS_TILE(2);
+          if (nu == 3) RBS_TILE(3);
+        }
+      }
+#undef RBS_TILE
       done += filled;
 #pragma unroll
       for (int u = 0; u < NT; ++u)
