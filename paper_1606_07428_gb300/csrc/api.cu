@@ -483,7 +483,7 @@ int rbs_get_stats(rbs_ctx* h, rbs_stats* out) {
   *out = c.stats;
   for (int k = 0; k < 5; ++k) out->pair_variant[k] = c.tuned[k];
   for (int k = 0; k < 2; ++k)  // the float32 sums run in the treecode kernel when it is on
-    if (c.tree.active) out->pair_variant[k] = c.tree.nt[k] ? kPacked + c.tree.nt[k] : 0;
+    if (c.tree.active) out->pair_variant[k] = c.tree.nt[k] ? rbs::kPacked + c.tree.nt[k] : 0;
   return RBS_OK;
 }
 
