@@ -530,8 +530,9 @@ def run_warmstart_experiment(args):
     susp = suspensions.WORKLOADS[args.workload]()
     tol = args.tol or 1e-8
     prec = rbs.RBS_PREC_MIXED
+    far = rbs.RBS_FAR_TREECODE if args.far_field == "tree" else rbs.RBS_FAR_DIRECT
     with rbs.Context(device=0, precision=prec, warm_start=rbs.RBS_WARM_PREVIOUS, warm_record=1,
-                     stream=stream.cuda_stream) as ctx:
+                     stream=stream.cuda_stream, far_field=far) as ctx:
         ctx.set_suspension(susp)
         t0 = time.perf_counter()
         its_train = rbs.rbs_advance(ctx.ctx, susp.F, susp.T, args.dt, args.train_steps, rbs.RBS_RK4, tol)
@@ -546,7 +547,7 @@ def run_warmstart_experiment(args):
     finals = {}
     for mode in ("ZERO", "PREVIOUS", "LEARNED"):
         with rbs.Context(device=0, precision=prec, warm_start=getattr(rbs, "RBS_WARM_" + mode),
-                         stream=stream.cuda_stream) as ctx:
+                         stream=stream.cuda_stream, far_field=far) as ctx:
             ctx.set_geometry(susp.semi_axes, susp.p, susp.nphi, cen, quat)
             if mode == "LEARNED":
                 rbs.rbs_warmstart_weights(ctx.ctx, params, scale=scale)
@@ -565,7 +566,7 @@ def run_warmstart_experiment(args):
                                  "ms": ms}
     drift = {m: float(np.abs(finals[m] - finals["ZERO"]).max()) for m in finals}
     line = {"experiment": "learned warm start in RK4 sedimentation", "workload": susp.name, "n_particles": susp.n,
-            "nodes": susp.total_nodes, "precision": "mixed", "tol": tol, "dt": args.dt,
+            "nodes": susp.total_nodes, "precision": "mixed", "far_field": args.far_field, "tol": tol, "dt": args.dt,
             "train_steps": args.train_steps, "train_samples": 4 * args.train_steps * susp.n,
             "train_iterations_per_solve": its_train / (4 * args.train_steps),
             "train_solve_seconds": t_train_solves, "epochs": args.epochs, "train_seconds": t_train,
@@ -595,8 +596,9 @@ def run_magnetic_experiment(args):
     tol = args.tol or 1e-8
     out = {}
     for prec in ("FP64", "MIXED"):
+        far = rbs.RBS_FAR_TREECODE if (args.far_field == "tree" and prec == "MIXED") else rbs.RBS_FAR_DIRECT
         with rbs.Context(device=0, precision=getattr(rbs, "RBS_PREC_" + prec), magnetic_field=tuple(H0),
-                         mu_ratio=2.0, timing=1) as ctx:
+                         mu_ratio=2.0, timing=1, far_field=far) as ctx:
             ctx.set_geometry(np.ones((n, 3)), 8, 16, cen, quats)
             t0 = time.perf_counter()
             F, T, q, its_m = rbs.rbs_magnetic_forces(ctx.ctx, H0, 2.0, tol, n, 9 * 16 * n)
@@ -616,7 +618,8 @@ def run_magnetic_experiment(args):
                                  "mobility_gmres_iterations": its_s, "rk4_step_s": t_step, "rk4_steps": steps,
                                  "max_force": float(np.abs(F).max())}
     line = {"experiment": "magnetorheological spheres (Fig. 1 set-up)", "n_particles": n, "p": 8,
-            "unknowns": 4 * 9 * 16 * n, "tol": tol, "H0": H0.tolist(), "mu_ratio": 2.0, "results": out,
+            "unknowns": 4 * 9 * 16 * n, "tol": tol, "H0": H0.tolist(), "mu_ratio": 2.0,
+            "far_field": f"{args.far_field} (mixed-precision stages)", "results": out,
             "paper_context": "about 5 minutes per time step on one Xeon E5-2690 v2 node with FMM (Fig. 1 caption)"}
     print(json.dumps(line), flush=True)
 
