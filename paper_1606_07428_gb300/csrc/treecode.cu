@@ -189,10 +189,11 @@ __global__ void __launch_bounds__(kTreeMaxTargets / NT)
                const float4* __restrict__ xhi, const float4* __restrict__ xlo, const float4* __restrict__ nrm32,
                const float4* __restrict__ shi, const float4* __restrict__ slo, const float4* __restrict__ sq,
                double* __restrict__ y) {
-  constexpr int TS = 512;
+  constexpr int TS = 1024;  // sources per tile: fewer block barriers per pair
   const int NTH = blockDim.x;
   __shared__ __align__(16) float ssx[TS], ssy[TS], ssz[TS], srx[TS], sry[TS], srz[TS];
   __shared__ __align__(16) int spid[TS];
+  __shared__ int sidx[TS];  // source of each slot, written and read by the slot's own thread
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const TreeItem w = items[it];
     const float4 oh = xhi[w.t0], ol = xlo[w.t0];
@@ -231,28 +232,34 @@ __global__ void __launch_bounds__(kTreeMaxTargets / NT)
     int seg = w.s0, off = 0, done = 0;
     while (seg < w.s1) {
       __syncthreads();
-      // fill up to TS slots from consecutive segments (the same walk in every thread)
+      // fill up to TS slots from consecutive segments: first the source index of each of this
+      // thread's slots (l = threadIdx.x mod NTH) from the same walk in every thread, then all of
+      // its loads at once, so a tile costs one memory latency rather than one per segment
       int filled = 0;
       while (filled < TS && seg < w.s1) {
         const int2 sg = segs[seg];
         const int take = min(sg.y - off, TS - filled);
-        for (int l = threadIdx.x; l < take; l += NTH) {
-          const int s = sg.x + off + l;
-          const float4 ph = shi[s], pl = slo[s], q = sq[s];
-          ssx[filled + l] = (oh.x - ph.x) + (ol.x - pl.x);
-          ssy[filled + l] = (oh.y - ph.y) + (ol.y - pl.y);
-          ssz[filled + l] = (oh.z - ph.z) + (ol.z - pl.z);
-          srx[filled + l] = q.x;
-          sry[filled + l] = q.y;
-          srz[filled + l] = q.z;
-          spid[filled + l] = __float_as_int(ph.w);
-        }
+        int l = threadIdx.x;
+        if (l < filled) l += ((filled - l + NTH - 1) / NTH) * NTH;  // first own slot >= filled
+        for (; l < filled + take; l += NTH) sidx[l] = sg.x + off + (l - filled);
         filled += take;
         off += take;
         if (off >= sg.y) {
           ++seg;
           off = 0;
         }
+      }
+#pragma unroll 4
+      for (int l = threadIdx.x; l < filled; l += NTH) {
+        const int s = sidx[l];
+        const float4 ph = shi[s], pl = slo[s], q = sq[s];
+        ssx[l] = (oh.x - ph.x) + (ol.x - pl.x);
+        ssy[l] = (oh.y - ph.y) + (ol.y - pl.y);
+        ssz[l] = (oh.z - ph.z) + (ol.z - pl.z);
+        srx[l] = q.x;
+        sry[l] = q.y;
+        srz[l] = q.z;
+        spid[l] = __float_as_int(ph.w);
       }
       const int cnt4 = (filled + 3) & ~3;
       for (int l = filled + threadIdx.x; l < cnt4; l += NTH) {
