@@ -609,13 +609,12 @@ Status build_far_field(Context& c) {
   std::vector<int> corder;
   T.charge_items.clear();
   T.charge_work = 0;
-  int proxy_pid;
+  // proxy points carry kProxyPid in the w bits of their hi position, like a node's particle id
+  float proxy_w;
   {
     const int v = kProxyPid;
-    std::memcpy(&proxy_pid, &v, sizeof(int));
+    std::memcpy(&proxy_w, &v, sizeof(float));
   }
-  float proxy_w;
-  std::memcpy(&proxy_w, &proxy_pid, sizeof(float));
   for (int u = 0; u < n_used; ++u) {
     const HCell& C = cells[used_cells[u]];
     double mid[3], half[3];
@@ -714,8 +713,7 @@ static Status launch_tree(Context& c, int kind, int nt, int items, double* y) {
 // Targets per thread of the treecode pair sum: rbs_options.pair_variant when set (its targets per
 // thread), otherwise the fastest of 1, 2 and 4 timed once per geometry and kind on a prefix of the
 // work items (the charges of the current apply as sources, into a scratch output).
-static int tree_variant(Context& c, int kind, const double* y_unused) {
-  (void)y_unused;
+static int tree_variant(Context& c, int kind) {
   TreeState& T = c.tree;
   if (c.opt.pair_variant > 0) {
     const int v = c.opt.pair_variant > kPacked ? c.opt.pair_variant - kPacked : c.opt.pair_variant;
@@ -770,7 +768,7 @@ Status apply_tree(Context& c, int kind, const double* x, double* y, int nt) {
   }
   const int items = (int)T.items.size();
   if (items == 0) return Status::Ok();
-  if (nt <= 0) nt = tree_variant(c, kind, y);
+  if (nt <= 0) nt = tree_variant(c, kind);
   KernelTimer timer(c, kind == 0 ? RBS_KC_PAIR_K32 : RBS_KC_PAIR_S32);
   RBS_TRY(launch_tree(c, kind, nt, items, y));
   RBS_CUDA_TRY(cudaGetLastError());
