@@ -72,9 +72,10 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
     ap.add_argument("--pair-variant", type=int, default=0,
                     help="pair-kernel variant (rbs_options.pair_variant); 0 lets the library's autotuner choose")
-    ap.add_argument("--far-field", default="tree", choices=["direct", "tree"],
-                    help="float32 inner applies: direct sums over all node pairs, or the treecode "
-                         "(rbs_options.far_field; double-float passes stay direct either way)")
+    ap.add_argument("--far-field", default="tree", choices=["direct", "tree", "tree-df"],
+                    help="direct sums over all node pairs; tree: the treecode for the float32 inner applies "
+                         "(double-float passes stay direct); tree-df: treecodes for both "
+                         "(rbs_options.far_field)")
     ap.add_argument("--experiment", default=None, choices=[None, "warmstart", "magnetic"],
                     help="warmstart: learned vs previous-step vs zero initial guesses in RK4 sedimentation; "
                          "magnetic: time steps of paramagnetic spheres in a uniform field (each prints its own "
@@ -280,19 +281,24 @@ def run_ours(args):
     susp = suspensions.WORKLOADS[args.workload]()
     n = susp.n
     stream = torch.cuda.current_stream()
-    far = rbs.RBS_FAR_TREECODE if args.far_field == "tree" else rbs.RBS_FAR_DIRECT
+    far = {"direct": rbs.RBS_FAR_DIRECT, "tree": rbs.RBS_FAR_TREECODE, "tree-df": rbs.RBS_FAR_TREECODE_DF}[args.far_field]
     ctx = rbs.Context(device=local, precision=rbs.RBS_PREC_MIXED, timing=1, stream=stream.cuda_stream,
                       pair_variant=args.pair_variant, far_field=far)
     ctx.set_suspension(susp)
     st0 = rbs.rbs_get_stats(ctx.ctx)
     setup_ms = st0["setup_ms"]
     tree_info = None
-    if far == rbs.RBS_FAR_TREECODE:
+    if far != rbs.RBS_FAR_DIRECT:
         opts = rbs.rbs_default_options()
         tree_info = {"theta": opts.tree_theta, "degree": opts.tree_degree, "cells": st0["tree_cells"],
                      "pairs_per_apply": st0["tree_pairs"], "proxy_pairs_per_apply": st0["tree_proxy_pairs"],
                      "direct_pairs_per_apply": st0["far_pairs"],
                      "reduction": st0["far_pairs"] / max(1, st0["tree_pairs"])}
+        if far == rbs.RBS_FAR_TREECODE_DF:
+            tree_info["double_float"] = {"theta": opts.tree_df_theta, "degree": opts.tree_df_degree,
+                                         "cells": st0["tree_df_cells"], "pairs_per_apply": st0["tree_df_pairs"],
+                                         "proxy_pairs_per_apply": st0["tree_df_proxy_pairs"],
+                                         "reduction": st0["far_pairs"] / max(1, st0["tree_df_pairs"])}
 
     draws = [suspensions.forces(100 + rank, n, k) for k in range(args.warmup + args.steps)]
     F_dev = torch.tensor(np.stack([d[0] for d in draws]), device="cuda")
@@ -305,7 +311,13 @@ def run_ours(args):
     # verified in double-float), then the largest candidate tolerance meeting the error bound
     F0 = draws[args.warmup][0]
     T0 = draws[args.warmup][1]
-    v_ref, om_ref, _, _ = rbs.rbs_mobility_solve(ctx.ctx, F0, T0, 1e-12)
+    if far == rbs.RBS_FAR_TREECODE_DF:
+        # the double-float passes approximate the far field too: the reference stays direct
+        with rbs.Context(device=local, precision=rbs.RBS_PREC_MIXED, stream=stream.cuda_stream) as ref_ctx:
+            ref_ctx.set_suspension(susp)
+            v_ref, om_ref, _, _ = rbs.rbs_mobility_solve(ref_ctx.ctx, F0, T0, 1e-12)
+    else:
+        v_ref, om_ref, _, _ = rbs.rbs_mobility_solve(ctx.ctx, F0, T0, 1e-12)
     V_ref = np.concatenate([v_ref, om_ref], 1)
 
     def error_of(v, om):
@@ -485,8 +497,10 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": susp.name, "n_particles": n, "p": int(susp.p[0]), "nodes": susp.total_nodes,
                        "unknowns": 3 * susp.total_nodes, "tol": args.tol, "precision": "mixed",
-                       "far_field": ("treecode for the float32 inner applies, direct double-float passes"
-                                     if tree_info else "direct sums"),
+                       "far_field": {"direct": "direct sums",
+                                     "tree": "treecode for the float32 inner applies, direct double-float passes",
+                                     "tree-df": "treecodes for the float32 applies and the double-float passes"}[
+                                         args.far_field],
                        "preconditioner": "block-diagonal", "gmres_iterations": iters,
                        "refinements_last": refinements, "setup_ms": setup_ms,
                        "l2": "flushed before every timed solve (258 MB write); working set > L2",
@@ -530,7 +544,7 @@ def run_warmstart_experiment(args):
     susp = suspensions.WORKLOADS[args.workload]()
     tol = args.tol or 1e-8
     prec = rbs.RBS_PREC_MIXED
-    far = rbs.RBS_FAR_TREECODE if args.far_field == "tree" else rbs.RBS_FAR_DIRECT
+    far = {"direct": rbs.RBS_FAR_DIRECT, "tree": rbs.RBS_FAR_TREECODE, "tree-df": rbs.RBS_FAR_TREECODE_DF}[args.far_field]
     with rbs.Context(device=0, precision=prec, warm_start=rbs.RBS_WARM_PREVIOUS, warm_record=1,
                      stream=stream.cuda_stream, far_field=far) as ctx:
         ctx.set_suspension(susp)
@@ -596,7 +610,10 @@ def run_magnetic_experiment(args):
     tol = args.tol or 1e-8
     out = {}
     for prec in ("FP64", "MIXED"):
-        far = rbs.RBS_FAR_TREECODE if (args.far_field == "tree" and prec == "MIXED") else rbs.RBS_FAR_DIRECT
+        far = rbs.RBS_FAR_DIRECT
+        if prec == "MIXED":
+            far = {"direct": rbs.RBS_FAR_DIRECT, "tree": rbs.RBS_FAR_TREECODE,
+                   "tree-df": rbs.RBS_FAR_TREECODE_DF}[args.far_field]
         with rbs.Context(device=0, precision=getattr(rbs, "RBS_PREC_" + prec), magnetic_field=tuple(H0),
                          mu_ratio=2.0, timing=1, far_field=far) as ctx:
             ctx.set_geometry(np.ones((n, 3)), 8, 16, cen, quats)

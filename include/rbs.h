@@ -111,16 +111,23 @@ typedef struct {
                           clusters of particles with a barycentric Lagrange treecode, the
                           hierarchical far field in place of Section 3.1's fast multipole method;
                           the double-float and float64 passes, and so the converged result, stay
-                          direct.  Only with precision RBS_PREC_MIXED */
+                          direct.  RBS_FAR_TREECODE_DF: the double-float passes use a treecode too,
+                          at tree_df_theta and tree_df_degree (relative error about 5e-11 at the
+                          defaults); float64 passes stay direct.  Only with precision
+                          RBS_PREC_MIXED */
   double tree_theta;   /* treecode opening criterion: a cluster of radius r_C is approximated for a
                           target particle of radius r_B at centre distance d when r_B + r_C <
                           tree_theta d (default 0.5; 0 < tree_theta < 1) */
   int tree_degree;     /* treecode interpolation degree n per axis: (n + 1)^3 Chebyshev proxy points
                           per cluster (default 7; 2 <= n <= 10) */
+  double tree_df_theta; /* opening criterion of the double-float passes' treecode (default 0.4) */
+  int tree_df_degree;  /* its interpolation degree (default 12; 2 <= n <= 12); its cluster charges are
+                          formed in float64 */
 } rbs_options;
 
 #define RBS_FAR_DIRECT 0
 #define RBS_FAR_TREECODE 1
+#define RBS_FAR_TREECODE_DF 2
 
 #define RBS_WARM_ZERO 0
 #define RBS_WARM_PREVIOUS 1
@@ -166,6 +173,9 @@ typedef struct {
                             proxy pairs; 0 without a treecode */
   long long tree_proxy_pairs; /* of these, the (target node, cluster proxy point) pairs */
   int tree_cells;        /* clusters that carry proxy points */
+  long long tree_df_pairs;       /* the same for the double-float passes' treecode (RBS_FAR_TREECODE_DF) */
+  long long tree_df_proxy_pairs;
+  int tree_df_cells;
 } rbs_stats;
 
 /* Fill *opt with the defaults listed above. */

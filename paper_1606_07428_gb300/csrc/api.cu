@@ -107,6 +107,8 @@ void rbs_default_options(rbs_options* o) {
   o->far_field = RBS_FAR_DIRECT;
   o->tree_theta = 0.5;
   o->tree_degree = 7;
+  o->tree_df_theta = 0.4;
+  o->tree_df_degree = 12;
 }
 
 int rbs_create(const rbs_options* opt, rbs_ctx** out) {
@@ -126,8 +128,9 @@ int rbs_create(const rbs_options* opt, rbs_ctx** out) {
        o.pair_variant != 9 && o.pair_variant != 10 && o.pair_variant != 12) ||
       o.warm_start > 2 || !(o.contact_gap >= 0.0) || !(o.mu_ratio > 0.0) ||
       !std::isfinite(o.magnetic_field[0]) || !std::isfinite(o.magnetic_field[1]) || !std::isfinite(o.magnetic_field[2]) ||
-      (o.far_field != RBS_FAR_DIRECT && o.far_field != RBS_FAR_TREECODE) ||
-      !(o.tree_theta > 0.0 && o.tree_theta < 1.0) || o.tree_degree < 2 || o.tree_degree > 10)
+      (o.far_field != RBS_FAR_DIRECT && o.far_field != RBS_FAR_TREECODE && o.far_field != RBS_FAR_TREECODE_DF) ||
+      !(o.tree_theta > 0.0 && o.tree_theta < 1.0) || o.tree_degree < 2 || o.tree_degree > 10 ||
+      !(o.tree_df_theta > 0.0 && o.tree_df_theta < 1.0) || o.tree_df_degree < 2 || o.tree_df_degree > 12)
     return RBS_EINVAL;
   rbs_ctx* h = new rbs_ctx();
   Context& c = h->c;

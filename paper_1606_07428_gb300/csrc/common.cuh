@@ -149,10 +149,11 @@ struct TreeItem {  // one work item of the treecode pair sum
 };
 struct TreeState {
   bool active = false;
+  bool df = false;           // sources in the double-float layout (the treecode of the double-float passes)
   int degree = 0, npx = 0;   // interpolation degree and (degree + 1)^3 proxy points per cluster
   int n_cells = 0;           // clusters with proxy points
   int tmax = 0;              // largest target count of a work item
-  int nt[2] = {0, 0};        // targets per thread chosen for (traction, Stokeslet), 0: not yet
+  int nt[3] = {0, 0, 0};     // targets per thread chosen for (traction, Stokeslet, both), 0: not yet
   double theta = 0.0;
   long long n_src = 0;       // sources: N nodes, then n_cells * npx proxy points
   std::vector<TreeItem> items;
@@ -164,10 +165,14 @@ struct TreeState {
   DevBuf<int> d_order;       // particles in tree order
   DevBuf<double> d_box;      // per cluster with proxies: box midpoint (3), 1 / half-width (3)
   DevBuf<float> d_cheb;      // Chebyshev points, then barycentric weights (degree + 1 each)
-  DevBuf<double> d_pbox;     // per particle: node bounding box lo (3), hi (3)
+  DevBuf<double> d_cheb64;   // the same in float64 (double-float layout)
   // sources for the pair kernel: positions as float32 hi + lo (w of hi: particle id bits, -3 for a
-  // proxy point) and float32 weighted density (nodes) or cluster charge (proxy points)
+  // proxy point) and float32 weighted density (nodes) or cluster charge (proxy points).  In the
+  // double-float layout: positions as exact three-float splits hi + x3m + lo, weighted densities and
+  // charges as float32 pairs q + wl, and the charges accumulated in float64 (q64, 3 per proxy point)
   DevBuf<float4> d_hi, d_lo, d_q;
+  DevBuf<float4> d_x3m, d_wl;
+  DevBuf<double> d_q64;
   long long direct_pairs = 0, proxy_pairs = 0, charge_work = 0;
   void release();
 };
@@ -274,7 +279,8 @@ struct Context {
   std::vector<Contact> contacts;
 
   MagState mag;  // magnetostatic coupling (magnetic.cu)
-  TreeState tree;  // treecode for the float32 smooth sums (treecode.cu)
+  TreeState tree;     // treecode for the float32 smooth sums (treecode.cu)
+  TreeState tree_df;  // treecode for the double-float smooth sums (RBS_FAR_TREECODE_DF)
 
   rbs_stats stats{};
   WarmState* warm = nullptr;       // learned warm start (warmstart.cu)
@@ -323,6 +329,8 @@ Status build_far_field(Context& c);
 // y += the treecode's float32 smooth pair sum of kind (0 traction, 1 Stokeslet) for density x, with
 // nt targets per thread (1, 2 or 4; 0: the fastest, timed once per geometry).
 Status apply_tree(Context& c, int kind, const double* x, double* y, int nt);
+// The same for the double-float passes: y += kind 0 or 1 sum; kind 2: y += traction, y2 += Stokeslet.
+Status apply_tree_df(Context& c, int kind, const double* x, double* y, double* y2);
 // Relative error assumed for a float32 operator application: rounding plus, with the treecode,
 // its approximation model C(theta) rho^-n.
 double f32_operator_error(const Context& c);

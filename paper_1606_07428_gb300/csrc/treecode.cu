@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "pairs32.cuh"
+#include "pairsdf.cuh"
 
 namespace rbs {
 
@@ -305,6 +306,273 @@ __global__ void __launch_bounds__(kTreeMaxTargets / NT)
   }
 }
 
+// ---- double-float layout (the treecode of the double-float passes)
+
+constexpr int kTreeMaxQ64 = 13;  // degree <= 12
+constexpr int kChargeTile64 = 128;
+constexpr int kProxyPerThread64 = (kTreeMaxQ64 * kTreeMaxQ64 * kTreeMaxQ64 + kChargeThreads - 1) / kChargeThreads;
+
+// Weighted density of the nodes as float32 pairs: (qh, ql)[t] = split(w_t mu_t).
+__global__ void k_tree_df_node_charges(long long N, const double4* __restrict__ x, const double* __restrict__ dens,
+                                       float4* __restrict__ qh, float4* __restrict__ ql) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const double w = x[t].w;
+  const dflt a = df_split(w * dens[3 * t]), b = df_split(w * dens[3 * t + 1]), e = df_split(w * dens[3 * t + 2]);
+  qh[t] = make_float4(a.h, b.h, e.h, 0.0f);
+  ql[t] = make_float4(a.l, b.l, e.l, 0.0f);
+}
+
+// Barycentric Lagrange basis in float64 (as lagrange_row).
+__device__ __forceinline__ void lagrange_row64(double u, const double* s, const double* bw, int nq, double* L) {
+  double t[kTreeMaxQ64];
+  double sum = 0.0;
+  int hit = -1;
+#pragma unroll
+  for (int k = 0; k < kTreeMaxQ64; ++k) {
+    t[k] = 0.0;
+    if (k < nq) {
+      const double d = u - s[k];
+      if (d == 0.0)
+        hit = k;
+      else
+        t[k] = bw[k] / d;
+      sum += t[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kTreeMaxQ64; ++k)
+    if (k < nq) L[k] = hit >= 0 ? (k == hit ? 1.0 : 0.0) : t[k] / sum;
+}
+
+// Cluster charges in float64 (as k_tree_charges, from the float64 density): q64[3 (u npx + k) + c].
+__global__ void __launch_bounds__(kChargeThreads) k_tree_charges64(const int4* __restrict__ items,
+                                                                   const int* __restrict__ order,
+                                                                   const long long* __restrict__ offset,
+                                                                   const double4* __restrict__ x,
+                                                                   const double* __restrict__ dens,
+                                                                   const double* __restrict__ box,
+                                                                   const double* __restrict__ cheb, int nq,
+                                                                   double* __restrict__ q64) {
+  constexpr int TS = kChargeTile64;
+  __shared__ double sL[3][TS][kTreeMaxQ64];
+  __shared__ double sq[TS][3];
+  __shared__ double s_pts[kTreeMaxQ64], s_bw[kTreeMaxQ64];
+  const int npx = nq * nq * nq;
+  if (threadIdx.x < nq) {
+    s_pts[threadIdx.x] = cheb[threadIdx.x];
+    s_bw[threadIdx.x] = cheb[nq + threadIdx.x];
+  }
+  const int4 it = items[blockIdx.x];
+  const int u = it.x;
+  const double m0 = box[6 * (size_t)u], m1 = box[6 * (size_t)u + 1], m2 = box[6 * (size_t)u + 2];
+  const double h0 = box[6 * (size_t)u + 3], h1 = box[6 * (size_t)u + 4], h2 = box[6 * (size_t)u + 5];
+  int ka[kProxyPerThread64], kb[kProxyPerThread64], kc[kProxyPerThread64];
+  double acc[kProxyPerThread64][3];
+#pragma unroll
+  for (int m = 0; m < kProxyPerThread64; ++m) {
+    const int k = threadIdx.x + kChargeThreads * m;
+    ka[m] = k / (nq * nq);
+    kb[m] = (k / nq) % nq;
+    kc[m] = k % nq;
+    acc[m][0] = acc[m][1] = acc[m][2] = 0.0;
+  }
+  for (int pi = it.y; pi < it.z; ++pi) {
+    const int j = order[pi];
+    const long long o = offset[j], e = offset[j + 1];
+    for (long long s0 = o; s0 < e; s0 += TS) {
+      const int cnt = (int)min((long long)TS, e - s0);
+      __syncthreads();
+      if ((int)threadIdx.x < cnt) {
+        const long long t = s0 + threadIdx.x;
+        const double4 p = x[t];
+        lagrange_row64((p.x - m0) * h0, s_pts, s_bw, nq, sL[0][threadIdx.x]);
+        lagrange_row64((p.y - m1) * h1, s_pts, s_bw, nq, sL[1][threadIdx.x]);
+        lagrange_row64((p.z - m2) * h2, s_pts, s_bw, nq, sL[2][threadIdx.x]);
+        sq[threadIdx.x][0] = p.w * dens[3 * t];
+        sq[threadIdx.x][1] = p.w * dens[3 * t + 1];
+        sq[threadIdx.x][2] = p.w * dens[3 * t + 2];
+      }
+      __syncthreads();
+      for (int l = 0; l < cnt; ++l) {
+        const double q0 = sq[l][0], q1 = sq[l][1], q2 = sq[l][2];
+#pragma unroll
+        for (int m = 0; m < kProxyPerThread64; ++m) {
+          if (threadIdx.x + kChargeThreads * m < npx) {
+            const double f = sL[0][l][ka[m]] * sL[1][l][kb[m]] * sL[2][l][kc[m]];
+            acc[m][0] = fma(f, q0, acc[m][0]);
+            acc[m][1] = fma(f, q1, acc[m][1]);
+            acc[m][2] = fma(f, q2, acc[m][2]);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < kProxyPerThread64; ++m) {
+    const int k = threadIdx.x + kChargeThreads * m;
+    if (k < npx)
+      for (int c = 0; c < 3; ++c) atomicAdd(q64 + 3 * ((size_t)u * npx + k) + c, acc[m][c]);
+  }
+}
+
+// Float64 cluster charges to the float32 pairs the double-float kernel reads.
+__global__ void k_tree_q64_split(long long count, const double* __restrict__ q64, float4* __restrict__ qh,
+                                 float4* __restrict__ ql) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const dflt a = df_split(q64[3 * k]), b = df_split(q64[3 * k + 1]), e = df_split(q64[3 * k + 2]);
+  qh[k] = make_float4(a.h, b.h, e.h, 0.0f);
+  ql[k] = make_float4(a.l, b.l, e.l, 0.0f);
+}
+
+// The double-float treecode pair sum: the packed double-float pair of the direct kernel (pairsdf.cuh)
+// over source tiles filled from the item's segments (as k_tree32x2).  KIND 0 traction into y, 1
+// Stokeslet into y, 2 traction into y and Stokeslet into y2.
+template <int KIND, int NT>
+__global__ void __launch_bounds__(kTreeMaxTargets / NT)
+    k_tree_df2(int nitems, const TreeItem* __restrict__ items, const int2* __restrict__ segs,
+               const float4* __restrict__ x3h, const float4* __restrict__ x3m, const float4* __restrict__ x3l,
+               const float4* __restrict__ nh, const float4* __restrict__ nl, const float4* __restrict__ shi,
+               const float4* __restrict__ smid, const float4* __restrict__ slo, const float4* __restrict__ sqh,
+               const float4* __restrict__ sql, double* __restrict__ y, double* __restrict__ y2) {
+  constexpr int TS = 256;
+  const int NTH = blockDim.x;
+  __shared__ __align__(16) float sa[12][TS];
+  __shared__ __align__(16) int spid[TS];
+  __shared__ int sidx[TS];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const TreeItem w = items[it];
+    const float4 oh = x3h[w.t0], om = x3m[w.t0], ol = x3l[w.t0];
+    df2 xt[NT][3], nt[NT][3];
+    int pt[NT];
+    bool valid[NT];
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      const int t = w.t0 + threadIdx.x + NTH * u;
+      valid[u] = t < w.t1;
+      float4 ah = oh, am = om, al = ol, bh = make_float4(0, 0, 0, 0), bl = make_float4(0, 0, 0, 0);
+      pt[u] = -1;
+      if (valid[u]) {
+        ah = x3h[t];
+        am = x3m[t];
+        al = x3l[t];
+        bh = nh[t];
+        bl = nl[t];
+        pt[u] = __float_as_int(ah.w);
+      }
+      const dflt dx = df_diff3(ah.x, am.x, al.x, oh.x, om.x, ol.x), dy = df_diff3(ah.y, am.y, al.y, oh.y, om.y, ol.y),
+                 dz = df_diff3(ah.z, am.z, al.z, oh.z, om.z, ol.z);
+      xt[u][0] = {dup2(dx.h), dup2(dx.l)};
+      xt[u][1] = {dup2(dy.h), dup2(dy.l)};
+      xt[u][2] = {dup2(dz.h), dup2(dz.l)};
+      nt[u][0] = {dup2(bh.x), dup2(bl.x)};
+      nt[u][1] = {dup2(bh.y), dup2(bl.y)};
+      nt[u][2] = {dup2(bh.z), dup2(bl.z)};
+    }
+    // target slots of this warp that hold a target (as k_tree32x2)
+    const int nu = min(NT, max(0, (w.t1 - w.t0 - (int)(threadIdx.x & ~31u) + NTH - 1) / NTH));
+    dflt a[NT][3], a2[NT][3];
+#pragma unroll
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a[u][c] = a2[u][c] = dflt{0.0f, 0.0f};
+    int seg = w.s0, off = 0, done = 0;
+    while (seg < w.s1) {
+      __syncthreads();
+      int filled = 0;
+      while (filled < TS && seg < w.s1) {
+        const int2 sg = segs[seg];
+        const int take = min(sg.y - off, TS - filled);
+        int l = threadIdx.x;
+        if (l < filled) l += ((filled - l + NTH - 1) / NTH) * NTH;  // first own slot >= filled
+        for (; l < filled + take; l += NTH) sidx[l] = sg.x + off + (l - filled);
+        filled += take;
+        off += take;
+        if (off >= sg.y) {
+          ++seg;
+          off = 0;
+        }
+      }
+#pragma unroll 2
+      for (int l = threadIdx.x; l < filled; l += NTH) {
+        const int s = sidx[l];
+        const float4 ph = shi[s], pm = smid[s], pl = slo[s], qh = sqh[s], ql = sql[s];
+        const dflt px = df_diff3(ph.x, pm.x, pl.x, oh.x, om.x, ol.x);
+        const dflt py = df_diff3(ph.y, pm.y, pl.y, oh.y, om.y, ol.y);
+        const dflt pz = df_diff3(ph.z, pm.z, pl.z, oh.z, om.z, ol.z);
+        sa[0][l] = px.h;
+        sa[1][l] = px.l;
+        sa[2][l] = py.h;
+        sa[3][l] = py.l;
+        sa[4][l] = pz.h;
+        sa[5][l] = pz.l;
+        sa[6][l] = qh.x;
+        sa[7][l] = ql.x;
+        sa[8][l] = qh.y;
+        sa[9][l] = ql.y;
+        sa[10][l] = qh.z;
+        sa[11][l] = ql.z;
+        spid[l] = __float_as_int(ph.w);
+      }
+      const int cnt2 = (filled + 1) & ~1;
+      for (int l = filled + threadIdx.x; l < cnt2; l += NTH) {
+        sa[0][l] = sa[2][l] = sa[4][l] = 1.0e4f;
+        sa[1][l] = sa[3][l] = sa[5][l] = 0.0f;
+        for (int q = 6; q < 12; ++q) sa[q][l] = 0.0f;
+        spid[l] = -2;
+      }
+      __syncthreads();
+      const bool masked = done < w.nmask;
+      df2 acc[NT][3], acc2[NT][3];
+#pragma unroll
+      for (int u = 0; u < NT; ++u)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[u][c] = acc2[u][c] = df2{dup2(0.0f), dup2(0.0f)};
+      if (nu > 0) {
+        for (int l = 0; l < cnt2; l += 2) {
+          df2 ys[3], den[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            ys[c] = {*reinterpret_cast<const float2*>(&sa[2 * c][l]), *reinterpret_cast<const float2*>(&sa[2 * c + 1][l])};
+            den[c] = {*reinterpret_cast<const float2*>(&sa[6 + 2 * c][l]),
+                      *reinterpret_cast<const float2*>(&sa[7 + 2 * c][l])};
+          }
+          const int2 pp = *reinterpret_cast<const int2*>(&spid[l]);
+#pragma unroll
+          for (int u = 0; u < NT; ++u) {
+            if (u < nu) {
+              if (masked)
+                pair2_df<KIND, true>(ys, den, pp, xt[u], nt[u], pt[u], acc[u], acc2[u]);
+              else
+                pair2_df<KIND, false>(ys, den, pp, xt[u], nt[u], pt[u], acc[u], acc2[u]);
+            }
+          }
+        }
+      }
+      done += filled;
+#pragma unroll
+      for (int u = 0; u < NT; ++u)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          a[u][c] = df_add_accurate(a[u][c], fold2(acc[u][c]));
+          if (KIND == 2) a2[u][c] = df_add_accurate(a2[u][c], fold2(acc2[u][c]));
+        }
+    }
+    const double sc = KIND == 1 ? kStokesletScale : kTractionScale;
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+      if (!valid[u]) continue;
+      const long long t = w.t0 + threadIdx.x + NTH * u;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        atomicAdd(y + 3 * t + c, sc * ((double)a[u][c].h + (double)a[u][c].l));
+        if (KIND == 2) atomicAdd(y2 + 3 * t + c, kStokesletScale * ((double)a2[u][c].h + (double)a2[u][c].l));
+      }
+    }
+  }
+}
+
 template <typename T>
 Status upload_vec(DevBuf<T>& buf, const std::vector<T>& host, cudaStream_t s) {
   RBS_TRY(buf.alloc(std::max<size_t>(1, host.size())));
@@ -407,20 +675,22 @@ struct TreeBuilder {
 void TreeState::release() {
   active = false;
   tmax = 0;
-  nt[0] = nt[1] = 0;
+  nt[0] = nt[1] = nt[2] = 0;
   n_cells = 0;
   n_src = 0;
   items.clear();
   segs.clear();
   charge_items.clear();
-  for (DevBuf<float4>* b : {&d_hi, &d_lo, &d_q}) b->release();
+  for (DevBuf<float4>* b : {&d_hi, &d_lo, &d_q, &d_x3m, &d_wl}) b->release();
   d_items.release();
   d_segs.release();
   d_charge_items.release();
   d_order.release();
   d_box.release();
   d_cheb.release();
-  d_pbox.release();
+  d_cheb64.release();
+  d_q64.release();
+  df = false;
   direct_pairs = proxy_pairs = charge_work = 0;
 }
 
@@ -434,28 +704,18 @@ double f32_operator_error(const Context& c) {
   return kF32OperatorError + C * std::pow(a + std::sqrt(a * a - 1.0), -c.tree.degree);
 }
 
-Status build_far_field(Context& c) {
-  TreeState& T = c.tree;
-  c.stats.tree_pairs = c.stats.tree_proxy_pairs = 0;
-  c.stats.tree_cells = 0;
-  if (c.opt.far_field != RBS_FAR_TREECODE || c.opt.precision != RBS_PREC_MIXED || c.n == 0) {
-    T.release();
-    return Status::Ok();
-  }
+// Tree, lists, work items and proxy points of one treecode (theta, degree) over the particles'
+// node boxes pbox; df: sources in the double-float layout (positions as exact three-float splits,
+// weighted densities and charges as float32 pairs, charges accumulated in float64).
+static Status build_lists(Context& c, TreeState& T, const std::vector<double>& pbox, double theta, int degree,
+                          bool df) {
   cudaStream_t s = c.stream;
   const int n = c.n;
-  const int degree = c.opt.tree_degree, nq = degree + 1, npx = nq * nq * nq;
+  const int nq = degree + 1, npx = nq * nq * nq;
   T.degree = degree;
   T.npx = npx;
-  T.theta = c.opt.tree_theta;
-
-  // 1. node bounding boxes of the particles
-  RBS_TRY(T.d_pbox.alloc(6 * (size_t)n));
-  k_particle_boxes<<<n, 128, 0, s>>>(n, c.d_offset.ptr, c.d_x.ptr, T.d_pbox.ptr);
-  RBS_CUDA_TRY(cudaGetLastError());
-  std::vector<double> pbox(6 * (size_t)n);
-  RBS_CUDA_TRY(cudaMemcpyAsync(pbox.data(), T.d_pbox.ptr, sizeof(double) * pbox.size(), cudaMemcpyDeviceToHost, s));
-  RBS_CUDA_TRY(cudaStreamSynchronize(s));
+  T.theta = theta;
+  T.df = df;
 
   // 2. one octree per suspension (particles of a suspension are contiguous)
   std::vector<int> order(n), leaf_of(n, -1), root_of(n, -1);
@@ -558,7 +818,7 @@ Status build_far_field(Context& c) {
     tiles += k;
     T.tmax = std::max(T.tmax, (np_i + k - 1) / k);
   }
-  if (T.tmax != old_tmax) T.nt[0] = T.nt[1] = 0;  // the block shape changed: time the variants again
+  if (T.tmax != old_tmax) T.nt[0] = T.nt[1] = T.nt[2] = 0;  // the block shape changed: time the variants again
   const long long want = 96LL * std::max(1, c.sm_count);
   const int splits = (int)std::max(1LL, (want + tiles - 1) / std::max(1LL, tiles));
   T.items.clear();
@@ -600,11 +860,11 @@ Status build_far_field(Context& c) {
 
   // 5. cluster boxes, proxy points and charge blocks
   std::vector<double> box(6 * (size_t)std::max(1, n_used));
-  std::vector<float4> phi((size_t)n_used * npx), plo((size_t)n_used * npx);
-  std::vector<float> cheb(2 * (size_t)nq);
+  std::vector<float4> phi((size_t)n_used * npx), plo((size_t)n_used * npx), pm(df ? (size_t)n_used * npx : 0);
+  std::vector<double> cheb(2 * (size_t)nq);
   for (int k = 0; k < nq; ++k) {
-    cheb[k] = (float)std::cos(k * kPi / degree);
-    cheb[nq + k] = (float)(((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == degree) ? 0.5 : 1.0));
+    cheb[k] = std::cos(k * kPi / degree);
+    cheb[nq + k] = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == degree) ? 0.5 : 1.0);
   }
   std::vector<int> corder;
   T.charge_items.clear();
@@ -629,14 +889,21 @@ Status build_far_field(Context& c) {
         for (int e = 0; e < nq; ++e) {
           const double v[3] = {mid[0] + half[0] * std::cos(a * kPi / degree), mid[1] + half[1] * std::cos(b * kPi / degree),
                                mid[2] + half[2] * std::cos(e * kPi / degree)};
-          float h[3], l[3];
+          float h[3], m[3], l[3];
           for (int d = 0; d < 3; ++d) {
             h[d] = (float)v[d];
-            l[d] = (float)(v[d] - (double)h[d]);
+            const double r = v[d] - (double)h[d];
+            m[d] = (float)r;
+            l[d] = df ? (float)(r - (double)m[d]) : 0.0f;
           }
           const size_t k = (size_t)u * npx + ((size_t)a * nq + b) * nq + e;
           phi[k] = make_float4(h[0], h[1], h[2], proxy_w);
-          plo[k] = make_float4(l[0], l[1], l[2], 0.0f);
+          if (df) {  // exact three-float split, as the nodes' x3h / x3m / x3l
+            pm[k] = make_float4(m[0], m[1], m[2], 0.0f);
+            plo[k] = make_float4(l[0], l[1], l[2], 0.0f);
+          } else {   // float32 hi + lo, as the nodes' xhi / xlo
+            plo[k] = make_float4(m[0], m[1], m[2], 0.0f);
+          }
         }
     // charge blocks over the cell's particles, about 4,096 nodes each
     int q = C.pb;
@@ -659,22 +926,70 @@ Status build_far_field(Context& c) {
   RBS_TRY(upload_vec(T.d_charge_items, T.charge_items, s));
   RBS_TRY(upload_vec(T.d_order, corder, s));
   RBS_TRY(upload_vec(T.d_box, box, s));
-  RBS_TRY(upload_vec(T.d_cheb, cheb, s));
-  RBS_TRY(T.d_hi.alloc(T.n_src));
-  RBS_TRY(T.d_lo.alloc(T.n_src));
-  RBS_TRY(T.d_q.alloc(T.n_src));
-  RBS_CUDA_TRY(cudaMemcpyAsync(T.d_hi.ptr, c.d_xhi.ptr, sizeof(float4) * N, cudaMemcpyDeviceToDevice, s));
-  RBS_CUDA_TRY(cudaMemcpyAsync(T.d_lo.ptr, c.d_xlo.ptr, sizeof(float4) * N, cudaMemcpyDeviceToDevice, s));
-  if (n_used > 0) {
-    RBS_CUDA_TRY(cudaMemcpyAsync(T.d_hi.ptr + N, phi.data(), sizeof(float4) * phi.size(), cudaMemcpyHostToDevice, s));
-    RBS_CUDA_TRY(cudaMemcpyAsync(T.d_lo.ptr + N, plo.data(), sizeof(float4) * plo.size(), cudaMemcpyHostToDevice, s));
+  {
+    std::vector<float> cheb32(cheb.begin(), cheb.end());
+    if (df)
+      RBS_TRY(upload_vec(T.d_cheb64, cheb, s));
+    else
+      RBS_TRY(upload_vec(T.d_cheb, cheb32, s));
+    RBS_TRY(T.d_hi.alloc(T.n_src));
+    RBS_TRY(T.d_lo.alloc(T.n_src));
+    RBS_TRY(T.d_q.alloc(T.n_src));  // float32 charges, or the hi parts of the double-float ones
+    const float4* node_hi = df ? c.d_x3h.ptr : c.d_xhi.ptr;
+    const float4* node_lo = df ? c.d_x3l.ptr : c.d_xlo.ptr;
+    RBS_CUDA_TRY(cudaMemcpyAsync(T.d_hi.ptr, node_hi, sizeof(float4) * N, cudaMemcpyDeviceToDevice, s));
+    RBS_CUDA_TRY(cudaMemcpyAsync(T.d_lo.ptr, node_lo, sizeof(float4) * N, cudaMemcpyDeviceToDevice, s));
+    if (df) {
+      RBS_TRY(T.d_x3m.alloc(T.n_src));
+      RBS_TRY(T.d_wl.alloc(T.n_src));
+      RBS_TRY(T.d_q64.alloc(std::max<size_t>(1, 3 * (size_t)n_used * npx)));
+      RBS_CUDA_TRY(cudaMemcpyAsync(T.d_x3m.ptr, c.d_x3m.ptr, sizeof(float4) * N, cudaMemcpyDeviceToDevice, s));
+    }
+    if (n_used > 0) {
+      RBS_CUDA_TRY(cudaMemcpyAsync(T.d_hi.ptr + N, phi.data(), sizeof(float4) * phi.size(), cudaMemcpyHostToDevice, s));
+      RBS_CUDA_TRY(cudaMemcpyAsync(T.d_lo.ptr + N, plo.data(), sizeof(float4) * plo.size(), cudaMemcpyHostToDevice, s));
+      if (df)
+        RBS_CUDA_TRY(cudaMemcpyAsync(T.d_x3m.ptr + N, pm.data(), sizeof(float4) * pm.size(), cudaMemcpyHostToDevice, s));
+    }
+    // the host vectors above must outlive their copies
+    RBS_CUDA_TRY(cudaStreamSynchronize(s));
   }
-  // the host vectors above must outlive their copies
-  RBS_CUDA_TRY(cudaStreamSynchronize(s));
   T.active = true;
-  c.stats.tree_pairs = T.direct_pairs + T.proxy_pairs;
-  c.stats.tree_proxy_pairs = T.proxy_pairs;
-  c.stats.tree_cells = n_used;
+  return Status::Ok();
+}
+
+Status build_far_field(Context& c) {
+  c.stats.tree_pairs = c.stats.tree_proxy_pairs = c.stats.tree_df_pairs = c.stats.tree_df_proxy_pairs = 0;
+  c.stats.tree_cells = c.stats.tree_df_cells = 0;
+  if (c.opt.far_field == RBS_FAR_DIRECT || c.opt.precision != RBS_PREC_MIXED || c.n == 0) {
+    c.tree.release();
+    c.tree_df.release();
+    return Status::Ok();
+  }
+  cudaStream_t s = c.stream;
+  const int n = c.n;
+  // 1. node bounding boxes of the particles
+  std::vector<double> pbox(6 * (size_t)n);
+  {
+    DevBuf<double> d_pbox;
+    RBS_TRY(d_pbox.alloc(6 * (size_t)n));
+    k_particle_boxes<<<n, 128, 0, s>>>(n, c.d_offset.ptr, c.d_x.ptr, d_pbox.ptr);
+    RBS_CUDA_TRY(cudaGetLastError());
+    RBS_CUDA_TRY(cudaMemcpyAsync(pbox.data(), d_pbox.ptr, sizeof(double) * pbox.size(), cudaMemcpyDeviceToHost, s));
+    RBS_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  RBS_TRY(build_lists(c, c.tree, pbox, c.opt.tree_theta, c.opt.tree_degree, false));
+  c.stats.tree_pairs = c.tree.direct_pairs + c.tree.proxy_pairs;
+  c.stats.tree_proxy_pairs = c.tree.proxy_pairs;
+  c.stats.tree_cells = c.tree.n_cells;
+  if (c.opt.far_field == RBS_FAR_TREECODE_DF) {
+    RBS_TRY(build_lists(c, c.tree_df, pbox, c.opt.tree_df_theta, c.opt.tree_df_degree, true));
+    c.stats.tree_df_pairs = c.tree_df.direct_pairs + c.tree_df.proxy_pairs;
+    c.stats.tree_df_proxy_pairs = c.tree_df.proxy_pairs;
+    c.stats.tree_df_cells = c.tree_df.n_cells;
+  } else {
+    c.tree_df.release();
+  }
   return Status::Ok();
 }
 
@@ -772,6 +1087,100 @@ Status apply_tree(Context& c, int kind, const double* x, double* y, int nt) {
   KernelTimer timer(c, kind == 0 ? RBS_KC_PAIR_K32 : RBS_KC_PAIR_S32);
   RBS_TRY(launch_tree(c, kind, nt, items, y));
   RBS_CUDA_TRY(cudaGetLastError());
+  timer.done((double)(T.direct_pairs + T.proxy_pairs));
+  return Status::Ok();
+}
+
+// Launch of the double-float treecode pair sum over the first `items` work items.
+static Status launch_tree_df(Context& c, int kind, int nt, int items, double* y, double* y2) {
+  TreeState& T = c.tree_df;
+  const int threads = ((T.tmax + nt - 1) / nt + 31) / 32 * 32;
+#define RBS_TREE_DF_ARGS items, T.d_items.ptr, T.d_segs.ptr, c.d_x3h.ptr, c.d_x3m.ptr, c.d_x3l.ptr, c.d_nrmh.ptr, \
+                         c.d_nrml.ptr, T.d_hi.ptr, T.d_x3m.ptr, T.d_lo.ptr, T.d_q.ptr, T.d_wl.ptr, y, y2
+  auto grid = [&](const void* k) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    return std::max(1, std::min(items, per_sm * std::max(1, c.sm_count)));
+  };
+  if (kind == 0) {
+    if (nt == 1)
+      k_tree_df2<0, 1><<<grid((const void*)k_tree_df2<0, 1>), threads, 0, c.stream>>>(RBS_TREE_DF_ARGS);
+    else
+      k_tree_df2<0, 2><<<grid((const void*)k_tree_df2<0, 2>), threads, 0, c.stream>>>(RBS_TREE_DF_ARGS);
+  } else if (kind == 1) {
+    if (nt == 1)
+      k_tree_df2<1, 1><<<grid((const void*)k_tree_df2<1, 1>), threads, 0, c.stream>>>(RBS_TREE_DF_ARGS);
+    else
+      k_tree_df2<1, 2><<<grid((const void*)k_tree_df2<1, 2>), threads, 0, c.stream>>>(RBS_TREE_DF_ARGS);
+  } else {
+    if (nt == 1)
+      k_tree_df2<2, 1><<<grid((const void*)k_tree_df2<2, 1>), threads, 0, c.stream>>>(RBS_TREE_DF_ARGS);
+    else
+      k_tree_df2<2, 2><<<grid((const void*)k_tree_df2<2, 2>), threads, 0, c.stream>>>(RBS_TREE_DF_ARGS);
+  }
+#undef RBS_TREE_DF_ARGS
+  RBS_CUDA_TRY(cudaGetLastError());
+  return Status::Ok();
+}
+
+// Targets per thread of the double-float treecode pair sum: 1 or 2, timed once per configuration and
+// kind on a prefix of the work items (the current charges as sources, into scratch outputs).
+static int tree_df_variant(Context& c, int kind) {
+  TreeState& T = c.tree_df;
+  if (c.opt.pair_variant > 0) return (c.opt.pair_variant == 2 || c.opt.pair_variant == kPacked + 2) ? 2 : 1;
+  if (T.nt[kind]) return T.nt[kind];
+  int best = 1;
+  const int items = std::min<int>((int)T.items.size(), 4 * std::max(1, c.sm_count));
+  double* scratch = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaMalloc(&scratch, sizeof(double) * 6 * c.N) == cudaSuccess && cudaEventCreate(&a) == cudaSuccess &&
+      cudaEventCreate(&b) == cudaSuccess) {
+    float best_ms = 1e30f;
+    for (int nt : {1, 2}) {
+      if (!launch_tree_df(c, kind, nt, items, scratch, scratch + 3 * c.N).ok()) continue;  // warm
+      cudaEventRecord(a, c.stream);
+      if (!launch_tree_df(c, kind, nt, items, scratch, scratch + 3 * c.N).ok()) continue;
+      cudaEventRecord(b, c.stream);
+      float ms = 0.0f;
+      if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = nt;
+      }
+      c.stats.launches += 2;
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (scratch) cudaFree(scratch);
+  cudaGetLastError();
+  T.nt[kind] = best;
+  return best;
+}
+
+Status apply_tree_df(Context& c, int kind, const double* x, double* y, double* y2) {
+  TreeState& T = c.tree_df;
+  const long long N = c.N;
+  {
+    KernelTimer timer(c, RBS_KC_TREE);
+    k_tree_df_node_charges<<<cdiv(N, 256), 256, 0, c.stream>>>(N, c.d_x.ptr, x, T.d_q.ptr, T.d_wl.ptr);
+    int launches = 1;
+    if (T.n_cells > 0) {
+      const long long np = (long long)T.n_cells * T.npx;
+      RBS_CUDA_TRY(cudaMemsetAsync(T.d_q64.ptr, 0, sizeof(double) * 3 * (size_t)np, c.stream));
+      k_tree_charges64<<<(unsigned)T.charge_items.size(), kChargeThreads, 0, c.stream>>>(
+          T.d_charge_items.ptr, T.d_order.ptr, c.d_offset.ptr, c.d_x.ptr, x, T.d_box.ptr, T.d_cheb64.ptr,
+          T.degree + 1, T.d_q64.ptr);
+      k_tree_q64_split<<<cdiv(np, 256), 256, 0, c.stream>>>(np, T.d_q64.ptr, T.d_q.ptr + N, T.d_wl.ptr + N);
+      launches = 3;
+    }
+    RBS_CUDA_TRY(cudaGetLastError());
+    timer.done((double)T.charge_work, launches);
+  }
+  const int items = (int)T.items.size();
+  if (items == 0) return Status::Ok();
+  const int nt = tree_df_variant(c, kind);
+  KernelTimer timer(c, kind == 0 ? RBS_KC_PAIR_KDF : (kind == 1 ? RBS_KC_PAIR_SDF : RBS_KC_PAIR_KSDF));
+  RBS_TRY(launch_tree_df(c, kind, nt, items, y, y2));
   timer.done((double)(T.direct_pairs + T.proxy_pairs));
   return Status::Ok();
 }

@@ -84,11 +84,14 @@ class rbs_options(ctypes.Structure):
         ("far_field", ctypes.c_int),
         ("tree_theta", ctypes.c_double),
         ("tree_degree", ctypes.c_int),
+        ("tree_df_theta", ctypes.c_double),
+        ("tree_df_degree", ctypes.c_int),
     ]
 
 
 RBS_FAR_DIRECT = 0
 RBS_FAR_TREECODE = 1
+RBS_FAR_TREECODE_DF = 2
 
 
 RBS_KC_PAIR_K32 = 0
@@ -128,6 +131,9 @@ class rbs_stats(ctypes.Structure):
         ("tree_pairs", ctypes.c_longlong),
         ("tree_proxy_pairs", ctypes.c_longlong),
         ("tree_cells", ctypes.c_int),
+        ("tree_df_pairs", ctypes.c_longlong),
+        ("tree_df_proxy_pairs", ctypes.c_longlong),
+        ("tree_df_cells", ctypes.c_int),
     ]
 
 

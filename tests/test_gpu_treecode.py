@@ -113,8 +113,8 @@ def test_tree_solve_on_the_eight_spheres_matches_lu(rbs):
 
 
 def test_tree_rejects_bad_parameters(rbs):
-    for kw in ({"far_field": 2}, {"tree_theta": 0.0}, {"tree_theta": 1.0}, {"tree_degree": 1},
-               {"tree_degree": 11}):
+    for kw in ({"far_field": 3}, {"tree_theta": 0.0}, {"tree_theta": 1.0}, {"tree_degree": 1},
+               {"tree_degree": 11}, {"tree_df_theta": 1.0}, {"tree_df_degree": 13}):
         with pytest.raises(rbs.RbsError):
             rbs.rbs_create(device=0, **kw)
 
@@ -137,6 +137,53 @@ def test_c2_tree_mixed_solve_residual_rows(rbs):
         yr = ref.apply_rows("K", x, rows, half=0.5, with_L=True)
         assert np.abs(y[rows] - yr).max() < (1e-5 + tc.tree_error_bound(0.5, 7)) * np.abs(yr).max()
         v, om, mu, its = rbs.rbs_mobility_solve(ctx.ctx, s.F, s.T, 1e-10, want_density=True)
+    rho = ref.incident_density(s.F, s.T)
+    b_rows = -ref.apply_rows("K", rho, rows, half=0.5)
+    r_rows = b_rows - ref.apply_rows("K", mu, rows, half=0.5, with_L=True)
+    assert np.abs(r_rows).max() < 1e-8 * np.abs(b_rows).max()
+
+
+def test_df_tree_lists_and_operator_match_the_oracle(rbs):
+    """The double-float passes' treecode (far_field = RBS_FAR_TREECODE_DF) on 64 ellipsoids at p = 8,
+    at theta 0.5 and degree 3 so that single particles are approximated: identical lists, and the
+    double-float traction operator equal to the oracle's treecode operator to double-float rounding
+    (the cluster charges are formed in float64 on both sides)."""
+    s = suspensions.random_ellipsoids(64, 8, 16, 0.10, 0.2, seed=12)
+    ref = oracle.System(s.semi_axes, s.p, s.nphi, s.centres, s.quats, s.suspension_id)
+    tree = tc.Treecode(ref, 0.5, 3)
+    direct, proxy = tree.pair_counts()
+    x = suspensions.random_density(34, s.total_nodes)
+    want = tc.offdiagonal_with_tree(ref, tree, "K", x)
+    with rbs.Context(device=0, precision=rbs.RBS_PREC_MIXED, far_field=rbs.RBS_FAR_TREECODE_DF, tree_df_theta=0.5,
+                     tree_df_degree=3) as ctx:
+        ctx.set_suspension(s)
+        st = rbs.rbs_get_stats(ctx.ctx)
+        assert st["tree_df_proxy_pairs"] == proxy > 0
+        assert st["tree_df_pairs"] == direct + proxy
+        assert st["tree_df_cells"] == len({id(c) for a, _ in tree.lists for c in a})
+        y = rbs.rbs_apply_operator(ctx.ctx, rbs.RBS_OP_K_OFF, rbs.RBS_PREC_DF, x)
+    assert np.abs(y - want).max() <= 1e-11 * np.abs(want).max()
+
+
+@pytest.mark.slow
+def test_c2_df_tree_solve(rbs):
+    """The 1,000-ellipsoid workload with treecodes in both the float32 and the double-float passes at
+    their defaults (theta 0.4, degree 12 for the latter): the solve's true residual at sampled rows
+    stays below the tolerance, and its velocities agree with the all-direct mixed solve to 1e-8."""
+    s = suspensions.c2_ellipsoids()
+    ref = oracle.System(s.semi_axes, s.p, s.nphi, s.centres, s.quats)
+    rng = np.random.default_rng(9)
+    rows = np.array(sorted(set(rng.choice(s.total_nodes, 6, replace=False)) | {0, s.total_nodes - 1}))
+    with rbs.Context(device=0, precision=rbs.RBS_PREC_MIXED, far_field=rbs.RBS_FAR_TREECODE_DF) as ctx:
+        ctx.set_suspension(s)
+        st = rbs.rbs_get_stats(ctx.ctx)
+        assert 0 < st["tree_df_pairs"] < st["far_pairs"]
+        v, om, mu, its = rbs.rbs_mobility_solve(ctx.ctx, s.F, s.T, 1e-10, want_density=True)
+    with rbs.Context(device=0, precision=rbs.RBS_PREC_MIXED) as d:
+        d.set_suspension(s)
+        v0, om0, _, _ = rbs.rbs_mobility_solve(d.ctx, s.F, s.T, 1e-12)
+    V, V0 = np.concatenate([v, om]), np.concatenate([v0, om0])
+    assert np.linalg.norm(V - V0) <= 1e-8 * np.linalg.norm(V0)
     rho = ref.incident_density(s.F, s.T)
     b_rows = -ref.apply_rows("K", rho, rows, half=0.5)
     r_rows = b_rows - ref.apply_rows("K", mu, rows, half=0.5, with_L=True)
