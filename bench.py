@@ -477,10 +477,15 @@ def run_ours(args):
     except Exception:
         hbm_peak = 6800.0
     rooflines = kernel_rooflines(kernels, f_mhz, hbm_peak)
-    if name in NCU_TRAFFIC:
+    # the captured counters belong to the direct kernels: a treecode kernel in the class has none yet
+    treecode_class = (name.endswith("_f32") and far != rbs.RBS_FAR_DIRECT) or \
+                     (name.endswith("_df") and far == rbs.RBS_FAR_TREECODE_DF)
+    if name in NCU_TRAFFIC and not treecode_class:
         bytes_, nodes_ = NCU_TRAFFIC[name]
         roof["traffic"] = bytes_ * susp.total_nodes / nodes_
         roof["traffic_basis"] = "ncu dram read+write of the 400-ellipsoid capture, scaled by node count"
+    elif treecode_class:
+        roof["traffic_basis"] = "null: no dram counters captured for the treecode kernel of this class"
     roof["ms_per_launch"] = per_launch_ms
     roof["share_of_step"] = e["ms"] / total_ms if world == 1 else None
 
