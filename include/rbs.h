@@ -383,6 +383,27 @@ int rbs_reset_stats(rbs_ctx* ctx);
 /* Message describing the last error of the context (empty when none); valid until the next call. */
 const char* rbs_last_error(const rbs_ctx* ctx);
 
+/*
+ * Host-only plan of the treecode far field (rbs_options.far_field): the tree, interaction lists and
+ * work split that a context builds for a geometry, computed on the host without any device work (so
+ * also without a GPU), from
+ *  n              number of particles, >= 1 (particles of a suspension contiguous)
+ *  nodes          n, node count per particle, >= 1
+ *  centres        n x 3
+ *  radius         n, bounding radius: every node lies within it of the centre
+ *  node_box       n x 6, the bounding box of each particle's nodes: lo x, y, z, then hi x, y, z
+ *  suspension_id  n, or NULL for one suspension
+ *  theta, degree, near_delta   as rbs_options.tree_theta, tree_degree (2..12) and near_delta
+ *  sm_count       SMs the work split is sized for (>= 1)
+ *  out            6 values: direct node pairs, proxy pairs, clusters with proxy points, work items,
+ *                 source segments, largest target count of a work item
+ * Returns RBS_EINVAL for a NULL pointer or an argument out of range.  The paper has no counterpart:
+ * its far field is a fast multipole method (Section 3.1).
+ */
+int rbs_treecode_plan(int n, const int* nodes, const double* centres, const double* radius, const double* node_box,
+                      const int* suspension_id, double theta, int degree, double near_delta, int sm_count,
+                      long long* out);
+
 #ifdef __cplusplus
 }
 #endif

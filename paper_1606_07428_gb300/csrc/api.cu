@@ -576,4 +576,30 @@ const char* rbs_last_error(const rbs_ctx* h) {
   return h->c.err.c_str();
 }
 
+int rbs_treecode_plan(int n, const int* nodes, const double* centres, const double* radius, const double* node_box,
+                      const int* suspension_id, double theta, int degree, double near_delta, int sm_count,
+                      long long* out) {
+  if (n < 1 || !nodes || !centres || !radius || !node_box || !out || !(theta > 0.0 && theta < 1.0) || degree < 2 ||
+      degree > 12 || !(near_delta >= 0.0) || sm_count < 1)
+    return RBS_EINVAL;
+  std::vector<long long> offset(n + 1, 0);
+  std::vector<int> sid(n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (nodes[i] < 1 || !(radius[i] >= 0.0)) return RBS_EINVAL;
+    offset[i + 1] = offset[i] + nodes[i];
+    if (suspension_id) sid[i] = suspension_id[i];
+  }
+  const rbs::PlanInput in{n, offset.data(), centres, radius, sid.data(), node_box, near_delta, sm_count};
+  rbs::TreePlan plan;
+  const rbs::Status s = rbs::plan_treecode(in, theta, degree, plan);
+  if (!s.ok()) return s.code;
+  out[0] = plan.direct_pairs;
+  out[1] = plan.proxy_pairs;
+  out[2] = plan.n_cells;
+  out[3] = (long long)plan.items.size();
+  out[4] = (long long)plan.segs.size();
+  out[5] = plan.tmax;
+  return RBS_OK;
+}
+
 }  // extern "C"

@@ -324,6 +324,31 @@ Status magnetic_forces(Context& c, const double H0[3], double mu_ratio, double t
 Status laplace_operator(Context& c, int kind, const double* x, double* y);
 
 // ---- treecode (treecode.cu)
+// Host inputs of the treecode plan: per particle its first node (offset, n + 1 entries), centre,
+// bounding radius, suspension id and node bounding box (lo x, y, z, hi x, y, z).
+struct PlanInput {
+  int n;
+  const long long* offset;
+  const double* centres;
+  const double* radius;
+  const int* sid;
+  const double* pbox;
+  double near_delta;
+  int sm_count;  // sizes the work split (about 96 items per SM)
+};
+// The plan: tree, interaction lists as source segments (nodes first, then (degree + 1)^3 proxy points
+// per accepted cluster), work items, cluster boxes, proxy positions and charge blocks.
+struct TreePlan {
+  std::vector<TreeItem> items;
+  std::vector<int2> segs;
+  std::vector<int4> charge_items;
+  std::vector<int> corder;
+  std::vector<double> box, proxy;
+  int n_cells = 0, tmax = 0;
+  long long n_src = 0, direct_pairs = 0, proxy_pairs = 0, charge_work = 0;
+};
+// Host only: no device work (also usable without a GPU).
+Status plan_treecode(const PlanInput& in, double theta, int degree, TreePlan& plan);
 // Builds (or clears) the treecode of the current geometry; called after the near-pair lists.
 Status build_far_field(Context& c);
 // y += the treecode's float32 smooth pair sum of kind (0 traction, 1 Stokeslet) for density x, with

@@ -593,8 +593,8 @@ struct HCell {
 };
 
 struct TreeBuilder {
-  const Context& c;
-  const std::vector<double>& pbox;
+  const PlanInput& c;
+  const double* pbox;
   std::vector<int>& order;
   std::vector<HCell>& cells;
   std::vector<int>& leaf_of;
@@ -620,7 +620,7 @@ struct TreeBuilder {
       const int j = order[q];
       const double dx = c.centres[3 * j] - h.cen[0], dy = c.centres[3 * j + 1] - h.cen[1],
                    dz = c.centres[3 * j + 2] - h.cen[2];
-      h.r = std::max(h.r, std::sqrt(dx * dx + dy * dy + dz * dz) + c.shapes[c.shape_of[j]].radius);
+      h.r = std::max(h.r, std::sqrt(dx * dx + dy * dy + dz * dz) + c.radius[j]);
     }
     const int id = (int)cells.size();
     cells.push_back(h);
@@ -704,18 +704,10 @@ double f32_operator_error(const Context& c) {
   return kF32OperatorError + C * std::pow(a + std::sqrt(a * a - 1.0), -c.tree.degree);
 }
 
-// Tree, lists, work items and proxy points of one treecode (theta, degree) over the particles'
-// node boxes pbox; df: sources in the double-float layout (positions as exact three-float splits,
-// weighted densities and charges as float32 pairs, charges accumulated in float64).
-static Status build_lists(Context& c, TreeState& T, const std::vector<double>& pbox, double theta, int degree,
-                          bool df) {
-  cudaStream_t s = c.stream;
+Status plan_treecode(const PlanInput& c, double theta, int degree, TreePlan& T) {
   const int n = c.n;
   const int nq = degree + 1, npx = nq * nq * nq;
-  T.degree = degree;
-  T.npx = npx;
-  T.theta = theta;
-  T.df = df;
+  const double* pbox = c.pbox;
 
   // 2. one octree per suspension (particles of a suspension are contiguous)
   std::vector<int> order(n), leaf_of(n, -1), root_of(n, -1);
@@ -732,7 +724,7 @@ static Status build_lists(Context& c, TreeState& T, const std::vector<double>& p
   }
 
   // 3. interaction lists and source segments per target particle
-  const long long N = c.N;
+  const long long N = c.offset[n];
   std::vector<std::vector<int2>> seg_of(n);
   std::vector<long long> proxy_src(n, 0);
   int n_used = 0;
@@ -753,7 +745,7 @@ static Status build_lists(Context& c, TreeState& T, const std::vector<double>& p
       const double dx = B.cen[0] - C.cen[0], dy = B.cen[1] - C.cen[1], dz = B.cen[2] - C.cen[2];
       const double d = std::sqrt(dx * dx + dy * dy + dz * dz);
       const double rr = B.r + C.r;
-      if (rr < T.theta * d && d >= rr + c.opt.near_delta && (long long)npx < C.nodes) {
+      if (rr < theta * d && d >= rr + c.near_delta && (long long)npx < C.nodes) {
         approx.push_back(id);
       } else if (C.nkid > 0) {
         for (int k = C.nkid - 1; k >= 0; --k) stack.push_back(C.kid[k]);
@@ -810,7 +802,6 @@ static Status build_lists(Context& c, TreeState& T, const std::vector<double>& p
     }
   }
   long long tiles = 0;
-  const int old_tmax = T.tmax;
   T.tmax = 0;
   for (int i = 0; i < n; ++i) {
     const int np_i = (int)(c.offset[i + 1] - c.offset[i]);
@@ -818,7 +809,6 @@ static Status build_lists(Context& c, TreeState& T, const std::vector<double>& p
     tiles += k;
     T.tmax = std::max(T.tmax, (np_i + k - 1) / k);
   }
-  if (T.tmax != old_tmax) T.nt[0] = T.nt[1] = T.nt[2] = 0;  // the block shape changed: time the variants again
   const long long want = 96LL * std::max(1, c.sm_count);
   const int splits = (int)std::max(1LL, (want + tiles - 1) / std::max(1LL, tiles));
   T.items.clear();
@@ -858,66 +848,106 @@ static Status build_lists(Context& c, TreeState& T, const std::vector<double>& p
     T.proxy_pairs += (long long)np_i * proxy_src[i];
   }
 
-  // 5. cluster boxes, proxy points and charge blocks
-  std::vector<double> box(6 * (size_t)std::max(1, n_used));
-  std::vector<float4> phi((size_t)n_used * npx), plo((size_t)n_used * npx), pm(df ? (size_t)n_used * npx : 0);
-  std::vector<double> cheb(2 * (size_t)nq);
-  for (int k = 0; k < nq; ++k) {
-    cheb[k] = std::cos(k * kPi / degree);
-    cheb[nq + k] = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == degree) ? 0.5 : 1.0);
-  }
-  std::vector<int> corder;
+  // 5. cluster boxes, proxy points (float64, index a (n+1)^2 + b (n+1) + c per cluster) and charge
+  // blocks
+  T.box.assign(6 * (size_t)std::max(1, n_used), 0.0);
+  T.proxy.assign(3 * (size_t)n_used * npx, 0.0);
+  T.corder.clear();
   T.charge_items.clear();
   T.charge_work = 0;
-  // proxy points carry kProxyPid in the w bits of their hi position, like a node's particle id
-  float proxy_w;
-  {
-    const int v = kProxyPid;
-    std::memcpy(&proxy_w, &v, sizeof(float));
-  }
   for (int u = 0; u < n_used; ++u) {
     const HCell& C = cells[used_cells[u]];
     double mid[3], half[3];
     for (int d = 0; d < 3; ++d) {
       mid[d] = 0.5 * (C.lo[d] + C.hi[d]);
       half[d] = 0.5 * (C.hi[d] - C.lo[d]);
-      box[6 * (size_t)u + d] = mid[d];
-      box[6 * (size_t)u + 3 + d] = half[d] > 0.0 ? 1.0 / half[d] : 0.0;
+      T.box[6 * (size_t)u + d] = mid[d];
+      T.box[6 * (size_t)u + 3 + d] = half[d] > 0.0 ? 1.0 / half[d] : 0.0;
     }
     for (int a = 0; a < nq; ++a)
       for (int b = 0; b < nq; ++b)
         for (int e = 0; e < nq; ++e) {
-          const double v[3] = {mid[0] + half[0] * std::cos(a * kPi / degree), mid[1] + half[1] * std::cos(b * kPi / degree),
-                               mid[2] + half[2] * std::cos(e * kPi / degree)};
-          float h[3], m[3], l[3];
-          for (int d = 0; d < 3; ++d) {
-            h[d] = (float)v[d];
-            const double r = v[d] - (double)h[d];
-            m[d] = (float)r;
-            l[d] = df ? (float)(r - (double)m[d]) : 0.0f;
-          }
           const size_t k = (size_t)u * npx + ((size_t)a * nq + b) * nq + e;
-          phi[k] = make_float4(h[0], h[1], h[2], proxy_w);
-          if (df) {  // exact three-float split, as the nodes' x3h / x3m / x3l
-            pm[k] = make_float4(m[0], m[1], m[2], 0.0f);
-            plo[k] = make_float4(l[0], l[1], l[2], 0.0f);
-          } else {   // float32 hi + lo, as the nodes' xhi / xlo
-            plo[k] = make_float4(m[0], m[1], m[2], 0.0f);
-          }
+          T.proxy[3 * k] = mid[0] + half[0] * std::cos(a * kPi / degree);
+          T.proxy[3 * k + 1] = mid[1] + half[1] * std::cos(b * kPi / degree);
+          T.proxy[3 * k + 2] = mid[2] + half[2] * std::cos(e * kPi / degree);
         }
     // charge blocks over the cell's particles, about 4,096 nodes each
     int q = C.pb;
     while (q < C.pe) {
-      const int first = (int)corder.size();
+      const int first = (int)T.corder.size();
       long long nodes = 0;
       while (q < C.pe && (nodes == 0 || nodes + (c.offset[order[q] + 1] - c.offset[order[q]]) <= 4096)) {
         nodes += c.offset[order[q] + 1] - c.offset[order[q]];
-        corder.push_back(order[q]);
+        T.corder.push_back(order[q]);
         ++q;
       }
-      T.charge_items.push_back(make_int4(u, first, (int)corder.size(), 0));
+      T.charge_items.push_back(make_int4(u, first, (int)T.corder.size(), 0));
     }
     T.charge_work += C.nodes * (long long)npx;
+  }
+  return Status::Ok();
+}
+
+// Tree, lists, work items and proxy points of one treecode (theta, degree) over the particles'
+// node boxes pbox, on the device; df: sources in the double-float layout (positions as exact
+// three-float splits, weighted densities and charges as float32 pairs, charges accumulated in float64).
+static Status build_lists(Context& c, TreeState& T, const std::vector<double>& pbox, double theta, int degree,
+                          bool df) {
+  cudaStream_t s = c.stream;
+  const int nq = degree + 1, npx = nq * nq * nq;
+  const long long N = c.N;
+  std::vector<double> radius(c.n);
+  for (int i = 0; i < c.n; ++i) radius[i] = c.shapes[c.shape_of[i]].radius;
+  const PlanInput in{c.n, c.offset.data(), c.centres.data(), radius.data(), c.sid.data(), pbox.data(),
+                     c.opt.near_delta, c.sm_count};
+  TreePlan P;
+  RBS_TRY(plan_treecode(in, theta, degree, P));
+  T.degree = degree;
+  T.npx = npx;
+  T.theta = theta;
+  T.df = df;
+  if (P.tmax != T.tmax) T.nt[0] = T.nt[1] = T.nt[2] = 0;  // the block shape changed: time the variants again
+  T.tmax = P.tmax;
+  T.n_cells = P.n_cells;
+  T.n_src = P.n_src;
+  T.direct_pairs = P.direct_pairs;
+  T.proxy_pairs = P.proxy_pairs;
+  T.charge_work = P.charge_work;
+  T.items.swap(P.items);
+  T.segs.swap(P.segs);
+  T.charge_items.swap(P.charge_items);
+  const int n_used = P.n_cells;
+  std::vector<double>& box = P.box;
+  std::vector<int>& corder = P.corder;
+  std::vector<float4> phi((size_t)n_used * npx), plo((size_t)n_used * npx), pm(df ? (size_t)n_used * npx : 0);
+  std::vector<double> cheb(2 * (size_t)nq);
+  for (int k = 0; k < nq; ++k) {
+    cheb[k] = std::cos(k * kPi / degree);
+    cheb[nq + k] = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == degree) ? 0.5 : 1.0);
+  }
+  // proxy points carry kProxyPid in the w bits of their hi position, like a node's particle id
+  float proxy_w;
+  {
+    const int v = kProxyPid;
+    std::memcpy(&proxy_w, &v, sizeof(float));
+  }
+  for (size_t k = 0; k < (size_t)n_used * npx; ++k) {
+    float h[3], m[3], l[3];
+    for (int d = 0; d < 3; ++d) {
+      const double v = P.proxy[3 * k + d];
+      h[d] = (float)v;
+      const double r = v - (double)h[d];
+      m[d] = (float)r;
+      l[d] = df ? (float)(r - (double)m[d]) : 0.0f;
+    }
+    phi[k] = make_float4(h[0], h[1], h[2], proxy_w);
+    if (df) {  // exact three-float split, as the nodes' x3h / x3m / x3l
+      pm[k] = make_float4(m[0], m[1], m[2], 0.0f);
+      plo[k] = make_float4(l[0], l[1], l[2], 0.0f);
+    } else {   // float32 hi + lo, as the nodes' xhi / xlo
+      plo[k] = make_float4(m[0], m[1], m[2], 0.0f);
+    }
   }
 
   // 6. device copies

@@ -45,7 +45,7 @@ EXPORTS = [
     "rbs_reset_stats", "rbs_last_error", "rbs_rigid_velocities_noalloc", "rbs_advance", "rbs_get_state",
     "rbs_warmstart_record", "rbs_warmstart_train", "rbs_warmstart_weights", "rbs_warmstart_features",
     "rbs_warmstart_targets", "rbs_warmstart_mlp", "rbs_set_geometry_sh", "rbs_get_contacts",
-    "rbs_magnetic_forces", "rbs_apply_laplace",
+    "rbs_magnetic_forces", "rbs_apply_laplace", "rbs_treecode_plan",
 ]
 
 RBS_MAX_SHAPE_DEGREE = 24
@@ -186,6 +186,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rbs_get_stats": (I, [P, ctypes.POINTER(rbs_stats)]),
         "rbs_reset_stats": (I, [P]),
         "rbs_last_error": (ctypes.c_char_p, [P]),
+        "rbs_treecode_plan": (I, [I, P, P, P, P, P, D, I, D, I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -270,6 +271,23 @@ def rbs_set_geometry_sh(ctx, shapes, shape_of, p, nphi, centres, quats, suspensi
     sid = None if suspension_id is None else _i32(suspension_id)
     _check(ctx, load().rbs_set_geometry_sh(ctx, n, len(shapes), _ptr(pg), _ptr(coef), _ptr(shape_of), _ptr(p),
                                            _ptr(nphi), _ptr(centres), _ptr(quats), _ptr(sid)))
+
+
+def rbs_treecode_plan(nodes, centres, radius, node_box, suspension_id=None, theta=0.5, degree=7, near_delta=1.0,
+                      sm_count=152) -> dict:
+    """Host-only treecode plan (no GPU): direct and proxy pair counts, clusters, work items, segments
+    and the largest work item's target count."""
+    nodes = _i32(nodes)
+    n = nodes.shape[0]
+    centres = _f64(centres, (n, 3))
+    radius = _f64(radius, (n,))
+    node_box = _f64(node_box, (n, 6))
+    sid = None if suspension_id is None else _i32(suspension_id)
+    out = np.zeros(6, np.int64)
+    _check(None, load().rbs_treecode_plan(n, _ptr(nodes), _ptr(centres), _ptr(radius), _ptr(node_box), _ptr(sid),
+                                          float(theta), int(degree), float(near_delta), int(sm_count), _ptr(out)))
+    keys = ["direct_pairs", "proxy_pairs", "cells", "items", "segments", "tmax"]
+    return {k: int(v) for k, v in zip(keys, out)}
 
 
 def rbs_get_contacts(ctx):

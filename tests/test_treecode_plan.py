@@ -1,0 +1,83 @@
+"""Host logic of the treecode (no GPU): the library's plan (rbs_treecode_plan, the same host code that
+builds a context's treecode) against the oracle's statement of the algorithm (oracle/treecode.py).
+Given the same particle centres, bounding radii and node boxes, the two must build the same trees and
+interaction lists, which the exact pair and cluster counts check, at the sizes of the workloads."""
+import numpy as np
+import pytest
+
+import oracle
+import suspensions
+from oracle import treecode as tc
+
+
+@pytest.fixture(scope="module")
+def rbs():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1606_07428_gb300 import rbs as m
+    return m
+
+
+def plan_inputs(system):
+    parts = system.particles
+    nodes = np.array([len(p.w) for p in parts])
+    centres = np.array([p.centre for p in parts])
+    radius = np.array([p.radius for p in parts])
+    box = np.array([np.concatenate(tc.particle_box(p)) for p in parts])
+    sid = np.array([p.suspension for p in parts])
+    return nodes, centres, radius, box, sid
+
+
+def check(rbs, system, theta, degree):
+    t = tc.Treecode(system, theta, degree)
+    direct, proxy = t.pair_counts()
+    cells = len({id(c) for a, _ in t.lists for c in a})
+    nodes, centres, radius, box, sid = plan_inputs(system)
+    plan = rbs.rbs_treecode_plan(nodes, centres, radius, box, sid, theta, degree, system.opt.delta)
+    assert (plan["direct_pairs"], plan["proxy_pairs"], plan["cells"]) == (direct, proxy, cells)
+    # every interacting pair of nodes is evaluated once, exactly or through a cluster
+    total = sum(len(p.w) * sum(len(q.w) for q in system.particles if q.suspension == p.suspension)
+                for p in system.particles)
+    covered = sum(len(p.w) * (sum(len(system.particles[j].w) for j in d) + sum(c.nodes for c in a))
+                  for p, (a, d) in zip(system.particles, t.lists))
+    assert covered == total
+    assert plan["items"] >= len(system.particles) and plan["segments"] >= len(system.particles)
+    assert 0 < plan["tmax"] <= 512
+    return plan
+
+
+@pytest.mark.parametrize("theta,degree", [(0.5, 2), (0.7, 3), (0.3, 2)])
+def test_plan_matches_oracle_small(rbs, theta, degree):
+    s = suspensions.random_ellipsoids(300, 2, 4, 0.10, 0.2, seed=11)
+    system = oracle.System(s.semi_axes, s.p, s.nphi, s.centres, s.quats, s.suspension_id)
+    plan = check(rbs, system, theta, degree)
+    assert plan["proxy_pairs"] > 0
+
+
+def test_plan_matches_oracle_with_several_suspensions(rbs):
+    parts = [suspensions.random_ellipsoids(k, 4, 8, 0.10, 0.2, seed=20 + k) for k in (5, 90, 160)]
+    cat = lambda f: np.concatenate([getattr(x, f) for x in parts])
+    sid = np.concatenate([np.full(x.n, i) for i, x in enumerate(parts)])
+    system = oracle.System(cat("semi_axes"), cat("p"), cat("nphi"), cat("centres"), cat("quats"), sid)
+    plan = check(rbs, system, 0.6, 3)
+    assert plan["proxy_pairs"] > 0
+
+
+@pytest.mark.parametrize("theta,degree", [(0.5, 7), (0.4, 12)])
+def test_plan_matches_oracle_at_the_1000_ellipsoid_size(rbs, theta, degree):
+    """The float32 (0.5, 7) and double-float (0.4, 12) treecodes of the 1,000-ellipsoid workload; the
+    pair counts are those the GPU runs reported (2.61e10 and 6.60e10 per apply)."""
+    s = suspensions.c2_ellipsoids()
+    system = oracle.System(s.semi_axes, s.p, s.nphi, s.centres, s.quats)
+    plan = check(rbs, system, theta, degree)
+    expected = {(0.5, 7): 26121955392, (0.4, 12): 66019686408}[(theta, degree)]
+    assert plan["direct_pairs"] + plan["proxy_pairs"] == expected
+
+
+def test_plan_rejects_bad_arguments(rbs):
+    nodes, centres, radius, box = [4], [[0, 0, 0]], [1.0], [[-1, -1, -1, 1, 1, 1]]
+    for kw in ({"theta": 1.0}, {"theta": 0.0}, {"degree": 1}, {"degree": 13}, {"sm_count": 0}):
+        with pytest.raises(rbs.RbsError):
+            rbs.rbs_treecode_plan(nodes, centres, radius, box, **kw)
+    with pytest.raises(rbs.RbsError):
+        rbs.rbs_treecode_plan([0], centres, radius, box)
