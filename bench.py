@@ -72,7 +72,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
     ap.add_argument("--pair-variant", type=int, default=0,
                     help="pair-kernel variant (rbs_options.pair_variant); 0 lets the library's autotuner choose")
-    ap.add_argument("--far-field", default="tree-df", choices=["direct", "tree", "tree-df"],
+    ap.add_argument("--far-field", default="tree", choices=["direct", "tree", "tree-df"],
                     help="direct sums over all node pairs; tree: the treecode for the float32 inner applies "
                          "(double-float passes stay direct); tree-df: treecodes for both "
                          "(rbs_options.far_field)")
