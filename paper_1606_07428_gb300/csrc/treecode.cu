@@ -1,5 +1,6 @@
-// Hierarchical far field for the float32 smooth pair sums: a barycentric Lagrange treecode (Wang,
-// Krasny and Tlupova, 2020) in place of the fast multipole method of Section 3.1.
+// Hierarchical far field for the smooth pair sums: barycentric Lagrange treecodes (Wang, Krasny and
+// Tlupova, 2020) in place of the fast multipole method of Section 3.1, one for the float32 applies of
+// the inner solve and, optionally, one at higher degree for the double-float passes.
 //
 // Per suspension, an octree over the particle centres (a cell with more than one particle splits at
 // the midpoint of its centres' bounding box; children in octant order, particles ascending).  Each
@@ -10,13 +11,15 @@
 // else descends, and evaluates the particles of unaccepted leaves directly.  An accepted cell
 // carries (n + 1)^3 proxy points on the tensor Chebyshev grid of its box and charges
 //   q_abc = sum_s L_a(y_s,x) L_b(y_s,y) L_c(y_s,z) w_s mu_s     (barycentric Lagrange basis L),
-// recomputed for every apply; the pair kernel then treats proxy points as ordinary sources.
+// recomputed for every apply; the pair kernels then treat proxy points as ordinary sources.
 //
-// Layout: one source array holds the N nodes (float32 hi + lo positions, weighted density) followed
-// by the proxy points of every accepted cell; each target particle has a list of (first, count)
-// segments into it: its own particle first (masked by particle id), then the directly evaluated
-// particles, then its accepted cells.  Work items pair 128 targets of one particle with a run of
-// those segments.
+// Layout: one source array holds the N nodes followed by the proxy points of every accepted cell
+// (float32: hi + lo positions and weighted density; double-float: three-float positions and float32
+// pairs of weighted density, with float64 cluster charges); each target particle has a list of
+// (first, count) segments into it: its own particle first (masked by particle id), then the directly
+// evaluated particles, then its accepted cells.  Work items pair the targets of one particle (or a
+// near-equal part of it, at most 512) with a run of those segments.  The host plan (plan_treecode)
+// does no device work, so it also serves the host-only entry point rbs_treecode_plan.
 #include <algorithm>
 #include <climits>
 #include <cmath>
