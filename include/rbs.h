@@ -404,6 +404,22 @@ int rbs_treecode_plan(int n, const int* nodes, const double* centres, const doub
                       const int* suspension_id, double theta, int degree, double near_delta, int sm_count,
                       long long* out);
 
+/*
+ * Host-only near-pair list (Section 3: close particles take their sources from an upsampled grid):
+ * the ordered pairs (i, j), i != j of one suspension with |c_i - c_j| < R_i + R_j + near_delta, as a
+ * context builds them, without device work.
+ *  n              number of particles, >= 1
+ *  centres        n x 3
+ *  radius         n, bounding radius R
+ *  rmin           n, inscribed radius: two particles whose inscribed spheres intersect overlap
+ *  suspension_id  n, or NULL for one suspension
+ *  pairs          2 x max_pairs ints, or NULL: the pairs (i, j), by i, then j, ascending
+ * Returns the number of near pairs (only the first max_pairs are written), RBS_EOVERLAP for
+ * overlapping particles or RBS_EINVAL for a bad argument.
+ */
+int rbs_near_plan(int n, const double* centres, const double* radius, const double* rmin, const int* suspension_id,
+                  double near_delta, int max_pairs, int* pairs);
+
 #ifdef __cplusplus
 }
 #endif

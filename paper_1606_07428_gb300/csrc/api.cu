@@ -1,5 +1,6 @@
 // The C ABI of include/rbs.h: argument checks, host <-> device copies and dispatch.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 
@@ -600,6 +601,23 @@ int rbs_treecode_plan(int n, const int* nodes, const double* centres, const doub
   out[4] = (long long)plan.segs.size();
   out[5] = plan.tmax;
   return RBS_OK;
+}
+
+int rbs_near_plan(int n, const double* centres, const double* radius, const double* rmin, const int* suspension_id,
+                  double near_delta, int max_pairs, int* pairs) {
+  if (n < 1 || !centres || !radius || !rmin || !(near_delta >= 0.0) || max_pairs < 0 || (max_pairs > 0 && !pairs))
+    return RBS_EINVAL;
+  std::vector<int> sid(n, 0);
+  if (suspension_id)
+    for (int i = 0; i < n; ++i) sid[i] = suspension_id[i];
+  std::vector<int2> out;
+  const rbs::Status s = rbs::plan_near(n, centres, radius, rmin, sid.data(), near_delta, out);
+  if (!s.ok()) return s.code;
+  for (size_t k = 0; k < out.size() && k < (size_t)max_pairs; ++k) {
+    pairs[2 * k] = out[k].x;
+    pairs[2 * k + 1] = out[k].y;
+  }
+  return (int)std::min<size_t>(out.size(), (size_t)INT_MAX);
 }
 
 }  // extern "C"

@@ -364,6 +364,9 @@ double f32_operator_error(const Context& c);
 Status build_geometry(Context& c);
 Status place_particles(Context& c);
 Status build_near(Context& c);
+// Host only: the near pairs of centres with bounding radii R and inscribed radii rmin (see build_near).
+Status plan_near(int n, const double* centres, const double* R, const double* rmin, const int* sid, double delta,
+                 std::vector<int2>& out);
 Status update_configuration(Context& c, const double* centres, const double* quats);
 void gauss_legendre_newton(int n, std::vector<double>& t, std::vector<double>& w);
 

@@ -802,52 +802,61 @@ Status place_particles(Context& c) {
   return Status::Ok();
 }
 
-// Near-pair list (Section 3, upsampling for close particles) and the upsampled source nodes.
+// Near pairs (Section 3, upsampling for close particles): ordered pairs (i, j), i != j of one
+// suspension with |c_i - c_j| < R_i + R_j + delta, found with a cell list; RBS_EOVERLAP when two
+// inscribed spheres (radius rmin) intersect.  Host only.
+Status plan_near(int n, const double* centres, const double* R, const double* rmin, const int* sid, double delta,
+                 std::vector<int2>& out) {
+  out.clear();
+  double rmax = 0.0;
+  for (int i = 0; i < n; ++i) rmax = std::max(rmax, R[i]);
+  const double cell = 2.0 * rmax + delta;
+  std::unordered_map<long long, std::vector<int>> cells;
+  // cells of one suspension only: independent suspensions may occupy the same region
+  auto key = [&](long long a, long long b, long long d, long long q) {
+    return (a * 73856093LL) ^ (b * 19349663LL) ^ (d * 83492791LL) ^ (q * 2654435761LL);
+  };
+  std::vector<long long> ci(3 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    for (int d = 0; d < 3; ++d) ci[3 * i + d] = (long long)std::floor(centres[3 * i + d] / cell);
+    cells[key(ci[3 * i], ci[3 * i + 1], ci[3 * i + 2], sid[i])].push_back(i);
+  }
+  for (int i = 0; i < n; ++i) {
+    std::vector<int> cand;
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dz = -1; dz <= 1; ++dz) {
+          auto it = cells.find(key(ci[3 * i] + dx, ci[3 * i + 1] + dy, ci[3 * i + 2] + dz, sid[i]));
+          if (it == cells.end()) continue;
+          for (int j : it->second) cand.push_back(j);
+        }
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    for (int j : cand) {
+      if (j == i || sid[j] != sid[i]) continue;
+      double dx = centres[3 * i] - centres[3 * j], dy = centres[3 * i + 1] - centres[3 * j + 1],
+             dz = centres[3 * i + 2] - centres[3 * j + 2];
+      double d = std::sqrt(dx * dx + dy * dy + dz * dz);
+      if (d < rmin[i] + rmin[j])
+        return Status::Err(RBS_EOVERLAP, "particles " + std::to_string(i) + " and " + std::to_string(j) +
+                                             " overlap (inscribed spheres intersect)");
+      if (d < R[i] + R[j] + delta) out.push_back(make_int2(i, j));
+    }
+  }
+  return Status::Ok();
+}
+
+// Near-pair list and the upsampled source nodes.
 Status build_near(Context& c) {
   cudaStream_t s = c.stream;
   const int n = c.n;
-  // near pairs: |c_i - c_j| < R_i + R_j + delta within one suspension, by a cell list
-  c.near_pairs.clear();
   {
-    std::vector<double> R(n);
-    double rmax = 0.0;
+    std::vector<double> R(n), rmin(n);
     for (int i = 0; i < n; ++i) {
       R[i] = c.shapes[c.shape_of[i]].radius;
-      rmax = std::max(rmax, R[i]);
+      rmin[i] = c.shapes[c.shape_of[i]].rmin;
     }
-    double cell = 2.0 * rmax + c.opt.near_delta;
-    std::unordered_map<long long, std::vector<int>> cells;
-    // cells of one suspension only: independent suspensions may occupy the same region
-    auto key = [&](long long a, long long b, long long d, long long q) {
-      return (a * 73856093LL) ^ (b * 19349663LL) ^ (d * 83492791LL) ^ (q * 2654435761LL);
-    };
-    std::vector<long long> ci(3 * (size_t)n);
-    for (int i = 0; i < n; ++i) {
-      for (int d = 0; d < 3; ++d) ci[3 * i + d] = (long long)std::floor(c.centres[3 * i + d] / cell);
-      cells[key(ci[3 * i], ci[3 * i + 1], ci[3 * i + 2], c.sid[i])].push_back(i);
-    }
-    for (int i = 0; i < n; ++i) {
-      std::vector<int> cand;
-      for (int dx = -1; dx <= 1; ++dx)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dz = -1; dz <= 1; ++dz) {
-            auto it = cells.find(key(ci[3 * i] + dx, ci[3 * i + 1] + dy, ci[3 * i + 2] + dz, c.sid[i]));
-            if (it == cells.end()) continue;
-            for (int j : it->second) cand.push_back(j);
-          }
-      std::sort(cand.begin(), cand.end());
-      cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-      for (int j : cand) {
-        if (j == i || c.sid[j] != c.sid[i]) continue;
-        double dx = c.centres[3 * i] - c.centres[3 * j], dy = c.centres[3 * i + 1] - c.centres[3 * j + 1],
-               dz = c.centres[3 * i + 2] - c.centres[3 * j + 2];
-        double d = std::sqrt(dx * dx + dy * dy + dz * dz);
-        if (d < c.shapes[c.shape_of[i]].rmin + c.shapes[c.shape_of[j]].rmin)
-          return Status::Err(RBS_EOVERLAP, "particles " + std::to_string(i) + " and " + std::to_string(j) +
-                                               " overlap (inscribed spheres intersect)");
-        if (d < R[i] + R[j] + c.opt.near_delta) c.near_pairs.push_back(make_int2(i, j));
-      }
-    }
+    RBS_TRY(plan_near(n, c.centres.data(), R.data(), rmin.data(), c.sid.data(), c.opt.near_delta, c.near_pairs));
   }
   RBS_TRY(upload(c.d_near, c.near_pairs, s));
   // upsampled sources

@@ -45,7 +45,7 @@ EXPORTS = [
     "rbs_reset_stats", "rbs_last_error", "rbs_rigid_velocities_noalloc", "rbs_advance", "rbs_get_state",
     "rbs_warmstart_record", "rbs_warmstart_train", "rbs_warmstart_weights", "rbs_warmstart_features",
     "rbs_warmstart_targets", "rbs_warmstart_mlp", "rbs_set_geometry_sh", "rbs_get_contacts",
-    "rbs_magnetic_forces", "rbs_apply_laplace", "rbs_treecode_plan",
+    "rbs_magnetic_forces", "rbs_apply_laplace", "rbs_treecode_plan", "rbs_near_plan",
 ]
 
 RBS_MAX_SHAPE_DEGREE = 24
@@ -187,6 +187,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rbs_reset_stats": (I, [P]),
         "rbs_last_error": (ctypes.c_char_p, [P]),
         "rbs_treecode_plan": (I, [I, P, P, P, P, P, D, I, D, I, P]),
+        "rbs_near_plan": (I, [I, P, P, P, P, D, I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -288,6 +289,22 @@ def rbs_treecode_plan(nodes, centres, radius, node_box, suspension_id=None, thet
                                           float(theta), int(degree), float(near_delta), int(sm_count), _ptr(out)))
     keys = ["direct_pairs", "proxy_pairs", "cells", "items", "segments", "tmax"]
     return {k: int(v) for k, v in zip(keys, out)}
+
+
+def rbs_near_plan(centres, radius, rmin, suspension_id=None, near_delta=1.0) -> np.ndarray:
+    """Host-only near pairs (n_pairs, 2) int32, as a context builds them (no GPU)."""
+    centres = _f64(centres, (-1, 3))
+    n = centres.shape[0]
+    radius = _f64(radius, (n,))
+    rmin = _f64(rmin, (n,))
+    sid = None if suspension_id is None else _i32(suspension_id)
+    cnt = _check(None, load().rbs_near_plan(n, _ptr(centres), _ptr(radius), _ptr(rmin), _ptr(sid), float(near_delta),
+                                            0, None), allow=range(0, 1 << 31))
+    pairs = np.zeros((cnt, 2), np.int32)
+    if cnt:
+        _check(None, load().rbs_near_plan(n, _ptr(centres), _ptr(radius), _ptr(rmin), _ptr(sid), float(near_delta),
+                                          cnt, _ptr(pairs)), allow=range(0, 1 << 31))
+    return pairs
 
 
 def rbs_get_contacts(ctx):

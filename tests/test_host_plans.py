@@ -1,7 +1,8 @@
-"""Host logic of the treecode (no GPU): the library's plan (rbs_treecode_plan, the same host code that
-builds a context's treecode) against the oracle's statement of the algorithm (oracle/treecode.py).
-Given the same particle centres, bounding radii and node boxes, the two must build the same trees and
-interaction lists, which the exact pair and cluster counts check, at the sizes of the workloads."""
+"""Host logic of the library without a GPU: the treecode plan (rbs_treecode_plan) and the near-pair
+list (rbs_near_plan), the same host code a context runs, against the oracle's statement of each
+(oracle/treecode.py; the near criterion of oracle.System).  Given the same particle centres, radii
+and node boxes, the two must build the same trees, interaction lists and near pairs, which exact pair,
+cluster and pair-set comparisons check at the sizes of the workloads."""
 import numpy as np
 import pytest
 
@@ -81,3 +82,39 @@ def test_plan_rejects_bad_arguments(rbs):
             rbs.rbs_treecode_plan(nodes, centres, radius, box, **kw)
     with pytest.raises(rbs.RbsError):
         rbs.rbs_treecode_plan([0], centres, radius, box)
+
+
+def test_near_plan_matches_oracle_near_pairs(rbs):
+    """The library's near-pair list (the host code a context runs) equals the oracle's near set on the
+    1,000-ellipsoid workload."""
+    s = suspensions.c2_ellipsoids()
+    system = oracle.System(s.semi_axes, s.p, s.nphi, s.centres, s.quats)
+    radius = np.array([p.radius for p in system.particles])
+    pairs = rbs.rbs_near_plan(s.centres, radius, s.semi_axes.min(1), None, system.opt.delta)
+    assert set(map(tuple, pairs.tolist())) == system.near
+    assert len(pairs) == len(system.near) > 0
+
+
+def test_near_plan_on_independent_suspensions(rbs):
+    """The 256-suspension workload (25,210 particles): pairs only within a suspension, exactly those
+    closer than R_i + R_j + 1 (brute force per suspension)."""
+    s = suspensions.c4_batched()
+    R = s.semi_axes.max(1)
+    pairs = rbs.rbs_near_plan(s.centres, R, s.semi_axes.min(1), s.suspension_id, 1.0)
+    got = set(map(tuple, pairs.tolist()))
+    want = set()
+    for k in np.unique(s.suspension_id):
+        idx = np.nonzero(s.suspension_id == k)[0]
+        d = np.linalg.norm(s.centres[idx, None, :] - s.centres[None, idx, :], axis=2)
+        hit = (d < R[idx, None] + R[None, idx] + 1.0) & ~np.eye(len(idx), dtype=bool)
+        want |= {(int(idx[a]), int(idx[b])) for a, b in zip(*np.nonzero(hit))}
+    assert got == want and len(got) > 0
+
+
+def test_near_plan_reports_overlap(rbs):
+    centres = np.array([[0.0, 0.0, 0.0], [1.5, 0.0, 0.0], [9.0, 0.0, 0.0]])
+    with pytest.raises(rbs.RbsError) as e:
+        rbs.rbs_near_plan(centres, [1.0, 1.0, 1.0], [0.8, 0.8, 0.8])
+    assert e.value.code == rbs.RBS_EOVERLAP
+    # in different suspensions the same centres do not interact
+    assert len(rbs.rbs_near_plan(centres, [1.0, 1.0, 1.0], [0.8, 0.8, 0.8], [0, 1, 2])) == 0
