@@ -265,22 +265,6 @@ __global__ void k_colsum(int M, int N, const float* __restrict__ A, float* __res
   out[cidx] = s;
 }
 
-// Adam (Kingma & Ba) on float32 masters; also refreshes the bfloat16 copy.
-__global__ void k_adam(long long n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2,
-                       __nv_bfloat16* __restrict__ wb) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    w[i] = wi;
-    if (wb) wb[i] = __float2bfloat16(wi);
-  }
-}
-
 // gather rows idx[r] of a (rows x cols) matrix
 template <typename T>
 __global__ void k_gather_rows(int rows, int cols, const int* __restrict__ idx, const T* __restrict__ src, T* __restrict__ dst) {
@@ -303,7 +287,8 @@ __global__ void k_gather_step(int rows, int cols, const int* __restrict__ perm, 
   }
 }
 
-// Adam with the step count t + 1 read from the device (bias corrections 1 - b^(t+1)).
+// Adam (Kingma & Ba) on float32 masters, refreshing the bfloat16 copy, with the step count t + 1 read
+// from the device (bias corrections 1 - b^(t+1)).
 __global__ void k_adam_dev(long long n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
                            float* __restrict__ v, float lr, float b1, float b2, float eps, const long long* __restrict__ t,
                            __nv_bfloat16* __restrict__ wb) {
