@@ -420,6 +420,22 @@ int rbs_treecode_plan(int n, const int* nodes, const double* centres, const doub
 int rbs_near_plan(int n, const double* centres, const double* radius, const double* rmin, const int* suspension_id,
                   double near_delta, int max_pairs, int* pairs);
 
+/*
+ * Host-only reflection-symmetry tables of the (p, n_phi) grid (Eq. 33), by which ellipsoid self blocks
+ * are stored as the rows of representative nodes and the preconditioner is inverted per irreducible
+ * representation.  The reflections h = 0..7 (bit 0: x -> -x, i.e. phi -> pi - phi; bit 1: y -> -y,
+ * phi -> -phi; bit 2: z -> -z, theta -> pi - theta) map grid nodes to grid nodes (n_phi even).
+ *  p, nphi   the grid: 2 <= p <= 32, n_phi even and >= 2p
+ *  rep_of    (p + 1) n_phi ints, or NULL: the representative (j, k), j <= p/2, k <= n_phi/4, of each
+ *            node's orbit, as j (n_phi/4 + 1) + k
+ *  g_of      (p + 1) n_phi ints, or NULL: a reflection taking the representative to the node
+ *  irrep_dim 8 ints, or NULL: the dimension of each irreducible representation's block of the
+ *            3 (p + 1) n_phi surface-field components (they sum to 3 (p + 1) n_phi)
+ * Returns the number of representatives, or RBS_EINVAL.  The paper has no counterpart (a storage
+ * scheme of this library, exact up to rounding).
+ */
+int rbs_grid_symmetry(int p, int nphi, int* rep_of, int* g_of, int* irrep_dim);
+
 #ifdef __cplusplus
 }
 #endif

@@ -603,6 +603,22 @@ int rbs_treecode_plan(int n, const int* nodes, const double* centres, const doub
   return RBS_OK;
 }
 
+int rbs_grid_symmetry(int p, int nphi, int* rep_of, int* g_of, int* irrep_dim) {
+  if (p < 2 || p > 32 || nphi < 2 * p || (nphi & 1)) return RBS_EINVAL;
+  std::vector<int> r, g;
+  int dims[8], nrep = 0;
+  const rbs::Status s = rbs::grid_symmetry_host(p, nphi, r, g, dims, &nrep);
+  if (!s.ok()) return s.code;
+  const size_t np = (size_t)(p + 1) * nphi;
+  for (size_t t = 0; t < np; ++t) {
+    if (rep_of) rep_of[t] = r[t];
+    if (g_of) g_of[t] = g[t];
+  }
+  if (irrep_dim)
+    for (int c = 0; c < 8; ++c) irrep_dim[c] = dims[c];
+  return nrep;
+}
+
 int rbs_near_plan(int n, const double* centres, const double* radius, const double* rmin, const int* suspension_id,
                   double near_delta, int max_pairs, int* pairs) {
   if (n < 1 || !centres || !radius || !rmin || !(near_delta >= 0.0) || max_pairs < 0 || (max_pairs > 0 && !pairs))

@@ -364,6 +364,9 @@ double f32_operator_error(const Context& c);
 Status build_geometry(Context& c);
 Status place_particles(Context& c);
 Status build_near(Context& c);
+// Host only: the reflection-symmetry tables of a (p, n_phi) grid (see rbs_grid_symmetry).
+Status grid_symmetry_host(int p, int nphi, std::vector<int>& rep_of, std::vector<int>& g_of, int irrep_dim[8],
+                          int* nrep);
 // Host only: the near pairs of centres with bounding radii R and inscribed radii rmin (see build_near).
 Status plan_near(int n, const double* centres, const double* R, const double* rmin, const int* sid, double delta,
                  std::vector<int2>& out);

@@ -602,6 +602,21 @@ static void build_symmetry(Grid& g) {
   }
 }
 
+// Host only: the symmetry tables of the (p, n_phi) grid (rep_of, g_of per node; irrep dimensions).
+Status grid_symmetry_host(int p, int nphi, std::vector<int>& rep_of, std::vector<int>& g_of, int irrep_dim[8],
+                          int* nrep) {
+  Grid g;
+  g.p = p;
+  g.nphi = nphi;
+  g.np = (p + 1) * nphi;
+  build_symmetry(g);
+  rep_of = g.rep_of;
+  g_of = g.g_of;
+  for (int c = 0; c < 8; ++c) irrep_dim[c] = g.irrep_dim[c];
+  *nrep = g.nrep;
+  return Status::Ok();
+}
+
 // Device layout of the symmetry tables: rep_of, g_of (np each), orbit (nrep), orb_node, orb_g
 // (8 nrep each), irrep_pos (24 nrep), irrep_list (24 nrep: per irrep, 3 r + beta of each basis vector).
 static SymTables sym_tables(const Grid& g) {

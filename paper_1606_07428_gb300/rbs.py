@@ -46,6 +46,7 @@ EXPORTS = [
     "rbs_warmstart_record", "rbs_warmstart_train", "rbs_warmstart_weights", "rbs_warmstart_features",
     "rbs_warmstart_targets", "rbs_warmstart_mlp", "rbs_set_geometry_sh", "rbs_get_contacts",
     "rbs_magnetic_forces", "rbs_apply_laplace", "rbs_treecode_plan", "rbs_near_plan",
+    "rbs_grid_symmetry",
 ]
 
 RBS_MAX_SHAPE_DEGREE = 24
@@ -188,6 +189,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rbs_last_error": (ctypes.c_char_p, [P]),
         "rbs_treecode_plan": (I, [I, P, P, P, P, P, D, I, D, I, P]),
         "rbs_near_plan": (I, [I, P, P, P, P, D, I, P]),
+        "rbs_grid_symmetry": (I, [I, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -305,6 +307,17 @@ def rbs_near_plan(centres, radius, rmin, suspension_id=None, near_delta=1.0) -> 
         _check(None, load().rbs_near_plan(n, _ptr(centres), _ptr(radius), _ptr(rmin), _ptr(sid), float(near_delta),
                                           cnt, _ptr(pairs)), allow=range(0, 1 << 31))
     return pairs
+
+
+def rbs_grid_symmetry(p: int, nphi: int):
+    """Host-only symmetry tables of a grid: (representatives, rep_of, g_of, irrep_dim)."""
+    np_ = (p + 1) * nphi
+    rep_of = np.zeros(np_, np.int32)
+    g_of = np.zeros(np_, np.int32)
+    dims = np.zeros(8, np.int32)
+    nrep = _check(None, load().rbs_grid_symmetry(int(p), int(nphi), _ptr(rep_of), _ptr(g_of), _ptr(dims)),
+                  allow=range(0, 1 << 31))
+    return nrep, rep_of, g_of, dims
 
 
 def rbs_get_contacts(ctx):

@@ -118,3 +118,42 @@ def test_near_plan_reports_overlap(rbs):
     assert e.value.code == rbs.RBS_EOVERLAP
     # in different suspensions the same centres do not interact
     assert len(rbs.rbs_near_plan(centres, [1.0, 1.0, 1.0], [0.8, 0.8, 0.8], [0, 1, 2])) == 0
+
+
+@pytest.mark.parametrize("p,nphi", [(2, 4), (5, 10), (8, 16), (10, 22), (12, 24), (16, 32)])
+def test_grid_symmetry_tables(rbs, p, nphi):
+    """The reflection tables behind the representative-row storage of ellipsoid self blocks, against
+    the oracle's grid (Eq. 33): each node is its representative reflected by g_of (sign flips of x, y,
+    z per bit), every representative is used, and each irreducible representation's dimension equals
+    an independent count over the orbits' stabilisers (computed from the node positions), the eight
+    summing to 3 (p + 1) n_phi."""
+    from oracle import sphere_grid
+    nrep, rep_of, g_of, dims = rbs.rbs_grid_symmetry(p, nphi)
+    th, ph, _ = sphere_grid.grid_points(p, nphi)
+    s = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
+    nk = nphi // 4 + 1
+    assert nrep == (p // 2 + 1) * nk
+    rep_node = (rep_of // nk) * nphi + rep_of % nk
+    flips = lambda h: np.array([-1.0 if h & 1 else 1.0, -1.0 if h & 2 else 1.0, -1.0 if h & 4 else 1.0])
+    sign = np.array([flips(int(g)) for g in g_of])
+    assert np.abs(s[rep_node] * sign - s).max() < 1e-12
+    assert set(rep_of.tolist()) == set(range(nrep))
+    # independent irrep dimensions: for the orbit of representative r with stabiliser H (the
+    # reflections fixing its position), component beta belongs to irrep c when
+    # (-1)^popcount(c & h) * (-1)^(bit beta of h) = 1 for every h in H
+    want = np.zeros(8, int)
+    reps = np.unique(rep_node)
+    for t in reps:
+        H = [h for h in range(8) if np.abs(s[t] * flips(h) - s[t]).max() < 1e-12]
+        for c in range(8):
+            for beta in range(3):
+                if all((-1) ** (bin(c & h).count("1") + ((h >> beta) & 1)) == 1 for h in H):
+                    want[c] += 1
+    assert dims.tolist() == want.tolist()
+    assert dims.sum() == 3 * (p + 1) * nphi
+
+
+def test_grid_symmetry_rejects_bad_grids(rbs):
+    for p, nphi in ((1, 4), (33, 66), (4, 7), (4, 6)):
+        with pytest.raises(rbs.RbsError):
+            rbs.rbs_grid_symmetry(p, nphi)
