@@ -4,9 +4,12 @@ pair and cluster counts), the float32 off-diagonal operators within float32 roun
 treecode and within the error model of the exact operator, and mixed solves that converge to the
 exact (direct-sum) answer because the double-float refinement passes stay direct.
 
-Cases: 300 ellipsoids at p = 2 (one target tile per particle, one source run), and 64 ellipsoids
-at p = 8 (two target tiles per particle, source lists split into several runs, whole-particle
-leaves approximated); the 1,000-ellipsoid workload at full size with the default parameters."""
+Cases: 300 ellipsoids at p = 2 (one work item per particle and source run), and 64 ellipsoids at
+p = 8 (source lists split into several runs, whole-particle leaves approximated); the 1,000-ellipsoid
+workload at full size with the default parameters.  The double-float passes' treecode
+(RBS_FAR_TREECODE_DF) is checked the same way: its lists and operator against the oracle's at a low
+degree, and a full-size solve with both treecodes against the exact residual and the all-direct
+solve."""
 import numpy as np
 import pytest
 
