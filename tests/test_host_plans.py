@@ -55,13 +55,16 @@ def test_plan_matches_oracle_small(rbs, theta, degree):
     assert plan["proxy_pairs"] > 0
 
 
-def test_plan_matches_oracle_with_several_suspensions(rbs):
-    parts = [suspensions.random_ellipsoids(k, 4, 8, 0.10, 0.2, seed=20 + k) for k in (5, 90, 160)]
+@pytest.mark.parametrize("sizes", [(5, 90, 160), (1, 2, 90), (1,)])
+def test_plan_matches_oracle_with_several_suspensions(rbs, sizes):
+    """Independent suspensions, including the degenerate ones: a single particle (a one-leaf tree with
+    nothing to approximate) and a pair."""
+    parts = [suspensions.random_ellipsoids(k, 4, 8, 0.10, 0.2, seed=20 + k) for k in sizes]
     cat = lambda f: np.concatenate([getattr(x, f) for x in parts])
     sid = np.concatenate([np.full(x.n, i) for i, x in enumerate(parts)])
     system = oracle.System(cat("semi_axes"), cat("p"), cat("nphi"), cat("centres"), cat("quats"), sid)
     plan = check(rbs, system, 0.6, 3)
-    assert plan["proxy_pairs"] > 0
+    assert (plan["proxy_pairs"] > 0) == (max(sizes) >= 90)
 
 
 @pytest.mark.parametrize("theta,degree", [(0.5, 7), (0.4, 12)])
