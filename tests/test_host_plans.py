@@ -160,3 +160,25 @@ def test_grid_symmetry_rejects_bad_grids(rbs):
     for p, nphi in ((1, 4), (33, 66), (4, 7), (4, 6)):
         with pytest.raises(rbs.RbsError):
             rbs.rbs_grid_symmetry(p, nphi)
+
+
+def test_plan_with_mixed_grids(rbs):
+    """Particles on different grids (p in {2, 4, 6}, as the batched workload mixes them): ragged node
+    counts per particle and per cluster."""
+    s = suspensions.random_ellipsoids(200, 2, None, 0.10, 0.2, seed=31)
+    rng = np.random.default_rng(31)
+    s.p = rng.choice(np.array([2, 4, 6], np.int32), size=s.n).astype(np.int32)
+    s.nphi = (2 * s.p).astype(np.int32)
+    system = oracle.System(s.semi_axes, s.p, s.nphi, s.centres, s.quats, s.suspension_id)
+    plan = check(rbs, system, 0.6, 3)
+    assert plan["proxy_pairs"] > 0
+
+
+def test_plan_refuses_more_sources_than_int32(rbs):
+    """Source indices are 32-bit: a geometry beyond 2^31 nodes is refused, not wrapped."""
+    nodes = [2_000_000_000, 2_000_000_000]
+    centres = [[0.0, 0.0, 0.0], [10.0, 0.0, 0.0]]
+    box = [[-1, -1, -1, 1, 1, 1], [9, -1, -1, 11, 1, 1]]
+    with pytest.raises(rbs.RbsError) as e:
+        rbs.rbs_treecode_plan(nodes, centres, [1.0, 1.0], box)
+    assert e.value.code == rbs.RBS_ENOMEM
