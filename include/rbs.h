@@ -123,6 +123,10 @@ typedef struct {
   double tree_df_theta; /* opening criterion of the double-float passes' treecode (default 0.4) */
   int tree_df_degree;  /* its interpolation degree (default 12; 2 <= n <= 12); its cluster charges are
                           formed in float64 */
+  int graphs;          /* 1 (default): the GMRES Arnoldi step of the mobility operator is captured once
+                          per configuration into a CUDA graph whose conditional loop runs a whole
+                          restart cycle on the device; 0: the same kernels are launched from the host,
+                          with one host read of the stopping flags per iteration */
 } rbs_options;
 
 #define RBS_FAR_DIRECT 0
@@ -145,12 +149,17 @@ typedef struct {
 #define RBS_KC_PAIR_KSDF 8 /* smooth traction and Stokeslet sums of one density in one pass, double-float */
 #define RBS_KC_TREE 9     /* treecode cluster charges (RBS_FAR_TREECODE); the treecode's pair sums count
                              under RBS_KC_PAIR_K32 / RBS_KC_PAIR_S32 with their evaluated pairs as units */
-#define RBS_KC_COUNT 10
+#define RBS_KC_GMRES_GRAPH 10 /* launches of the captured GMRES cycle graph (rbs_options.graphs); units =
+                             Arnoldi steps it ran.  Kernels replayed inside it are not counted under
+                             their own classes (their launches still count in rbs_stats.launches) */
+#define RBS_KC_COUNT 11
 
 typedef struct {
-  int iterations;        /* total GMRES iterations of the last solve (inner iterations for mixed) */
+  int iterations;        /* GMRES iterations of the last solve (inner iterations for mixed), the largest
+                            over the suspensions (rbs_get_suspension_results gives each) */
   int refinements;       /* outer float64 refinement steps of the last solve (0 for FP64) */
-  double residual;       /* final relative residual ||b - A mu|| / ||b|| in float64 */
+  double residual;       /* final relative residual ||b_s - A mu_s|| / ||b_s|| in float64, the largest over
+                            the suspensions s */
   double setup_ms;       /* wall time of the last rbs_set_geometry */
   double solve_ms;       /* wall time of the last rbs_mobility_solve */
   long long total_nodes;
@@ -266,13 +275,17 @@ int rbs_get_surface(rbs_ctx* ctx, double* x, double* normal, double* weight);
 
 /*
  * The mobility solve (the three steps at the start of Section 3; Algorithm 1 lines 3-5 without
- * contact).
+ * contact).  Suspensions (rbs_set_geometry's suspension_id) do not interact, so each is its own
+ * system and converges on its own: GMRES keeps one Krylov recursion per suspension, and a suspension
+ * stops iterating once its own residual is within tolerance.
  *  F, T        n x 3 forces and torques
- *  tol         relative residual ||b - A mu||_2 / ||b||_2 at which GMRES stops (b the right-hand side
- *              of Eq. 25); for RBS_PREC_MIXED the float64 refinement stops at this tolerance
+ *  tol         relative residual ||b_s - A mu_s||_2 / ||b_s||_2 at which GMRES stops, for every
+ *              suspension s (b the right-hand side of Eq. 25); for RBS_PREC_MIXED the float64
+ *              refinement stops when every suspension is at this tolerance
  *  v, omega    n x 3 outputs
  *  density     NULL, or total_nodes x 3 output receiving mu (lab frame)
- *  iterations  NULL, or one int receiving the GMRES iteration count
+ *  iterations  NULL, or rbs_suspension_count() ints receiving each suspension's GMRES iterations (in
+ *              the order the suspensions appear; one int for a single suspension)
  * Returns RBS_ENOTCONV (outputs written) when max_iters is reached first.
  */
 int rbs_mobility_solve(rbs_ctx* ctx, const double* F, const double* T, double tol, double* v,
@@ -282,6 +295,14 @@ int rbs_mobility_solve(rbs_ctx* ctx, const double* F, const double* T, double to
  * total_nodes x 3).  Work is ordered on the context's stream; the call returns after it completes. */
 int rbs_mobility_solve_device(rbs_ctx* ctx, const double* F_dev, const double* T_dev, double tol,
                               double* v_dev, double* omega_dev, double* density_dev, int* iterations);
+
+/* Number of suspensions of the current geometry (runs of equal suspension_id; 1 without ids). */
+int rbs_suspension_count(const rbs_ctx* ctx);
+
+/* Per-suspension outcome of the last mobility solve: iterations (NULL or rbs_suspension_count() ints,
+ * GMRES iterations, summed over refinements and contact solves) and residual (NULL or that many
+ * doubles, the final relative residual ||b_s - A mu_s|| / ||b_s|| of suspension s; 0 when b_s = 0). */
+int rbs_get_suspension_results(rbs_ctx* ctx, int* iterations, double* residual);
 
 /* Explicit Runge-Kutta schemes for rbs_advance. */
 #define RBS_RK_EULER 1
@@ -295,8 +316,8 @@ int rbs_mobility_solve_device(rbs_ctx* ctx, const double* F_dev, const double* T
  * Every stage is one mobility solve to relative tolerance tol at the stage configuration (the
  * body-frame self blocks and preconditioner are reused, Eq. 38), with the contact correction of
  * Section 3.4 when rbs_options.contact_gap > 0; quaternions are renormalised after each step.  The
- * context's configuration is updated in place; iterations (may be NULL) receives the total GMRES
- * iterations.  Returns RBS_EOVERLAP if the inscribed spheres of two particles intersect.
+ * context's configuration is updated in place; iterations (may be NULL) receives the GMRES iterations
+ * summed over the stage solves (each stage counting its largest suspension).  Returns RBS_EOVERLAP if the inscribed spheres of two particles intersect.
  */
 int rbs_advance(rbs_ctx* ctx, const double* F, const double* T, double dt, int steps, int scheme, double tol,
                 int* iterations);
@@ -312,19 +333,23 @@ int rbs_rigid_velocities(rbs_ctx* ctx, const double* u, double* v, double* omega
 
 /*
  * Allocation-free variant of rbs_rigid_velocities, on device buffers.  The paper has no counterpart:
- * this entry point exists for callers that may not allocate device memory at call time, such as code
- * running while a stream is captured into a CUDA graph (where cudaMalloc is not allowed), real-time
- * stepping loops that forbid allocator calls, or hosts that give the library a fixed memory budget.
+ * this entry point exists for callers that may not allocate device memory at call time, such as
+ * frameworks that reserve nearly all device memory for their own pool (a cudaMalloc from inside them
+ * can fail), real-time stepping loops that forbid allocator calls, or hosts that give the library a
+ * fixed memory budget.
  *  u_dev      total_nodes x 3 surface velocity (device)
  *  v_dev, omega_dev   n x 3 outputs (device), Eqs. 41-42
  * The per-particle intermediate lives in a fixed device array of 6 x 65,536 float64 (3 MiB), which
  * every GPU that loads the library holds until the process exits; geometries with more than 65,536
  * particles are rejected with RBS_EINVAL.  No cudaMalloc, cudaFree or allocating library routine is
  * called.  The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All calls share the array
- * and each overwrites the entries it reads, so calls whose work overlaps on the GPU (other contexts or
- * streams at the same time) race and must be ordered by the caller.  Work runs on the context's
- * stream; the call returns after it completes.
+ * that device current and keeps it for the process: make that first call before any stream capture,
+ * and do not reset the device (cudaDeviceReset) afterwards, since the array may then move and the
+ * kept address would be stale.  All calls, from every context of the process, share the one array per
+ * device, and each call overwrites the entries it reads, so calls whose work overlaps on the GPU
+ * (other contexts or streams at the same time) race and must be ordered by the caller.  Work runs on
+ * the context's stream and the call waits for it to complete before returning; the caller's current
+ * device is restored.
  */
 int rbs_rigid_velocities_noalloc(rbs_ctx* ctx, const double* u_dev, double* v_dev, double* omega_dev);
 

@@ -110,6 +110,7 @@ void rbs_default_options(rbs_options* o) {
   o->tree_degree = 7;
   o->tree_df_theta = 0.4;
   o->tree_df_degree = 12;
+  o->graphs = 1;
 }
 
 int rbs_create(const rbs_options* opt, rbs_ctx** out) {
@@ -131,7 +132,8 @@ int rbs_create(const rbs_options* opt, rbs_ctx** out) {
       !std::isfinite(o.magnetic_field[0]) || !std::isfinite(o.magnetic_field[1]) || !std::isfinite(o.magnetic_field[2]) ||
       (o.far_field != RBS_FAR_DIRECT && o.far_field != RBS_FAR_TREECODE && o.far_field != RBS_FAR_TREECODE_DF) ||
       !(o.tree_theta > 0.0 && o.tree_theta < 1.0) || o.tree_degree < 2 || o.tree_degree > 10 ||
-      !(o.tree_df_theta > 0.0 && o.tree_df_theta < 1.0) || o.tree_df_degree < 2 || o.tree_df_degree > 12)
+      !(o.tree_df_theta > 0.0 && o.tree_df_theta < 1.0) || o.tree_df_degree < 2 || o.tree_df_degree > 12 ||
+      (o.graphs != 0 && o.graphs != 1))
     return RBS_EINVAL;
   rbs_ctx* h = new rbs_ctx();
   Context& c = h->c;
@@ -294,7 +296,28 @@ static int solve_common(rbs_ctx* h, const double* F, const double* T, double tol
     return finish(c, Status::Err(RBS_EINVAL, "mobility_solve: non-finite force or torque"));
   Status s = enter(c);
   if (!s.ok()) return finish(c, s);
-  return finish(c, rbs::mobility_solve(c, F, T, tol, v, omega, density, iterations, device_io));
+  int its = 0;
+  s = rbs::mobility_solve(c, F, T, tol, v, omega, density, &its, device_io);
+  if (iterations && (s.ok() || s.code == RBS_ENOTCONV))
+    for (int k = 0; k < c.seg3.S; ++k) iterations[k] = k < (int)c.susp_iters.size() ? c.susp_iters[k] : 0;
+  return finish(c, s);
+}
+
+int rbs_suspension_count(const rbs_ctx* h) {
+  if (!h) return RBS_EINVAL;
+  return h->c.have_geometry ? h->c.seg3.S : 0;
+}
+
+int rbs_get_suspension_results(rbs_ctx* h, int* iterations, double* residual) {
+  if (!h) return RBS_EINVAL;
+  Context& c = h->c;
+  if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
+  const int S = c.seg3.S;
+  for (int k = 0; k < S; ++k) {
+    if (iterations) iterations[k] = k < (int)c.susp_iters.size() ? c.susp_iters[k] : 0;
+    if (residual) residual[k] = k < (int)c.susp_res.size() ? c.susp_res[k] : 0.0;
+  }
+  return finish(c, Status::Ok());
 }
 
 int rbs_mobility_solve(rbs_ctx* h, const double* F, const double* T, double tol, double* v, double* omega,

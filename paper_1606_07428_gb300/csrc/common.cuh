@@ -177,6 +177,65 @@ struct TreeState {
   void release();
 };
 
+// Contiguous segments of a vector (the suspensions of a batch) for the segmented GMRES (gmres.cu):
+// element offsets, and chunks of at most 4,096 elements that never straddle a segment.
+struct SegChunk {
+  long long b, e;
+  int seg, pad;
+};
+struct SegSet {
+  int S = 0, nch = 0;
+  long long n = 0;
+  std::vector<long long> off;  // S + 1 element offsets
+  DevBuf<SegChunk> d_chunks;
+  DevBuf<int> d_c0;            // S + 1: first chunk of each segment
+  Status build(const std::vector<long long>& offsets, cudaStream_t s);
+};
+// Per-segment outcome of a segmented GMRES solve.
+struct SegResult {
+  std::vector<int> iters;
+  std::vector<double> res;   // final residual estimate (absolute)
+  std::vector<char> conv;
+  int cycles = 0;
+};
+// Device workspace of the segmented GMRES (Krylov basis, per-segment Hessenberg matrices, rotations,
+// coefficients, flags) and pinned host mirrors of its per-segment outputs.
+struct GmresWork {
+  DevBuf<double> H, cs, sn, g, y, coef, partial, segd, vin, V, w, z, r;
+  DevBuf<int> segi;
+  double* host = nullptr;  // host_cap doubles, then 4 S + 8 ints (hint), the last 8 of them hctrl
+  int* hint = nullptr;
+  int* hctrl = nullptr;
+  size_t host_cap = 0;
+  int max_iters = 0;
+  long long version = 0;  // bumped when a buffer is reallocated (captured graphs hold its pointers)
+  GmresWork() = default;
+  ~GmresWork() {
+    if (host) cudaFreeHost(host);
+  }
+  GmresWork(const GmresWork&) = delete;
+  GmresWork& operator=(const GmresWork&) = delete;
+};
+// Captured Arnoldi-step graphs (a WHILE conditional node around one step), one slot per operator and
+// arithmetic, each valid for the configuration and workspace it was captured with.
+struct GmresGraphs {
+  static constexpr int kSlots = 8;
+  struct Slot {
+    cudaGraphExec_t exec = nullptr;
+    long long config = -1, work = -1;
+    int S = 0, m = 0;
+    bool failed = false;
+    long long launches_per_step = 0;
+  };
+  Slot slot[kSlots];
+  cudaStream_t cap_stream = nullptr;
+  void release();
+  GmresGraphs() = default;
+  ~GmresGraphs() { release(); }
+  GmresGraphs(const GmresGraphs&) = delete;
+  GmresGraphs& operator=(const GmresGraphs&) = delete;
+};
+
 struct Context {
   rbs_options opt{};
   cudaStream_t stream = nullptr;
@@ -266,10 +325,21 @@ struct Context {
 
   // scratch vectors (3N doubles each) and GMRES workspace
   DevBuf<double> d_vec[10];
-  DevBuf<double> d_V, d_H, d_givens, d_partials;
+  DevBuf<double> d_partials;
   DevBuf<double> d_FT;  // forces and torques, n x 6
   DevBuf<double> d_vo;  // velocities, n x 6
   double* h_pinned = nullptr;
+
+  // segmented GMRES: the suspensions as segments of 3N-vectors, a one-segment set for single systems,
+  // the workspace and the captured step graphs; config_version counts configuration rebuilds
+  SegSet seg3, seg_single;
+  GmresWork gw;
+  GmresGraphs graphs;
+  long long config_version = 0;
+  bool capturing = false;  // kernels are being captured into a graph: no timing events
+  // per-suspension outcome of the last mobility solve: iterations and relative residuals
+  std::vector<int> susp_iters;
+  std::vector<double> susp_res;
 
   // contacts of the last mobility solve (Section 3.4): particles i < j, point x*, force f on i
   struct Contact {
@@ -308,12 +378,20 @@ struct Context {
 // right preconditioner z = P v (empty: none; aux is scratch of length n).
 struct LinOp {
   long long n = 0;
+  int graph_key = -1;  // >= 0: the Arnoldi step of this operator may run as a captured graph (slot)
   std::function<Status(const double* v, double* w, double* z)> apply_AP;
   std::function<Status(const double* x, double* y)> apply_A;
   std::function<Status(const double* v, double* z, double* aux)> apply_P;
 };
 Status gmres_op(Context& c, const LinOp& op, const double* b, double* x, bool x_zero, double tol_abs, int max_iters,
                 int* iters, double* res_out, bool* converged);
+// GMRES for every segment of sg at once (the operator must not couple segments): segment s stops when
+// its residual estimate is within tol_abs[s] or after max_iters iterations.
+Status gmres_seg(Context& c, const LinOp& op, const SegSet& sg, const double* b, double* x, bool x_zero,
+                 const std::vector<double>& tol_abs, int max_iters, SegResult& out);
+// Per-segment dot products a . b into the device array out (S doubles); per-segment norms to the host.
+Status seg_dot(Context& c, const SegSet& sg, const double* a, const double* b, double* out);
+Status seg_norms_host(Context& c, const SegSet& sg, const double* v, std::vector<double>& out);
 
 // ---- magnetostatic coupling (magnetic.cu)
 // Net magnetic force and torque (n x 6 interleaved, device) of the current geometry in the uniform
@@ -426,7 +504,7 @@ struct KernelTimer {
   Context& c;
   Context::Timed t{};
   bool on;
-  KernelTimer(Context& ctx, int cls) : c(ctx), on(ctx.opt.timing != 0) {
+  KernelTimer(Context& ctx, int cls) : c(ctx), on(ctx.opt.timing != 0 && !ctx.capturing) {
     t.cls = cls;
     if (on && !c.time_begin(cls, &t).ok()) on = false;
   }

@@ -865,6 +865,7 @@ Status plan_near(int n, const double* centres, const double* R, const double* rm
 Status build_near(Context& c) {
   cudaStream_t s = c.stream;
   const int n = c.n;
+  ++c.config_version;  // captured GMRES step graphs hold this configuration's lists and pointers
   {
     std::vector<double> R(n), rmin(n);
     for (int i = 0; i < n; ++i) {
@@ -1243,12 +1244,16 @@ Status build_geometry(Context& c) {
   RBS_TRY(upload(c.d_bwork, c.bwork, s));
   RBS_TRY(upload(c.d_sym_list, c.sym_list, s));
 
-  // workspace
+  // workspace; the suspensions (contiguous runs of equal ids) as segments of the 3N unknowns
   for (auto& v : c.d_vec) RBS_TRY(v.alloc(3 * c.N));
-  int m = c.opt.restart;
-  RBS_TRY(c.d_V.alloc((size_t)(m + 1) * 3 * c.N));
-  RBS_TRY(c.d_H.alloc((size_t)(m + 1) * (m + 1) + 4 * (size_t)(m + 2)));
-  RBS_TRY(c.d_partials.alloc((size_t)(m + 2) * 1024));
+  RBS_TRY(c.d_partials.alloc(64));
+  {
+    std::vector<long long> so(1, 0);
+    for (int i = 1; i <= n; ++i)
+      if (i == n || c.sid[i] != c.sid[i - 1]) so.push_back(3 * c.offset[i]);
+    RBS_TRY(c.seg3.build(so, s));
+  }
+  ++c.config_version;
   RBS_TRY(c.d_FT.alloc((size_t)6 * n));
   RBS_TRY(c.d_vo.alloc((size_t)6 * n));
   RBS_CUDA_TRY(cudaStreamSynchronize(s));

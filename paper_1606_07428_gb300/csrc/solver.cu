@@ -4,8 +4,8 @@
 //      block-diagonal preconditioner; in the mixed mode the operator of the inner GMRES is applied in
 //      float32 and float64 iterative refinement recovers the float64 solution;
 //   3. u = S[rho + mu] and the rigid velocities v (Eq. 41), omega (Eq. 42).
-// Arnoldi (two-pass classical Gram-Schmidt), Givens rotations and the least-squares solve run in
-// float64 on the GPU; the host reads one residual estimate per iteration.
+// The suspensions of a batch are solved together but converge separately: GMRES (gmres.cu) keeps a
+// Krylov recursion per suspension, and the refinement of the mixed mode decides per suspension.
 #include <algorithm>
 #include <chrono>
 #include <climits>
@@ -17,8 +17,6 @@
 namespace rbs {
 
 namespace {
-
-constexpr int kDotThreads = 256;
 
 // Incident density of Eq. 19 at every node.
 __global__ void k_incident(long long N, const int* __restrict__ pid, const double4* __restrict__ x,
@@ -83,64 +81,6 @@ __global__ void __launch_bounds__(256) k_rigid(const long long* __restrict__ off
   }
 }
 
-// partial[i * nchunk + chunk] = sum over the chunk of V_i . w, for i < nv.
-__global__ void __launch_bounds__(kDotThreads) k_multidot(const double* __restrict__ V, long long ldv, int nv,
-                                                          const double* __restrict__ w, long long n, int nchunk,
-                                                          double* __restrict__ partial) {
-  __shared__ double red[kDotThreads / 32];
-  const int i = blockIdx.y;
-  const long long per = (n + nchunk - 1) / nchunk;
-  const long long b = per * blockIdx.x, e = min(n, b + per);
-  const double* v = V + ldv * i;
-  double acc = 0.0;
-  for (long long k = b + threadIdx.x; k < e; k += blockDim.x) acc = fma(v[k], w[k], acc);
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int q = 0; q < kDotThreads / 32; ++q) s += red[q];
-    partial[(long long)i * nchunk + blockIdx.x] = s;
-  }
-}
-
-// out[i] = sum of the partials of i (fixed order); if accum is not null, accum[i] += out[i].
-__global__ void k_reduce_partials(const double* __restrict__ partial, int nchunk, double* __restrict__ out,
-                                  double* __restrict__ accum) {
-  __shared__ double red[256];
-  const int i = blockIdx.x;
-  double s = 0.0;
-  for (int k = threadIdx.x; k < nchunk; k += blockDim.x) s += partial[(long long)i * nchunk + k];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    out[i] = red[0];
-    if (accum) accum[i] += red[0];
-  }
-}
-
-// w[k] = alpha * (w[k] or 0) + sum_i coef[i] * V_i[k]   (coef from device memory).
-__global__ void k_combine(double* __restrict__ w, double alpha, const double* __restrict__ V, long long ldv, int nv,
-                          const double* __restrict__ coef, double sign, long long n) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    double acc = (alpha == 0.0) ? 0.0 : alpha * w[k];
-    for (int i = 0; i < nv; ++i) acc = fma(sign * coef[i], V[ldv * i + k], acc);
-    w[k] = acc;
-  }
-}
-
-// out = in * (*sc) (or in / *sc when divide).
-__global__ void k_scale(double* __restrict__ out, const double* __restrict__ in, const double* __restrict__ sc, int divide,
-                        long long n) {
-  const double f = divide ? 1.0 / *sc : *sc;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-    out[k] = in[k] * f;
-}
-
 __global__ void k_axpby(double* __restrict__ y, double a, const double* __restrict__ x, double b, long long n) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
     y[k] = a * x[k] + b * y[k];
@@ -152,80 +92,13 @@ __global__ void k_add(double* __restrict__ z, const double* __restrict__ x, cons
     z[k] = x[k] + y[k];
 }
 
-// One Givens step of GMRES on column k of the Hessenberg matrix (stored column-major, leading
-// dimension ld).  On entry col[k + 1] holds ||w||^2; the new basis norm goes to *hnorm.  Writes the
-// least-squares residual |g[k + 1]| to *res.
-__global__ void k_givens(double* H, int ld, int k, double* cs, double* sn, double* g, double* hnorm, double* res) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* col = H + (long long)k * ld;
-  const double hn = sqrt(col[k + 1]);
-  *hnorm = hn;
-  col[k + 1] = hn;
-  for (int i = 0; i < k; ++i) {
-    const double a = col[i], b = col[i + 1];
-    col[i] = cs[i] * a + sn[i] * b;
-    col[i + 1] = -sn[i] * a + cs[i] * b;
-  }
-  const double a = col[k], b = col[k + 1];
-  const double den = hypot(a, b);
-  const double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
-  cs[k] = c;
-  sn[k] = s;
-  col[k] = den;
-  col[k + 1] = 0.0;
-  g[k + 1] = -s * g[k];
-  g[k] = c * g[k];
-  *res = fabs(g[k + 1]);
-}
-
-// y = R^{-1} g for the k x k upper-triangular R left in H by the rotations.
-__global__ void k_trisolve(const double* H, int ld, int k, const double* g, double* y) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int i = k - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int j = i + 1; j < k; ++j) s -= H[(long long)j * ld + i] * y[j];
-    y[i] = s / H[(long long)i * ld + i];
-  }
-}
-
-__global__ void k_init_g(double* g, int len, const double* beta2) {
-  for (int i = threadIdx.x; i < len; i += blockDim.x) g[i] = 0.0;
-  __syncthreads();
-  if (threadIdx.x == 0) g[0] = sqrt(*beta2);
-}
-
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
-// Vector helpers on the context stream.
+// Vector helpers and GMRES on the context stream.
 
 static int vec_blocks(const Context& c, long long n) {
   return (int)std::min<long long>(std::max(1, 8 * c.sm_count), std::max<long long>(1, (n + 255) / 256));
-}
-
-static int chunks_for(long long n) { return (int)std::min<long long>(1024, std::max<long long>(1, n / 4096)); }
-
-// out[0..nv) = V_i . w (and accum[i] += out[i] if accum).
-static Status multidot(Context& c, const double* V, long long ldv, int nv, const double* w, long long n, double* out,
-                       double* accum) {
-  int nchunk = chunks_for(n);
-  dim3 g(nchunk, nv);
-  c.stats.launches += 2;
-  k_multidot<<<g, kDotThreads, 0, c.stream>>>(V, ldv, nv, w, n, nchunk, c.d_partials.ptr);
-  k_reduce_partials<<<nv, 256, 0, c.stream>>>(c.d_partials.ptr, nchunk, out, accum);
-  RBS_CUDA_TRY(cudaGetLastError());
-  return Status::Ok();
-}
-
-static Status norm2_dev(Context& c, const double* w, long long n, double* out_sq) {
-  return multidot(c, w, 0, 1, w, n, out_sq, nullptr);
-}
-
-static Status read_scalar(Context& c, const double* dev, double* host) {
-  RBS_CUDA_TRY(cudaMemcpyAsync(c.h_pinned, dev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-  RBS_CUDA_TRY(cudaStreamSynchronize(c.stream));
-  *host = *c.h_pinned;
-  return Status::Ok();
 }
 
 // The operator inside GMRES: with the preconditioner, w = (1/2 I + K + L) P v = v + K_off P v
@@ -238,113 +111,21 @@ static Status gmres_operator(Context& c, int prec, const double* v, double* w, d
   return apply_operator(c, RBS_OP_A, prec, v, w);
 }
 
-// Restarted, right-preconditioned GMRES for A x = b with the operator `op` (vectors of length op.n).
-// x is the initial guess (x_zero: treat it as zero without reading it).  Stops when the residual
-// estimate is <= tol_abs.
-Status gmres_op(Context& c, const LinOp& op, const double* b, double* x, bool x_zero, double tol_abs, int max_iters,
-                int* iters, double* res_out, bool* converged) {
-  const long long n3 = op.n;
-  const int m = c.opt.restart;
-  const int ld = m + 1;
-  double* H = c.d_H.ptr;
-  double* cs = H + (size_t)ld * (m + 1);
-  double* sn = cs + (m + 2);
-  double* g = sn + (m + 2);
-  double* y = g + (m + 2);
-  double* scal = c.d_partials.ptr + (size_t)(m + 1) * 1024;  // 16 scratch scalars after the partials
-  double* hvec = scal + 4;
-  double* V = c.d_V.ptr;
-  double* w = c.d_vec[4].ptr;
-  double* z = c.d_vec[5].ptr;
-  double* r = c.d_vec[6].ptr;
-  const int nbk = vec_blocks(c, n3);
-  *iters = 0;
-  *converged = false;
-  if (x_zero) RBS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n3, c.stream));
-  bool first = true;
-  double res = 0.0;
-  while (true) {
-    // r = b - A x (x = 0 on the first cycle of a zero start)
-    if (first && x_zero) {
-      RBS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
-    } else {
-      RBS_TRY(op.apply_A(x, r));
-      c.stats.launches++;
-      k_axpby<<<nbk, 256, 0, c.stream>>>(r, 1.0, b, -1.0, n3);
-    }
-    first = false;
-    RBS_TRY(norm2_dev(c, r, n3, scal));
-    double beta2;
-    RBS_TRY(read_scalar(c, scal, &beta2));
-    res = std::sqrt(beta2);
-    if (res <= tol_abs) {
-      *converged = true;
-      break;
-    }
-    if (*iters >= max_iters) break;
-    RBS_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(double) * (size_t)ld * (m + 1), c.stream));
-    c.stats.launches++;
-    k_init_g<<<1, 64, 0, c.stream>>>(g, m + 2, scal);
-    c.stats.launches++;
-    k_scale<<<nbk, 256, 0, c.stream>>>(V, r, g, 1, n3);  // V_0 = r / beta
-    int kdone = 0;
-    for (int k = 0; k < m && *iters < max_iters; ++k) {
-      double* vk = V + (size_t)k * n3;
-      RBS_TRY(op.apply_AP(vk, w, z));
-      double* hcol = H + (size_t)k * ld;
-      for (int pass = 0; pass < 2; ++pass) {
-        RBS_TRY(multidot(c, V, n3, k + 1, w, n3, hvec, hcol));
-        c.stats.launches++;
-        k_combine<<<nbk, 256, 0, c.stream>>>(w, 1.0, V, n3, k + 1, hvec, -1.0, n3);
-      }
-      RBS_TRY(norm2_dev(c, w, n3, hcol + k + 1));
-      c.stats.launches++;
-      k_givens<<<1, 1, 0, c.stream>>>(H, ld, k, cs, sn, g, scal + 1, scal + 2);
-      c.stats.launches++;
-      k_scale<<<nbk, 256, 0, c.stream>>>(V + (size_t)(k + 1) * n3, w, scal + 1, 1, n3);
-      RBS_CUDA_TRY(cudaGetLastError());
-      RBS_TRY(read_scalar(c, scal + 2, &res));
-      ++*iters;
-      kdone = k + 1;
-      if (!(res > tol_abs)) break;  // also stops on NaN
-    }
-    // x += P (V y)
-    c.stats.launches++;
-    k_trisolve<<<1, 1, 0, c.stream>>>(H, ld, kdone, g, y);
-    if (op.apply_P) {
-      c.stats.launches++;
-      k_combine<<<nbk, 256, 0, c.stream>>>(w, 0.0, V, n3, kdone, y, 1.0, n3);
-      RBS_TRY(op.apply_P(w, z, r));
-      c.stats.launches++;
-      k_axpby<<<nbk, 256, 0, c.stream>>>(x, 1.0, z, 1.0, n3);
-    } else {
-      c.stats.launches++;
-      k_combine<<<nbk, 256, 0, c.stream>>>(x, 1.0, V, n3, kdone, y, 1.0, n3);
-    }
-    RBS_CUDA_TRY(cudaGetLastError());
-    if (std::isnan(res)) return Status::Err(RBS_ENOTCONV, "GMRES produced NaN");
-    if (res <= tol_abs) {
-      *converged = true;
-      break;
-    }
-  }
-  *res_out = res;
-  return Status::Ok();
-}
-
-// The mobility system's operator for gmres_op: A = 1/2 I + K + L on 3N-vectors in arithmetic prec,
-// right-preconditioned by the block-diagonal inverse when the context has one.
-static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zero, double tol_abs, int max_iters,
-                    int* iters, double* res_out, bool* converged) {
+// The mobility system's operator for the segmented GMRES: A = 1/2 I + K + L on 3N-vectors in
+// arithmetic prec, right-preconditioned by the block-diagonal inverse when the context has one, one
+// segment per suspension (A does not couple suspensions).  Its Arnoldi step may run as a graph.
+static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zero, const std::vector<double>& tol_abs,
+                    int max_iters, SegResult& out) {
   LinOp op;
   op.n = 3 * c.N;
+  op.graph_key = 2 * (prec == RBS_PREC_MIXED ? 1 : 0) + (c.opt.preconditioner ? 1 : 0);
   op.apply_AP = [&c, prec](const double* v, double* w, double* z) { return gmres_operator(c, prec, v, w, z); };
   op.apply_A = [&c, prec](const double* xx, double* y) { return apply_operator(c, RBS_OP_A, prec, xx, y); };
   if (c.opt.preconditioner)
     op.apply_P = [&c, prec](const double* v, double* z, double* aux) {
       return apply_blocks(c, kModePrecond, prec, v, z, aux, 1.0);
     };
-  return gmres_op(c, op, b, x, x_zero, tol_abs, max_iters, iters, res_out, converged);
+  return gmres_seg(c, op, c.seg3, b, x, x_zero, tol_abs, max_iters, out);
 }
 
 Status incident_density(Context& c, const double* FT_dev, double* rho) {
@@ -406,16 +187,20 @@ static Status residual_and_velocity(Context& c, int prec, const double* rho, con
 
 // One mobility solve of the forces and torques in c.d_FT (n x 6, device) in the context's arithmetic:
 // the scattered density in d_vec[2] and the rigid velocities in c.d_vo (n x 6).  `warm` allows the
-// configured warm start.
-static Status solve_core(Context& c, double tol, bool warm, int* iters_out, int* refinements_out, double* rel_out,
-                         bool* converged_out) {
+// configured warm start.  Every suspension converges on its own right-hand side: its GMRES iterations
+// are added to iters[s] and its final relative residual ||b_s - A mu_s|| / ||b_s|| goes to rel[s].
+static Status solve_core(Context& c, double tol, bool warm, std::vector<int>& iters, std::vector<double>& rel,
+                         int* refinements_out, bool* converged_out) {
   const long long n3 = 3 * c.N;
   const int nbk = vec_blocks(c, n3);
+  const int S = c.seg3.S;
   double* rho = c.d_vec[0].ptr;
   double* b = c.d_vec[1].ptr;
   double* x = c.d_vec[2].ptr;
   double* r = c.d_vec[3].ptr;
   double* d = c.d_vec[7].ptr;
+  iters.resize(S, 0);
+  rel.assign(S, 0.0);
   // 1. incident density; right-hand side b = -(1/2 I + K) rho (Eq. 25): float64 for the float64 path;
   //    float32 for the mixed path, where b only seeds the first inner solve (every refinement residual
   //    below is formed from rho in float64-class arithmetic, so b's float32 error does not persist)
@@ -425,21 +210,19 @@ static Status solve_core(Context& c, double tol, bool warm, int* iters_out, int*
   RBS_TRY(apply_operator(c, RBS_OP_HALF_K, mixed ? RBS_PREC_MIXED : RBS_PREC_FP64, rho, b));
   c.stats.launches++;
   k_axpby<<<nbk, 256, 0, c.stream>>>(b, 0.0, b, -1.0, n3);
-  double* sc = c.d_partials.ptr + (size_t)(c.opt.restart + 1) * 1024 + 8;
-  RBS_TRY(norm2_dev(c, b, n3, sc));
-  double bn2;
-  RBS_TRY(read_scalar(c, sc, &bn2));
-  const double bnorm = std::sqrt(bn2);
-  int total_iters = 0, refinements = 0;
-  double rel = 0.0;
+  std::vector<double> bn;
+  RBS_TRY(seg_norms_host(c, c.seg3, b, bn));
+  double bmax = 0.0;
+  for (double v : bn) bmax = std::max(bmax, v);
+  int refinements = 0;
   bool converged = true;
   // initial guess: zero, the previous solution, or the learned warm start
   bool have_x0 = false;
   double* x0 = d;
-  if (warm && bnorm > 0.0 && c.opt.warm_start == RBS_WARM_PREVIOUS && c.have_prev && c.d_prev.n == (size_t)n3) {
+  if (warm && bmax > 0.0 && c.opt.warm_start == RBS_WARM_PREVIOUS && c.have_prev && c.d_prev.n == (size_t)n3) {
     RBS_CUDA_TRY(cudaMemcpyAsync(x0, c.d_prev.ptr, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
     have_x0 = true;
-  } else if (warm && bnorm > 0.0 && c.opt.warm_start == RBS_WARM_LEARNED) {
+  } else if (warm && bmax > 0.0 && c.opt.warm_start == RBS_WARM_LEARNED) {
     RBS_TRY(warm_guess(c, c.d_FT.ptr, x0));
     have_x0 = true;
   }
@@ -448,24 +231,30 @@ static Status solve_core(Context& c, double tol, bool warm, int* iters_out, int*
   double* w = c.d_vec[4].ptr;
   bool u_done = false;
   // 2. the scattered density
-  if (bnorm == 0.0) {
+  if (bmax == 0.0) {
     RBS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n3, c.stream));
   } else if (!mixed) {
-    int its = 0;
-    double res = 0.0;
     if (have_x0) RBS_CUDA_TRY(cudaMemcpyAsync(x, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
-    RBS_TRY(gmres(c, RBS_PREC_FP64, b, x, !have_x0, tol * bnorm, c.opt.max_iters, &its, &res, &converged));
-    total_iters = its;
-    rel = res / bnorm;
+    std::vector<double> tl(S);
+    for (int s = 0; s < S; ++s) tl[s] = tol * bn[s];
+    SegResult R;
+    RBS_TRY(gmres(c, RBS_PREC_FP64, b, x, !have_x0, tl, c.opt.max_iters, R));
+    for (int s = 0; s < S; ++s) {
+      iters[s] += R.iters[s];
+      rel[s] = bn[s] > 0.0 ? R.res[s] / bn[s] : 0.0;
+      if (!R.conv[s]) converged = false;
+    }
   } else {
     // Iterative refinement around float32 inner solves.  A float64-class pass gives the true
     // residual r = b - A x and, from the same pair sums, u = S[rho + x].  After a pass, a small
     // correction d may instead update r -= A d and u += S d in float32: the float32 operator's error
     // on d is f32_operator_error ||A d||, and these updates are taken only while that error, summed
-    // since the last pass, stays below a tenth of the tolerance.
+    // since the last pass, stays below a tenth of the tolerance in every suspension the correction
+    // touched.  Suspensions within tolerance after a float64-class pass take no further inner
+    // iterations.
     double* lrho = c.d_vec[8].ptr;  // L rho (Eq. 26), float64
     RBS_TRY(apply_blocks(c, kModeL, RBS_PREC_FP64, rho, lrho, nullptr, 1.0));
-    double rn = bnorm;
+    std::vector<double> rn = bn;
     if (have_x0) {
       // the first inner solve starts from the warm start's residual in float32 arithmetic, like a
       // zero start from b; the float64-class pass follows it
@@ -474,55 +263,68 @@ static Status solve_core(Context& c, double tol, bool warm, int* iters_out, int*
       RBS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
       c.stats.launches++;
       k_axpby<<<nbk, 256, 0, c.stream>>>(r, -1.0, w, 1.0, n3);
-      RBS_TRY(norm2_dev(c, r, n3, sc));
-      double rn2;
-      RBS_TRY(read_scalar(c, sc, &rn2));
-      rn = std::sqrt(rn2);
+      RBS_TRY(seg_norms_host(c, c.seg3, r, rn));
     } else {
       RBS_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n3, c.stream));
       RBS_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
     }
     // sigma accumulates the corrections applied in float32 since the last float64-class pass
-    if (u_done) RBS_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(double) * n3, c.stream));
-    double pending = 0.0;
-    converged = u_done && rn <= tol * bnorm;
-    while (!converged && refinements < c.opt.max_refinements && total_iters < c.opt.max_iters) {
-      int its = 0;
-      double res = 0.0;
-      bool conv_inner = false;
-      // each inner solve reduces its residual by inner_tol, or only as far as the final tolerance needs
-      // (half of tol ||b||), whichever is looser
-      const double inner = std::min(0.5, std::max(c.opt.inner_tol, 0.5 * tol * bnorm / rn));
-      RBS_TRY(gmres(c, RBS_PREC_MIXED, r, d, true, inner * rn, c.opt.max_iters - total_iters, &its, &res,
-                    &conv_inner));
-      total_iters += its;
+    std::vector<double> pending(S, 0.0);
+    std::vector<int> used(S, 0);
+    const double ferr = f32_operator_error(c);
+    converged = false;
+    int used_max = 0;
+    while (!converged && refinements < c.opt.max_refinements && used_max < c.opt.max_iters) {
+      // each inner solve reduces a suspension's residual by inner_tol, or only as far as the final
+      // tolerance needs (half of tol ||b_s||), whichever is looser; suspensions already within
+      // tolerance after a float64-class pass are left out
+      std::vector<double> tl(S);
+      for (int s = 0; s < S; ++s) {
+        if (u_done && rn[s] <= tol * bn[s]) {
+          tl[s] = INFINITY;
+        } else {
+          const double need = rn[s] > 0.0 ? 0.5 * tol * bn[s] / rn[s] : 1.0;
+          tl[s] = std::min(0.5, std::max(c.opt.inner_tol, need)) * rn[s];
+        }
+      }
+      SegResult R;
+      RBS_TRY(gmres(c, RBS_PREC_MIXED, r, d, true, tl, c.opt.max_iters - used_max, R));
+      int moved = 0;
+      for (int s = 0; s < S; ++s) {
+        iters[s] += R.iters[s];
+        used[s] += R.iters[s];
+        used_max = std::max(used_max, used[s]);
+        moved = std::max(moved, R.iters[s]);
+      }
       ++refinements;
       c.stats.launches++;
       k_axpby<<<nbk, 256, 0, c.stream>>>(x, 1.0, d, 1.0, n3);
-      if (u_done && f32_operator_error(c) * (pending + rn) <= 0.1 * tol * bnorm) {
+      bool f32_ok = u_done;
+      for (int s = 0; s < S && f32_ok; ++s)
+        if (R.iters[s] > 0 && ferr * (pending[s] + rn[s]) > 0.1 * tol * bn[s]) f32_ok = false;
+      if (f32_ok) {
         RBS_TRY(apply_operator(c, RBS_OP_A, RBS_PREC_MIXED, d, w));
         c.stats.launches += 2;
         k_axpby<<<nbk, 256, 0, c.stream>>>(r, -1.0, w, 1.0, n3);
         k_axpby<<<nbk, 256, 0, c.stream>>>(sigma, 1.0, d, 1.0, n3);
-        pending += rn;
+        for (int s = 0; s < S; ++s)
+          if (R.iters[s] > 0) pending[s] += rn[s];
       } else {
         RBS_TRY(residual_and_velocity(c, hi, rho, lrho, x, sigma, r, u));
         u_done = true;
         RBS_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(double) * n3, c.stream));
-        pending = 0.0;
+        std::fill(pending.begin(), pending.end(), 0.0);
       }
-      RBS_TRY(norm2_dev(c, r, n3, sc));
-      double rn2;
-      RBS_TRY(read_scalar(c, sc, &rn2));
-      rn = std::sqrt(rn2);
-      if (rn <= tol * bnorm) {
-        converged = true;
-        break;
-      }
-      if (its == 0) break;  // the inner solve could not move
+      RBS_TRY(seg_norms_host(c, c.seg3, r, rn));
+      converged = u_done;
+      for (int s = 0; s < S; ++s)
+        if (!(rn[s] <= tol * bn[s])) converged = false;
+      if (moved == 0) break;  // the inner solves could not move
     }
-    rel = rn / bnorm;
-    if (u_done && pending > 0.0) {
+    for (int s = 0; s < S; ++s) rel[s] = bn[s] > 0.0 ? rn[s] / bn[s] : 0.0;
+    bool any_pending = false;
+    for (double p : pending) any_pending = any_pending || p > 0.0;
+    if (u_done && any_pending) {
       RBS_TRY(apply_operator(c, RBS_OP_S, RBS_PREC_MIXED, sigma, w));
       c.stats.launches++;
       k_axpby<<<nbk, 256, 0, c.stream>>>(u, 1.0, w, 1.0, n3);
@@ -536,9 +338,7 @@ static Status solve_core(Context& c, double tol, bool warm, int* iters_out, int*
   }
   RBS_TRY(rigid_velocities(c, u, c.d_vo.ptr));
   RBS_CUDA_TRY(cudaGetLastError());
-  *iters_out = total_iters;
   *refinements_out = refinements;
-  *rel_out = rel;
   *converged_out = converged;
   return Status::Ok();
 }
@@ -704,7 +504,7 @@ static Status dense_solve(std::vector<double> A, std::vector<double>& y, int m) 
 // Contact correction of the solve just made (its forces in c.d_FT, velocities in c.d_vo): the
 // columns M C from 3 n_c solves, the contact forces from (D M C) F_c = -D V_0, and a final solve with
 // the forces and torques F + C F_c, which gives the corrected velocities and density together.
-static Status contact_correction(Context& c, double tol, int* iters) {
+static Status contact_correction(Context& c, double tol) {
   RBS_TRY(find_contacts(c));
   c.stats.n_contacts = (int)c.contacts.size();
   const int nc = (int)c.contacts.size();
@@ -719,12 +519,11 @@ static Status contact_correction(Context& c, double tol, int* iters) {
     std::fill(FT.begin(), FT.end(), 0.0);
     add_contact_column(c, col / 3, col % 3, 1.0, FT);
     RBS_CUDA_TRY(cudaMemcpyAsync(c.d_FT.ptr, FT.data(), sizeof(double) * FT.size(), cudaMemcpyHostToDevice, c.stream));
-    int its = 0, refs = 0;
-    double rel = 0.0;
+    int refs = 0;
     bool conv = false;
-    RBS_TRY(solve_core(c, tol, false, &its, &refs, &rel, &conv));
+    std::vector<double> rel;
+    RBS_TRY(solve_core(c, tol, false, c.susp_iters, rel, &refs, &conv));
     if (!conv) return Status::Err(RBS_ENOTCONV, "a contact column solve did not converge");
-    *iters += its;
     RBS_CUDA_TRY(cudaMemcpyAsync(Vk.data(), c.d_vo.ptr, sizeof(double) * Vk.size(), cudaMemcpyDeviceToHost, c.stream));
     RBS_CUDA_TRY(cudaStreamSynchronize(c.stream));
     for (int k = 0; k < nc; ++k) {
@@ -744,12 +543,10 @@ static Status contact_correction(Context& c, double tol, int* iters) {
   for (int k = 0; k < nc; ++k)
     for (int q = 0; q < 3; ++q) c.contacts[k].f[q] = rhs[3 * k + q];
   RBS_CUDA_TRY(cudaMemcpyAsync(c.d_FT.ptr, FT.data(), sizeof(double) * FT.size(), cudaMemcpyHostToDevice, c.stream));
-  int its = 0, refs = 0;
-  double rel = 0.0;
+  int refs = 0;
   bool conv = false;
-  RBS_TRY(solve_core(c, tol, false, &its, &refs, &rel, &conv));
+  RBS_TRY(solve_core(c, tol, false, c.susp_iters, c.susp_res, &refs, &conv));
   if (!conv) return Status::Err(RBS_ENOTCONV, "the contact-corrected solve did not converge");
-  *iters += its;
   return Status::Ok();
 }
 
@@ -771,13 +568,17 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
     k_pack_ft<<<cdiv(n, 128), 128, 0, c.stream>>>(n, c.d_vo.ptr, c.d_vo.ptr + 3 * n, c.d_FT.ptr);
   }
   RBS_CUDA_TRY(cudaGetLastError());
-  int total_iters = 0, refinements = 0;
-  double rel = 0.0;
+  int refinements = 0;
   bool converged = false;
-  RBS_TRY(solve_core(c, tol, true, &total_iters, &refinements, &rel, &converged));
+  c.susp_iters.assign(c.seg3.S, 0);
+  RBS_TRY(solve_core(c, tol, true, c.susp_iters, c.susp_res, &refinements, &converged));
   c.stats.n_contacts = 0;
   c.contacts.clear();
-  if (converged && c.opt.contact_gap > 0.0) RBS_TRY(contact_correction(c, tol, &total_iters));
+  if (converged && c.opt.contact_gap > 0.0) RBS_TRY(contact_correction(c, tol));
+  int total_iters = 0;
+  double rel = 0.0;
+  for (int v : c.susp_iters) total_iters = std::max(total_iters, v);
+  for (double v : c.susp_res) rel = std::max(rel, v);
   // keep the density for a previous-solution warm start and for recording training samples
   if (c.d_prev.n != (size_t)n3) RBS_TRY(c.d_prev.alloc(n3));
   RBS_CUDA_TRY(cudaMemcpyAsync(c.d_prev.ptr, x, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
@@ -812,11 +613,11 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
 
 // ------------------------------------------------------------------------------------------
 // Allocation-free rigid velocities.  Some callers may not allocate device memory when they call in:
-// code that runs while a stream is being captured into a CUDA graph (cudaMalloc is not permitted
-// then), real-time time-stepping loops that forbid allocator calls, and hosts that hand the library
-// a fixed memory budget up front.  For them rbs_rigid_velocities_noalloc reads u and writes v and
-// omega in caller buffers, and keeps its one intermediate (the interleaved n x 6 result of the
-// per-particle reduction) in the fixed device array below instead of a context buffer.
+// frameworks that reserve nearly all device memory for their own pool up front (so a cudaMalloc from a
+// library they call would fail), real-time time-stepping loops that forbid allocator calls, and hosts
+// that hand the library a fixed memory budget.  For them rbs_rigid_velocities_noalloc reads u and
+// writes v and omega in caller buffers, and keeps its one intermediate (the interleaved n x 6 result of
+// the per-particle reduction) in the fixed device array below instead of a context buffer.
 namespace rbs {
 namespace {
 
@@ -856,19 +657,28 @@ extern "C" int rbs_rigid_velocities_noalloc(rbs_ctx* h, const double* u_dev, dou
     return fail(rbs::Status::Err(RBS_EINVAL, "rigid_velocities_noalloc: " + std::to_string(c.n) +
                                                  " particles exceed the fixed scratch limit of " +
                                                  std::to_string(rbs::kNoAllocMaxParticles)));
-  cudaError_t e = cudaSetDevice(c.device);
+  // the work runs on the context's device; the caller's current device is put back before returning
+  int prev_device = -1;
+  cudaError_t e = cudaGetDevice(&prev_device);
   if (e != cudaSuccess) return fail(rbs::Status::Err(RBS_ECUDA, cudaGetErrorString(e)));
+  auto restore = [&](int code) {
+    if (prev_device >= 0 && prev_device != c.device) cudaSetDevice(prev_device);
+    return code;
+  };
+  e = cudaSetDevice(c.device);
+  if (e != cudaSuccess) return restore(fail(rbs::Status::Err(RBS_ECUDA, cudaGetErrorString(e))));
   double* scratch = nullptr;
   rbs::Status s = rbs::rigid_scratch(c.device, &scratch);
-  if (!s.ok()) return fail(s);
+  if (!s.ok()) return restore(fail(s));
   // every scratch entry read below is written first by k_rigid, so nothing needs clearing
   rbs::k_rigid<<<c.n, 256, 0, c.stream>>>(c.d_offset.ptr, c.d_x.ptr, c.d_centre.ptr, c.d_area.ptr, c.d_tauinv.ptr,
                                          u_dev, 1.0 / c.opt.viscosity, scratch);
   rbs::k_unpack_vo<<<rbs::cdiv(c.n, 128), 128, 0, c.stream>>>(c.n, scratch, v_dev, omega_dev);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
-  if (e != cudaSuccess) return fail(rbs::Status::Err(RBS_ECUDA, std::string("rigid_velocities_noalloc: ") + cudaGetErrorString(e)));
+  if (e != cudaSuccess)
+    return restore(fail(rbs::Status::Err(RBS_ECUDA, std::string("rigid_velocities_noalloc: ") + cudaGetErrorString(e))));
   c.stats.launches += 2;
   c.err.clear();
-  return RBS_OK;
+  return restore(RBS_OK);
 }

@@ -46,7 +46,7 @@ EXPORTS = [
     "rbs_warmstart_record", "rbs_warmstart_train", "rbs_warmstart_weights", "rbs_warmstart_features",
     "rbs_warmstart_targets", "rbs_warmstart_mlp", "rbs_set_geometry_sh", "rbs_get_contacts",
     "rbs_magnetic_forces", "rbs_apply_laplace", "rbs_treecode_plan", "rbs_near_plan",
-    "rbs_grid_symmetry",
+    "rbs_grid_symmetry", "rbs_suspension_count", "rbs_get_suspension_results",
 ]
 
 RBS_MAX_SHAPE_DEGREE = 24
@@ -87,6 +87,7 @@ class rbs_options(ctypes.Structure):
         ("tree_degree", ctypes.c_int),
         ("tree_df_theta", ctypes.c_double),
         ("tree_df_degree", ctypes.c_int),
+        ("graphs", ctypes.c_int),
     ]
 
 
@@ -105,10 +106,11 @@ RBS_KC_PAIR_KDF = 6
 RBS_KC_PAIR_SDF = 7
 RBS_KC_PAIR_KSDF = 8
 RBS_KC_TREE = 9
-RBS_KC_COUNT = 10
+RBS_KC_GMRES_GRAPH = 10
+RBS_KC_COUNT = 11
 KERNEL_CLASSES = ["pair_traction_f32", "pair_stokeslet_f32", "pair_traction_f64", "pair_stokeslet_f64",
                   "particle_blocks", "near_correction", "pair_traction_df", "pair_stokeslet_df", "pair_both_df",
-                  "tree_charges"]
+                  "tree_charges", "gmres_graph"]
 
 
 class rbs_stats(ctypes.Structure):
@@ -190,6 +192,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "rbs_treecode_plan": (I, [I, P, P, P, P, P, D, I, D, I, P]),
         "rbs_near_plan": (I, [I, P, P, P, P, D, I, P]),
         "rbs_grid_symmetry": (I, [I, I, P, P, P]),
+        "rbs_suspension_count": (I, [P]),
+        "rbs_get_suspension_results": (I, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -365,25 +369,40 @@ def rbs_get_surface(ctx):
     return x, nrm, w
 
 
-def rbs_mobility_solve(ctx, F, T, tol, want_density=False, allow_notconv=False):
+def rbs_suspension_count(ctx) -> int:
+    return _check(ctx, load().rbs_suspension_count(ctx), allow=range(0, 1 << 31))
+
+
+def rbs_get_suspension_results(ctx):
+    """Per-suspension outcome of the last solve: (iterations int32 array, relative residuals)."""
+    S = rbs_suspension_count(ctx)
+    its = np.zeros(S, np.int32)
+    res = np.zeros(S)
+    _check(ctx, load().rbs_get_suspension_results(ctx, _ptr(its), _ptr(res)))
+    return its, res
+
+
+def rbs_mobility_solve(ctx, F, T, tol, want_density=False, allow_notconv=False, per_suspension=False):
+    """Returns (v, omega, density or None, iterations): iterations is the per-suspension int32 array
+    the C call fills when per_suspension is set, else its largest entry."""
     F = _f64(F, (-1, 3))
     T = _f64(T, F.shape)
     v = np.zeros_like(F)
     om = np.zeros_like(F)
     dens = np.zeros((rbs_total_nodes(ctx), 3)) if want_density else None
-    its = ctypes.c_int(0)
-    rc = load().rbs_mobility_solve(ctx, _ptr(F), _ptr(T), float(tol), _ptr(v), _ptr(om), _ptr(dens),
-                                   ctypes.addressof(its))
+    its = np.zeros(max(1, rbs_suspension_count(ctx)), np.int32)
+    rc = load().rbs_mobility_solve(ctx, _ptr(F), _ptr(T), float(tol), _ptr(v), _ptr(om), _ptr(dens), _ptr(its))
     _check(ctx, rc, (RBS_ENOTCONV,) if allow_notconv else ())
-    return v, om, dens, its.value
+    return v, om, dens, (its if per_suspension else int(its.max()))
 
 
-def rbs_mobility_solve_device(ctx, F_dev, T_dev, tol, v_dev, omega_dev, density_dev=None, allow_notconv=False) -> int:
-    its = ctypes.c_int(0)
+def rbs_mobility_solve_device(ctx, F_dev, T_dev, tol, v_dev, omega_dev, density_dev=None, allow_notconv=False,
+                              per_suspension=False):
+    its = np.zeros(max(1, rbs_suspension_count(ctx)), np.int32)
     rc = load().rbs_mobility_solve_device(ctx, _ptr(F_dev), _ptr(T_dev), float(tol), _ptr(v_dev), _ptr(omega_dev),
-                                          _ptr(density_dev), ctypes.addressof(its))
+                                          _ptr(density_dev), _ptr(its))
     _check(ctx, rc, (RBS_ENOTCONV,) if allow_notconv else ())
-    return its.value
+    return its if per_suspension else int(its.max())
 
 
 def rbs_advance(ctx, F, T, dt, steps, scheme=RBS_RK4, tol=1e-10) -> int:

@@ -215,6 +215,13 @@ def profile_ellipsoids() -> Suspension:
     return random_ellipsoids(400, 8, 16, 0.10, 0.2, seed=1, name="profile_400_ellipsoids_p8")
 
 
+def c3_profile() -> Suspension:
+    """2,000 ellipsoids drawn like the 10,000-ellipsoid workload (~15% volume fraction, gap 0.2, p = 8
+    on a 9 x 16 grid, 288,000 nodes; seed 2): a case of the same treecode kernels small enough for
+    hardware-counter captures (pair sums of well under a second per launch)."""
+    return random_ellipsoids(2000, 8, 16, 0.15, 0.2, seed=2, name="c3_profile_2000_ellipsoids_p8")
+
+
 def c5_small() -> Suspension:
     """The sedimenting-ellipsoid workload at 256 particles (same distributions as the 2,048-particle
     one: p = 10 on an 11 x 22 grid, ~10% volume fraction, gap 0.2, F = (0, 0, -1), T = 0; seed 4),
@@ -230,6 +237,7 @@ WORKLOADS = {
     "profile": profile_ellipsoids,
     "c2": c2_ellipsoids,
     "c3": c3_ellipsoids,
+    "c3_profile": c3_profile,
     "c4": c4_batched,
     "c5": c5_sedimenting,
     "c5_small": c5_small,

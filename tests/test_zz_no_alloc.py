@@ -1,11 +1,12 @@
 """The allocation-free rigid-velocity entry point (rbs_rigid_velocities_noalloc).
 
-Callers that may not allocate device memory at call time (for example while a stream is captured
-into a CUDA graph, or in a real-time loop that forbids allocator calls) use this variant; it keeps its
-intermediate in a fixed device array instead of a context buffer.  This file runs last so that a
-failure here does not hide the other GPU tests.  Results must equal those of rbs_rigid_velocities,
-the existing entry point, to the tolerance the other rigid-velocity tests use (1e-13), on two calls
-in a row (the second call reuses the array the first one filled).
+Callers that may not allocate device memory at call time (for example frameworks that reserve nearly
+all device memory for their own pool, or real-time loops that forbid allocator calls) use this
+variant; it keeps its intermediate in a fixed device array instead of a context buffer.  This file
+runs last so that a failure here does not hide the other GPU tests.  Results must equal those of
+rbs_rigid_velocities, the existing entry point, to the tolerance the other rigid-velocity tests use
+(1e-13), on two calls in a row (the second call reuses the array the first one filled); the second
+call must leave the device's free memory unchanged.
 """
 import numpy as np
 import pytest
@@ -40,8 +41,13 @@ def test_noalloc_matches_rigid_velocities_on_two_calls(rbs):
             u_dev = torch.tensor(u, device="cuda")
             v_dev = torch.full((s.n, 3), float("nan"), dtype=torch.float64, device="cuda")
             om_dev = torch.full((s.n, 3), float("nan"), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info(0)[0]
             rbs.rbs_rigid_velocities_noalloc(ctx.ctx, u_dev, v_dev, om_dev)
             torch.cuda.synchronize()
+            if seed == 42:  # the first call may load the kernels; the second allocates nothing at all
+                assert torch.cuda.mem_get_info(0)[0] == free_before
+            assert torch.cuda.current_device() == 0
             assert rel(v_dev.cpu().numpy(), v_ref) < 1e-13
             assert rel(om_dev.cpu().numpy(), om_ref) < 1e-13
 
