@@ -1,17 +1,21 @@
 """Benchmark of the rigid-particle mobility solve on GB300.
 
 One step = one complete mobility solve (forces and torques in, velocities out) of the chosen
-arithmetic (float32 inner GMRES with float64 refinement, right-hand side and velocity) on a fixed
-suspension, for a fresh seeded (F, T) draw resident in device memory.  The default workload is
-1,000 triaxial ellipsoids at p = 12 (312,000 nodes, 936,000 unknowns), GMRES to 1e-10.
+arithmetic (float32 inner GMRES with float64 refinement, double-float right-hand side, residuals and
+velocity) on a fixed suspension, for a fresh seeded (F, T) draw resident in device memory.  The
+default workload is the metric's: 10,000 triaxial ellipsoids at p = 8 (1.44M nodes, 4.32M unknowns,
+~15% volume fraction), at the largest GMRES tolerance in {1e-8, 1e-9, 1e-10} whose (v, omega) error
+against a 1e-12 solve is <= 1e-8 (in practice 1e-8), with treecodes for the float32 inner applies and
+the double-float passes.
 
 The JSON line carries: device-timed solves/s (value), the same through the host-buffer C ABI call
-(e2e), the plain float64 solve rate on the same suspension, the error of the chosen path against
-the float64 path, Stokeslet and traction pair rates, the dominant kernel's roofline (device time from
-the library's CUDA events on its stream), SM clocks sampled during the timed region, and the
-float64 CPU oracle timed on a bounded sample (cpu_baseline).
+(e2e), the plain float64 solve rate extrapolated from timed float64 operator applications, the error of
+the chosen path against a 1e-12 solve, Stokeslet and traction pair rates, the dominant kernel's
+roofline (its algorithmic flops over its device time from the library's CUDA events on its stream,
+against the float32 FMA peak at the sampled clock), SM clocks sampled during the timed region, and the
+float64 CPU oracle timed on a bounded sample on every host core and on one (cpu_baseline).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c2]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c3]
 Under torchrun each rank solves its own draws on its own GPU (independent replicas, weak scaling);
 rank 0 prints the line.
 """
@@ -42,19 +46,24 @@ SMS = 152
 L2_BYTES = 129 * 2 ** 20
 FP64_DFMA_PER_CLK_SM = 2     # float64 FMA lanes per SM per clock (measured 1.19 TFLOP/s at 2.07 GHz)
 FP32_LANES_PER_SM = 128
-# minimal float32-pipe instructions per pair: traction 20, Stokeslet 18; float64 ops
-# per pair (with the float64 reciprocal square root counted as 7): traction 27, Stokeslet 25
-FLOPS_PER_PAIR = {"traction": 30.0, "stokeslet": 28.0}
+# algorithmic work per node pair (minimal float32 flops with FMA = 2): traction 29 (20 FMA-pipe
+# instructions + 1 MUFU), Stokeslet 28 (18 + 1 MUFU); the fused double-float pass evaluates both (57);
+# float64 operations per pair (the float64 reciprocal square root counted as 7): traction 27, Stokeslet 25
+FLOPS_PER_PAIR = {"traction": 29.0, "stokeslet": 28.0, "both": 57.0}
 FP64_OPS_PER_PAIR = {"traction": 27.0, "stokeslet": 25.0}
-# DRAM bytes per launch from ncu captures on the 400-ellipsoid profiling case (57,600 nodes), scaled
-# by node count to the benchmarked case: the pair kernels read their inputs once
-# (sources are re-read from L2), so traffic grows with N, not with the N^2 pairs
+# DRAM bytes per launch from ncu captures of the direct kernels on the 400-ellipsoid profiling case
+# (57,600 nodes), scaled by node count to the benchmarked case: the pair kernels read their inputs
+# once (sources are re-read from L2), so traffic grows with N, not with the N^2 pairs
 NCU_TRAFFIC = {"pair_traction_df": (6.404864e6, 57600), "pair_traction_f32": (4.872192e6, 57600),
                "pair_both_df": (8.511744e6, 57600)}
-# float32-pipe operations per pair of the double-float kernels, counted from the source of
-# pair_tile_df (separation 24, r^2 28, reciprocal square root 8, r . density 28, powers 8, then the
-# traction tail 76, the Stokeslet tail 76, or both tails sharing 1/r^5 and r . n: 152)
+# float32-pipe operations per pair the double-float kernels issue, counted from the source of
+# pair2_df (separation 24, r^2 28, reciprocal square root 8, r . density 28, powers 8, then the
+# traction tail 76, the Stokeslet tail 76, or both tails sharing 1/r^5 and r . n: 152): the issue
+# efficiency of a double-float kernel is measured against this count, its roofline against the flops
 DF_INSTR_PER_PAIR = {"traction": 172.0, "stokeslet": 172.0, "both": 248.0}
+# DRAM bytes per launch of the fused double-float treecode kernel from an ncu capture on the
+# 2,000-ellipsoid profiling case (288,000 nodes), or None before a capture of the current kernel
+TREE_DF_TRAFFIC = None
 
 
 def parse_args():
@@ -63,16 +72,20 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(suspensions.WORKLOADS))
+    ap.add_argument("--workload", default="c3", choices=sorted(suspensions.WORKLOADS))
     ap.add_argument("--tol", type=float, default=None,
                     help="GMRES tolerance; default: the largest of 1e-8, 1e-9, 1e-10 whose (v, omega) error "
                          "against a 1e-12 reference solve is <= 1e-8")
-    ap.add_argument("--fp64-steps", type=int, default=1, help="timed plain float64 solves (0 skips)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=0, help="timed plain float64 solves (0: extrapolate)")
+    ap.add_argument("--fp64-subset", type=int, default=1500,
+                    help="particles of the workload whose float64 operator applications are timed to extrapolate "
+                         "the plain float64 solve when --fp64-steps is 0 (0 skips)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU sample")
+    ap.add_argument("--cpu-procs", type=int, default=0, help="oracle sample processes (0: every host core)")
     ap.add_argument("--pair-variant", type=int, default=0,
                     help="pair-kernel variant (rbs_options.pair_variant); 0 lets the library's autotuner choose")
-    ap.add_argument("--far-field", default="tree", choices=["direct", "tree", "tree-df"],
+    ap.add_argument("--far-field", default="tree-df", choices=["direct", "tree", "tree-df"],
                     help="direct sums over all node pairs; tree: the treecode for the float32 inner applies "
                          "(double-float passes stay direct); tree-df: treecodes for both "
                          "(rbs_options.far_field)")
@@ -151,38 +164,78 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(susp, budget_s: float, iterations: int):
-    """Time the float64 oracle on a bounded sample of the workload: rows of the system operator
-    (1/2 I + K + L) at seeded target nodes, each computed in full (every source particle, the near
-    upsampling and a singular-rule row).  Extrapolates to one solve = (iterations + 2) operator
-    applications plus one single-layer application of the same cost.  Returns (solves/s, sample)."""
+_ORACLE = None
+
+
+def _oracle_worker_init(arrays):
+    """Worker set-up (spawned process, one thread): the oracle's system for the workload's arrays."""
+    global _ORACLE
     import oracle
-    try:
-        import threadpoolctl
-        threads = max([d.get("num_threads", 1) for d in threadpoolctl.threadpool_info()] or [1])
-    except Exception:
-        threads = 1
-    t0 = time.perf_counter()
-    ref = oracle.System(susp.semi_axes, susp.p, susp.nphi, susp.centres, susp.quats, susp.suspension_id)
-    t_setup = time.perf_counter() - t0
-    mu = suspensions.random_density(9, susp.total_nodes)
-    rng = np.random.default_rng(9)
+    semi_axes, p, nphi, centres, quats, sid = arrays
+    _ORACLE = (oracle.System(semi_axes, p, nphi, centres, quats, sid), int((p + 1) @ nphi))
+
+
+def _oracle_rows(args):
+    """Rows of the float64 system operator (1/2 I + K + L) at seeded random nodes for budget seconds:
+    returns (rows, seconds)."""
+    seed, budget = args
+    ref, total = _ORACLE
+    mu = suspensions.random_density(9, total)
+    rng = np.random.default_rng([seed, 11])
     rows = 0
-    t1 = time.perf_counter()
+    t0 = time.perf_counter()
     while True:
-        node = int(rng.integers(susp.total_nodes))
-        ref.apply_rows("K", mu, [node], half=0.5, with_L=True)
+        ref.apply_rows("K", mu, [int(rng.integers(total))], half=0.5, with_L=True)
         rows += 1
-        el = time.perf_counter() - t1
-        if el > budget_s or rows >= 4096:
-            break
-    per_row = el / rows
-    matvec_s = per_row * susp.total_nodes
-    solve_s = matvec_s * (iterations + 3)
-    sample = (f"{rows} rows of the float64 operator at random nodes of the {susp.name} workload "
-              f"({el:.1f} s, {per_row * 1e3:.1f} ms per row; oracle set-up {t_setup:.1f} s excluded); "
-              f"one solve extrapolated as {iterations} GMRES + 3 operator applications")
-    return 1.0 / solve_s, sample, threads, el
+        el = time.perf_counter() - t0
+        if el > budget or rows >= 4096:
+            return rows, el
+
+
+class OracleSampler:
+    """The float64 oracle timed on a bounded sample of the workload: rows of the system operator at
+    random nodes, each computed in full (every source particle, the near upsampling and a singular-rule
+    row), on `procs` spawned single-threaded processes at once (all host cores by default).  One solve
+    is extrapolated as (iterations + 3) operator applications."""
+
+    def __init__(self, susp, procs: int):
+        import multiprocessing as mp
+        self.susp = susp
+        self.procs = procs
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        arrays = (susp.semi_axes, susp.p, susp.nphi, susp.centres, susp.quats, susp.suspension_id)
+        t0 = time.perf_counter()
+        self.pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_worker_init, initargs=(arrays,))
+        self.pool.map(_oracle_rows, [(k, 0.0) for k in range(procs)])  # every worker has built its system
+        self.setup_s = time.perf_counter() - t0
+        self.draw = 0
+
+    def sample(self, budget_s: float, iterations: int, procs: int | None = None):
+        procs = procs or self.procs
+        t0 = time.perf_counter()
+        out = self.pool.map(_oracle_rows, [(1000 * self.draw + k, budget_s) for k in range(procs)], chunksize=1)
+        wall = time.perf_counter() - t0
+        self.draw += 1
+        rows = sum(r for r, _ in out)
+        per_row = wall / rows  # wall time per row with `procs` processes at work
+        solve_s = per_row * self.susp.total_nodes * (iterations + 3)
+        sample = (f"{rows} rows of the float64 operator at random nodes of the {self.susp.name} workload on "
+                  f"{procs} processes ({wall:.1f} s wall, {per_row * 1e3:.1f} ms per row aggregate; oracle "
+                  f"set-up {self.setup_s:.1f} s excluded); one solve extrapolated as {iterations} GMRES + 3 "
+                  f"operator applications")
+        return 1.0 / solve_s, sample, wall
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 # ---------------------------------------------------------------------------------------------- reference arm
@@ -192,22 +245,24 @@ def run_reference(args):
     if rank != 0:
         return
     susp = suspensions.WORKLOADS[args.workload]()
-    iters = 12
+    iters = 21  # the chosen path's GMRES iterations at this workload (its bench line reports them)
+    procs = args.cpu_procs or host_cores()
+    sampler = OracleSampler(susp, procs)
+    per_step = max(2.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
     vals = []
     sample = ""
-    threads = 1
-    per_step = max(2.0, args.cpu_seconds / max(1, args.steps + args.warmup))
     for k in range(args.warmup + args.steps):
-        v, sample, threads, el = oracle_sample(susp, per_step, iters)
+        v, sample, _ = sampler.sample(per_step, iters)
         if k >= args.warmup:
             vals.append(v)
+    sampler.close()
     value = float(np.mean(vals))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": susp.name, "n_particles": susp.n, "unknowns": 3 * susp.total_nodes,
-                       "tol": args.tol},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+            "config": {"workload": susp.name, "n_particles": susp.n, "p": int(susp.p[0]), "nodes": susp.total_nodes,
+                       "unknowns": 3 * susp.total_nodes, "tol": args.tol or 1e-8},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": procs, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -215,11 +270,17 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------------------------- our arm
 
+def pair_kind(name: str) -> str:
+    return "traction" if "traction" in name else ("both" if "both" in name else "stokeslet")
+
+
 def kernel_rooflines(kernels, f_mhz, hbm_gbs):
-    """Achieved rate of every timed kernel class against the roofline that bounds it: float32 issue
-    (minimal instructions per pair) for float32 and double-float pair sums, the float64 FMA rate for
-    float64 pair sums, HBM bandwidth for the particle-block kernel (bytes of block entries)."""
+    """Achieved rate of every timed kernel class against the roofline that bounds it: the float32 FMA
+    peak (algorithmic flops per pair) for float32 and double-float pair sums, with the issue efficiency
+    of the double-float kernels beside it; the float64 FMA rate for float64 pair sums; HBM bandwidth
+    for the particle-block kernel (bytes of block entries)."""
     f = f_mhz * 1e6
+    fp32 = SMS * FP32_LANES_PER_SM * 2 * f
     out = {}
     for name, e in kernels.items():
         if e["ms"] <= 0 or not e["launches"]:
@@ -227,21 +288,25 @@ def kernel_rooflines(kernels, f_mhz, hbm_gbs):
         rate = e["units"] / (e["ms"] / 1e3)
         row = {"ms_per_launch": e["ms"] / e["launches"]}
         if name.startswith("pair_"):
-            kind = "traction" if "traction" in name else ("both" if "both" in name else "stokeslet")
-            if name.endswith("_f32"):
-                instr = {"traction": 20.0, "stokeslet": 18.0}[kind]
-                peak = SMS * FP32_LANES_PER_SM * f / instr
-            elif name.endswith("_df"):
-                peak = SMS * FP32_LANES_PER_SM * f / DF_INSTR_PER_PAIR[kind]
+            kind = pair_kind(name)
+            row["achieved_gpair_s"] = rate / 1e9
+            if name.endswith("_f32") or name.endswith("_df"):
+                tf = rate * FLOPS_PER_PAIR[kind]
+                row.update({"achieved_tflops": tf / 1e12, "peak_tflops": fp32 / 1e12, "frac": tf / fp32,
+                            "bound": "alu"})
+                if name.endswith("_df"):
+                    row["issue_efficiency"] = rate * DF_INSTR_PER_PAIR[kind] / (SMS * FP32_LANES_PER_SM * f)
             else:
                 peak = SMS * FP64_DFMA_PER_CLK_SM * f / FP64_OPS_PER_PAIR[kind]
-            row.update({"achieved_gpair_s": rate / 1e9, "peak_gpair_s": peak / 1e9, "frac": rate / peak,
-                        "bound": "alu"})
+                row.update({"peak_gpair_s": peak / 1e9, "frac": rate / peak, "bound": "alu"})
         elif name == "particle_blocks":
             row.update({"achieved_gb_s": rate / 1e9, "peak_gb_s": hbm_gbs, "frac": rate / 1e9 / hbm_gbs,
                         "bound": "hbm"})
+        elif name == "gmres_graph":
+            row = {"ms_per_launch": e["ms"] / e["launches"], "arnoldi_steps": e["units"],
+                   "ms_per_step": e["ms"] / max(1.0, e["units"])}
         else:
-            row.update({"achieved_gpair_s": rate / 1e9})
+            row["achieved_gpair_s"] = rate / 1e9
         out[name] = row
     return out
 
@@ -254,6 +319,34 @@ def kernel_table(stats):
             out[name] = {"ms": stats["kernel_ms"][k], "launches": stats["kernel_count"][k],
                          "units": stats["kernel_units"][k]}
     return out
+
+
+def subset(susp, count: int):
+    """The first `count` particles of a suspension (the same draws, placed first)."""
+    k = min(count, susp.n)
+    return suspensions.Suspension(susp.semi_axes[:k], susp.p[:k], susp.nphi[:k], susp.centres[:k], susp.quats[:k],
+                                  susp.F[:k], susp.T[:k], susp.suspension_id[:k], f"{susp.name}_first{k}")
+
+
+def plain_fp64_extrapolated(rbs, susp, args, iterations, stream, local):
+    """The plain float64 solve (float64 everything, same preconditioner, zero start) extrapolated from
+    timed float64 operator applications on the first fp64_subset particles of the workload: the
+    per-pair rates of the float64 traction and Stokeslet sums and the per-unit times of the particle
+    blocks and the near correction, scaled to the workload's pairs, nodes and near units; one solve =
+    (iterations + 3) applications of A plus one of S."""
+    import torch
+    sub = subset(susp, args.fp64_subset)
+    with rbs.Context(device=local, precision=rbs.RBS_PREC_FP64, timing=1, stream=stream.cuda_stream) as c64:
+        c64.set_suspension(sub)
+        x = torch.tensor(suspensions.random_density(5, sub.total_nodes), device="cuda")
+        y = torch.zeros_like(x)
+        rbs.rbs_apply_operator_device(c64.ctx, rbs.RBS_OP_A, rbs.RBS_PREC_FP64, x, y)  # warm
+        rbs.rbs_reset_stats(c64.ctx)
+        for op in (rbs.RBS_OP_A, rbs.RBS_OP_S):
+            rbs.rbs_apply_operator_device(c64.ctx, op, rbs.RBS_PREC_FP64, x, y)
+        torch.cuda.synchronize()
+        st = rbs.rbs_get_stats(c64.ctx)
+    return kernel_table(st), sub, st
 
 
 def run_ours(args):
@@ -349,7 +442,7 @@ def run_ours(args):
             ends[k].record(stream)
             iters.append(its)
         torch.cuda.synchronize()
-    times = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    times = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
     total_ms = sum(times)
     stats = rbs.rbs_get_stats(ctx.ctx)
     refinements = stats["refinements"]
@@ -358,34 +451,7 @@ def run_ours(args):
     kernels = kernel_table(stats)
     launches = stats["launches"]
     clocks = clk.summary()
-
-    # the plain float64 path on the same suspension and tolerance
-    plain = None
-    ctx64 = None
-    if args.fp64_steps > 0:
-        ctx64 = rbs.Context(device=local, precision=rbs.RBS_PREC_FP64, timing=1, stream=stream.cuda_stream)
-        ctx64.set_suspension(susp)
-        barrier()
-        rbs.rbs_reset_stats(ctx64.ctx)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        its64 = 0
-        for k in range(args.fp64_steps):
-            Fk = F_dev[args.warmup + k]
-            Tk = T_dev[args.warmup + k]
-            its64 = rbs.rbs_mobility_solve_device(ctx64.ctx, Fk, Tk, args.tol, v_dev, om_dev)
-            if k == 0:
-                v64 = v_dev.cpu().numpy().copy()
-                om64 = om_dev.cpu().numpy().copy()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1) / args.fp64_steps
-        st64 = rbs.rbs_get_stats(ctx64.ctx)
-        k64 = kernel_table(st64)
-        plain = {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "steps": args.fp64_steps, "warmup": 0,
-                 "tol": args.tol, "gmres_iterations": its64, "error_vs_reference": error_of(v64, om64),
-                 "kernels": k64}
+    mean_iters = float(np.mean(iters)) if iters else 0.0
 
     # end to end through the host-buffer entry point (pinned host arrays, copies inside the timing)
     e2e = None
@@ -394,29 +460,79 @@ def run_ours(args):
         Th = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
         vh = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
         omh = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+        its_h = np.zeros(max(1, rbs.rbs_suspension_count(ctx.ctx)), np.int32)
         lib = rbs.load()
-        import ctypes
-        its_c = ctypes.c_int(0)
         barrier()
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
             Fh[:] = draws[(args.warmup + k) % len(draws)][0]
             Th[:] = draws[(args.warmup + k) % len(draws)][1]
             rc = lib.rbs_mobility_solve(ctx.ctx, Fh.ctypes.data, Th.ctypes.data, args.tol, vh.ctypes.data,
-                                        omh.ctypes.data, None, ctypes.addressof(its_c))
+                                        omh.ctypes.data, None, its_h.ctypes.data)
             if rc != 0:
                 raise RuntimeError(rbs.rbs_last_error(ctx.ctx))
         el = reduce_max(time.perf_counter() - t0, world, "cuda")
-        e2e = {"value": whole_job_rate(args.e2e_steps, world, el * 1e3), "unit": "solves/s", "h2d_bytes_per_step": 2 * 3 * 8 * n,
-               "d2h_bytes_per_step": 2 * 3 * 8 * n}
+        e2e = {"value": whole_job_rate(args.e2e_steps, world, el * 1e3), "unit": "solves/s",
+               "h2d_bytes_per_step": 2 * 3 * 8 * n, "d2h_bytes_per_step": 2 * 3 * 8 * n}
 
-    # Stokeslet pair rates in each arithmetic (one application of the off-diagonal single layer)
+    # per-kernel rates outside the solve (the inner solve's kernels run inside the captured GMRES graph,
+    # which is timed as one unit): one apply of each operator in each arithmetic, timed by class
     x_dev = torch.tensor(suspensions.random_density(3, susp.total_nodes), device="cuda")
     y_dev = torch.zeros_like(x_dev)
     rbs.rbs_reset_stats(ctx.ctx)
-    for prec in (rbs.RBS_PREC_MIXED, rbs.RBS_PREC_MIXED, rbs.RBS_PREC_DF):
-        rbs.rbs_apply_operator_device(ctx.ctx, rbs.RBS_OP_S_OFF, prec, x_dev, y_dev)
-    srates = kernel_table(rbs.rbs_get_stats(ctx.ctx))
+    for op, prec in ((rbs.RBS_OP_A, rbs.RBS_PREC_MIXED), (rbs.RBS_OP_S_OFF, rbs.RBS_PREC_MIXED),
+                     (rbs.RBS_OP_S_OFF, rbs.RBS_PREC_DF)):
+        rbs.rbs_apply_operator_device(ctx.ctx, op, prec, x_dev, y_dev)
+    op_kernels = kernel_table(rbs.rbs_get_stats(ctx.ctx))
+
+    # the plain float64 path at the same tolerance: timed solves, or extrapolated from a subset
+    plain = None
+    if args.fp64_steps > 0:
+        with rbs.Context(device=local, precision=rbs.RBS_PREC_FP64, timing=1, stream=stream.cuda_stream) as c64:
+            c64.set_suspension(susp)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(args.fp64_steps):
+                its64 = rbs.rbs_mobility_solve_device(c64.ctx, F_dev[args.warmup + k], T_dev[args.warmup + k],
+                                                      args.tol, v_dev, om_dev)
+                if k == 0:
+                    v64 = v_dev.cpu().numpy().copy()
+                    om64 = om_dev.cpu().numpy().copy()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        plain = {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "steps": args.fp64_steps, "tol": args.tol,
+                 "gmres_iterations": its64, "error_vs_reference": error_of(v64, om64), "basis": "timed"}
+    elif args.fp64_subset > 0 and world == 1:
+        tab, sub, st_sub = plain_fp64_extrapolated(rbs, susp, args, mean_iters, stream, local)
+
+        def per_unit(name):
+            e = tab.get(name)
+            return (e["ms"] / e["units"]) if e and e["units"] > 0 else 0.0
+
+        near_sub = tab.get("near_correction", {"ms": 0.0, "launches": 1})
+        # the workload's units per application: far pairs, stored block bytes (float64 = twice the
+        # float32 bytes the mixed path reads), near pair-nodes
+        far_full = st0["far_pairs"]
+        t_K = per_unit("pair_traction_f64") * far_full
+        t_S = per_unit("pair_stokeslet_f64") * far_full
+        blocks_per_node = (tab["particle_blocks"]["ms"] / tab["particle_blocks"]["launches"]) / sub.total_nodes \
+            if "particle_blocks" in tab else 0.0
+        t_blocks = blocks_per_node * susp.total_nodes
+        t_near = (near_sub["ms"] / max(1, near_sub["launches"])) * (st0["near_pairs"] / max(1, st_sub["near_pairs"]))
+        t_A = t_K + 2 * t_blocks + t_near  # preconditioner + system blocks, pairs, near
+        its64 = max(1, int(round(mean_iters)))
+        ms64 = (its64 + 3) * t_A + t_S + t_blocks + t_near
+        plain = {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "tol": args.tol, "gmres_iterations": its64,
+                 "basis": (f"extrapolated: float64 operator applications timed on the first {sub.n} particles "
+                           f"({sub.total_nodes} nodes) of the workload, scaled to its {far_full:.4g} far pairs, "
+                           f"{susp.total_nodes} nodes and {st0['near_pairs']} near pairs; one solve = "
+                           f"(iterations + 3) applications of A plus one of S, iterations taken from the chosen path"),
+                 "subset_kernels": tab,
+                 "traction_f64_gpair_s": (1.0 / per_unit("pair_traction_f64") / 1e6) if per_unit("pair_traction_f64") else None,
+                 "stokeslet_f64_gpair_s": (1.0 / per_unit("pair_stokeslet_f64") / 1e6) if per_unit("pair_stokeslet_f64") else None}
 
     # pair rates and the roofline of the dominant kernel of the chosen path
     f_mhz = clocks.get("sm_mhz") or 2070.0
@@ -427,40 +543,39 @@ def run_ours(args):
         e = tab.get(name)
         return None if not e or e["ms"] <= 0 else e["units"] / (e["ms"] / 1e3) / 1e9
 
-    gpairs = {"stokeslet_f32": rate(srates, "pair_stokeslet_f32"),
-              "stokeslet_df": rate(srates, "pair_stokeslet_df"),
-              "traction_f32": rate(kernels, "pair_traction_f32"),
-              "traction_df": rate(kernels, "pair_traction_df"),
-              "traction_and_stokeslet_df": rate(kernels, "pair_both_df"),
-              "traction_f64": rate(kernels, "pair_traction_f64")}
-    if plain:
-        gpairs["stokeslet_f64_plain"] = rate(plain["kernels"], "pair_stokeslet_f64")
-        gpairs["traction_f64_plain"] = rate(plain["kernels"], "pair_traction_f64")
-    dom = max(kernels.items(), key=lambda kv: kv[1]["ms"])
+    gpairs = {"stokeslet_f32": rate(op_kernels, "pair_stokeslet_f32"),
+              "stokeslet_df": rate(op_kernels, "pair_stokeslet_df"),
+              "traction_f32": rate(op_kernels, "pair_traction_f32"),
+              "traction_and_stokeslet_df": rate(kernels, "pair_both_df")}
+    if plain and "traction_f64_gpair_s" in plain:
+        gpairs["traction_f64_plain"] = plain["traction_f64_gpair_s"]
+        gpairs["stokeslet_f64_plain"] = plain["stokeslet_f64_gpair_s"]
+    timed = {k: v for k, v in kernels.items() if k != "gmres_graph"}
+    dom = max(timed.items(), key=lambda kv: kv[1]["ms"])
     name, e = dom
     per_launch_ms = e["ms"] / e["launches"]
     units_per_launch = e["units"] / e["launches"]
-    if name.startswith("pair_"):
-        kind = "traction" if "traction" in name else ("both" if "both" in name else "stokeslet")
+    if name.startswith("pair_") and not name.endswith("f64"):
+        kind = pair_kind(name)
+        pairs_s = units_per_launch / (per_launch_ms / 1e3)
+        achieved = pairs_s * FLOPS_PER_PAIR[kind] / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak_tflops, "traffic": None, "kernel": name,
+                "peak_basis": f"float32 FMA peak derived from the unit counts: {SMS} SMs x 128 lanes x 2 flop x "
+                              f"{f_mhz:.0f} MHz (median SM clock sampled under load); not in MEASURED_PEAKS.json",
+                "achieved_basis": f"{FLOPS_PER_PAIR[kind]:.0f} algorithmic flops per evaluated pair "
+                                  f"x {units_per_launch:.4g} pairs per launch / CUDA-event time per launch",
+                "gpair_s": pairs_s / 1e9}
         if name.endswith("_df"):
-            # double-float: reported as the float64-equivalent pair rate against the float32 issue rate
-            # at the kernel's own instruction count per pair (DF_INSTR_PER_PAIR)
-            achieved = units_per_launch / (per_launch_ms / 1e3) / 1e9
-            peak = SMS * FP32_LANES_PER_SM * f_mhz * 1e6 / DF_INSTR_PER_PAIR[kind] / 1e9
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": name,
-                    "peak_basis": f"float32 issue: {SMS} SMs x 128 lanes x {f_mhz:.0f} MHz / "
-                                  f"{DF_INSTR_PER_PAIR[kind]} double-float instructions per pair"}
-        elif name.endswith("f32"):
-            achieved = units_per_launch * FLOPS_PER_PAIR[kind] / (per_launch_ms / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / fp32_peak_tflops, "traffic": None, "kernel": name,
-                    "peak_basis": f"float32 FMA: {SMS} SMs x 128 lanes x 2 flop x {f_mhz:.0f} MHz (median under load)"}
-        else:
-            achieved = units_per_launch * FP64_OPS_PER_PAIR[kind] * 2 / (per_launch_ms / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_peak_tflops, "traffic": None, "kernel": name,
-                    "peak_basis": f"float64 FMA: {SMS} SMs x 2 lanes x 2 flop x {f_mhz:.0f} MHz"}
+            roof["issue_efficiency"] = pairs_s * DF_INSTR_PER_PAIR[kind] / (SMS * FP32_LANES_PER_SM * f_mhz * 1e6)
+            roof["issue_basis"] = (f"{DF_INSTR_PER_PAIR[kind]:.0f} float32 operations the double-float kernel issues "
+                                   f"per pair against {SMS} SMs x 128 lanes x {f_mhz:.0f} MHz")
+    elif name.startswith("pair_"):
+        kind = pair_kind(name)
+        achieved = units_per_launch * FP64_OPS_PER_PAIR[kind] * 2 / (per_launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak_tflops, "traffic": None, "kernel": name,
+                "peak_basis": f"float64 FMA: {SMS} SMs x 2 lanes x 2 flop x {f_mhz:.0f} MHz"}
     else:
         peaks = {}
         try:
@@ -471,29 +586,40 @@ def run_ours(args):
         achieved = units_per_launch / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": name,
-                "peak_basis": "measured copy bandwidth" if peaks else "fallback 6.8 TB/s"}
+                "peak_basis": "of measured copy bandwidth" if peaks else "of fallback 6.8 TB/s"}
     try:
         hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
     except Exception:
         hbm_peak = 6800.0
-    rooflines = kernel_rooflines(kernels, f_mhz, hbm_peak)
-    # the captured counters belong to the direct kernels: a treecode kernel in the class has none yet
-    treecode_class = (name.endswith("_f32") and far != rbs.RBS_FAR_DIRECT) or \
-                     (name.endswith("_df") and far == rbs.RBS_FAR_TREECODE_DF)
-    if name in NCU_TRAFFIC and not treecode_class:
+    rooflines = kernel_rooflines({**op_kernels, **kernels}, f_mhz, hbm_peak)
+    # the captured counters belong to the direct kernels (and the double-float treecode kernel, captured
+    # on its own profiling case): a treecode kernel without a capture has none
+    tree_df_class = name.endswith("_df") and far == rbs.RBS_FAR_TREECODE_DF
+    treecode_class = (name.endswith("_f32") and far != rbs.RBS_FAR_DIRECT)
+    if tree_df_class and TREE_DF_TRAFFIC is not None:
+        bytes_, nodes_ = TREE_DF_TRAFFIC
+        roof["traffic"] = bytes_ * susp.total_nodes / nodes_
+        roof["traffic_basis"] = ("ncu dram read+write of the double-float treecode kernel on the 2,000-ellipsoid "
+                                 "profiling case, scaled by node count")
+    elif name in NCU_TRAFFIC and not treecode_class and not tree_df_class:
         bytes_, nodes_ = NCU_TRAFFIC[name]
         roof["traffic"] = bytes_ * susp.total_nodes / nodes_
         roof["traffic_basis"] = "ncu dram read+write of the 400-ellipsoid capture, scaled by node count"
-    elif treecode_class:
-        roof["traffic_basis"] = "null: no dram counters captured for the treecode kernel of this class"
+    else:
+        roof["traffic_basis"] = "null: no dram counters captured for this kernel"
     roof["ms_per_launch"] = per_launch_ms
     roof["share_of_step"] = e["ms"] / total_ms if world == 1 else None
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
-        its_plain = plain["gmres_iterations"] if plain else (int(np.mean(iters)) if iters else 12)
-        cpu_val, sample, threads, _ = oracle_sample(susp, args.cpu_seconds, its_plain)
-        cpu = {"value": cpu_val, "unit": "solves/s", "cores": threads, "kind": "oracle", "sample": sample}
+        procs = args.cpu_procs or host_cores()
+        sampler = OracleSampler(susp, procs)
+        its_c = max(1, int(round(mean_iters)))
+        cpu_val, sample, _ = sampler.sample(args.cpu_seconds, its_c)
+        one_val, one_sample, _ = sampler.sample(max(3.0, args.cpu_seconds / 2), its_c, procs=1)
+        sampler.close()
+        cpu = {"value": cpu_val, "unit": "solves/s", "cores": procs, "kind": "oracle", "sample": sample,
+               "single_core": {"value": one_val, "unit": "solves/s", "cores": 1, "sample": one_sample}}
 
     if rank == 0:
         line = {
@@ -506,8 +632,8 @@ def run_ours(args):
                                      "tree": "treecode for the float32 inner applies, direct double-float passes",
                                      "tree-df": "treecodes for the float32 applies and the double-float passes"}[
                                          args.far_field],
-                       "preconditioner": "block-diagonal", "gmres_iterations": iters,
-                       "refinements_last": refinements, "setup_ms": setup_ms,
+                       "preconditioner": "block-diagonal", "gmres": "per-suspension, graph-captured Arnoldi cycle",
+                       "gmres_iterations": iters, "refinements_last": refinements, "setup_ms": setup_ms,
                        "l2": "flushed before every timed solve (258 MB write); working set > L2",
                        "parallelism": f"replicas x{world}"},
             "error_vs_reference": err,
@@ -516,9 +642,9 @@ def run_ours(args):
             "speedup_vs_plain_fp64": (value / world) / plain["solves_per_s"] if plain else None,
             "gpair_per_s": gpairs,
             "kernels": kernels,
+            "operator_kernels": op_kernels,
             "pair_variant": dict(zip(["traction_f32", "stokeslet_f32", "traction_df", "stokeslet_df",
-                                      "traction_and_stokeslet_df"],
-                                     stats.get("pair_variant", []))),
+                                      "traction_and_stokeslet_df"], stats.get("pair_variant", []))),
             "treecode": tree_info,
             "roofline": roof,
             "kernel_rooflines": rooflines,
@@ -526,11 +652,10 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": launches,
+            "gpu_launches_per_step": launches / max(1, args.steps),
         }
         print(json.dumps(line), flush=True)
     ctx.close()
-    if ctx64 is not None:
-        ctx64.close()
     if world > 1:
         dist.destroy_process_group()
 

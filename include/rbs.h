@@ -47,9 +47,16 @@ extern "C" {
 #define RBS_PREC_MIXED 1 /* float32 inner GMRES; right-hand side, refinement residuals and velocity
                             in the arithmetic of rbs_options.refine_precision; float64 vectors,
                             Arnoldi, refinement updates, projection and velocity extraction */
-#define RBS_PREC_DF 2    /* float64-class operator: pair sums in double-float arithmetic (unevaluated
+#define RBS_PREC_MIXED_FP16 2 /* RBS_PREC_MIXED with the self blocks of the inner GMRES (the
+                            block-diagonal preconditioner of Section 3.2 and the K self blocks of its
+                            restarts) stored in float16 and applied with float32 accumulation: on the
+                            tensor cores for particles sharing a shape (a batched GEMM), on CUDA cores
+                            otherwise.  Refinement residuals and float32 corrections keep float32
+                            blocks, so only the inner operator's accuracy changes (about 5e-4) */
+#define RBS_PREC_DF 3    /* float64-class operator: pair sums in double-float arithmetic (unevaluated
                             sums of two float32 numbers, ~1e-12 relative), blocks and vectors in
                             float64 (rbs_apply_operator and rbs_options.refine_precision only) */
+#define RBS_PREC_MIXED_BF16 4 /* as RBS_PREC_MIXED_FP16 with bfloat16 self blocks (about 4e-3) */
 
 /* Operators for rbs_apply_operator (each acts on a surface field, Section 2). */
 #define RBS_OP_A 0        /* (1/2 I + K + L), the system operator of Eq. 25 */
@@ -64,7 +71,8 @@ extern "C" {
 typedef struct rbs_ctx rbs_ctx;
 
 typedef struct {
-  int precision;       /* RBS_PREC_FP64 (default) or RBS_PREC_MIXED */
+  int precision;       /* RBS_PREC_FP64 (default), RBS_PREC_MIXED, RBS_PREC_MIXED_FP16 or
+                          RBS_PREC_MIXED_BF16 */
   int restart;         /* GMRES restart length (default 50) */
   int max_iters;       /* cap on GMRES iterations per solve (default 500) */
   int preconditioner;  /* 1 (default): right block-diagonal preconditioner, the inverse of each
@@ -90,8 +98,11 @@ typedef struct {
                           the targets per thread alone); 0 (default) times the candidates once per
                           context and kernel and keeps the fastest */
   int warm_start;      /* initial GMRES guess: RBS_WARM_ZERO (default), RBS_WARM_PREVIOUS (the last
-                          solved density of this context) or RBS_WARM_LEARNED (the trained network);
-                          the converged solution does not depend on it */
+                          solved density of this context), RBS_WARM_LEARNED (the trained network's
+                          density for the current configuration) or RBS_WARM_LEARNED_DELTA (the last
+                          solved density plus the change the network predicts between the last
+                          solve's configuration and the current one; the network's guess alone on
+                          the first solve); the converged solution does not depend on it */
   int warm_record;     /* 1: rbs_advance records a training sample (rbs_warmstart_record) after every
                           stage solve (default 0) */
   double contact_gap;  /* 0 (default): no contact handling; > 0: the contact algorithm of Section
@@ -136,6 +147,7 @@ typedef struct {
 #define RBS_WARM_ZERO 0
 #define RBS_WARM_PREVIOUS 1
 #define RBS_WARM_LEARNED 2
+#define RBS_WARM_LEARNED_DELTA 3
 
 /* Kernel classes timed when rbs_options.timing is set (indices into rbs_stats.kernel_*). */
 #define RBS_KC_PAIR_K32 0 /* smooth traction pair sum, float32 */
@@ -176,7 +188,8 @@ typedef struct {
   int pair_variant[5];   /* variant in use (as rbs_options.pair_variant): float32 traction, float32
                             Stokeslet (the treecode kernel's with RBS_FAR_TREECODE), double-float
                             traction, double-float Stokeslet, fused double-float traction and
-                            Stokeslet (0 = not yet chosen) */
+                            Stokeslet (the double-float treecode kernel's targets per thread with
+                            RBS_FAR_TREECODE_DF; 0 = not yet chosen) */
   long long tree_pairs;  /* RBS_FAR_TREECODE: (target node, source) pairs one treecode apply evaluates,
                             direct node pairs (the target's own particle included, masked) plus
                             proxy pairs; 0 without a treecode */
@@ -356,8 +369,10 @@ int rbs_rigid_velocities_noalloc(rbs_ctx* ctx, const double* u_dev, double* v_de
 /*
  * Apply one discrete operator (RBS_OP_*) to a surface field: y = op(x), x and y total_nodes x 3 host
  * arrays.  precision RBS_PREC_FP64 applies it in float64; RBS_PREC_MIXED in the float32 arithmetic of
- * the inner solve (pair sums with compensated accumulation, float32 self blocks); RBS_PREC_DF with
- * double-float pair sums and float64 blocks.
+ * the inner solve (pair sums with compensated accumulation, float32 self blocks); RBS_PREC_MIXED_FP16
+ * and RBS_PREC_MIXED_BF16 the same with the K self blocks in float16 or bfloat16 (float32 accumulation;
+ * the context must have been created with that precision; the S self blocks stay float64);
+ * RBS_PREC_DF with double-float pair sums and float64 blocks.
  */
 int rbs_apply_operator(rbs_ctx* ctx, int op, int precision, const double* x, double* y);
 

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "librbs.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["setup.cu", "linalg.cu", "operators.cu", "solver.cu", "gmres.cu", "timestep.cu", "warmstart.cu", "magnetic.cu", "treecode.cu", "api.cu"]
+SOURCES = ["setup.cu", "linalg.cu", "operators.cu", "solver.cu", "gmres.cu", "selfgemm.cu", "timestep.cu", "warmstart.cu", "magnetic.cu", "treecode.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wno-deprecated-declarations",
          "-diag-suppress", "1444", "-Xptxas", "-warn-spills"]

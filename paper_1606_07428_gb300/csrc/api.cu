@@ -124,11 +124,11 @@ int rbs_create(const rbs_options* opt, rbs_ctx** out) {
   if (o.restart < 1 || o.restart > 500 || o.max_iters < 1 || o.p_up_factor < 1 || o.p_up_factor > 4 ||
       o.p_self_factor < 1 || o.p_self_factor > 4 || !(o.viscosity > 0) || !(o.near_delta >= 0) ||
       !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_refinements < 1 ||
-      (o.precision != RBS_PREC_FP64 && o.precision != RBS_PREC_MIXED) ||
+      (o.precision != RBS_PREC_FP64 && !rbs::prec_f32(o.precision)) ||
       (o.refine_precision != RBS_PREC_FP64 && o.refine_precision != RBS_PREC_DF) || o.warm_start < 0 ||
       (o.pair_variant != 0 && o.pair_variant != 1 && o.pair_variant != 2 && o.pair_variant != 4 &&
        o.pair_variant != 9 && o.pair_variant != 10 && o.pair_variant != 12) ||
-      o.warm_start > 2 || !(o.contact_gap >= 0.0) || !(o.mu_ratio > 0.0) ||
+      o.warm_start > 3 || !(o.contact_gap >= 0.0) || !(o.mu_ratio > 0.0) ||
       !std::isfinite(o.magnetic_field[0]) || !std::isfinite(o.magnetic_field[1]) || !std::isfinite(o.magnetic_field[2]) ||
       (o.far_field != RBS_FAR_DIRECT && o.far_field != RBS_FAR_TREECODE && o.far_field != RBS_FAR_TREECODE_DF) ||
       !(o.tree_theta > 0.0 && o.tree_theta < 1.0) || o.tree_degree < 2 || o.tree_degree > 10 ||
@@ -472,8 +472,10 @@ int rbs_apply_operator_device(rbs_ctx* h, int op, int precision, const double* x
   Context& c = h->c;
   if (!c.have_geometry) return finish(c, Status::Err(RBS_ESTATE, "no geometry"));
   if (!x_dev || !y_dev || x_dev == y_dev) return finish(c, Status::Err(RBS_EINVAL, "apply_operator: bad buffers"));
-  if (precision != RBS_PREC_FP64 && precision != RBS_PREC_MIXED && precision != RBS_PREC_DF)
+  if (precision != RBS_PREC_FP64 && !rbs::prec_f32(precision) && precision != RBS_PREC_DF)
     return finish(c, Status::Err(RBS_EINVAL, "apply_operator: bad precision"));
+  if (rbs::prec_16(precision) && c.opt.precision != precision)
+    return finish(c, Status::Err(RBS_EINVAL, "apply_operator: 16-bit self blocks need a context of that precision"));
   Status s = enter(c);
   if (!s.ok()) return finish(c, s);
   s = rbs::apply_operator(c, op, precision, x_dev, y_dev);
@@ -481,6 +483,7 @@ int rbs_apply_operator_device(rbs_ctx* h, int op, int precision, const double* x
     cudaError_t e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) s = Status::Err(RBS_ECUDA, cudaGetErrorString(e));
   }
+  if (s.ok()) s = rbs::check_self_gemm(c);
   return finish(c, s);
 }
 
@@ -511,6 +514,8 @@ int rbs_get_stats(rbs_ctx* h, rbs_stats* out) {
   for (int k = 0; k < 5; ++k) out->pair_variant[k] = c.tuned[k];
   for (int k = 0; k < 2; ++k)  // the float32 sums run in the treecode kernel when it is on
     if (c.tree.active) out->pair_variant[k] = c.tree.nt[k] ? rbs::kPacked + c.tree.nt[k] : 0;
+  for (int k = 0; k < 3; ++k)  // and the double-float ones in the double-float treecode kernel
+    if (c.tree_df.active) out->pair_variant[2 + k] = c.tree_df.nt[k];
   return RBS_OK;
 }
 

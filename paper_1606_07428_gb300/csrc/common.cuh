@@ -1,9 +1,11 @@
 // Internal declarations shared by the translation units of the rbs library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <memory>
 #include <cstdint>
 #include <functional>
 #include <map>
@@ -16,6 +18,13 @@
 namespace rbs {
 
 struct WarmState;
+
+// Arithmetic classes of the precision codes: float32 pair sums (the mixed modes), and self blocks
+// stored in 16 bits (float16 or bfloat16) for the inner solve.
+inline bool prec_f32(int prec) {
+  return prec == RBS_PREC_MIXED || prec == RBS_PREC_MIXED_FP16 || prec == RBS_PREC_MIXED_BF16;
+}
+inline bool prec_16(int prec) { return prec == RBS_PREC_MIXED_FP16 || prec == RBS_PREC_MIXED_BF16; }
 
 constexpr double kPi = 3.14159265358979323846;
 
@@ -104,6 +113,7 @@ struct Grid {
 struct SymTables {
   const int *rep_of, *g_of, *orbit, *orb_node, *orb_g, *irrep_pos, *irrep_list;
 };
+SymTables sym_tables(const Grid& g);
 
 // One distinct body shape: an ellipsoid (semi-axes) or an input coefficient surface, on one
 // (p, n_phi) grid.
@@ -219,7 +229,7 @@ struct GmresWork {
 // Captured Arnoldi-step graphs (a WHILE conditional node around one step), one slot per operator and
 // arithmetic, each valid for the configuration and workspace it was captured with.
 struct GmresGraphs {
-  static constexpr int kSlots = 8;
+  static constexpr int kSlots = 16;
   struct Slot {
     cudaGraphExec_t exec = nullptr;
     long long config = -1, work = -1;
@@ -234,6 +244,22 @@ struct GmresGraphs {
   ~GmresGraphs() { release(); }
   GmresGraphs(const GmresGraphs&) = delete;
   GmresGraphs& operator=(const GmresGraphs&) = delete;
+};
+
+// Particles sharing one ellipsoid shape whose 16-bit self blocks are applied as a GEMM on the tensor
+// cores (selfgemm.cu): the full body-frame blocks K0 and P0 (3 N_p rows, row pitch Kp, 16-bit, scaled
+// by ascale), the packed body-frame inputs Z (one row per particle), and their TMA descriptors.
+constexpr int kGemmMinParticles = 64;
+struct GemmGroup {
+  int shape = 0, np = 0, Kp = 0, rows = 0;
+  std::vector<int> parts;
+  DevBuf<int> d_list;
+  DevBuf<uint16_t> K, P, Z;
+  DevBuf<float> inv;
+  DevBuf<double> mom;
+  float ascaleK = 1.0f, ascaleP = 1.0f;
+  CUtensorMap tmZ, tmK, tmP;
+  double flops = 0.0;  // tensor-core flops issued since creation
 };
 
 struct Context {
@@ -287,6 +313,9 @@ struct Context {
   DevBuf<long long> d_sh_coef_off;
   DevBuf<double> d_blockK, d_blockS, d_precond;  // body-frame 3np x 3np per shape, float64
   DevBuf<float> d_blockK32, d_precond32;
+  // 16-bit copies (float16 or bfloat16 bits, as the context's precision says) of K0 and P0 for the
+  // inner solve of RBS_PREC_MIXED_FP16 / RBS_PREC_MIXED_BF16
+  DevBuf<uint16_t> d_blockK16, d_precond16;
   DevBuf<long long> d_block_off;  // nshape
 
   // near-field data
@@ -307,6 +336,11 @@ struct Context {
   DevBuf<int4> d_bwork;
   std::vector<int> sym_list;
   DevBuf<int> d_sym_list;
+  // 16-bit modes: shape groups applied by GEMM, and the other ellipsoids (sym_rest)
+  std::vector<std::unique_ptr<GemmGroup>> gemm;
+  std::vector<int> sym_rest;
+  DevBuf<int> d_sym_rest;
+  DevBuf<int> d_gemm_err;
   int max_np_sym = 0;
   int max_np = 0;
   int max_np_shape = 0;
@@ -356,6 +390,8 @@ struct Context {
   WarmState* warm = nullptr;       // learned warm start (warmstart.cu)
   DevBuf<double> d_prev;           // last solved density (previous-solution warm start)
   bool have_prev = false;
+  DevBuf<double> d_pred_prev;      // the network's guess at the last solve (RBS_WARM_LEARNED_DELTA)
+  bool have_pred = false;
   // kernel timing: (class, start, stop, units) of launches not yet harvested
   struct Timed {
     int cls;
@@ -450,6 +486,11 @@ Status plan_near(int n, const double* centres, const double* R, const double* rm
                  std::vector<int2>& out);
 Status update_configuration(Context& c, const double* centres, const double* quats);
 void gauss_legendre_newton(int n, std::vector<double>& t, std::vector<double>& w);
+
+// ---- self blocks by tensor-core GEMM (selfgemm.cu)
+Status build_self_gemm(Context& c);
+Status apply_self_gemm(Context& c, int mode, const double* x, double* y, double* aux, double scale);
+Status check_self_gemm(Context& c);
 
 // ---- dense kernels (linalg.cu)
 Status dgemm_batched(cudaStream_t s, int M, int N, int K, const double* A, long long lda, long long strideA,

@@ -9,6 +9,8 @@
 //    from the source's upsampled grid (Section 3: upsampling for close targets).
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "dfloat.cuh"
 #include "pairs32.cuh"
@@ -169,12 +171,30 @@ __device__ __forceinline__ int reflect_node_dev(int g, int t, int p, int nphi) {
 }
 
 
-template <typename TB>
+// Block entries as stored (float64, float32, or the bits of float16 / bfloat16) to the arithmetic type.
+__device__ __forceinline__ double load_entry(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float load_entry(const float* p) { return __ldg(p); }
+struct F16Bits {
+  uint16_t v;
+};
+struct BF16Bits {
+  uint16_t v;
+};
+__device__ __forceinline__ float load_entry(const F16Bits* p) {
+  return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+}
+__device__ __forceinline__ float load_entry(const BF16Bits* p) {
+  return __uint_as_float((unsigned)__ldg(reinterpret_cast<const unsigned short*>(p)) << 16);
+}
+
+// TS: storage type of the block entries; TB: the arithmetic of the products and sums (float64 for
+// float64 blocks, float32 otherwise).
+template <typename TS, typename TB>
 __global__ void __launch_bounds__(256) k_blocks_sym(int mode, const int* __restrict__ sym_list,
                                                     const long long* __restrict__ offset, const int* __restrict__ pvec,
                                                     const int* __restrict__ nphivec, const double* __restrict__ rot,
                                                     const double* __restrict__ centre, const int* __restrict__ shape_of,
-                                                    const long long* __restrict__ block_off, const TB* __restrict__ blocks,
+                                                    const long long* __restrict__ block_off, const TS* __restrict__ blocks,
                                                     const double4* __restrict__ x, const double* __restrict__ in,
                                                     double* __restrict__ out, double* __restrict__ aux, double scale) {
   extern __shared__ __align__(16) unsigned char zraw[];
@@ -265,14 +285,14 @@ __global__ void __launch_bounds__(256) k_blocks_sym(int mode, const int* __restr
     for (int t = threadIdx.x; t < np; t += blockDim.x) finish(t, 0.0, 0.0, 0.0);
     return;
   }
-  const TB* A = blocks + block_off[shape_of[i]];
+  const TS* A = blocks + block_off[shape_of[i]];
   for (int r = warp; r < nrep; r += (int)(blockDim.x >> 5)) {
     TB y[8][3];
 #pragma unroll
     for (int g = 0; g < 8; ++g) y[g][0] = y[g][1] = y[g][2] = (TB)0;
-    const TB* row = A + (long long)(3 * r) * dim;
+    const TS* row = A + (long long)(3 * r) * dim;
     for (int col = lane; col < dim; col += 32) {
-      const TB a0 = __ldg(row + col), a1 = __ldg(row + dim + col), a2 = __ldg(row + 2 * dim + col);
+      const TB a0 = load_entry(row + col), a1 = load_entry(row + dim + col), a2 = load_entry(row + 2 * dim + col);
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
         const TB zv = zg[g * dim + col];
@@ -1204,7 +1224,7 @@ static int pair_variant(Context& c, int kind, int prec, const double* x) {
       cudaEventCreate(&b) == cudaSuccess) {
     float best_ms = 1e30f;
     std::vector<int> cands = {1, 2, 4};
-    if (prec == RBS_PREC_MIXED) cands.insert(cands.end(), {kPacked + 1, kPacked + 2, kPacked + 4});
+    if (prec_f32(prec)) cands.insert(cands.end(), {kPacked + 1, kPacked + 2, kPacked + 4});
     if (prec == RBS_PREC_DF) cands.insert(cands.end(), {kPacked + 1, kPacked + 2});
     for (int nt : cands) {
       launch_pairs(c, kind, prec, nt, items, x, scratch, scratch + 3 * c.N);  // warm (first launch of this variant)
@@ -1238,25 +1258,51 @@ Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, 
   }
   const int nb = (int)c.bwork.size();
   const int ns = (int)c.sym_list.size();
-  bool use32 = (prec == RBS_PREC_MIXED) && (mode == kModeSelfK || mode == kModeSelfKNoL || mode == kModeKOnlySelf ||
-                                             mode == kModePrecond);
+  const bool kblock = mode == kModeSelfK || mode == kModeSelfKNoL || mode == kModeKOnlySelf || mode == kModePrecond;
+  const bool use32 = prec_f32(prec) && kblock;
+  // 16-bit entries for the ellipsoid blocks of the inner solve's arithmetic (coefficient surfaces,
+  // which store every row, keep float32 blocks)
+  const bool use16 = prec_16(prec) && kblock && c.d_blockK16.ptr;
   const double bytes = (mode == kModeL) ? 0.0 : (double)c.particle_block_entries * (use32 ? 4.0 : 8.0);
   KernelTimer timer(c, RBS_KC_BLOCKS);
-  if (ns > 0) {
+  // 16-bit modes: ellipsoids of shapes shared by many particles go through the tensor-core GEMM, the
+  // others through the CUDA-core kernel below
+  const bool gemm = use16 && !c.gemm.empty();
+  const int* sym_ids = gemm ? c.d_sym_rest.ptr : c.d_sym_list.ptr;
+  const int nsym = gemm ? (int)c.sym_rest.size() : ns;
+  if (gemm) RBS_TRY(apply_self_gemm(c, mode, x, y, aux, scale));
+  if (nsym > 0) {
     const size_t zs = (use32 ? sizeof(float) : sizeof(double)) * 8 * 3 * (size_t)c.max_np_sym;
 #define RBS_SYM_ARGS                                                                                              \
-  mode, c.d_sym_list.ptr, c.d_offset.ptr, c.d_p.ptr, c.d_nphi.ptr, c.d_rot.ptr, c.d_centre.ptr, c.d_shape.ptr, \
+  mode, sym_ids, c.d_offset.ptr, c.d_p.ptr, c.d_nphi.ptr, c.d_rot.ptr, c.d_centre.ptr, c.d_shape.ptr, \
       c.d_block_off.ptr, B, c.d_x.ptr, x, y, aux, scale
-    if (use32) {
+    if (use16) {
+      const uint16_t* B16 = (mode == kModePrecond) ? c.d_precond16.ptr : c.d_blockK16.ptr;
+      if (prec == RBS_PREC_MIXED_FP16) {
+        const F16Bits* B = reinterpret_cast<const F16Bits*>(B16);
+        if (zs > 48 * 1024)
+          RBS_CUDA_TRY(cudaFuncSetAttribute(k_blocks_sym<F16Bits, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)zs));
+        k_blocks_sym<F16Bits, float><<<nsym, 256, zs, c.stream>>>(RBS_SYM_ARGS);
+      } else {
+        const BF16Bits* B = reinterpret_cast<const BF16Bits*>(B16);
+        if (zs > 48 * 1024)
+          RBS_CUDA_TRY(cudaFuncSetAttribute(k_blocks_sym<BF16Bits, float>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs));
+        k_blocks_sym<BF16Bits, float><<<nsym, 256, zs, c.stream>>>(RBS_SYM_ARGS);
+      }
+    } else if (use32) {
       const float* B = (mode == kModePrecond) ? c.d_precond32.ptr : c.d_blockK32.ptr;
       if (zs > 48 * 1024)
-        RBS_CUDA_TRY(cudaFuncSetAttribute(k_blocks_sym<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs));
-      k_blocks_sym<float><<<ns, 256, zs, c.stream>>>(RBS_SYM_ARGS);
+        RBS_CUDA_TRY(cudaFuncSetAttribute(k_blocks_sym<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)zs));
+      k_blocks_sym<float, float><<<nsym, 256, zs, c.stream>>>(RBS_SYM_ARGS);
     } else {
       const double* B = (mode == kModePrecond) ? c.d_precond.ptr : (mode == kModeSelfS ? c.d_blockS.ptr : c.d_blockK.ptr);
       if (zs > 48 * 1024)
-        RBS_CUDA_TRY(cudaFuncSetAttribute(k_blocks_sym<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs));
-      k_blocks_sym<double><<<ns, 256, zs, c.stream>>>(RBS_SYM_ARGS);
+        RBS_CUDA_TRY(cudaFuncSetAttribute(k_blocks_sym<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)zs));
+      k_blocks_sym<double, double><<<nsym, 256, zs, c.stream>>>(RBS_SYM_ARGS);
     }
 #undef RBS_SYM_ARGS
     RBS_CUDA_TRY(cudaGetLastError());
@@ -1320,7 +1366,7 @@ static Status near_sums(Context& c, int kind, int prec, const double* x, double*
       k_near_tiled<0, true><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
     else
       k_near_tiled<1, true><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
-  } else if (prec == RBS_PREC_MIXED) {
+  } else if (prec_f32(prec)) {
     if (kind == 0)
       k_near_tiled<0, false><<<nn, nthr, 0, c.stream>>>(RBS_NEAR_ARGS);
     else
@@ -1338,7 +1384,7 @@ static Status near_sums(Context& c, int kind, int prec, const double* x, double*
 
 Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y) {
   const int nw = (int)c.work.size();
-  const bool f32 = (prec == RBS_PREC_MIXED);
+  const bool f32 = prec_f32(prec);
   if (f32 && c.tree.active) {
     RBS_TRY(apply_tree(c, kind, x, y, 0));  // treecode in place of the direct float32 sum
   } else if (prec == RBS_PREC_DF && c.tree_df.active) {
@@ -1362,7 +1408,7 @@ Status apply_pairs(Context& c, int kind, int prec, const double* x, double* y) {
 }
 
 Status apply_pairs_both(Context& c, int prec, const double* x, double* yK, double* yS) {
-  if (prec == RBS_PREC_MIXED) {
+  if (prec_f32(prec)) {
     RBS_TRY(apply_pairs(c, 0, prec, x, yK));
     return apply_pairs(c, 1, prec, x, yS);
   }

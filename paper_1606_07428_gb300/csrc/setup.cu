@@ -9,6 +9,9 @@
 #include <tuple>
 #include <unordered_map>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "surface.cuh"
 
@@ -481,6 +484,12 @@ __global__ void k_to_float(const double* in, float* out, long long n) {
     out[i] = (float)in[i];
 }
 
+// float64 to the bits of float16 (bf16 = 0) or bfloat16 (bf16 = 1), rounded to nearest.
+__global__ void k_to_16bit(const double* in, uint16_t* out, long long n, int bf16) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = bf16 ? __bfloat16_as_ushort(__double2bfloat16(in[i])) : __half_as_ushort(__double2half(in[i]));
+}
+
 // Upsampled source nodes of every near-source particle: lab positions and weights on its
 // (pup + 1) x nphi_up grid.
 __global__ void k_up_nodes(int nu, const int* up_particle, const long long* up_off, const int* pvec, const int* nphivec,
@@ -619,7 +628,7 @@ Status grid_symmetry_host(int p, int nphi, std::vector<int>& rep_of, std::vector
 
 // Device layout of the symmetry tables: rep_of, g_of (np each), orbit (nrep), orb_node, orb_g
 // (8 nrep each), irrep_pos (24 nrep), irrep_list (24 nrep: per irrep, 3 r + beta of each basis vector).
-static SymTables sym_tables(const Grid& g) {
+SymTables sym_tables(const Grid& g) {
   const int* b = g.d_sym.ptr;
   SymTables t;
   t.rep_of = b;
@@ -1175,10 +1184,16 @@ Status build_geometry(Context& c) {
       }
       RBS_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    // the float32 copy serves the inner solves of the mixed path, the float64 one the float64 path
-    if (c.opt.precision == RBS_PREC_MIXED) {
+    // the float32 copy serves the inner solves of the mixed path, the float64 one the float64 path;
+    // the 16-bit modes keep a float16 or bfloat16 copy for the inner solve as well
+    if (prec_f32(c.opt.precision)) {
       RBS_TRY(c.d_precond32.alloc(c.block_elems));
       k_to_float<<<1024, 256, 0, s>>>(c.d_precond.ptr, c.d_precond32.ptr, (long long)c.block_elems);
+      if (prec_16(c.opt.precision)) {
+        RBS_TRY(c.d_precond16.alloc(c.block_elems));
+        k_to_16bit<<<1024, 256, 0, s>>>(c.d_precond.ptr, c.d_precond16.ptr, (long long)c.block_elems,
+                                        c.opt.precision == RBS_PREC_MIXED_BF16);
+      }
       RBS_CUDA_TRY(cudaStreamSynchronize(s));
       c.d_precond.release();
     } else {
@@ -1187,6 +1202,14 @@ Status build_geometry(Context& c) {
   }
   RBS_TRY(c.d_blockK32.alloc(c.block_elems));
   k_to_float<<<1024, 256, 0, s>>>(c.d_blockK.ptr, c.d_blockK32.ptr, (long long)c.block_elems);
+  if (prec_16(c.opt.precision)) {
+    RBS_TRY(c.d_blockK16.alloc(c.block_elems));
+    k_to_16bit<<<1024, 256, 0, s>>>(c.d_blockK.ptr, c.d_blockK16.ptr, (long long)c.block_elems,
+                                    c.opt.precision == RBS_PREC_MIXED_BF16);
+  } else {
+    c.d_blockK16.release();
+    c.d_precond16.release();
+  }
   RBS_CUDA_TRY(cudaGetLastError());
 
   RBS_TRY(build_near(c));
@@ -1279,6 +1302,7 @@ Status build_geometry(Context& c) {
   c.particle_block_entries = 0;
   for (int k = 0; k < n; ++k) c.particle_block_entries += (double)c.shapes[c.shape_of[k]].rows * 3.0 * nodes[k];
 
+  RBS_TRY(build_self_gemm(c));
   c.stats.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   c.have_geometry = true;
   return Status::Ok();

@@ -118,7 +118,7 @@ static Status gmres(Context& c, int prec, const double* b, double* x, bool x_zer
                     int max_iters, SegResult& out) {
   LinOp op;
   op.n = 3 * c.N;
-  op.graph_key = 2 * (prec == RBS_PREC_MIXED ? 1 : 0) + (c.opt.preconditioner ? 1 : 0);
+  op.graph_key = 2 * prec + (c.opt.preconditioner ? 1 : 0);
   op.apply_AP = [&c, prec](const double* v, double* w, double* z) { return gmres_operator(c, prec, v, w, z); };
   op.apply_A = [&c, prec](const double* xx, double* y) { return apply_operator(c, RBS_OP_A, prec, xx, y); };
   if (c.opt.preconditioner)
@@ -205,7 +205,7 @@ static Status solve_core(Context& c, double tol, bool warm, std::vector<int>& it
   //    float32 for the mixed path, where b only seeds the first inner solve (every refinement residual
   //    below is formed from rho in float64-class arithmetic, so b's float32 error does not persist)
   RBS_TRY(incident_density(c, c.d_FT.ptr, rho));
-  const bool mixed = (c.opt.precision == RBS_PREC_MIXED);
+  const bool mixed = prec_f32(c.opt.precision);
   const int hi = mixed ? c.opt.refine_precision : RBS_PREC_FP64;
   RBS_TRY(apply_operator(c, RBS_OP_HALF_K, mixed ? RBS_PREC_MIXED : RBS_PREC_FP64, rho, b));
   c.stats.launches++;
@@ -224,6 +224,25 @@ static Status solve_core(Context& c, double tol, bool warm, std::vector<int>& it
     have_x0 = true;
   } else if (warm && bmax > 0.0 && c.opt.warm_start == RBS_WARM_LEARNED) {
     RBS_TRY(warm_guess(c, c.d_FT.ptr, x0));
+    have_x0 = true;
+  } else if (warm && bmax > 0.0 && c.opt.warm_start == RBS_WARM_LEARNED_DELTA) {
+    // x0 = mu_prev + (net(now) - net(prev)): the network's guess for the current configuration, shifted
+    // by its error at the last solved configuration; the network's guess alone without a last solve
+    RBS_TRY(warm_guess(c, c.d_FT.ptr, x0));
+    const bool have_pred = c.have_prev && c.d_prev.n == (size_t)n3 && c.d_pred_prev.n == (size_t)n3 && c.have_pred;
+    if (c.d_pred_prev.n != (size_t)n3) RBS_TRY(c.d_pred_prev.alloc(n3));
+    double* tmp = c.d_vec[5].ptr;
+    if (have_pred) {
+      // tmp = x0 - pred_prev + prev; pred_prev = x0
+      c.stats.launches += 2;
+      k_add<<<nbk, 256, 0, c.stream>>>(tmp, x0, c.d_prev.ptr, n3);
+      k_axpby<<<nbk, 256, 0, c.stream>>>(tmp, -1.0, c.d_pred_prev.ptr, 1.0, n3);
+      RBS_CUDA_TRY(cudaMemcpyAsync(c.d_pred_prev.ptr, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+      RBS_CUDA_TRY(cudaMemcpyAsync(x0, tmp, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+    } else {
+      RBS_CUDA_TRY(cudaMemcpyAsync(c.d_pred_prev.ptr, x0, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c.stream));
+      c.have_pred = true;
+    }
     have_x0 = true;
   }
   double* sigma = c.d_vec[9].ptr;
@@ -288,7 +307,8 @@ static Status solve_core(Context& c, double tol, bool warm, std::vector<int>& it
         }
       }
       SegResult R;
-      RBS_TRY(gmres(c, RBS_PREC_MIXED, r, d, true, tl, c.opt.max_iters - used_max, R));
+      // the inner operator: float32 pair sums, self blocks in the context's inner arithmetic
+      RBS_TRY(gmres(c, c.opt.precision, r, d, true, tl, c.opt.max_iters - used_max, R));
       int moved = 0;
       for (int s = 0; s < S; ++s) {
         iters[s] += R.iters[s];
@@ -598,6 +618,7 @@ Status mobility_solve(Context& c, const double* F, const double* T, double tol, 
     RBS_CUDA_TRY(cudaStreamSynchronize(c.stream));
   }
   RBS_CUDA_TRY(cudaGetLastError());
+  RBS_TRY(check_self_gemm(c));
   if (iters_out) *iters_out = total_iters;
   c.stats.iterations = total_iters;
   c.stats.refinements = refinements;

@@ -432,8 +432,12 @@ __global__ void k_tree_q64_split(long long count, const double* __restrict__ q64
 // The double-float treecode pair sum: the packed double-float pair of the direct kernel (pairsdf.cuh)
 // over source tiles filled from the item's segments (as k_tree32x2).  KIND 0 traction into y, 1
 // Stokeslet into y, 2 traction into y and Stokeslet into y2.
+// Registers are capped (96 for one target per thread) so that four 160-thread blocks, the size a
+// p = 8 particle's targets take, are resident per SM: the double-float pair is a long dependent chain,
+// and with the uncapped 126 registers only three blocks (or, at two targets per thread, 238 registers
+// and two 96-thread blocks: under five warps per SM) hid its latency.
 template <int KIND, int NT>
-__global__ void __launch_bounds__(kTreeMaxTargets / NT)
+__global__ void __maxnreg__(NT == 1 ? 96 : 168)
     k_tree_df2(int nitems, const TreeItem* __restrict__ items, const int2* __restrict__ segs,
                const float4* __restrict__ x3h, const float4* __restrict__ x3m, const float4* __restrict__ x3l,
                const float4* __restrict__ nh, const float4* __restrict__ nl, const float4* __restrict__ shi,
@@ -994,7 +998,7 @@ static Status build_lists(Context& c, TreeState& T, const std::vector<double>& p
 Status build_far_field(Context& c) {
   c.stats.tree_pairs = c.stats.tree_proxy_pairs = c.stats.tree_df_pairs = c.stats.tree_df_proxy_pairs = 0;
   c.stats.tree_cells = c.stats.tree_df_cells = 0;
-  if (c.opt.far_field == RBS_FAR_DIRECT || c.opt.precision != RBS_PREC_MIXED || c.n == 0) {
+  if (c.opt.far_field == RBS_FAR_DIRECT || !prec_f32(c.opt.precision) || c.n == 0) {
     c.tree.release();
     c.tree_df.release();
     return Status::Ok();
@@ -1163,7 +1167,8 @@ static int tree_df_variant(Context& c, int kind) {
   if (c.opt.pair_variant > 0) return (c.opt.pair_variant == 2 || c.opt.pair_variant == kPacked + 2) ? 2 : 1;
   if (T.nt[kind]) return T.nt[kind];
   int best = 1;
-  const int items = std::min<int>((int)T.items.size(), 4 * std::max(1, c.sm_count));
+  // a prefix of eight items per SM: whole rounds of the persistent grid for either variant
+  const int items = std::min<int>((int)T.items.size(), 8 * std::max(1, c.sm_count));
   double* scratch = nullptr;
   cudaEvent_t a = nullptr, b = nullptr;
   if (cudaMalloc(&scratch, sizeof(double) * 6 * c.N) == cudaSuccess && cudaEventCreate(&a) == cudaSuccess &&

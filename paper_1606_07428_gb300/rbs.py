@@ -26,7 +26,9 @@ RBS_ESTATE = -7
 
 RBS_PREC_FP64 = 0
 RBS_PREC_MIXED = 1
-RBS_PREC_DF = 2
+RBS_PREC_MIXED_FP16 = 2
+RBS_PREC_DF = 3
+RBS_PREC_MIXED_BF16 = 4
 
 RBS_OP_A = 0
 RBS_OP_HALF_K = 1
@@ -54,6 +56,7 @@ RBS_MAX_SHAPE_DEGREE = 24
 RBS_WARM_ZERO = 0
 RBS_WARM_PREVIOUS = 1
 RBS_WARM_LEARNED = 2
+RBS_WARM_LEARNED_DELTA = 3
 
 RBS_RK_EULER = 1
 RBS_RK_TRAPEZOID = 2

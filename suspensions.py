@@ -222,6 +222,31 @@ def c3_profile() -> Suspension:
     return random_ellipsoids(2000, 8, 16, 0.15, 0.2, seed=2, name="c3_profile_2000_ellipsoids_p8")
 
 
+def shared_shape(n: int, p: int, seed: int, spacing: float = 2.6, jitter: float = 0.2,
+                 axes=(1.0, 0.5, 0.5), name: str = "") -> Suspension:
+    """n identical ellipsoids (semi-axes (1, 0.5, 0.5) by default, the shape of the paper's ellipsoid
+    lattices, Section 4.2) on a cubic lattice of the given spacing, centres perturbed uniformly by up
+    to `jitter` per axis and uniformly random orientations (seeded); n_phi = 2p; F, T ~ N(0, 1).  With
+    the default spacing and jitter the bounding spheres keep a gap of at least 0.2."""
+    rng = np.random.default_rng(seed)
+    m = int(math.ceil(n ** (1.0 / 3.0) - 1e-9))
+    g = np.arange(m) * spacing
+    cen = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)[:n]
+    cen = cen - cen.mean(axis=0) + rng.uniform(-jitter, jitter, size=(n, 3))
+    quats = random_quaternions(rng, n)
+    F = rng.normal(size=(n, 3))
+    T = rng.normal(size=(n, 3))
+    return Suspension(np.tile(np.asarray(axes, np.float64), (n, 1)), np.full(n, p, np.int32),
+                      np.full(n, 2 * p, np.int32), cen, quats, F, T, np.zeros(n, np.int32), name)
+
+
+def s_shared() -> Suspension:
+    """10,000 identical (1, 0.5, 0.5) ellipsoids on a perturbed cubic lattice (spacing 2.6, jitter 0.2,
+    random orientations; seed 5) at p = 16 on a 17 x 32 grid (544 nodes per particle, 5.44M nodes): every
+    particle shares one self block of 1,632 x 1,632, so the block applications form a GEMM."""
+    return shared_shape(10000, 16, seed=5, name="s_shared_10000_ellipsoids_p16")
+
+
 def c5_small() -> Suspension:
     """The sedimenting-ellipsoid workload at 256 particles (same distributions as the 2,048-particle
     one: p = 10 on an 11 x 22 grid, ~10% volume fraction, gap 0.2, F = (0, 0, -1), T = 0; seed 4),
@@ -238,6 +263,7 @@ WORKLOADS = {
     "c2": c2_ellipsoids,
     "c3": c3_ellipsoids,
     "c3_profile": c3_profile,
+    "s_shared": s_shared,
     "c4": c4_batched,
     "c5": c5_sedimenting,
     "c5_small": c5_small,
