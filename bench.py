@@ -89,10 +89,12 @@ def parse_args():
                     help="direct sums over all node pairs; tree: the treecode for the float32 inner applies "
                          "(double-float passes stay direct); tree-df: treecodes for both "
                          "(rbs_options.far_field)")
-    ap.add_argument("--experiment", default=None, choices=[None, "warmstart", "magnetic"],
+    ap.add_argument("--experiment", default=None, choices=[None, "warmstart", "magnetic", "selfgemm"],
                     help="warmstart: learned vs previous-step vs zero initial guesses in RK4 sedimentation; "
                          "magnetic: time steps of paramagnetic spheres in a uniform field (each prints its own "
                          "JSON line; the default run is the benchmark above)")
+    ap.add_argument("--solves", type=int, default=1,
+                    help="selfgemm experiment: mobility solves per arithmetic after the operator timings (0 skips)")
     ap.add_argument("--train-steps", type=int, default=10)
     ap.add_argument("--eval-steps", type=int, default=10)
     ap.add_argument("--epochs", type=int, default=60)
@@ -719,6 +721,78 @@ def run_warmstart_experiment(args):
     print(json.dumps(line), flush=True)
 
 
+def run_selfgemm_experiment(args):
+    """Self blocks on the tensor cores (the workload's particles share one shape, so their block
+    applications form a GEMM): for float32 blocks (CUDA cores) and for float16 and bfloat16 blocks
+    (tcgen05 GEMM), times `--warmup` + `--steps` applications of each arithmetic's K self-block
+    operator (the GEMM kernel alone by its CUDA events: TFLOP/s against the measured bf16 peak), then,
+    unless --solves is 0, one mobility solve per arithmetic at the chosen tolerance with its GMRES
+    iterations, refinements and double-float passes, and its (v, omega) error against the float32-block
+    solve at 1e-10."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1606_07428_gb300 import rbs
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    susp = suspensions.WORKLOADS[args.workload]()
+    tol = args.tol or 1e-8
+    far = {"direct": rbs.RBS_FAR_DIRECT, "tree": rbs.RBS_FAR_TREECODE, "tree-df": rbs.RBS_FAR_TREECODE_DF}[args.far_field]
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        bf16_peak = float(peaks["bf16_tflops"])
+        peak_basis = "of measured (MEASURED_PEAKS.json bf16_tflops, burst; float16 has the same dense rate)"
+    except Exception:
+        bf16_peak, peak_basis = 1900.0, "of fallback 1.9 PFLOP/s"
+    x_dev = torch.tensor(suspensions.random_density(3, susp.total_nodes), device="cuda")
+    y_dev = torch.zeros_like(x_dev)
+    out = {}
+    V_ref = None
+    for name in ("MIXED", "MIXED_FP16", "MIXED_BF16"):
+        prec = getattr(rbs, "RBS_PREC_" + name)
+        with rbs.Context(device=0, precision=prec, timing=1, stream=stream.cuda_stream, far_field=far) as ctx:
+            ctx.set_suspension(susp)
+            setup_ms = rbs.rbs_get_stats(ctx.ctx)["setup_ms"]
+            for k in range(args.warmup):
+                rbs.rbs_apply_operator_device(ctx.ctx, rbs.RBS_OP_K_SELF, prec, x_dev, y_dev)
+            torch.cuda.synchronize()
+            rbs.rbs_reset_stats(ctx.ctx)
+            for k in range(max(1, args.steps)):
+                rbs.rbs_apply_operator_device(ctx.ctx, rbs.RBS_OP_K_SELF, prec, x_dev, y_dev)
+            torch.cuda.synchronize()
+            tab = kernel_table(rbs.rbs_get_stats(ctx.ctx))
+            row = {"setup_ms": setup_ms, "self_apply_kernels": tab}
+            if "self_gemm" in tab:
+                e = tab["self_gemm"]
+                tf = e["units"] / (e["ms"] / 1e3) / 1e12
+                row["self_gemm"] = {"ms_per_launch": e["ms"] / e["launches"], "tflops": tf, "peak_tflops": bf16_peak,
+                                    "frac": tf / bf16_peak, "peak_basis": peak_basis,
+                                    "flops_per_launch": e["units"] / e["launches"]}
+            if "particle_blocks" in tab:
+                e = tab["particle_blocks"]
+                row["block_apply_ms"] = e["ms"] / e["launches"]
+            if args.solves > 0:
+                if V_ref is None and name == "MIXED":
+                    v0, om0, _, _ = rbs.rbs_mobility_solve(ctx.ctx, susp.F, susp.T, 1e-10)
+                    V_ref = np.concatenate([v0, om0], 1)
+                rbs.rbs_reset_stats(ctx.ctx)
+                t0 = time.perf_counter()
+                v, om, _, its = rbs.rbs_mobility_solve(ctx.ctx, susp.F, susp.T, tol)
+                el = time.perf_counter() - t0
+                st = rbs.rbs_get_stats(ctx.ctx)
+                tabs = kernel_table(st)
+                df_passes = sum(tabs[k]["launches"] for k in ("pair_both_df",) if k in tabs)
+                row.update({"solve_s": el, "gmres_iterations": its, "refinements": st["refinements"],
+                            "double_float_passes": df_passes,
+                            "error_vs_float32_blocks_1e-10": float(np.linalg.norm(np.concatenate([v, om], 1) - V_ref) /
+                                                                   np.linalg.norm(V_ref))})
+            out[name.lower()] = row
+    line = {"experiment": "self blocks on the tensor cores (shared shape)", "workload": susp.name,
+            "n_particles": susp.n, "p": int(susp.p[0]), "nodes": susp.total_nodes, "tol": tol,
+            "far_field": args.far_field, "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_magnetic_experiment(args):
     """The magnetorheological set-up of the paper's Fig. 1 (Section 4.1.3): 512 unit spheres at p = 8
     on a perturbed 8 x 8 x 8 cubic lattice (spacing 3, seeded perturbation 0.2) in the field
@@ -778,6 +852,9 @@ def main():
         return
     if args.experiment == "magnetic":
         run_magnetic_experiment(args)
+        return
+    if args.experiment == "selfgemm":
+        run_selfgemm_experiment(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -164,7 +164,9 @@ typedef struct {
 #define RBS_KC_GMRES_GRAPH 10 /* launches of the captured GMRES cycle graph (rbs_options.graphs); units =
                              Arnoldi steps it ran.  Kernels replayed inside it are not counted under
                              their own classes (their launches still count in rbs_stats.launches) */
-#define RBS_KC_COUNT 11
+#define RBS_KC_SELF_GEMM 11 /* tensor-core GEMM of the 16-bit self blocks of a shared shape (the GEMM kernel
+                             alone; units = its flops, 2 n_g (3 N_p)^2 per launch) */
+#define RBS_KC_COUNT 12
 
 typedef struct {
   int iterations;        /* GMRES iterations of the last solve (inner iterations for mixed), the largest

@@ -546,10 +546,14 @@ Status apply_self_gemm(Context& c, int mode, const double* x, double* y, double*
     ep.err = c.d_gemm_err.ptr;
     const int m_tiles = (G.rows + kBM - 1) / kBM, n_tiles = (3 * G.np + kBN - 1) / kBN, k_blocks = G.Kp / kBK;
     const int grid = std::max(1, std::min(m_tiles * n_tiles, c.sm_count));
+    const double flops = 2.0 * G.rows * (3.0 * G.np) * (3.0 * G.np);
+    KernelTimer timer(c, RBS_KC_SELF_GEMM);
     k_self_gemm<<<grid, kGemmThreads, kGemmSmem, c.stream>>>(G.tmZ, pre ? G.tmP : G.tmK, m_tiles, n_tiles, k_blocks,
                                                             idesc, ep);
     RBS_CUDA_TRY(cudaGetLastError());
-    G.flops += 2.0 * G.rows * (3.0 * G.np) * (3.0 * G.np);
+    timer.done(flops);
+    c.stats.launches -= 1;  // counted with the pack kernel above
+    G.flops += flops;
   }
   return Status::Ok();
 }

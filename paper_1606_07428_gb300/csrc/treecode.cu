@@ -35,6 +35,8 @@ namespace {
 
 constexpr int kTreeMaxQ = 11;        // degree <= 10
 constexpr int kTreeMaxTargets = 512; // targets per work item at most
+constexpr int kTreeTile32 = 128;     // sources per warp tile of the float32 treecode sum
+constexpr int kTreeTileDf = 64;      // and of the double-float one
 constexpr int kProxyPid = -3;        // particle id carried by proxy points (never a target's)
 
 // Bounding box of each particle's nodes: lo (3) then hi (3) per particle.
@@ -182,24 +184,37 @@ __global__ void __launch_bounds__(kChargeThreads) k_tree_charges(const int4* __r
   }
 }
 
-// The treecode's pair sum: the packed float32 tile loop of the direct kernel (pairs32.cuh) over
-// source tiles filled from the item's segments.  Coordinates are relative to the item's first target;
-// tiles that may hold nodes of the targets' own particle (the first nmask sources) mask them by
-// particle id.  The block size is chosen at launch so that blockDim.x * NT covers the largest item
-// (a whole particle where it fits), so a particle's targets share every staged tile.
+// The float32 treecode pair sum: the packed tile loop of the direct kernel (pairs32.cuh) over source
+// tiles filled from the item's segments.  Coordinates are relative to the item's first target; tiles
+// that may hold nodes of the targets' own particle (the first nmask sources) mask them by particle id.
+// The block size is chosen at launch so that blockDim.x * NT covers the largest item (a whole particle
+// where it fits).  Each warp stages its own tiles of 128 sources and never waits for the other warps
+// of its block: a block of an odd warp count (five warps for a 144-node particle) spreads unevenly over
+// the SM's four schedulers, so block-wide tiles left the warps of the lighter schedulers waiting at
+// every tile barrier.  Registers are capped (64 at one target per thread: six 160-thread blocks per SM).
 template <int KIND, int NT>
-__global__ void __launch_bounds__(kTreeMaxTargets / NT)
+__global__ void __maxnreg__(NT == 1 ? 64 : (NT == 2 ? 128 : 168))
     k_tree32x2(int nitems, const TreeItem* __restrict__ items, const int2* __restrict__ segs,
                const float4* __restrict__ xhi, const float4* __restrict__ xlo, const float4* __restrict__ nrm32,
                const float4* __restrict__ shi, const float4* __restrict__ slo, const float4* __restrict__ sq,
                double* __restrict__ y) {
-  constexpr int TS = 1024;  // sources per tile: fewer block barriers per pair
+  constexpr int TW = kTreeTile32, SL = TW / 32;
   const int NTH = blockDim.x;
-  __shared__ __align__(16) float ssx[TS], ssy[TS], ssz[TS], srx[TS], sry[TS], srz[TS];
-  __shared__ __align__(16) int spid[TS];
-  __shared__ int sidx[TS];  // source of each slot, written and read by the slot's own thread
+  const int lane = threadIdx.x & 31;
+  extern __shared__ __align__(16) float tree_smem32[];
+  float* const ssx = tree_smem32 + (threadIdx.x >> 5) * (7 * TW);
+  float* const ssy = ssx + TW;
+  float* const ssz = ssx + 2 * TW;
+  float* const srx = ssx + 3 * TW;
+  float* const sry = ssx + 4 * TW;
+  float* const srz = ssx + 5 * TW;
+  int* const spid = reinterpret_cast<int*>(ssx + 6 * TW);
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const TreeItem w = items[it];
+    // target slots of this warp that hold a target: u < nu for lane 0 (the warp's last slot may be
+    // partly empty; later slots are skipped, and a warp without targets skips the item)
+    const int nu = min(NT, max(0, (w.t1 - w.t0 - (int)(threadIdx.x & ~31u) + NTH - 1) / NTH));
+    if (nu == 0) continue;
     const float4 oh = xhi[w.t0], ol = xlo[w.t0];
     float2 xt[NT][3], nt[NT][3];
     int pt[NT];
@@ -230,22 +245,22 @@ __global__ void __launch_bounds__(kTreeMaxTargets / NT)
     float sa[NT][3], ea[NT][3];
 #pragma unroll
     for (int u = 0; u < NT; ++u) sa[u][0] = sa[u][1] = sa[u][2] = ea[u][0] = ea[u][1] = ea[u][2] = 0.0f;
-    // target slots of this warp that hold a target: u < nu for lane 0 (the warp's last slot may be
-    // partly empty; later slots are skipped, so a ragged particle costs whole warps only where it fills them)
-    const int nu = min(NT, max(0, (w.t1 - w.t0 - (int)(threadIdx.x & ~31u) + NTH - 1) / NTH));
     int seg = w.s0, off = 0, done = 0;
     while (seg < w.s1) {
-      __syncthreads();
-      // fill up to TS slots from consecutive segments: first the source index of each of this
-      // thread's slots (l = threadIdx.x mod NTH) from the same walk in every thread, then all of
-      // its loads at once, so a tile costs one memory latency rather than one per segment
+      // the source of each of this lane's slots (lane + 32 k) from a walk over consecutive segments
+      // that every lane of the warp takes in step, then all of its loads at once
+      int sidx[SL];
+#pragma unroll
+      for (int k = 0; k < SL; ++k) sidx[k] = 0;
       int filled = 0;
-      while (filled < TS && seg < w.s1) {
+      while (filled < TW && seg < w.s1) {
         const int2 sg = segs[seg];
-        const int take = min(sg.y - off, TS - filled);
-        int l = threadIdx.x;
-        if (l < filled) l += ((filled - l + NTH - 1) / NTH) * NTH;  // first own slot >= filled
-        for (; l < filled + take; l += NTH) sidx[l] = sg.x + off + (l - filled);
+        const int take = min(sg.y - off, TW - filled);
+#pragma unroll
+        for (int k = 0; k < SL; ++k) {
+          const int l = lane + 32 * k;
+          if (l >= filled && l < filled + take) sidx[k] = sg.x + off + (l - filled);
+        }
         filled += take;
         off += take;
         if (off >= sg.y) {
@@ -253,25 +268,28 @@ __global__ void __launch_bounds__(kTreeMaxTargets / NT)
           off = 0;
         }
       }
-#pragma unroll 4
-      for (int l = threadIdx.x; l < filled; l += NTH) {
-        const int s = sidx[l];
-        const float4 ph = shi[s], pl = slo[s], q = sq[s];
-        ssx[l] = (oh.x - ph.x) + (ol.x - pl.x);
-        ssy[l] = (oh.y - ph.y) + (ol.y - pl.y);
-        ssz[l] = (oh.z - ph.z) + (ol.z - pl.z);
-        srx[l] = q.x;
-        sry[l] = q.y;
-        srz[l] = q.z;
-        spid[l] = __float_as_int(ph.w);
-      }
       const int cnt4 = (filled + 3) & ~3;
-      for (int l = filled + threadIdx.x; l < cnt4; l += NTH) {
-        ssx[l] = ssy[l] = ssz[l] = 1.0e4f;
-        srx[l] = sry[l] = srz[l] = 0.0f;
-        spid[l] = -2;
+      __syncwarp();  // the warp's reads of the previous tile are done
+#pragma unroll 2
+      for (int k = 0; k < SL; ++k) {
+        const int l = lane + 32 * k;
+        if (l < filled) {
+          const int s = sidx[k];
+          const float4 ph = shi[s], pl = slo[s], q = sq[s];
+          ssx[l] = (oh.x - ph.x) + (ol.x - pl.x);
+          ssy[l] = (oh.y - ph.y) + (ol.y - pl.y);
+          ssz[l] = (oh.z - ph.z) + (ol.z - pl.z);
+          srx[l] = q.x;
+          sry[l] = q.y;
+          srz[l] = q.z;
+          spid[l] = __float_as_int(ph.w);
+        } else if (l < cnt4) {
+          ssx[l] = ssy[l] = ssz[l] = 1.0e4f;
+          srx[l] = sry[l] = srz[l] = 0.0f;
+          spid[l] = -2;
+        }
       }
-      __syncthreads();
+      __syncwarp();
       float2 p[NT][3];
 #pragma unroll
       for (int u = 0; u < NT; ++u) p[u][0] = p[u][1] = p[u][2] = f2(0.0f, 0.0f);
@@ -432,10 +450,14 @@ __global__ void k_tree_q64_split(long long count, const double* __restrict__ q64
 // The double-float treecode pair sum: the packed double-float pair of the direct kernel (pairsdf.cuh)
 // over source tiles filled from the item's segments (as k_tree32x2).  KIND 0 traction into y, 1
 // Stokeslet into y, 2 traction into y and Stokeslet into y2.
-// Registers are capped (96 for one target per thread) so that four 160-thread blocks, the size a
-// p = 8 particle's targets take, are resident per SM: the double-float pair is a long dependent chain,
-// and with the uncapped 126 registers only three blocks (or, at two targets per thread, 238 registers
-// and two 96-thread blocks: under five warps per SM) hid its latency.
+// The double-float treecode pair sum: the packed double-float pair of the direct kernel (pairsdf.cuh)
+// over source tiles filled from the item's segments (as k_tree32x2: each warp stages its own tiles, of
+// 64 sources here, and never waits for the rest of its block).  KIND 0 traction into y, 1 Stokeslet
+// into y, 2 traction into y and Stokeslet into y2.  Registers are capped (96 for one target per
+// thread) so that four 160-thread blocks, the size a p = 8 particle's targets take, are resident per
+// SM: the double-float pair is a long dependent chain, and with the uncapped 126 registers only three
+// blocks (or, at two targets per thread, 238 registers and two 96-thread blocks: under five warps per
+// SM) hid its latency.
 template <int KIND, int NT>
 __global__ void __maxnreg__(NT == 1 ? 96 : 168)
     k_tree_df2(int nitems, const TreeItem* __restrict__ items, const int2* __restrict__ segs,
@@ -443,14 +465,26 @@ __global__ void __maxnreg__(NT == 1 ? 96 : 168)
                const float4* __restrict__ nh, const float4* __restrict__ nl, const float4* __restrict__ shi,
                const float4* __restrict__ smid, const float4* __restrict__ slo, const float4* __restrict__ sqh,
                const float4* __restrict__ sql, double* __restrict__ y, double* __restrict__ y2) {
-  constexpr int TS = 256;
+  constexpr int TW = kTreeTileDf, SL = TW / 32;
   const int NTH = blockDim.x;
-  __shared__ __align__(16) float sa[12][TS];
-  __shared__ __align__(16) int spid[TS];
-  __shared__ int sidx[TS];
+  const int lane = threadIdx.x & 31;
+  extern __shared__ __align__(16) float tree_smem_df[];
+  // per warp: the tile (12 float rows and the particle ids), then the item's origin (three float4)
+  float(*sa)[TW] = reinterpret_cast<float(*)[TW]>(tree_smem_df + (threadIdx.x >> 5) * (13 * TW + 12));
+  int* const spid = reinterpret_cast<int*>(&sa[12][0]);
+  float4* const org = reinterpret_cast<float4*>(&sa[13][0]);
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const TreeItem w = items[it];
-    const float4 oh = x3h[w.t0], om = x3m[w.t0], ol = x3l[w.t0];
+    // target slots of this warp that hold a target (as k_tree32x2); a warp without targets skips
+    const int nu = min(NT, max(0, (w.t1 - w.t0 - (int)(threadIdx.x & ~31u) + NTH - 1) / NTH));
+    if (nu == 0) continue;
+    __syncwarp();  // the warp's reads of the previous item's origin are done
+    if (lane == 0) {
+      org[0] = x3h[w.t0];
+      org[1] = x3m[w.t0];
+      org[2] = x3l[w.t0];
+    }
+    __syncwarp();
     df2 xt[NT][3], nt[NT][3];
     int pt[NT];
     bool valid[NT];
@@ -458,6 +492,7 @@ __global__ void __maxnreg__(NT == 1 ? 96 : 168)
     for (int u = 0; u < NT; ++u) {
       const int t = w.t0 + threadIdx.x + NTH * u;
       valid[u] = t < w.t1;
+      const float4 oh = org[0], om = org[1], ol = org[2];
       float4 ah = oh, am = om, al = ol, bh = make_float4(0, 0, 0, 0), bl = make_float4(0, 0, 0, 0);
       pt[u] = -1;
       if (valid[u]) {
@@ -477,8 +512,6 @@ __global__ void __maxnreg__(NT == 1 ? 96 : 168)
       nt[u][1] = {dup2(bh.y), dup2(bl.y)};
       nt[u][2] = {dup2(bh.z), dup2(bl.z)};
     }
-    // target slots of this warp that hold a target (as k_tree32x2)
-    const int nu = min(NT, max(0, (w.t1 - w.t0 - (int)(threadIdx.x & ~31u) + NTH - 1) / NTH));
     dflt a[NT][3], a2[NT][3];
 #pragma unroll
     for (int u = 0; u < NT; ++u)
@@ -486,14 +519,18 @@ __global__ void __maxnreg__(NT == 1 ? 96 : 168)
       for (int c = 0; c < 3; ++c) a[u][c] = a2[u][c] = dflt{0.0f, 0.0f};
     int seg = w.s0, off = 0, done = 0;
     while (seg < w.s1) {
-      __syncthreads();
+      int sidx[SL];
+#pragma unroll
+      for (int k = 0; k < SL; ++k) sidx[k] = 0;
       int filled = 0;
-      while (filled < TS && seg < w.s1) {
+      while (filled < TW && seg < w.s1) {
         const int2 sg = segs[seg];
-        const int take = min(sg.y - off, TS - filled);
-        int l = threadIdx.x;
-        if (l < filled) l += ((filled - l + NTH - 1) / NTH) * NTH;  // first own slot >= filled
-        for (; l < filled + take; l += NTH) sidx[l] = sg.x + off + (l - filled);
+        const int take = min(sg.y - off, TW - filled);
+#pragma unroll
+        for (int k = 0; k < SL; ++k) {
+          const int l = lane + 32 * k;
+          if (l >= filled && l < filled + take) sidx[k] = sg.x + off + (l - filled);
+        }
         filled += take;
         off += take;
         if (off >= sg.y) {
@@ -501,59 +538,61 @@ __global__ void __maxnreg__(NT == 1 ? 96 : 168)
           off = 0;
         }
       }
-#pragma unroll 2
-      for (int l = threadIdx.x; l < filled; l += NTH) {
-        const int s = sidx[l];
-        const float4 ph = shi[s], pm = smid[s], pl = slo[s], qh = sqh[s], ql = sql[s];
-        const dflt px = df_diff3(ph.x, pm.x, pl.x, oh.x, om.x, ol.x);
-        const dflt py = df_diff3(ph.y, pm.y, pl.y, oh.y, om.y, ol.y);
-        const dflt pz = df_diff3(ph.z, pm.z, pl.z, oh.z, om.z, ol.z);
-        sa[0][l] = px.h;
-        sa[1][l] = px.l;
-        sa[2][l] = py.h;
-        sa[3][l] = py.l;
-        sa[4][l] = pz.h;
-        sa[5][l] = pz.l;
-        sa[6][l] = qh.x;
-        sa[7][l] = ql.x;
-        sa[8][l] = qh.y;
-        sa[9][l] = ql.y;
-        sa[10][l] = qh.z;
-        sa[11][l] = ql.z;
-        spid[l] = __float_as_int(ph.w);
-      }
       const int cnt2 = (filled + 1) & ~1;
-      for (int l = filled + threadIdx.x; l < cnt2; l += NTH) {
-        sa[0][l] = sa[2][l] = sa[4][l] = 1.0e4f;
-        sa[1][l] = sa[3][l] = sa[5][l] = 0.0f;
-        for (int q = 6; q < 12; ++q) sa[q][l] = 0.0f;
-        spid[l] = -2;
+      __syncwarp();  // the warp's reads of the previous tile are done
+#pragma unroll 1
+      for (int k = 0; k < SL; ++k) {
+        const int l = lane + 32 * k;
+        if (l < filled) {
+          const int s = sidx[k];
+          const float4 ph = shi[s], pm = smid[s], pl = slo[s], qh = sqh[s], ql = sql[s];
+          const float4 oh = org[0], om = org[1], ol = org[2];
+          const dflt px = df_diff3(ph.x, pm.x, pl.x, oh.x, om.x, ol.x);
+          const dflt py = df_diff3(ph.y, pm.y, pl.y, oh.y, om.y, ol.y);
+          const dflt pz = df_diff3(ph.z, pm.z, pl.z, oh.z, om.z, ol.z);
+          sa[0][l] = px.h;
+          sa[1][l] = px.l;
+          sa[2][l] = py.h;
+          sa[3][l] = py.l;
+          sa[4][l] = pz.h;
+          sa[5][l] = pz.l;
+          sa[6][l] = qh.x;
+          sa[7][l] = ql.x;
+          sa[8][l] = qh.y;
+          sa[9][l] = ql.y;
+          sa[10][l] = qh.z;
+          sa[11][l] = ql.z;
+          spid[l] = __float_as_int(ph.w);
+        } else if (l < cnt2) {
+          sa[0][l] = sa[2][l] = sa[4][l] = 1.0e4f;
+          sa[1][l] = sa[3][l] = sa[5][l] = 0.0f;
+          for (int q = 6; q < 12; ++q) sa[q][l] = 0.0f;
+          spid[l] = -2;
+        }
       }
-      __syncthreads();
+      __syncwarp();
       const bool masked = done < w.nmask;
       df2 acc[NT][3], acc2[NT][3];
 #pragma unroll
       for (int u = 0; u < NT; ++u)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[u][c] = acc2[u][c] = df2{dup2(0.0f), dup2(0.0f)};
-      if (nu > 0) {
-        for (int l = 0; l < cnt2; l += 2) {
-          df2 ys[3], den[3];
+      for (int l = 0; l < cnt2; l += 2) {
+        df2 ys[3], den[3];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            ys[c] = {*reinterpret_cast<const float2*>(&sa[2 * c][l]), *reinterpret_cast<const float2*>(&sa[2 * c + 1][l])};
-            den[c] = {*reinterpret_cast<const float2*>(&sa[6 + 2 * c][l]),
-                      *reinterpret_cast<const float2*>(&sa[7 + 2 * c][l])};
-          }
-          const int2 pp = *reinterpret_cast<const int2*>(&spid[l]);
+        for (int c = 0; c < 3; ++c) {
+          ys[c] = {*reinterpret_cast<const float2*>(&sa[2 * c][l]), *reinterpret_cast<const float2*>(&sa[2 * c + 1][l])};
+          den[c] = {*reinterpret_cast<const float2*>(&sa[6 + 2 * c][l]),
+                    *reinterpret_cast<const float2*>(&sa[7 + 2 * c][l])};
+        }
+        const int2 pp = *reinterpret_cast<const int2*>(&spid[l]);
 #pragma unroll
-          for (int u = 0; u < NT; ++u) {
-            if (u < nu) {
-              if (masked)
-                pair2_df<KIND, true>(ys, den, pp, xt[u], nt[u], pt[u], acc[u], acc2[u]);
-              else
-                pair2_df<KIND, false>(ys, den, pp, xt[u], nt[u], pt[u], acc[u], acc2[u]);
-            }
+        for (int u = 0; u < NT; ++u) {
+          if (u < nu) {
+            if (masked)
+              pair2_df<KIND, true>(ys, den, pp, xt[u], nt[u], pt[u], acc[u], acc2[u]);
+            else
+              pair2_df<KIND, false>(ys, den, pp, xt[u], nt[u], pt[u], acc[u], acc2[u]);
           }
         }
       }
@@ -1035,27 +1074,29 @@ Status build_far_field(Context& c) {
 static Status launch_tree(Context& c, int kind, int nt, int items, double* y) {
   TreeState& T = c.tree;
   const int threads = ((T.tmax + nt - 1) / nt + 31) / 32 * 32;
+  const size_t smem = (size_t)(threads / 32) * 7 * kTreeTile32 * sizeof(float);  // one tile per warp
 #define RBS_TREE_ARGS items, T.d_items.ptr, T.d_segs.ptr, c.d_xhi.ptr, c.d_xlo.ptr, c.d_nrm32.ptr, T.d_hi.ptr, T.d_lo.ptr, \
                       T.d_q.ptr, y
   auto grid = [&](const void* k) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     return std::max(1, std::min(items, per_sm * std::max(1, c.sm_count)));
   };
   if (kind == 0) {
     if (nt == 1)
-      k_tree32x2<0, 1><<<grid((const void*)k_tree32x2<0, 1>), threads, 0, c.stream>>>(RBS_TREE_ARGS);
+      k_tree32x2<0, 1><<<grid((const void*)k_tree32x2<0, 1>), threads, smem, c.stream>>>(RBS_TREE_ARGS);
     else if (nt == 4)
-      k_tree32x2<0, 4><<<grid((const void*)k_tree32x2<0, 4>), threads, 0, c.stream>>>(RBS_TREE_ARGS);
+      k_tree32x2<0, 4><<<grid((const void*)k_tree32x2<0, 4>), threads, smem, c.stream>>>(RBS_TREE_ARGS);
     else
-      k_tree32x2<0, 2><<<grid((const void*)k_tree32x2<0, 2>), threads, 0, c.stream>>>(RBS_TREE_ARGS);
+      k_tree32x2<0, 2><<<grid((const void*)k_tree32x2<0, 2>), threads, smem, c.stream>>>(RBS_TREE_ARGS);
   } else {
     if (nt == 1)
-      k_tree32x2<1, 1><<<grid((const void*)k_tree32x2<1, 1>), threads, 0, c.stream>>>(RBS_TREE_ARGS);
+      k_tree32x2<1, 1><<<grid((const void*)k_tree32x2<1, 1>), threads, smem, c.stream>>>(RBS_TREE_ARGS);
     else if (nt == 4)
-      k_tree32x2<1, 4><<<grid((const void*)k_tree32x2<1, 4>), threads, 0, c.stream>>>(RBS_TREE_ARGS);
+      k_tree32x2<1, 4><<<grid((const void*)k_tree32x2<1, 4>), threads, smem, c.stream>>>(RBS_TREE_ARGS);
     else
-      k_tree32x2<1, 2><<<grid((const void*)k_tree32x2<1, 2>), threads, 0, c.stream>>>(RBS_TREE_ARGS);
+      k_tree32x2<1, 2><<<grid((const void*)k_tree32x2<1, 2>), threads, smem, c.stream>>>(RBS_TREE_ARGS);
   }
 #undef RBS_TREE_ARGS
   RBS_CUDA_TRY(cudaGetLastError());
@@ -1132,28 +1173,30 @@ Status apply_tree(Context& c, int kind, const double* x, double* y, int nt) {
 static Status launch_tree_df(Context& c, int kind, int nt, int items, double* y, double* y2) {
   TreeState& T = c.tree_df;
   const int threads = ((T.tmax + nt - 1) / nt + 31) / 32 * 32;
+  const size_t smem = (size_t)(threads / 32) * (13 * kTreeTileDf + 12) * sizeof(float);  // one tile per warp
 #define RBS_TREE_DF_ARGS items, T.d_items.ptr, T.d_segs.ptr, c.d_x3h.ptr, c.d_x3m.ptr, c.d_x3l.ptr, c.d_nrmh.ptr, \
                          c.d_nrml.ptr, T.d_hi.ptr, T.d_x3m.ptr, T.d_lo.ptr, T.d_q.ptr, T.d_wl.ptr, y, y2
   auto grid = [&](const void* k) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
     return std::max(1, std::min(items, per_sm * std::max(1, c.sm_count)));
   };
   if (kind == 0) {
     if (nt == 1)
-      k_tree_df2<0, 1><<<grid((const void*)k_tree_df2<0, 1>), threads, 0, c.stream>>>(RBS_TREE_DF_ARGS);
+      k_tree_df2<0, 1><<<grid((const void*)k_tree_df2<0, 1>), threads, smem, c.stream>>>(RBS_TREE_DF_ARGS);
     else
-      k_tree_df2<0, 2><<<grid((const void*)k_tree_df2<0, 2>), threads, 0, c.stream>>>(RBS_TREE_DF_ARGS);
+      k_tree_df2<0, 2><<<grid((const void*)k_tree_df2<0, 2>), threads, smem, c.stream>>>(RBS_TREE_DF_ARGS);
   } else if (kind == 1) {
     if (nt == 1)
-      k_tree_df2<1, 1><<<grid((const void*)k_tree_df2<1, 1>), threads, 0, c.stream>>>(RBS_TREE_DF_ARGS);
+      k_tree_df2<1, 1><<<grid((const void*)k_tree_df2<1, 1>), threads, smem, c.stream>>>(RBS_TREE_DF_ARGS);
     else
-      k_tree_df2<1, 2><<<grid((const void*)k_tree_df2<1, 2>), threads, 0, c.stream>>>(RBS_TREE_DF_ARGS);
+      k_tree_df2<1, 2><<<grid((const void*)k_tree_df2<1, 2>), threads, smem, c.stream>>>(RBS_TREE_DF_ARGS);
   } else {
     if (nt == 1)
-      k_tree_df2<2, 1><<<grid((const void*)k_tree_df2<2, 1>), threads, 0, c.stream>>>(RBS_TREE_DF_ARGS);
+      k_tree_df2<2, 1><<<grid((const void*)k_tree_df2<2, 1>), threads, smem, c.stream>>>(RBS_TREE_DF_ARGS);
     else
-      k_tree_df2<2, 2><<<grid((const void*)k_tree_df2<2, 2>), threads, 0, c.stream>>>(RBS_TREE_DF_ARGS);
+      k_tree_df2<2, 2><<<grid((const void*)k_tree_df2<2, 2>), threads, smem, c.stream>>>(RBS_TREE_DF_ARGS);
   }
 #undef RBS_TREE_DF_ARGS
   RBS_CUDA_TRY(cudaGetLastError());
