@@ -62,8 +62,9 @@ NCU_TRAFFIC = {"pair_traction_df": (6.404864e6, 57600), "pair_traction_f32": (4.
 # efficiency of a double-float kernel is measured against this count, its roofline against the flops
 DF_INSTR_PER_PAIR = {"traction": 172.0, "stokeslet": 172.0, "both": 248.0}
 # DRAM bytes per launch of the fused double-float treecode kernel from an ncu capture on the
-# 2,000-ellipsoid profiling case (288,000 nodes), or None before a capture of the current kernel
-TREE_DF_TRAFFIC = None
+# 2,000-ellipsoid profiling case (288,000 nodes; 91.07 MB read + 10.95 MB written, theta 0.4), scaled by
+# node count like the direct kernels' figures
+TREE_DF_TRAFFIC = (1.02018816e8, 288000)
 
 
 def parse_args():
@@ -89,12 +90,18 @@ def parse_args():
                     help="direct sums over all node pairs; tree: the treecode for the float32 inner applies "
                          "(double-float passes stay direct); tree-df: treecodes for both "
                          "(rbs_options.far_field)")
+    ap.add_argument("--tree-df-theta", type=float, default=0.45,
+                    help="opening angle of the double-float passes' treecode (rbs_options.tree_df_theta) with "
+                         "--far-field tree-df; at degree 12, 0.45 measured 1.6e-10 relative error on the far sum "
+                         "of the 10,000-ellipsoid geometry (0.4: 3.6e-11) with 17% fewer pairs")
     ap.add_argument("--experiment", default=None, choices=[None, "warmstart", "magnetic", "selfgemm"],
                     help="warmstart: learned vs previous-step vs zero initial guesses in RK4 sedimentation; "
                          "magnetic: time steps of paramagnetic spheres in a uniform field (each prints its own "
                          "JSON line; the default run is the benchmark above)")
     ap.add_argument("--solves", type=int, default=1,
                     help="selfgemm experiment: mobility solves per arithmetic after the operator timings (0 skips)")
+    ap.add_argument("--warm-modes", default="ZERO,PREVIOUS,LEARNED,LEARNED_DELTA",
+                    help="warmstart experiment: initial guesses compared (RBS_WARM_* names)")
     ap.add_argument("--train-steps", type=int, default=10)
     ap.add_argument("--eval-steps", type=int, default=10)
     ap.add_argument("--epochs", type=int, default=60)
@@ -378,7 +385,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     far = {"direct": rbs.RBS_FAR_DIRECT, "tree": rbs.RBS_FAR_TREECODE, "tree-df": rbs.RBS_FAR_TREECODE_DF}[args.far_field]
     ctx = rbs.Context(device=local, precision=rbs.RBS_PREC_MIXED, timing=1, stream=stream.cuda_stream,
-                      pair_variant=args.pair_variant, far_field=far)
+                      pair_variant=args.pair_variant, far_field=far, tree_df_theta=args.tree_df_theta)
     ctx.set_suspension(susp)
     st0 = rbs.rbs_get_stats(ctx.ctx)
     setup_ms = st0["setup_ms"]
@@ -390,7 +397,7 @@ def run_ours(args):
                      "direct_pairs_per_apply": st0["far_pairs"],
                      "reduction": st0["far_pairs"] / max(1, st0["tree_pairs"])}
         if far == rbs.RBS_FAR_TREECODE_DF:
-            tree_info["double_float"] = {"theta": opts.tree_df_theta, "degree": opts.tree_df_degree,
+            tree_info["double_float"] = {"theta": args.tree_df_theta, "degree": opts.tree_df_degree,
                                          "cells": st0["tree_df_cells"], "pairs_per_apply": st0["tree_df_pairs"],
                                          "proxy_pairs_per_apply": st0["tree_df_proxy_pairs"],
                                          "reduction": st0["far_pairs"] / max(1, st0["tree_df_pairs"])}
@@ -691,11 +698,11 @@ def run_warmstart_experiment(args):
         cen, quat = rbs.rbs_get_state(ctx.ctx, susp.n)
     out = {}
     finals = {}
-    for mode in ("ZERO", "PREVIOUS", "LEARNED"):
+    for mode in args.warm_modes.split(","):
         with rbs.Context(device=0, precision=prec, warm_start=getattr(rbs, "RBS_WARM_" + mode),
                          stream=stream.cuda_stream, far_field=far) as ctx:
             ctx.set_geometry(susp.semi_axes, susp.p, susp.nphi, cen, quat)
-            if mode == "LEARNED":
+            if mode.startswith("LEARNED"):
                 rbs.rbs_warmstart_weights(ctx.ctx, params, scale=scale)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -710,14 +717,15 @@ def run_warmstart_experiment(args):
             finals[mode] = c_end
             out[mode.lower()] = {"gmres_iterations_per_solve": its / solves, "solves_per_s": solves / (ms / 1e3),
                                  "ms": ms}
-    drift = {m: float(np.abs(finals[m] - finals["ZERO"]).max()) for m in finals}
+    base = "ZERO" if "ZERO" in finals else "PREVIOUS"
+    drift = {m: float(np.abs(finals[m] - finals[base]).max()) for m in finals}
     line = {"experiment": "learned warm start in RK4 sedimentation", "workload": susp.name, "n_particles": susp.n,
             "nodes": susp.total_nodes, "precision": "mixed", "far_field": args.far_field, "tol": tol, "dt": args.dt,
             "train_steps": args.train_steps, "train_samples": 4 * args.train_steps * susp.n,
             "train_iterations_per_solve": its_train / (4 * args.train_steps),
             "train_solve_seconds": t_train_solves, "epochs": args.epochs, "train_seconds": t_train,
             "loss_first_epoch": loss_first, "loss_last_epoch": loss, "eval_steps": args.eval_steps,
-            "results": out, "max_centre_difference_vs_zero_start": drift}
+            "results": out, f"max_centre_difference_vs_{base.lower()}_start": drift}
     print(json.dumps(line), flush=True)
 
 

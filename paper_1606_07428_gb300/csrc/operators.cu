@@ -162,12 +162,19 @@ __global__ void __launch_bounds__(256) k_blocks(int mode, const int4* __restrict
 // three rows once for all eight reflections (one fused multiply-add per reflection and entry, in
 // the block type), and lane g writes node g(t) when no smaller reflection reaches it.  1/2 x, L x and
 // the preconditioner's copy of x are added as in k_blocks.
-__device__ __forceinline__ int reflect_node_dev(int g, int t, int p, int nphi) {
-  int j = t / nphi, k = t - (t / nphi) * nphi;
+// Node (j, k) under the reflection g, without divisions (k in [0, n_phi)).
+__device__ __forceinline__ int reflect_jk(int g, int j, int k, int p, int nphi) {
   if (g & 4) j = p - j;
   if (g & 2) k = k == 0 ? 0 : nphi - k;
-  if (g & 1) k = (nphi / 2 - k + nphi) % nphi;
+  if (g & 1) {
+    k = nphi / 2 - k;
+    if (k < 0) k += nphi;
+  }
   return j * nphi + k;
+}
+__device__ __forceinline__ int reflect_node_dev(int g, int t, int p, int nphi) {
+  const int j = t / nphi;
+  return reflect_jk(g, j, t - j * nphi, p, nphi);
 }
 
 
@@ -187,8 +194,42 @@ __device__ __forceinline__ float load_entry(const BF16Bits* p) {
   return __uint_as_float((unsigned)__ldg(reinterpret_cast<const unsigned short*>(p)) << 16);
 }
 
+// Two consecutive entries (an even column of a row: 8-, 16- or 4-byte aligned).
+__device__ __forceinline__ void load_pair(const double* p, double& a, double& b) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void load_pair(const float* p, float& a, float& b) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void load_pair(const F16Bits* p, float& a, float& b) {
+  const unsigned u = __ldg(reinterpret_cast<const unsigned*>(p));
+  a = __half2float(__ushort_as_half((unsigned short)(u & 0xffffu)));
+  b = __half2float(__ushort_as_half((unsigned short)(u >> 16)));
+}
+__device__ __forceinline__ void load_pair(const BF16Bits* p, float& a, float& b) {
+  const unsigned u = __ldg(reinterpret_cast<const unsigned*>(p));
+  a = __uint_as_float(u << 16);
+  b = __uint_as_float(u & 0xffff0000u);
+}
+
+// Two consecutive staged inputs (an even column) in one shared-memory access.
+__device__ __forceinline__ void load_pair_shared(const float* p, float& a, float& b) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void load_pair_shared(const double* p, double& a, double& b) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  a = v.x;
+  b = v.y;
+}
+
 // TS: storage type of the block entries; TB: the arithmetic of the products and sums (float64 for
-// float64 blocks, float32 otherwise).
+// float64 blocks, float32 otherwise).  Rows are read two columns per lane (3 N_p is even).
 template <typename TS, typename TB>
 __global__ void __launch_bounds__(256) k_blocks_sym(int mode, const int* __restrict__ sym_list,
                                                     const long long* __restrict__ offset, const int* __restrict__ pvec,
@@ -219,9 +260,10 @@ __global__ void __launch_bounds__(256) k_blocks_sym(int mode, const int* __restr
       const double z0 = R0 * a + R3 * b + R6 * cc;
       const double z1 = R1 * a + R4 * b + R7 * cc;
       const double z2 = R2 * a + R5 * b + R8 * cc;
+      const int js = sp / nphi, ks = sp - js * nphi;
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
-        const int sn = reflect_node_dev(g, sp, p, nphi);  // g is an involution: z_{g(sn)} = z_{sp}
+        const int sn = reflect_jk(g, js, ks, p, nphi);  // g is an involution: z_{g(sn)} = z_{sp}
         TB* zz = zg + g * dim + 3 * sn;
         zz[0] = (TB)((g & 1) ? -z0 : z0);
         zz[1] = (TB)((g & 2) ? -z1 : z1);
@@ -291,28 +333,33 @@ __global__ void __launch_bounds__(256) k_blocks_sym(int mode, const int* __restr
 #pragma unroll
     for (int g = 0; g < 8; ++g) y[g][0] = y[g][1] = y[g][2] = (TB)0;
     const TS* row = A + (long long)(3 * r) * dim;
-    for (int col = lane; col < dim; col += 32) {
-      const TB a0 = load_entry(row + col), a1 = load_entry(row + dim + col), a2 = load_entry(row + 2 * dim + col);
+#pragma unroll 2
+    for (int col = 2 * lane; col < dim; col += 64) {
+      TB a0, a0b, a1, a1b, a2, a2b;
+      load_pair(row + col, a0, a0b);
+      load_pair(row + dim + col, a1, a1b);
+      load_pair(row + 2 * dim + col, a2, a2b);
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
-        const TB zv = zg[g * dim + col];
-        y[g][0] = fma_t(a0, zv, y[g][0]);
-        y[g][1] = fma_t(a1, zv, y[g][1]);
-        y[g][2] = fma_t(a2, zv, y[g][2]);
+        TB zv, zw;
+        load_pair_shared(zg + g * dim + col, zv, zw);
+        y[g][0] = fma_t(a0b, zw, fma_t(a0, zv, y[g][0]));
+        y[g][1] = fma_t(a1b, zw, fma_t(a1, zv, y[g][1]));
+        y[g][2] = fma_t(a2b, zw, fma_t(a2, zv, y[g][2]));
       }
     }
 #pragma unroll
     for (int g = 0; g < 8; ++g)
 #pragma unroll
       for (int q = 0; q < 3; ++q) y[g][q] = warp_sum_t(y[g][q]);
-    const int t0 = (r / nk) * nphi + r % nk;
+    const int j0 = r / nk, k0 = r - (r / nk) * nk;
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
       if (lane != g) continue;
-      const int t = reflect_node_dev(g, t0, p, nphi);
+      const int t = reflect_jk(g, j0, k0, p, nphi);
       bool first = true;
       for (int h = 0; h < g; ++h)
-        if (reflect_node_dev(h, t0, p, nphi) == t) first = false;
+        if (reflect_jk(h, j0, k0, p, nphi) == t) first = false;
       if (!first) continue;
       const double b0 = (double)y[g][0], b1 = (double)y[g][1], b2 = (double)y[g][2];
       finish(t, (g & 1) ? -b0 : b0, (g & 2) ? -b1 : b1, (g & 4) ? -b2 : b2);

@@ -35,7 +35,11 @@ constexpr int kAccCols = 256, kTmemCols = 2 * kAccCols;
 constexpr uint32_t kBytesA = kBM * kBK * 2, kBytesB = kBN * kBK * 2;
 constexpr long long kSpin = 1LL << 24;
 constexpr int kGemmThreads = 192;
-constexpr size_t kGemmSmem = 1024 + (size_t)kStages * (kBytesA + kBytesB) + 256;
+// epilogue staging per epilogue warp: 32 rows x 24 float64 (row stride 25) and the rows' offsets,
+// L moments and centres
+constexpr int kEpiCols = 24, kEpiStride = 25;
+constexpr size_t kEpiWarpBytes = 32 * kEpiStride * 4 + 32 * 8 + 32 * 6 * 8 + 32 * 3 * 8;
+constexpr size_t kGemmSmem = 1024 + (size_t)kStages * (kBytesA + kBytesB) + 4 * kEpiWarpBytes + 256;
 
 struct GemmEpi {
   int mode;              // kModePrecond, kModeKOnlySelf, kModeSelfKNoL or kModeSelfK
@@ -54,6 +58,17 @@ struct GemmEpi {
   int* err;
 };
 
+// A finite float32 value as float64, assembled from its bit fields on the integer pipe (IEEE 754:
+// re-bias the exponent by 1023 - 127 and widen the significand); subnormal inputs, below 1.2e-38, give
+// signed zero.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned hi = (u & 0x80000000u) | (e ? (((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)) : 0u);
+  const unsigned lo = e ? (u << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort, long long limit) {
   for (long long i = 0; i < limit; ++i) {
     const bool done = umma::mbar_try_wait(bar, parity);
@@ -71,7 +86,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - raw);
   const uint32_t sZ = base, sA = base + kStages * kBytesA;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(gbase + kStages * (kBytesA + kBytesB));
+  uint8_t* epi_base = gbase + kStages * (kBytesA + kBytesB);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_base + 4 * kEpiWarpBytes);
   // barriers: full[0, S), empty[S, 2S), acc_full[2S, 2S + 2), acc_empty[2S + 2, 2S + 4), drain 2S + 4
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -185,9 +201,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       umma::mbar_wait(bar(2 * kStages + 4), 0, &never, kSpin);
     }
   } else {
-    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31, one particle per lane
+    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31, one particle per lane.
+    // A chunk of 24 columns (8 nodes) is rotated to the lab frame in registers, staged in shared
+    // memory, and written row by row, 24 consecutive float64 per particle and store instruction.
     const int q = warp & 3;
     const int r = q * 32 + lane;
+    uint8_t* ew = epi_base + (warp - 2) * kEpiWarpBytes;
+    float(*stage)[kEpiStride] = reinterpret_cast<float(*)[kEpiStride]>(ew);
+    long long* s_off = reinterpret_cast<long long*>(ew + 32 * kEpiStride * 4);
+    double(*s_mom)[6] = reinterpret_cast<double(*)[6]>(ew + 32 * kEpiStride * 4 + 32 * 8);
+    double(*s_cen)[3] = reinterpret_cast<double(*)[3]>(ew + 32 * kEpiStride * 4 + 32 * 8 + 32 * 6 * 8);
+    const bool half_x = ep.mode == kModeSelfK || ep.mode == kModeSelfKNoL;
+    const bool with_L = ep.mode == kModeSelfK;
     int acc = 0;
     uint32_t aphase = 0;
     bool ok = true;
@@ -200,59 +225,67 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       const int mt = t / n_tiles, nt = t % n_tiles;
       const int j = mt * kBM + r;
       const bool valid = j < ep.rows;
-      int pid = 0;
-      long long o = 0;
-      double R[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, m[6] = {0, 0, 0, 0, 0, 0}, cx = 0, cy = 0, cz = 0;
-      float inv = 0.0f;
+      const int row0 = mt * kBM + q * 32;  // this warp's first row
+      float R[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // R_j / (row scale * block scale), float32
+      __syncwarp();  // the previous tile's reads of the row parameters are done
       if (valid) {
-        pid = ep.list[j];
-        o = ep.offset[pid];
+        const int pid = ep.list[j];
+        s_off[lane] = ep.offset[pid];
+        const float inv = ep.inv[j];  // a power of two: exact in the product below
 #pragma unroll
-        for (int k = 0; k < 9; ++k) R[k] = ep.rot[9 * pid + k];
-        inv = ep.inv[j];
-        if (ep.mode == kModeSelfK) {
+        for (int k = 0; k < 9; ++k) R[k] = (float)ep.rot[9 * pid + k] * inv;
+        if (with_L) {
 #pragma unroll
-          for (int k = 0; k < 6; ++k) m[k] = ep.mom[6 * (long long)j + k];
-          cx = ep.centre[3 * pid];
-          cy = ep.centre[3 * pid + 1];
-          cz = ep.centre[3 * pid + 2];
+          for (int k = 0; k < 6; ++k) s_mom[lane][k] = ep.mom[6 * (long long)j + k];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) s_cen[lane][k] = ep.centre[3 * pid + k];
         }
       }
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
 #pragma unroll 1
-      for (int ch = 0; ch < kBN / 48; ++ch) {
-        float v[48];
-        float* v0 = v;
-        umma::tmem_ld16(taddr + 48 * ch, *reinterpret_cast<float(*)[16]>(v0));
-        umma::tmem_ld16(taddr + 48 * ch + 16, *reinterpret_cast<float(*)[16]>(v0 + 16));
-        umma::tmem_ld16(taddr + 48 * ch + 32, *reinterpret_cast<float(*)[16]>(v0 + 32));
+      for (int ch = 0; ch < kBN / kEpiCols; ++ch) {
+        float v[kEpiCols];
+        umma::tmem_ld16(taddr + kEpiCols * ch, *reinterpret_cast<float(*)[16]>(v));
+        umma::tmem_ld8(taddr + kEpiCols * ch + 16, v + 16);
         umma::tmem_ld_wait();
-        if (!valid) continue;
+        __syncwarp();  // the previous chunk's stores have read the stage
+        if (valid) {
+          // the lab-frame product in float32 (the 16-bit operands bound its accuracy far above float32
+          // rounding; GB300's float64 rate would make this rotation the kernel's bottleneck)
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const int node = nt * (kBN / 3) + ch * 16 + u;
-          if (node >= ep.np) break;
-          const double b0 = (double)(v[3 * u] * inv), b1 = (double)(v[3 * u + 1] * inv),
-                       b2 = (double)(v[3 * u + 2] * inv);
-          double l0 = R[0] * b0 + R[1] * b1 + R[2] * b2;
-          double l1 = R[3] * b0 + R[4] * b1 + R[5] * b2;
-          double l2 = R[6] * b0 + R[7] * b1 + R[8] * b2;
-          const long long gi = o + node;
-          if (ep.mode == kModeSelfK || ep.mode == kModeSelfKNoL) {
-            l0 += 0.5 * ep.in[3 * gi];
-            l1 += 0.5 * ep.in[3 * gi + 1];
-            l2 += 0.5 * ep.in[3 * gi + 2];
+          for (int u = 0; u < kEpiCols / 3; ++u) {
+            const float b0 = v[3 * u], b1 = v[3 * u + 1], b2 = v[3 * u + 2];
+            stage[lane][3 * u] = fmaf(R[0], b0, fmaf(R[1], b1, R[2] * b2));
+            stage[lane][3 * u + 1] = fmaf(R[3], b0, fmaf(R[4], b1, R[5] * b2));
+            stage[lane][3 * u + 2] = fmaf(R[6], b0, fmaf(R[7], b1, R[8] * b2));
           }
-          if (ep.mode == kModeSelfK) {
-            const double4 p = ep.x[gi];
-            const double rx = p.x - cx, ry = p.y - cy, rz = p.z - cz;
-            l0 += m[0] + (m[4] * rz - m[5] * ry);
-            l1 += m[1] + (m[5] * rx - m[3] * rz);
-            l2 += m[2] + (m[3] * ry - m[4] * rx);
+        }
+        __syncwarp();
+        // row by row: lane e < 24 writes entry e of the chunk (node e / 3, component e % 3)
+        const int node = nt * (kBN / 3) + ch * (kEpiCols / 3) + lane / 3;
+        const int comp = lane % 3;
+        if (lane < kEpiCols && node < ep.np) {
+          const bool plain = !half_x && !with_L && ep.scale == 1.0;
+          const int nrows = min(32, ep.rows - row0);
+          if (plain) {
+#pragma unroll 8
+            for (int rr = 0; rr < nrows; ++rr) ep.out[3 * (s_off[rr] + node) + comp] = f32_to_f64_bits(stage[rr][lane]);
+          } else {
+          for (int rr = 0; rr < nrows; ++rr) {
+            const long long gi = s_off[rr] + node;
+            const float sv = stage[rr][lane];
+            double val = (double)sv;
+            if (half_x) val += 0.5 * ep.in[3 * gi + comp];
+            if (with_L) {
+              const double4 pp = ep.x[gi];
+              const double rx = pp.x - s_cen[rr][0], ry = pp.y - s_cen[rr][1], rz = pp.z - s_cen[rr][2];
+              const double* m = s_mom[rr];
+              val += comp == 0 ? m[0] + (m[4] * rz - m[5] * ry)
+                               : (comp == 1 ? m[1] + (m[5] * rx - m[3] * rz) : m[2] + (m[3] * ry - m[4] * rx));
+            }
+            ep.out[3 * gi + comp] = ep.scale * val;
           }
-          ep.out[3 * gi] = ep.scale * l0;
-          ep.out[3 * gi + 1] = ep.scale * l1;
-          ep.out[3 * gi + 2] = ep.scale * l2;
+          }
         }
       }
       umma::tc_fence_before();
