@@ -540,6 +540,38 @@ Status advance(Context& c, const double* F, const double* T, double dt, int step
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// Shared memory of the reflection-symmetric block kernel (one CTA of kSymWarps warps per particle):
+// a ring of block-row copies (lane_bytes a lane), the eight reflected inputs z_g with row stride
+// sym_zstride, and, for float32 arithmetic, the row sums of every node until the block-wide finish.
+constexpr int kSymWarps = 8;
+__host__ __device__ constexpr int sym_lane_bytes(int ts_bytes) { return ts_bytes == 8 ? 96 : 192; }
+// at least 64 ceil(3 N_p / 64) entries and an odd number of 16-byte units, so that the eight rows
+// read at one column offset fall in distinct shared-memory banks
+__host__ __device__ inline int sym_zstride(int dim, int tb_bytes) { return (dim + 63) / 64 * 64 + 16 / tb_bytes; }
+__host__ __device__ inline long long sym_smem_bytes(int np, int ts_bytes, int tb_bytes) {
+  return (long long)kSymWarps * 32 * sym_lane_bytes(ts_bytes) + 8LL * sym_zstride(3 * np, tb_bytes) * tb_bytes +
+         (tb_bytes == 4 ? 3LL * np * tb_bytes : 0);
+}
+
+// Conversions between float64 and float32 from the IEEE 754 bit fields on the integer pipe (GB300's
+// float64 pipe, 2 operations per clock per SM, would bound kernels that only widen or narrow): the
+// exponent is re-biased by 1023 - 127 and the significand widened or truncated.  Finite values of the
+// float32 range only; magnitudes below 2^-126 give signed zero, and narrowing truncates (an error
+// below one float32 ulp).
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned hi = (u & 0x80000000u) | (e ? (((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)) : 0u);
+  const unsigned lo = e ? (u << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ float f64_to_f32_trunc(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
+  if (e <= 0) return __uint_as_float(hi & 0x80000000u);
+  return __uint_as_float((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
 // Brackets one timed launch: records events only when timing is on; always counts the launch.
 struct KernelTimer {
   Context& c;

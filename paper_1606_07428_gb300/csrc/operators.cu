@@ -8,6 +8,7 @@
 //  * near correction: for near particle pairs, the base-grid contribution is replaced by the one
 //    from the source's upsampled grid (Section 3: upsampling for close targets).
 #include <algorithm>
+#include <type_traits>
 
 #include <cuda_fp16.h>
 
@@ -157,11 +158,9 @@ __global__ void __launch_bounds__(256) k_blocks(int mode, const int4* __restrict
 // Particle-block kernel for shapes stored by the rows of their representative nodes (ellipsoids).
 // The blocks commute with the grid's eight reflections g (node map g(.), sign matrix D_g):
 // A_{g(t), g(s)} = D_g A_{t,s} D_g, so y_{g(t)} = D_g sum_s A_{t,s} (D_g z_{g(s)}) for each stored
-// row t.  One block per particle, 256 threads: the eight reflected copies of z = R_i^T x_i are staged
-// in shared memory (in the block type), each warp takes one representative at a time and reads its
-// three rows once for all eight reflections (one fused multiply-add per reflection and entry, in
-// the block type), and lane g writes node g(t) when no smaller reflection reaches it.  1/2 x, L x and
-// the preconditioner's copy of x are added as in k_blocks.
+// row t.  The eight reflected copies of z = R_i^T x_i are staged in shared memory, so each stored row
+// is read once for all eight reflections (k_blocks_sym below); 1/2 x, L x and the preconditioner's
+// copy of x are added as in k_blocks.
 // Node (j, k) under the reflection g, without divisions (k in [0, n_phi)).
 __device__ __forceinline__ int reflect_jk(int g, int j, int k, int p, int nphi) {
   if (g & 4) j = p - j;
@@ -172,107 +171,177 @@ __device__ __forceinline__ int reflect_jk(int g, int j, int k, int p, int nphi) 
   }
   return j * nphi + k;
 }
-__device__ __forceinline__ int reflect_node_dev(int g, int t, int p, int nphi) {
-  const int j = t / nphi;
-  return reflect_jk(g, j, t - j * nphi, p, nphi);
-}
 
-
-// Block entries as stored (float64, float32, or the bits of float16 / bfloat16) to the arithmetic type.
-__device__ __forceinline__ double load_entry(const double* p) { return __ldg(p); }
-__device__ __forceinline__ float load_entry(const float* p) { return __ldg(p); }
+// Block entries stored as the bits of float16 / bfloat16.
 struct F16Bits {
   uint16_t v;
 };
 struct BF16Bits {
   uint16_t v;
 };
-__device__ __forceinline__ float load_entry(const F16Bits* p) {
-  return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+
+// Four consecutive entries of a staged block row, or of a staged input row, in the arithmetic type
+// (one 16-, 8- or two 16-byte shared-memory loads; aligned to their size).
+__device__ __forceinline__ void load_quad(const float* p, float (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w;
 }
-__device__ __forceinline__ float load_entry(const BF16Bits* p) {
-  return __uint_as_float((unsigned)__ldg(reinterpret_cast<const unsigned short*>(p)) << 16);
+__device__ __forceinline__ void load_quad(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+}
+__device__ __forceinline__ void load_quad(const F16Bits* p, float (&v)[4]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+  const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  v[0] = f0.x, v[1] = f0.y, v[2] = f1.x, v[3] = f1.y;
+}
+__device__ __forceinline__ void load_quad(const BF16Bits* p, float (&v)[4]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  v[0] = __uint_as_float(u.x << 16), v[1] = __uint_as_float(u.x & 0xffff0000u);
+  v[2] = __uint_as_float(u.y << 16), v[3] = __uint_as_float(u.y & 0xffff0000u);
 }
 
-// Two consecutive entries (an even column of a row: 8-, 16- or 4-byte aligned).
-__device__ __forceinline__ void load_pair(const double* p, double& a, double& b) {
-  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
-  a = v.x;
-  b = v.y;
+// Asynchronous global-to-shared copy of BYTES (4, 8 or 16) by one thread; src_bytes = 0 writes zeros
+// and reads nothing.  Completion is tracked by commit groups.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_zfill(uint32_t dst, const void* src, uint32_t src_bytes) {
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(src), "n"(BYTES), "r"(src_bytes)
+                 : "memory");
 }
-__device__ __forceinline__ void load_pair(const float* p, float& a, float& b) {
-  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-  a = v.x;
-  b = v.y;
-}
-__device__ __forceinline__ void load_pair(const F16Bits* p, float& a, float& b) {
-  const unsigned u = __ldg(reinterpret_cast<const unsigned*>(p));
-  a = __half2float(__ushort_as_half((unsigned short)(u & 0xffffu)));
-  b = __half2float(__ushort_as_half((unsigned short)(u >> 16)));
-}
-__device__ __forceinline__ void load_pair(const BF16Bits* p, float& a, float& b) {
-  const unsigned u = __ldg(reinterpret_cast<const unsigned*>(p));
-  a = __uint_as_float(u << 16);
-  b = __uint_as_float(u & 0xffff0000u);
-}
-
-// Two consecutive staged inputs (an even column) in one shared-memory access.
-__device__ __forceinline__ void load_pair_shared(const float* p, float& a, float& b) {
-  const float2 v = *reinterpret_cast<const float2*>(p);
-  a = v.x;
-  b = v.y;
-}
-__device__ __forceinline__ void load_pair_shared(const double* p, double& a, double& b) {
-  const double2 v = *reinterpret_cast<const double2*>(p);
-  a = v.x;
-  b = v.y;
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // TS: storage type of the block entries; TB: the arithmetic of the products and sums (float64 for
-// float64 blocks, float32 otherwise).  Rows are read two columns per lane (3 N_p is even).
+// float64 blocks, float32 otherwise).  One CTA of kSymWarps warps per particle.  Each warp takes one
+// representative r at a time and streams its three rows through a ring of asynchronous copies, one
+// step of 512 bytes a row (each lane copies 16 bytes of each row; the ring runs several steps ahead).
+// Lane (c, h) = (lane mod 16, lane / 16) multiplies the column quads 4c + 64 s of the step with the
+// reflected inputs z_g, g = 4h .. 4h + 3, keeping twelve partial sums; at the end of r a reduce-scatter
+// over the sixteen column groups leaves reflection g's three sums in lanes 4g .. 4g + 3.  In float32
+// arithmetic the row sums go to shared memory and every node is finished by the whole CTA at the end;
+// in float64 lane 4g finishes node g(r) at once.
 template <typename TS, typename TB>
-__global__ void __launch_bounds__(256) k_blocks_sym(int mode, const int* __restrict__ sym_list,
-                                                    const long long* __restrict__ offset, const int* __restrict__ pvec,
-                                                    const int* __restrict__ nphivec, const double* __restrict__ rot,
-                                                    const double* __restrict__ centre, const int* __restrict__ shape_of,
-                                                    const long long* __restrict__ block_off, const TS* __restrict__ blocks,
-                                                    const double4* __restrict__ x, const double* __restrict__ in,
-                                                    double* __restrict__ out, double* __restrict__ aux, double scale) {
+__global__ void __launch_bounds__(kSymWarps * 32, sizeof(TB) == 4 ? 3 : 2)
+    k_blocks_sym(int mode, const int* __restrict__ sym_list, const long long* __restrict__ offset,
+                 const int* __restrict__ pvec, const int* __restrict__ nphivec, const double* __restrict__ rot,
+                 const double* __restrict__ centre, const int* __restrict__ shape_of,
+                 const long long* __restrict__ block_off, const TS* __restrict__ blocks, const double4* __restrict__ x,
+                 const double* __restrict__ in, double* __restrict__ out, double* __restrict__ aux, double scale) {
+  constexpr bool kF32 = sizeof(TB) == 4;
+  constexpr int E = 16 / (int)sizeof(TS);  // entries of a 16-byte chunk
+  constexpr int SC = 32 * E;               // columns of a step
+  constexpr int S = sym_lane_bytes(sizeof(TS)) / 48;  // ring stages
+  constexpr int kRingBytes = kSymWarps * 32 * sym_lane_bytes(sizeof(TS));
   extern __shared__ __align__(16) unsigned char zraw[];
-  TB* zg = reinterpret_cast<TB*>(zraw);  // 8 x 3 N_p
-  __shared__ double red[8][6];
-  __shared__ double mom[6];
+  __shared__ TB red[kSymWarps][6];
+  __shared__ TB mom[6];
+  // float64 inputs in the block's arithmetic: float32 blocks convert on the integer pipe (the float64
+  // pipe would otherwise bound this kernel: rotations, moments and the L term are float64-pipe work)
+  auto cv = [](double d) -> TB {
+    if constexpr (kF32)
+      return f64_to_f32_trunc(d);
+    else
+      return d;
+  };
+  auto wide = [](TB v) -> double {
+    if constexpr (kF32)
+      return f32_to_f64_bits(v);
+    else
+      return v;
+  };
   const int i = sym_list[blockIdx.x];
   const int p = pvec[i], nphi = nphivec[i], np = (p + 1) * nphi, dim = 3 * np;
   const int nk = nphi / 4 + 1, nrep = (p / 2 + 1) * nk;
+  const int zs = sym_zstride(dim, sizeof(TB));
+  TB* zg = reinterpret_cast<TB*>(zraw + kRingBytes);  // 8 rows of stride zs
+  TB* ynode = zg + 8 * zs;                            // float32: 3 N_p row sums
   const long long o = offset[i];
   const double* R = rot + 9 * i;
-  const double R0 = R[0], R1 = R[1], R2 = R[2], R3 = R[3], R4 = R[4], R5 = R[5], R6 = R[6], R7 = R[7], R8 = R[8];
-  const double cx = centre[3 * i], cy = centre[3 * i + 1], cz = centre[3 * i + 2];
+  const TB R0 = cv(R[0]), R1 = cv(R[1]), R2 = cv(R[2]), R3 = cv(R[3]), R4 = cv(R[4]), R5 = cv(R[5]), R6 = cv(R[6]),
+           R7 = cv(R[7]), R8 = cv(R[8]);
+  const double cxd = centre[3 * i], cyd = centre[3 * i + 1], czd = centre[3 * i + 2];
+  const TB sc = cv(scale);
   const bool has_block = (mode != kModeL);
   const bool has_L = (mode == kModeSelfK || mode == kModeL);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double m[6] = {0, 0, 0, 0, 0, 0};
+
+  // the copies: step = (representative of this warp, SC-column slice), one commit group per step;
+  // 16-byte copies where the rows are 16-byte aligned, else copies of two entries
+  const TS* A = blocks + block_off[shape_of[i]];
+  const int nst = (dim + SC - 1) / SC;
+  const bool al16 = ((reinterpret_cast<uintptr_t>(A) & 15u) == 0) && (dim % E == 0);
+  const uint32_t ring_l = static_cast<uint32_t>(__cvta_generic_to_shared(zraw)) + warp * (S * 3 * 512) + lane * 16;
+  int iss_left = (has_block && warp < nrep) ? ((nrep - 1 - warp) / kSymWarps + 1) * nst : 0;
+  int iss_it = 0, iss_slot = 0;
+  const TS* iss_src = A + (long long)(3 * warp) * dim + E * lane;
+  const long long rep_jump = (long long)3 * kSymWarps * dim - (long long)SC * nst;
+  auto issue = [&]() {
+    if (iss_left > 0) {
+      // entries past the row end are zero-filled (nothing is read there)
+      const int col = E * lane + SC * iss_it;
+      const uint32_t dst = ring_l + iss_slot * (3 * 512);
+      if (al16) {
+        const bool inb = col < dim;
+        const TS* s0 = inb ? iss_src : A;
+        const long long d1 = inb ? dim : 0;
+        const uint32_t nb = inb ? 16u : 0u;
+        cp_async_zfill<16>(dst, s0, nb);
+        cp_async_zfill<16>(dst + 512, s0 + d1, nb);
+        cp_async_zfill<16>(dst + 1024, s0 + 2 * d1, nb);
+      } else {
+#pragma unroll
+        for (int j = 0; j < E / 2; ++j) {
+          constexpr int B2 = 2 * (int)sizeof(TS);
+          const bool inb = col + 2 * j < dim;
+          const TS* s0 = inb ? iss_src + 2 * j : A;
+          const long long d1 = inb ? dim : 0;
+          const uint32_t nb = inb ? (uint32_t)B2 : 0u;
+          cp_async_zfill<B2>(dst + j * B2, s0, nb);
+          cp_async_zfill<B2>(dst + 512 + j * B2, s0 + d1, nb);
+          cp_async_zfill<B2>(dst + 1024 + j * B2, s0 + 2 * d1, nb);
+        }
+      }
+      --iss_left;
+      iss_src += SC;
+      if (++iss_it == nst) {  // on to this warp's next representative
+        iss_it = 0;
+        iss_src += rep_jump;
+      }
+      iss_slot = (iss_slot + 1 == S) ? 0 : iss_slot + 1;
+    }
+    cp_async_commit();  // empty past the end
+  };
+  // the first stages load while the inputs are staged
+  for (int q = 0; q < S - 1; ++q) issue();
+
+  TB m[6] = {0, 0, 0, 0, 0, 0};
   for (int sp = threadIdx.x; sp < np; sp += blockDim.x) {
     const double* xs = in + 3 * (o + sp);
-    const double a = xs[0], b = xs[1], cc = xs[2];
+    const TB a = cv(xs[0]), b = cv(xs[1]), cc = cv(xs[2]);
     if (has_block) {
-      const double z0 = R0 * a + R3 * b + R6 * cc;
-      const double z1 = R1 * a + R4 * b + R7 * cc;
-      const double z2 = R2 * a + R5 * b + R8 * cc;
+      const TB z0 = R0 * a + R3 * b + R6 * cc;
+      const TB z1 = R1 * a + R4 * b + R7 * cc;
+      const TB z2 = R2 * a + R5 * b + R8 * cc;
       const int js = sp / nphi, ks = sp - js * nphi;
 #pragma unroll
       for (int g = 0; g < 8; ++g) {
         const int sn = reflect_jk(g, js, ks, p, nphi);  // g is an involution: z_{g(sn)} = z_{sp}
-        TB* zz = zg + g * dim + 3 * sn;
-        zz[0] = (TB)((g & 1) ? -z0 : z0);
-        zz[1] = (TB)((g & 2) ? -z1 : z1);
-        zz[2] = (TB)((g & 4) ? -z2 : z2);
+        TB* zz = zg + g * zs + 3 * sn;
+        zz[0] = (g & 1) ? -z0 : z0;
+        zz[1] = (g & 2) ? -z1 : z1;
+        zz[2] = (g & 4) ? -z2 : z2;
       }
     }
     if (has_L) {
       const double4 q = x[o + sp];
-      const double rx = q.x - cx, ry = q.y - cy, rz = q.z - cz, w = q.w;
+      const TB rx = cv(q.x - cxd), ry = cv(q.y - cyd), rz = cv(q.z - czd), w = cv(q.w);
       m[0] += w * a;
       m[1] += w * b;
       m[2] += w * cc;
@@ -281,35 +350,42 @@ __global__ void __launch_bounds__(256) k_blocks_sym(int mode, const int* __restr
       m[5] += w * (rx * b - ry * a);
     }
   }
+  if (has_block) {  // the padding columns [3 N_p, zs) of each z_g (their block entries are zero)
+    const int pad = zs - dim;
+    for (int e = threadIdx.x; e < 8 * pad; e += blockDim.x) {
+      const int g = e / pad;
+      zg[g * zs + dim + (e - g * pad)] = (TB)0;
+    }
+  }
   if (has_L) {
 #pragma unroll
-    for (int q = 0; q < 6; ++q) m[q] = warp_sum(m[q]);
+    for (int q = 0; q < 6; ++q) m[q] = warp_sum_t(m[q]);
     if (lane == 0)
 #pragma unroll
       for (int q = 0; q < 6; ++q) red[warp][q] = m[q];
   }
   __syncthreads();
   if (has_L && threadIdx.x < 6) {
-    double acc = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][threadIdx.x];
+    TB acc = 0;
+    for (int w = 0; w < kSymWarps; ++w) acc += red[w][threadIdx.x];
     mom[threadIdx.x] = acc;
   }
   __syncthreads();
   // finish one node t of the particle from its body-frame block product (l0, l1, l2)
-  auto finish = [&](int t, double l0b, double l1b, double l2b) {
+  auto finish = [&](int t, TB l0b, TB l1b, TB l2b) {
     const long long gi = o + t;
-    double l0 = R0 * l0b + R1 * l1b + R2 * l2b;
-    double l1 = R3 * l0b + R4 * l1b + R5 * l2b;
-    double l2 = R6 * l0b + R7 * l1b + R8 * l2b;
+    TB l0 = R0 * l0b + R1 * l1b + R2 * l2b;
+    TB l1 = R3 * l0b + R4 * l1b + R5 * l2b;
+    TB l2 = R6 * l0b + R7 * l1b + R8 * l2b;
     const double* xt = in + 3 * gi;
     if (mode == kModeSelfK || mode == kModeSelfKNoL) {
-      l0 += 0.5 * xt[0];
-      l1 += 0.5 * xt[1];
-      l2 += 0.5 * xt[2];
+      l0 += (TB)0.5 * cv(xt[0]);
+      l1 += (TB)0.5 * cv(xt[1]);
+      l2 += (TB)0.5 * cv(xt[2]);
     }
     if (has_L) {
       const double4 q = x[gi];
-      const double rx = q.x - cx, ry = q.y - cy, rz = q.z - cz;
+      const TB rx = cv(q.x - cxd), ry = cv(q.y - cyd), rz = cv(q.z - czd);
       l0 += mom[0] + (mom[4] * rz - mom[5] * ry);
       l1 += mom[1] + (mom[5] * rx - mom[3] * rz);
       l2 += mom[2] + (mom[3] * ry - mom[4] * rx);
@@ -319,51 +395,113 @@ __global__ void __launch_bounds__(256) k_blocks_sym(int mode, const int* __restr
       aux[3 * gi + 1] = xt[1];
       aux[3 * gi + 2] = xt[2];
     }
-    out[3 * gi + 0] = scale * l0;
-    out[3 * gi + 1] = scale * l1;
-    out[3 * gi + 2] = scale * l2;
+    out[3 * gi + 0] = wide(sc * l0);
+    out[3 * gi + 1] = wide(sc * l1);
+    out[3 * gi + 2] = wide(sc * l2);
   };
   if (!has_block) {
-    for (int t = threadIdx.x; t < np; t += blockDim.x) finish(t, 0.0, 0.0, 0.0);
+    for (int t = threadIdx.x; t < np; t += blockDim.x) finish(t, (TB)0, (TB)0, (TB)0);
     return;
   }
-  const TS* A = blocks + block_off[shape_of[i]];
-  for (int r = warp; r < nrep; r += (int)(blockDim.x >> 5)) {
-    TB y[8][3];
+
+  const int kc = lane & 15, hg = lane >> 4;
+  const TS* ring_k = reinterpret_cast<const TS*>(zraw) + warp * (S * 3 * SC) + 4 * kc;
+  const TB* zl = zg + (4 * hg) * zs + 4 * kc;
+  int slot = 0;
+  for (int r = warp; r < nrep; r += kSymWarps) {
+    float2 y2[4][3];
+    TB yd[4][3];
 #pragma unroll
-    for (int g = 0; g < 8; ++g) y[g][0] = y[g][1] = y[g][2] = (TB)0;
-    const TS* row = A + (long long)(3 * r) * dim;
-#pragma unroll 2
-    for (int col = 2 * lane; col < dim; col += 64) {
-      TB a0, a0b, a1, a1b, a2, a2b;
-      load_pair(row + col, a0, a0b);
-      load_pair(row + dim + col, a1, a1b);
-      load_pair(row + 2 * dim + col, a2, a2b);
+    for (int gl = 0; gl < 4; ++gl)
 #pragma unroll
-      for (int g = 0; g < 8; ++g) {
-        TB zv, zw;
-        load_pair_shared(zg + g * dim + col, zv, zw);
-        y[g][0] = fma_t(a0b, zw, fma_t(a0, zv, y[g][0]));
-        y[g][1] = fma_t(a1b, zw, fma_t(a1, zv, y[g][1]));
-        y[g][2] = fma_t(a2b, zw, fma_t(a2, zv, y[g][2]));
+      for (int q = 0; q < 3; ++q) {
+        y2[gl][q] = make_float2(0.f, 0.f);
+        yd[gl][q] = (TB)0;
+      }
+    for (int c0 = 0; c0 < SC * nst; c0 += SC) {
+      issue();
+      cp_async_wait<S - 1>();  // this lane's copies of the step have landed ...
+      __syncwarp();            // ... and so have the other lanes'
+      const TS* st = ring_k + slot * (3 * SC);
+#pragma unroll
+      for (int sq = 0; sq < SC / 64; ++sq) {
+        if (c0 + 64 * sq + 4 * kc >= dim) continue;
+        TB a[3][4];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) load_quad(st + q * SC + 64 * sq, a[q]);
+#pragma unroll
+        for (int gl = 0; gl < 4; ++gl) {
+          TB z[4];
+          load_quad(zl + gl * zs + c0 + 64 * sq, z);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            if constexpr (kF32) {
+              y2[gl][q] = __ffma2_rn(make_float2(a[q][0], a[q][1]), make_float2(z[0], z[1]), y2[gl][q]);
+              y2[gl][q] = __ffma2_rn(make_float2(a[q][2], a[q][3]), make_float2(z[2], z[3]), y2[gl][q]);
+            } else {
+              yd[gl][q] = fma(a[q][0], z[0], fma(a[q][1], z[1], fma(a[q][2], z[2], fma(a[q][3], z[3], yd[gl][q]))));
+            }
+          }
+        }
+      }
+      __syncwarp();  // every lane has read the stage before it is refilled
+      slot = (slot + 1 == S) ? 0 : slot + 1;
+    }
+    // reduce-scatter over the sixteen column groups: halve the set at lane bits 3 and 2, then sum
+    TB v12[12], v6[6], v3[3];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      if constexpr (kF32)
+        v12[k] = y2[k / 3][k % 3].x + y2[k / 3][k % 3].y;
+      else
+        v12[k] = yd[k / 3][k % 3];
+    }
+    {
+      const bool hi = lane & 8;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const TB lo_v = v12[k], hi_v = v12[6 + k];
+        v6[k] = (hi ? hi_v : lo_v) + __shfl_xor_sync(0xffffffffu, hi ? lo_v : hi_v, 8);
+      }
+    }
+    {
+      const bool hi = lane & 4;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const TB lo_v = v6[k], hi_v = v6[3 + k];
+        v3[k] = (hi ? hi_v : lo_v) + __shfl_xor_sync(0xffffffffu, hi ? lo_v : hi_v, 4);
       }
     }
 #pragma unroll
-    for (int g = 0; g < 8; ++g)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) y[g][q] = warp_sum_t(y[g][q]);
-    const int j0 = r / nk, k0 = r - (r / nk) * nk;
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      if (lane != g) continue;
-      const int t = reflect_jk(g, j0, k0, p, nphi);
-      bool first = true;
-      for (int h = 0; h < g; ++h)
-        if (reflect_jk(h, j0, k0, p, nphi) == t) first = false;
-      if (!first) continue;
-      const double b0 = (double)y[g][0], b1 = (double)y[g][1], b2 = (double)y[g][2];
-      finish(t, (g & 1) ? -b0 : b0, (g & 2) ? -b1 : b1, (g & 4) ? -b2 : b2);
+    for (int k = 0; k < 3; ++k) {
+      v3[k] += __shfl_xor_sync(0xffffffffu, v3[k], 2);
+      v3[k] += __shfl_xor_sync(0xffffffffu, v3[k], 1);
     }
+    // lane 4g holds reflection g's sums: node g(r) unless a smaller reflection reaches it
+    const int g = lane >> 2;
+    const int j0 = r / nk, k0 = r - j0 * nk;
+    const int t = reflect_jk(g, j0, k0, p, nphi);
+    bool first = true;
+#pragma unroll
+    for (int h = 0; h < 7; ++h) {
+      const int th = __shfl_sync(0xffffffffu, t, 4 * h);
+      if (h < g && th == t) first = false;
+    }
+    if ((lane & 3) == 0 && first) {
+      const TB b0 = (g & 1) ? -v3[0] : v3[0], b1 = (g & 2) ? -v3[1] : v3[1], b2 = (g & 4) ? -v3[2] : v3[2];
+      if constexpr (kF32) {
+        ynode[3 * t] = b0;
+        ynode[3 * t + 1] = b1;
+        ynode[3 * t + 2] = b2;
+      } else {
+        finish(t, b0, b1, b2);
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if constexpr (kF32) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < np; t += blockDim.x) finish(t, ynode[3 * t], ynode[3 * t + 1], ynode[3 * t + 2]);
   }
 }
 
@@ -1310,7 +1448,7 @@ Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, 
   // 16-bit entries for the ellipsoid blocks of the inner solve's arithmetic (coefficient surfaces,
   // which store every row, keep float32 blocks)
   const bool use16 = prec_16(prec) && kblock && c.d_blockK16.ptr;
-  const double bytes = (mode == kModeL) ? 0.0 : (double)c.particle_block_entries * (use32 ? 4.0 : 8.0);
+  const double bytes = (mode == kModeL) ? 0.0 : (double)c.particle_block_entries * (use16 ? 2.0 : use32 ? 4.0 : 8.0);
   KernelTimer timer(c, RBS_KC_BLOCKS);
   // 16-bit modes: ellipsoids of shapes shared by many particles go through the tensor-core GEMM, the
   // others through the CUDA-core kernel below
@@ -1319,7 +1457,7 @@ Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, 
   const int nsym = gemm ? (int)c.sym_rest.size() : ns;
   if (gemm) RBS_TRY(apply_self_gemm(c, mode, x, y, aux, scale));
   if (nsym > 0) {
-    const size_t zs = (use32 ? sizeof(float) : sizeof(double)) * 8 * 3 * (size_t)c.max_np_sym;
+    const size_t zs = (size_t)sym_smem_bytes(c.max_np_sym, use16 ? 2 : use32 ? 4 : 8, use32 ? 4 : 8);
 #define RBS_SYM_ARGS                                                                                              \
   mode, sym_ids, c.d_offset.ptr, c.d_p.ptr, c.d_nphi.ptr, c.d_rot.ptr, c.d_centre.ptr, c.d_shape.ptr, \
       c.d_block_off.ptr, B, c.d_x.ptr, x, y, aux, scale
@@ -1330,26 +1468,26 @@ Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, 
         if (zs > 48 * 1024)
           RBS_CUDA_TRY(cudaFuncSetAttribute(k_blocks_sym<F16Bits, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)zs));
-        k_blocks_sym<F16Bits, float><<<nsym, 256, zs, c.stream>>>(RBS_SYM_ARGS);
+        k_blocks_sym<F16Bits, float><<<nsym, kSymWarps * 32, zs, c.stream>>>(RBS_SYM_ARGS);
       } else {
         const BF16Bits* B = reinterpret_cast<const BF16Bits*>(B16);
         if (zs > 48 * 1024)
           RBS_CUDA_TRY(cudaFuncSetAttribute(k_blocks_sym<BF16Bits, float>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs));
-        k_blocks_sym<BF16Bits, float><<<nsym, 256, zs, c.stream>>>(RBS_SYM_ARGS);
+        k_blocks_sym<BF16Bits, float><<<nsym, kSymWarps * 32, zs, c.stream>>>(RBS_SYM_ARGS);
       }
     } else if (use32) {
       const float* B = (mode == kModePrecond) ? c.d_precond32.ptr : c.d_blockK32.ptr;
       if (zs > 48 * 1024)
         RBS_CUDA_TRY(cudaFuncSetAttribute(k_blocks_sym<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)zs));
-      k_blocks_sym<float, float><<<nsym, 256, zs, c.stream>>>(RBS_SYM_ARGS);
+      k_blocks_sym<float, float><<<nsym, kSymWarps * 32, zs, c.stream>>>(RBS_SYM_ARGS);
     } else {
       const double* B = (mode == kModePrecond) ? c.d_precond.ptr : (mode == kModeSelfS ? c.d_blockS.ptr : c.d_blockK.ptr);
       if (zs > 48 * 1024)
         RBS_CUDA_TRY(cudaFuncSetAttribute(k_blocks_sym<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)zs));
-      k_blocks_sym<double, double><<<nsym, 256, zs, c.stream>>>(RBS_SYM_ARGS);
+      k_blocks_sym<double, double><<<nsym, kSymWarps * 32, zs, c.stream>>>(RBS_SYM_ARGS);
     }
 #undef RBS_SYM_ARGS
     RBS_CUDA_TRY(cudaGetLastError());

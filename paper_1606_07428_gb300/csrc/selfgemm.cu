@@ -58,17 +58,6 @@ struct GemmEpi {
   int* err;
 };
 
-// A finite float32 value as float64, assembled from its bit fields on the integer pipe (IEEE 754:
-// re-bias the exponent by 1023 - 127 and widen the significand); subnormal inputs, below 1.2e-38, give
-// signed zero.
-__device__ __forceinline__ double f32_to_f64_bits(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  const unsigned hi = (u & 0x80000000u) | (e ? (((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)) : 0u);
-  const unsigned lo = e ? (u << 29) : 0u;
-  return __hiloint2double((int)hi, (int)lo);
-}
-
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort, long long limit) {
   for (long long i = 0; i < limit; ++i) {
     const bool done = umma::mbar_try_wait(bar, parity);

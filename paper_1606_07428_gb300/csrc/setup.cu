@@ -1065,7 +1065,8 @@ Status build_geometry(Context& c) {
       sh.np = c.grids[sh.grid]->np;
       // ellipsoids store representative rows when the eight reflected copies of a float64 surface
       // field fit in shared memory (N_p <= 1066, e.g. p = 16 on a 17 x 32 grid)
-      sh.sym = (sh.kind == 0) && 24LL * sh.np * (long long)sizeof(double) <= 200 * 1024;
+      // the float64 block kernel's shared memory (the largest variant) within the 227 KB of a CTA
+      sh.sym = (sh.kind == 0) && sym_smem_bytes(sh.np, 8, 8) + 1024 <= 227 * 1024;
       sh.rows = sh.sym ? 3 * c.grids[sh.grid]->nrep : 3 * sh.np;
       sh.block_off = c.block_elems;
       c.block_elems += (size_t)sh.rows * 3 * sh.np;

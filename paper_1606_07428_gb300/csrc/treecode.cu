@@ -199,8 +199,8 @@ __global__ void __maxnreg__(NT == 1 ? 64 : (NT == 2 ? 128 : 168))
                const float4* __restrict__ shi, const float4* __restrict__ slo, const float4* __restrict__ sq,
                double* __restrict__ y) {
   constexpr int TW = kTreeTile32, SL = TW / 32;
-  const int NTH = blockDim.x;
   const int lane = threadIdx.x & 31;
+  const int wbase = (threadIdx.x >> 5) * 32 * NT;  // the warp's targets: wbase + 32 u + lane of the item
   extern __shared__ __align__(16) float tree_smem32[];
   float* const ssx = tree_smem32 + (threadIdx.x >> 5) * (7 * TW);
   float* const ssy = ssx + TW;
@@ -211,9 +211,10 @@ __global__ void __maxnreg__(NT == 1 ? 64 : (NT == 2 ? 128 : 168))
   int* const spid = reinterpret_cast<int*>(ssx + 6 * TW);
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const TreeItem w = items[it];
-    // target slots of this warp that hold a target: u < nu for lane 0 (the warp's last slot may be
-    // partly empty; later slots are skipped, and a warp without targets skips the item)
-    const int nu = min(NT, max(0, (w.t1 - w.t0 - (int)(threadIdx.x & ~31u) + NTH - 1) / NTH));
+    // target slots of this warp that hold a target: u < nu (a warp owns 32 NT consecutive targets, so
+    // only the item's last warp has empty slots; they are skipped, and a warp without targets skips
+    // the item)
+    const int nu = min(NT, max(0, (w.t1 - w.t0 - wbase + 31) / 32));
     if (nu == 0) continue;
     const float4 oh = xhi[w.t0], ol = xlo[w.t0];
     float2 xt[NT][3], nt[NT][3];
@@ -221,7 +222,7 @@ __global__ void __maxnreg__(NT == 1 ? 64 : (NT == 2 ? 128 : 168))
     bool valid[NT];
 #pragma unroll
     for (int u = 0; u < NT; ++u) {
-      const int t = w.t0 + threadIdx.x + NTH * u;
+      const int t = w.t0 + wbase + 32 * u + lane;
       valid[u] = t < w.t1;
       float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, n0 = 0.0f, n1 = 0.0f, n2 = 0.0f;
       pt[u] = -1;
@@ -320,7 +321,7 @@ __global__ void __maxnreg__(NT == 1 ? 64 : (NT == 2 ? 128 : 168))
 #pragma unroll
     for (int u = 0; u < NT; ++u) {
       if (!valid[u]) continue;
-      const long long t = w.t0 + threadIdx.x + NTH * u;
+      const long long t = w.t0 + wbase + 32 * u + lane;
 #pragma unroll
       for (int c = 0; c < 3; ++c) atomicAdd(y + 3 * t + c, sc * ((double)sa[u][c] + (double)ea[u][c]));
     }
@@ -466,8 +467,8 @@ __global__ void __maxnreg__(NT == 1 ? 96 : 168)
                const float4* __restrict__ smid, const float4* __restrict__ slo, const float4* __restrict__ sqh,
                const float4* __restrict__ sql, double* __restrict__ y, double* __restrict__ y2) {
   constexpr int TW = kTreeTileDf, SL = TW / 32;
-  const int NTH = blockDim.x;
   const int lane = threadIdx.x & 31;
+  const int wbase = (threadIdx.x >> 5) * 32 * NT;  // the warp's targets: wbase + 32 u + lane of the item
   extern __shared__ __align__(16) float tree_smem_df[];
   // per warp: the tile (12 float rows and the particle ids), then the item's origin (three float4)
   float(*sa)[TW] = reinterpret_cast<float(*)[TW]>(tree_smem_df + (threadIdx.x >> 5) * (13 * TW + 12));
@@ -476,7 +477,7 @@ __global__ void __maxnreg__(NT == 1 ? 96 : 168)
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const TreeItem w = items[it];
     // target slots of this warp that hold a target (as k_tree32x2); a warp without targets skips
-    const int nu = min(NT, max(0, (w.t1 - w.t0 - (int)(threadIdx.x & ~31u) + NTH - 1) / NTH));
+    const int nu = min(NT, max(0, (w.t1 - w.t0 - wbase + 31) / 32));
     if (nu == 0) continue;
     __syncwarp();  // the warp's reads of the previous item's origin are done
     if (lane == 0) {
@@ -490,7 +491,7 @@ __global__ void __maxnreg__(NT == 1 ? 96 : 168)
     bool valid[NT];
 #pragma unroll
     for (int u = 0; u < NT; ++u) {
-      const int t = w.t0 + threadIdx.x + NTH * u;
+      const int t = w.t0 + wbase + 32 * u + lane;
       valid[u] = t < w.t1;
       const float4 oh = org[0], om = org[1], ol = org[2];
       float4 ah = oh, am = om, al = ol, bh = make_float4(0, 0, 0, 0), bl = make_float4(0, 0, 0, 0);
@@ -609,7 +610,7 @@ __global__ void __maxnreg__(NT == 1 ? 96 : 168)
 #pragma unroll
     for (int u = 0; u < NT; ++u) {
       if (!valid[u]) continue;
-      const long long t = w.t0 + threadIdx.x + NTH * u;
+      const long long t = w.t0 + wbase + 32 * u + lane;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         atomicAdd(y + 3 * t + c, sc * ((double)a[u][c].h + (double)a[u][c].l));

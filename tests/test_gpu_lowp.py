@@ -33,10 +33,13 @@ def rel(a, b):
 
 
 def cases():
-    """distinct: 7 ellipsoids of their own shapes (CUDA-core path); shared_p4 / shared_p8: 72 and 130
-    identical ellipsoids (tensor-core path; one and two 128-particle tiles, 120 and 432 block rows)."""
+    """distinct: 7 ellipsoids of their own shapes at p = 6 (CUDA-core path; 252-entry rows, copied in
+    4-byte pieces); distinct_p8: 4 at p = 8 (432-entry rows, 16-byte aligned: 16-byte copies);
+    shared_p4 / shared_p8: 72 and 130 identical ellipsoids (tensor-core path; one and two 128-particle
+    tiles, 120 and 432 block rows)."""
     return {
         "distinct": suspensions.random_ellipsoids(7, 6, 12, 0.12, 0.2, seed=71),
+        "distinct_p8": suspensions.random_ellipsoids(4, 8, 16, 0.12, 0.2, seed=74),
         "shared_p4": suspensions.shared_shape(72, 4, seed=72),
         "shared_p8": suspensions.shared_shape(130, 8, seed=73),
     }
