@@ -609,20 +609,19 @@ def run_ours(args):
         hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
     except Exception:
         hbm_peak = 6800.0
-    # the block kernel inside the float32 operator apply (float32 entries, HBM-bound) and, separately,
-    # its float64 launches outside the captured graph (the double-float passes; float64-pipe-bound)
+    # the block kernel with float32 entries (HBM-bound) and with float64 entries (float64-pipe-bound)
     rooflines = kernel_rooflines({**op_kernels, **{k: v for k, v in kernels.items() if k != "particle_blocks"}},
                                  f_mhz, hbm_peak)
-    if "particle_blocks" in kernels and kernels["particle_blocks"]["ms"] > 0:
-        e = kernels["particle_blocks"]
+    if "particle_blocks_f64" in kernels and kernels["particle_blocks_f64"]["ms"] > 0:
+        e = kernels["particle_blocks_f64"]
         flops = 16.0 * e["units"] / 8.0  # 8 reflections x one multiply-add per stored float64 entry
         fp64 = SMS * FP64_DFMA_PER_CLK_SM * 2 * f_mhz * 1e6
         rate = flops / (e["ms"] / 1e3)
         rooflines["particle_blocks_f64"] = {
             "ms_per_launch": e["ms"] / e["launches"], "launches": e["launches"], "achieved_tflops": rate / 1e12,
             "peak_tflops": fp64 / 1e12, "frac": rate / fp64, "bound": "fp64",
-            "basis": "launches outside the captured GMRES graph (float64 blocks of the double-float passes): 16 "
-                     "flops per stored entry against 152 SMs x 2 float64 FMA per clock"}
+            "basis": "float64 block applies of the double-float passes (with the L-only applies): 16 flops per "
+                     "stored entry against 152 SMs x 2 float64 FMA per clock"}
     # the captured counters belong to the direct kernels (and the double-float treecode kernel, captured
     # on its own profiling case): a treecode kernel without a capture has none
     tree_df_class = name.endswith("_df") and far == rbs.RBS_FAR_TREECODE_DF

@@ -154,7 +154,8 @@ typedef struct {
 #define RBS_KC_PAIR_S32 1 /* smooth Stokeslet pair sum, float32 */
 #define RBS_KC_PAIR_K64 2 /* smooth traction pair sum, float64 */
 #define RBS_KC_PAIR_S64 3 /* smooth Stokeslet pair sum, float64 */
-#define RBS_KC_BLOCKS 4   /* particle-block kernel (self blocks, projection, preconditioner) */
+#define RBS_KC_BLOCKS 4   /* particle-block kernel (self blocks, projection, preconditioner) with float32 or
+                             16-bit entries (the inner solve's arithmetic) */
 #define RBS_KC_NEAR 5     /* near correction (upsampling and upsampled pair sums) */
 #define RBS_KC_PAIR_KDF 6 /* smooth traction pair sum, double-float */
 #define RBS_KC_PAIR_SDF 7 /* smooth Stokeslet pair sum, double-float */
@@ -166,7 +167,9 @@ typedef struct {
                              their own classes (their launches still count in rbs_stats.launches) */
 #define RBS_KC_SELF_GEMM 11 /* tensor-core GEMM of the 16-bit self blocks of a shared shape (the GEMM kernel
                              alone; units = its flops, 2 n_g (3 N_p)^2 per launch) */
-#define RBS_KC_COUNT 12
+#define RBS_KC_BLOCKS_F64 12 /* particle-block kernel with float64 entries (the float64 and double-float
+                             applies), and applies of the L term alone */
+#define RBS_KC_COUNT 13
 
 typedef struct {
   int iterations;        /* GMRES iterations of the last solve (inner iterations for mixed), the largest

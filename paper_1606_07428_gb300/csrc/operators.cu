@@ -1449,7 +1449,7 @@ Status apply_blocks(Context& c, int mode, int prec, const double* x, double* y, 
   // which store every row, keep float32 blocks)
   const bool use16 = prec_16(prec) && kblock && c.d_blockK16.ptr;
   const double bytes = (mode == kModeL) ? 0.0 : (double)c.particle_block_entries * (use16 ? 2.0 : use32 ? 4.0 : 8.0);
-  KernelTimer timer(c, RBS_KC_BLOCKS);
+  KernelTimer timer(c, use32 ? RBS_KC_BLOCKS : RBS_KC_BLOCKS_F64);
   // 16-bit modes: ellipsoids of shapes shared by many particles go through the tensor-core GEMM, the
   // others through the CUDA-core kernel below
   const bool gemm = use16 && !c.gemm.empty();

@@ -111,10 +111,11 @@ RBS_KC_PAIR_KSDF = 8
 RBS_KC_TREE = 9
 RBS_KC_GMRES_GRAPH = 10
 RBS_KC_SELF_GEMM = 11
-RBS_KC_COUNT = 12
+RBS_KC_BLOCKS_F64 = 12
+RBS_KC_COUNT = 13
 KERNEL_CLASSES = ["pair_traction_f32", "pair_stokeslet_f32", "pair_traction_f64", "pair_stokeslet_f64",
                   "particle_blocks", "near_correction", "pair_traction_df", "pair_stokeslet_df", "pair_both_df",
-                  "tree_charges", "gmres_graph", "self_gemm"]
+                  "tree_charges", "gmres_graph", "self_gemm", "particle_blocks_f64"]
 
 
 class rbs_stats(ctypes.Structure):
