@@ -95,8 +95,13 @@ def parse_args():
                          "(rbs_options.far_field)")
     ap.add_argument("--tree-df-theta", type=float, default=0.45,
                     help="opening angle of the double-float passes' treecode (rbs_options.tree_df_theta) with "
-                         "--far-field tree-df; at degree 12, 0.45 measured 1.6e-10 relative error on the far sum "
-                         "of the 10,000-ellipsoid geometry (0.4: 3.6e-11) with 17% fewer pairs")
+                         "--far-field tree-df")
+    ap.add_argument("--tree-df-degree", type=int, default=11,
+                    help="its interpolation degree (rbs_options.tree_df_degree).  Relative error of the far "
+                         "traction sum on the 10,000-ellipsoid geometry (float64 treecode against the exact "
+                         "sum at six particles) and pairs per apply: theta 0.45 / degree 11: 1.0e-9, 5.5e11; "
+                         "0.45 / 12: 1.6e-10, 6.6e11; 0.4 / 10: 1.2e-9, 5.6e11; 0.5 / 12: 3.0e-9, 5.5e11; "
+                         "0.5 / 11: 1.1e-8, 4.5e11")
     ap.add_argument("--experiment", default=None, choices=[None, "warmstart", "magnetic", "selfgemm"],
                     help="warmstart: learned vs previous-step vs zero initial guesses in RK4 sedimentation; "
                          "magnetic: time steps of paramagnetic spheres in a uniform field (each prints its own "
@@ -388,7 +393,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     far = {"direct": rbs.RBS_FAR_DIRECT, "tree": rbs.RBS_FAR_TREECODE, "tree-df": rbs.RBS_FAR_TREECODE_DF}[args.far_field]
     ctx = rbs.Context(device=local, precision=rbs.RBS_PREC_MIXED, timing=1, stream=stream.cuda_stream,
-                      pair_variant=args.pair_variant, far_field=far, tree_df_theta=args.tree_df_theta)
+                      pair_variant=args.pair_variant, far_field=far, tree_df_theta=args.tree_df_theta,
+                      tree_df_degree=args.tree_df_degree)
     ctx.set_suspension(susp)
     st0 = rbs.rbs_get_stats(ctx.ctx)
     setup_ms = st0["setup_ms"]
@@ -400,7 +406,7 @@ def run_ours(args):
                      "direct_pairs_per_apply": st0["far_pairs"],
                      "reduction": st0["far_pairs"] / max(1, st0["tree_pairs"])}
         if far == rbs.RBS_FAR_TREECODE_DF:
-            tree_info["double_float"] = {"theta": args.tree_df_theta, "degree": opts.tree_df_degree,
+            tree_info["double_float"] = {"theta": args.tree_df_theta, "degree": args.tree_df_degree,
                                          "cells": st0["tree_df_cells"], "pairs_per_apply": st0["tree_df_pairs"],
                                          "proxy_pairs_per_apply": st0["tree_df_proxy_pairs"],
                                          "reduction": st0["far_pairs"] / max(1, st0["tree_df_pairs"])}
