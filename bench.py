@@ -62,9 +62,9 @@ NCU_TRAFFIC = {"pair_traction_df": (6.404864e6, 57600), "pair_traction_f32": (4.
 # efficiency of a double-float kernel is measured against this count, its roofline against the flops
 DF_INSTR_PER_PAIR = {"traction": 172.0, "stokeslet": 172.0, "both": 248.0}
 # DRAM bytes per launch of the fused double-float treecode kernel from an ncu capture on the
-# 2,000-ellipsoid profiling case (288,000 nodes; 91.07 MB read + 10.95 MB written, theta 0.4), scaled by
-# node count like the direct kernels' figures
-TREE_DF_TRAFFIC = (1.02018816e8, 288000)
+# 2,000-ellipsoid profiling case (288,000 nodes; 83.27 MB read + 6.95 MB written, theta 0.45, degree 11,
+# one target per thread), scaled by node count like the direct kernels' figures
+TREE_DF_TRAFFIC = (9.0224640e7, 288000)
 
 
 def parse_args():
