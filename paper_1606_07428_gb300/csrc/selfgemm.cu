@@ -233,10 +233,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kAccCols);
 #pragma unroll 1
       for (int ch = 0; ch < kBN / kEpiCols; ++ch) {
+        uint32_t raw[kEpiCols];
+        umma::tmem_ld24(taddr + kEpiCols * ch, raw);
+        umma::tmem_ld_wait24(raw);
         float v[kEpiCols];
-        umma::tmem_ld16(taddr + kEpiCols * ch, *reinterpret_cast<float(*)[16]>(v));
-        umma::tmem_ld8(taddr + kEpiCols * ch + 16, v + 16);
-        umma::tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < kEpiCols; ++k) v[k] = __uint_as_float(raw[k]);
         __syncwarp();  // the previous chunk's stores have read the stage
         if (valid) {
           // the lab-frame product in float32 (the 16-bit operands bound its accuracy far above float32
