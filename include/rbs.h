@@ -361,9 +361,8 @@ int rbs_rigid_velocities(rbs_ctx* ctx, const double* u, double* v, double* omega
  * every GPU that loads the library holds until the process exits; geometries with more than 65,536
  * particles are rejected with RBS_EINVAL.  No cudaMalloc, cudaFree or allocating library routine is
  * called.  The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current and keeps it for the process: make that first call before any stream capture,
- * and do not reset the device (cudaDeviceReset) afterwards, since the array may then move and the
- * kept address would be stale.  All calls, from every context of the process, share the one array per
+ * that device current and keeps it for the process; do not reset the device (cudaDeviceReset)
+ * afterwards, since the array may then move and the kept address would be stale.  All calls, from every context of the process, share the one array per
  * device, and each call overwrites the entries it reads, so calls whose work overlaps on the GPU
  * (other contexts or streams at the same time) race and must be ordered by the caller.  Work runs on
  * the context's stream and the call waits for it to complete before returning; the caller's current
