@@ -35,9 +35,10 @@ constexpr int kAccCols = 256, kTmemCols = 2 * kAccCols;
 constexpr uint32_t kBytesA = kBM * kBK * 2, kBytesB = kBN * kBK * 2;
 constexpr long long kSpin = 1LL << 24;
 constexpr int kGemmThreads = 192;
-// epilogue staging per epilogue warp: 32 rows x 24 float64 (row stride 25) and the rows' offsets,
+// epilogue staging per epilogue warp: 32 rows x 48 float32 (row stride 49) and the rows' offsets,
 // L moments and centres
-constexpr int kEpiCols = 24, kEpiStride = 25;
+constexpr int kEpiCols = 48, kEpiStride = 49;
+static_assert(kBN % kEpiCols == 0 && kEpiCols % 16 == 0 && kEpiCols <= 64, "epilogue chunks");
 constexpr size_t kEpiWarpBytes = 32 * kEpiStride * 4 + 32 * 8 + 32 * 6 * 8 + 32 * 3 * 8;
 constexpr size_t kGemmSmem = 1024 + (size_t)kStages * (kBytesA + kBytesB) + 4 * kEpiWarpBytes + 256;
 
@@ -191,8 +192,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
   } else {
     // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31, one particle per lane.
-    // A chunk of 24 columns (8 nodes) is rotated to the lab frame in registers, staged in shared
-    // memory, and written row by row, 24 consecutive float64 per particle and store instruction.
+    // A chunk of 48 columns (16 nodes) is rotated to the lab frame in registers, staged in shared
+    // memory, and written row by row, 32 and then 16 consecutive float64 per particle.
     const int q = warp & 3;
     const int r = q * 32 + lane;
     uint8_t* ew = epi_base + (warp - 2) * kEpiWarpBytes;
@@ -234,8 +235,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 #pragma unroll 1
       for (int ch = 0; ch < kBN / kEpiCols; ++ch) {
         uint32_t raw[kEpiCols];
-        umma::tmem_ld24(taddr + kEpiCols * ch, raw);
-        umma::tmem_ld_wait24(raw);
+#pragma unroll
+        for (int k = 0; k < kEpiCols / 16; ++k) umma::tmem_ld16_raw(taddr + kEpiCols * ch + 16 * k, raw + 16 * k);
+        umma::tmem_wait_ld16(raw);
+#pragma unroll
+        for (int k = 1; k < kEpiCols / 16; ++k) umma::reg_fence16(raw + 16 * k);
         float v[kEpiCols];
 #pragma unroll
         for (int k = 0; k < kEpiCols; ++k) v[k] = __uint_as_float(raw[k]);
@@ -252,30 +256,34 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           }
         }
         __syncwarp();
-        // row by row: lane e < 24 writes entry e of the chunk (node e / 3, component e % 3)
-        const int node = nt * (kBN / 3) + ch * (kEpiCols / 3) + lane / 3;
-        const int comp = lane % 3;
-        if (lane < kEpiCols && node < ep.np) {
-          const bool plain = !half_x && !with_L && ep.scale == 1.0;
-          const int nrows = min(32, ep.rows - row0);
+        // row by row: lane e writes entries e and 32 + e of the chunk (node e / 3, component e % 3), so
+        // one row takes 32 and then 16 consecutive float64
+        const bool plain = !half_x && !with_L && ep.scale == 1.0;
+        const int nrows = min(32, ep.rows - row0);
+#pragma unroll
+        for (int h = 0; h < (kEpiCols + 31) / 32; ++h) {
+          const int e = lane + 32 * h;
+          const int node = nt * (kBN / 3) + ch * (kEpiCols / 3) + e / 3;
+          const int comp = e % 3;
+          if (e >= kEpiCols || node >= ep.np) continue;
           if (plain) {
 #pragma unroll 8
-            for (int rr = 0; rr < nrows; ++rr) ep.out[3 * (s_off[rr] + node) + comp] = f32_to_f64_bits(stage[rr][lane]);
+            for (int rr = 0; rr < nrows; ++rr) ep.out[3 * (s_off[rr] + node) + comp] = f32_to_f64_bits(stage[rr][e]);
           } else {
-          for (int rr = 0; rr < nrows; ++rr) {
-            const long long gi = s_off[rr] + node;
-            const float sv = stage[rr][lane];
-            double val = (double)sv;
-            if (half_x) val += 0.5 * ep.in[3 * gi + comp];
-            if (with_L) {
-              const double4 pp = ep.x[gi];
-              const double rx = pp.x - s_cen[rr][0], ry = pp.y - s_cen[rr][1], rz = pp.z - s_cen[rr][2];
-              const double* m = s_mom[rr];
-              val += comp == 0 ? m[0] + (m[4] * rz - m[5] * ry)
-                               : (comp == 1 ? m[1] + (m[5] * rx - m[3] * rz) : m[2] + (m[3] * ry - m[4] * rx));
+            for (int rr = 0; rr < nrows; ++rr) {
+              const long long gi = s_off[rr] + node;
+              const float sv = stage[rr][e];
+              double val = (double)sv;
+              if (half_x) val += 0.5 * ep.in[3 * gi + comp];
+              if (with_L) {
+                const double4 pp = ep.x[gi];
+                const double rx = pp.x - s_cen[rr][0], ry = pp.y - s_cen[rr][1], rz = pp.z - s_cen[rr][2];
+                const double* m = s_mom[rr];
+                val += comp == 0 ? m[0] + (m[4] * rz - m[5] * ry)
+                                 : (comp == 1 ? m[1] + (m[5] * rx - m[3] * rz) : m[2] + (m[3] * ry - m[4] * rx));
+              }
+              ep.out[3 * gi + comp] = ep.scale * val;
             }
-            ep.out[3 * gi + comp] = ep.scale * val;
-          }
           }
         }
       }

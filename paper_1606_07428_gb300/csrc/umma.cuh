@@ -102,27 +102,33 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// 24 consecutive float32 columns of this thread's tensor-memory lane as raw bits (warp-wide), without
-// waiting: the registers hold the values only after tmem_ld_wait24 on the same array.
-__device__ __forceinline__ void tmem_ld24(uint32_t taddr, uint32_t (&r)[24]) {
+// 16 consecutive float32 columns of this thread's tensor-memory lane as raw bits into r[0, 16)
+// (warp-wide), without waiting: the registers hold the values only after tmem_wait_ld16 (and
+// reg_fence16 for further groups loaded before the same wait).
+__device__ __forceinline__ void tmem_ld16_raw(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
       "[%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
-               : "r"(taddr + 16));
 }
-// Waits for this thread's tensor-memory loads; the array passes through the wait, so no use of its
-// registers can be scheduled before it.
-__device__ __forceinline__ void tmem_ld_wait24(uint32_t (&r)[24]) {
+// Waits for this thread's tensor-memory loads; r[0, 16) pass through the wait, so no use of them can
+// be scheduled before it.
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;"
                : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
                  "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                 "+r"(r[22]), "+r"(r[23])
+                 "+r"(r[15])
+               :
+               : "memory");
+}
+// No instruction: ties r[0, 16) to this point of the program (placed after tmem_wait_ld16).
+__device__ __forceinline__ void reg_fence16(uint32_t* r) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15])
                :
                : "memory");
 }
