@@ -328,6 +328,19 @@ def kernel_rooflines(kernels, f_mhz, hbm_gbs):
     return out
 
 
+def block_f64_roofline(e, f_mhz):
+    """The particle-block kernel's float64 launches (RBS_KC_BLOCKS_F64; units = bytes of float64 entries)
+    against the float64 FMA peak: each stored entry is multiplied with the input of all 8 reflections,
+    16 flops per entry."""
+    flops = 16.0 * e["units"] / 8.0
+    fp64 = SMS * FP64_DFMA_PER_CLK_SM * 2 * f_mhz * 1e6
+    rate = flops / (e["ms"] / 1e3)
+    return {"ms_per_launch": e["ms"] / e["launches"], "launches": e["launches"], "achieved_tflops": rate / 1e12,
+            "peak_tflops": fp64 / 1e12, "frac": rate / fp64, "bound": "fp64",
+            "basis": "float64 block applies of the double-float passes (with the L-only applies): 16 flops per "
+                     "stored entry against 152 SMs x 2 float64 FMA per clock"}
+
+
 def kernel_table(stats):
     from paper_1606_07428_gb300 import rbs
     out = {}
@@ -619,15 +632,7 @@ def run_ours(args):
     rooflines = kernel_rooflines({**op_kernels, **{k: v for k, v in kernels.items() if k != "particle_blocks"}},
                                  f_mhz, hbm_peak)
     if "particle_blocks_f64" in kernels and kernels["particle_blocks_f64"]["ms"] > 0:
-        e = kernels["particle_blocks_f64"]
-        flops = 16.0 * e["units"] / 8.0  # 8 reflections x one multiply-add per stored float64 entry
-        fp64 = SMS * FP64_DFMA_PER_CLK_SM * 2 * f_mhz * 1e6
-        rate = flops / (e["ms"] / 1e3)
-        rooflines["particle_blocks_f64"] = {
-            "ms_per_launch": e["ms"] / e["launches"], "launches": e["launches"], "achieved_tflops": rate / 1e12,
-            "peak_tflops": fp64 / 1e12, "frac": rate / fp64, "bound": "fp64",
-            "basis": "float64 block applies of the double-float passes (with the L-only applies): 16 flops per "
-                     "stored entry against 152 SMs x 2 float64 FMA per clock"}
+        rooflines["particle_blocks_f64"] = block_f64_roofline(kernels["particle_blocks_f64"], f_mhz)
     # the captured counters belong to the direct kernels (and the double-float treecode kernel, captured
     # on its own profiling case): a treecode kernel without a capture has none
     tree_df_class = name.endswith("_df") and far == rbs.RBS_FAR_TREECODE_DF
