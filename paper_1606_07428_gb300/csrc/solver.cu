@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(256) k_rigid(const long long* __restrict__ off
   }
 }
 
-__global__ void k_axpby(double* __restrict__ y, double a, const double* __restrict__ x, double b, long long n) {
+// y = a x + b y elementwise; x may be y (no restrict: the right-hand side's b = -b passes both)
+__global__ void k_axpby(double* y, double a, const double* x, double b, long long n) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
     y[k] = a * x[k] + b * y[k];
 }
